@@ -1,0 +1,40 @@
+"""CPU oracle for the one-shot Parareal topology-optimisation pass (arXiv 2411.19030).
+
+TEST INFRASTRUCTURE ONLY.  Plain, slow, FP64 NumPy/SciPy code that restates the
+paper's method step by step.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.  The CUDA
+product path never imports, links or calls anything here, and this package never
+imports the product package: the two share no code.
+
+Modules
+-------
+``fem``        Sec. 2.1-2.2: SIMP interpolation (Eq. 2.5-2.6), Galerkin bilinear
+               element matrices by Gauss quadrature, global K, C and load vectors.
+``stepping``   Sec. 2.2 and 4.1: backward Euler (Eq. 2.7), the power-mean objective
+               (Eq. 2.11), the discrete adjoint (Eq. 4.4-4.7) and the sequential pass.
+               Each linear solve is a banded Cholesky factorisation (factored once per
+               matrix) followed by two triangular solves.
+``parareal``   Sec. 4.2-4.4, Algorithms 1-3: the propagators H, F, G, the modified
+               (history-storing) forward Parareal, the reverse vanilla Parareal, the
+               k-iteration scheme, the one-shot pass and the PLT variant (Sec. 7).
+``allatonce``  Eq. 2.8-2.9 and 4.3: dense brute-force space-time solves, used only on
+               tiny grids as an independent check of the time-stepping recursions.
+
+Pins (``tests/test_oracle_*.py``, run with ``-m "not gpu"``): the separable-eigenmode
+closed form, the discrete energy balance, the dense all-at-once solve, central
+finite differences of the gradient, Parareal's exactness after N_tau iterations,
+the M = 1 and N_tau = 1 degenerate cases, the one-shot fixed point, mirror symmetry,
+the constant-field objective identity and the homogeneity of Theta in q.
+The one-shot estimate for a design that differs from the warm-start design has
+no closed form: beyond the fixed point it is "parity unpinned" (it is the literal
+algorithm, checked only for consistency with the pinned pieces it is made of).
+"""
+from .fem import Material, Problem, element_matrices, simp, assemble
+from .stepping import Operator, objective, sequential_primal, sequential_adjoint, sequential_pass, sensitivity_term
+from .parareal import (F_pri, G_pri, F_adj, G_adj, oneshot_pass, parareal, coarse_states_from_sequential)
+
+__all__ = [
+    "Material", "Problem", "element_matrices", "simp", "assemble",
+    "Operator", "objective", "sequential_primal", "sequential_adjoint", "sequential_pass", "sensitivity_term",
+    "F_pri", "G_pri", "F_adj", "G_adj", "oneshot_pass", "parareal", "coarse_states_from_sequential",
+]
