@@ -1,0 +1,405 @@
+#!/usr/bin/env python3
+"""Benchmark of the one-shot Parareal pass (one design iteration of Algorithm 3, lines 5-12).
+
+Workload (one "step"): 128x128 bilinear grid (16 641 nodes, 13 Dirichlet), Nt = 1024 fine
+backward-Euler steps in N_tau = 32 slices (M = 32), SIMP k = 1e-3 + (1 - 1e-3) rho^3, unit
+capacity and source, power-mean exponent p = 8; design rho ~ U(0.2, 0.8) seed 0 for the warm
+start, the timed design clip(rho + U(-0.01, 0.01), 0, 1) seed 1000.  One step = assemble (a1)
++ F_pri of all slices (a2) + G_pri (a3) + forward correction (a4) + F_adj (a5) + G_adj (a3) +
+reverse correction with the fused sensitivity sums (a4/a6), FP32 CG with FP64 refinement.
+
+Metric: fine DOF*steps/s = 2 N_free Nt / t_pass (primal and adjoint), and ms per one-shot
+design iteration; the comparator is sequential FP64 GPU time stepping of the same design
+(chained F_pri then F_adj on one cluster, FP64 CG).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--precision fp64]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+WORKLOAD = "oneshot128"
+METRIC = "fine DOF*steps/s of the one-shot Parareal pass (ms per design iteration vs sequential FP64 GPU)"
+UNIT = "DOF*steps/s"
+
+
+def problem_arrays(name=WORKLOAD):
+    w = W.workload(name)
+    n = w["n"]
+    h = w["h"]
+    rho_old = W.rho_uniform(n, n, 0, 0.2, 0.8)
+    rho = W.rho_warm_perturb(rho_old, seed=1000, amp=0.01)
+    sink = W.dirichlet_left_centre(n, n, h)
+    return w, rho_old, rho, sink
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling in the background during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self) -> dict:
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2411_19030_gb300 import Operator, PassBuffers, SolveConfig, oneshot_pass, sequential_pass
+    from paper_2411_19030_gb300.build import build_library
+
+    rank, world, local = dist_env()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if rank == 0:
+        build_library()
+    if world > 1:
+        dist.barrier()
+    w, rho_old_np, rho_np, sink = problem_arrays()
+    n, Nt, Ntau, dt, p = w["n"], w["Nt"], w["Ntau"], w["dt"], w["p"]
+    N_free = (n + 1) ** 2 - int(sink.sum())
+    solve = SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=2000, refine_max=8)
+    op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink, solve=solve, device=local)
+    seq_op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink,
+                      solve=SolveConfig("fp64", rtol=1e-13, cg_iters_max=4000, refine_max=8), device=local)
+    buf = PassBuffers(op)
+    rho_old = torch.tensor(rho_old_np, dtype=torch.float64, device=device)
+    rho = torch.tensor(rho_np, dtype=torch.float64, device=device)
+    stream = torch.cuda.current_stream(device)
+
+    # warm start: the exact sequential coarse states of rho_old (sequential FP64 pass, untimed)
+    seq_op.assemble(rho_old)
+    sequential_pass(seq_op, buf)
+    torch.cuda.synchronize()
+    flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device=device)   # > L2 (129 MiB)
+
+    kinds = ["assemble", "fine_primal", "coarse_primal", "correct_primal", "fine_adjoint", "coarse_adjoint",
+             "correct_adjoint"]
+
+    def timed_step(ev):
+        """One one-shot design iteration with an event pair around every ABI call."""
+        from paper_2411_19030_gb300 import PTG_ADJOINT, PTG_PRIMAL
+        e = ev
+        e[0].record(stream)
+        op.assemble(rho)
+        e[1].record(stream)
+        op.fine_propagate_slices(buf.U_T, buf.U_th, buf.F_T, buf.F_th, T_hist=buf.T_hist)
+        e[2].record(stream)
+        op.coarse_sweep(PTG_PRIMAL, buf.U_T, buf.U_th, buf.G_T, buf.G_th)
+        e[3].record(stream)
+        buf.U_T_new[0].copy_(buf.U_T[0])
+        buf.U_th_new[0].copy_(buf.U_th[0])
+        op.parareal_correct(PTG_PRIMAL, buf.F_T, buf.F_th, buf.G_T, buf.G_th, buf.U_T_new, buf.U_th_new,
+                            T_hist=buf.T_hist)
+        e[4].record(stream)
+        Theta = buf.U_th_new[Ntau:Ntau + 1]
+        op.adjoint_sweep(buf.T_hist, Theta, buf.V_l, buf.V_g, buf.F_l, buf.F_g)
+        e[5].record(stream)
+        op.coarse_sweep(PTG_ADJOINT, buf.V_l, buf.V_g, buf.G_l, buf.G_g, T_hist=buf.T_hist, Theta=Theta)
+        e[6].record(stream)
+        op.parareal_correct(PTG_ADJOINT, buf.F_l, buf.F_g, buf.G_l, buf.G_g, buf.V_l_new, buf.V_g_new,
+                            T_hist=buf.T_hist, Theta=Theta)
+        e[7].record(stream)
+
+    def new_events():
+        return [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        timed_step(new_events())
+    torch.cuda.synchronize()
+    op.reset_stats()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.fill_(1.0)                    # L2 flushed between steps (outside the events)
+            ev = new_events()
+            timed_step(ev)
+            evs.append(ev)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    per_kind = np.zeros(len(kinds))
+    step_ms = []
+    for ev in evs:
+        d = [ev[i].elapsed_time(ev[i + 1]) for i in range(7)]
+        per_kind += np.array(d)
+        step_ms.append(ev[0].elapsed_time(ev[7]))
+    ms = float(np.sum(step_ms)) / args.steps
+    stats = op.stats()
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    dof_steps = 2.0 * N_free * Nt
+    value = world * dof_steps / (ms * 1e-3)
+    kind_ms = {k: float(v / args.steps) for k, v in zip(kinds, per_kind)}
+
+    # end to end through the public API with host buffers: H2D of rho, D2H of Theta and grad
+    rho_host = torch.from_numpy(rho_np).pin_memory()
+    out_host = torch.empty(1 + n * n, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for _ in range(max(2, min(args.steps, 5))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rho.copy_(rho_host, non_blocking=True)
+        op.assemble(rho)
+        Theta, grad = oneshot_pass(op, buf)
+        out_host[:1].copy_(Theta, non_blocking=True)
+        out_host[1:].copy_(grad, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e = float(np.mean(e2e_ms))
+
+    # comparator: sequential FP64 GPU time stepping of the same design (bounded repetitions)
+    seq_buf = PassBuffers(seq_op)
+    seq_op.assemble(rho)
+    seq_op.reset_stats()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    Theta_seq, grad_seq = sequential_pass(seq_op, seq_buf)
+    b.record(stream)
+    b.synchronize()
+    seq_ms = a.elapsed_time(b)
+    seq_stats = seq_op.stats()
+    # accuracy of the one-shot estimate and of the mixed arithmetic against sequential FP64
+    Theta_os = float(buf.U_th_new[Ntau].item())
+    g_os = buf.V_g_new[0]
+    err_theta = abs(Theta_os - float(Theta_seq.item())) / abs(float(Theta_seq.item()))
+    err_grad = float(torch.linalg.norm(g_os - grad_seq) / torch.linalg.norm(grad_seq))
+
+    roof = roofline(kind_ms, stats, w, N_free, args)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "fp32_refine" else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: 128x128 grid, Nt=1024, Ntau=32 (M=32), p=8, SIMP k, warm start from "
+                               "the sequential coarse states of a design 1% away",
+                   "precision": args.precision, "rtol": args.rtol, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "wall_s": wall},
+        "per_kernel_ms": kind_ms,
+        "cg": {"solves": stats["solves"], "cg_iters": stats["cg_iters"], "refinements": stats["refinements"],
+               "mean_cg_per_solve": stats["cg_iters"] / max(1, stats["solves"])},
+        "comparator_sequential_fp64": {"ms": seq_ms, "value": dof_steps / (seq_ms * 1e-3), "unit": UNIT,
+                                       "speedup_of_oneshot": seq_ms / ms,
+                                       "cg_iters": seq_stats["cg_iters"], "solves": seq_stats["solves"]},
+        "accuracy_vs_sequential_fp64": {"Theta_rel": err_theta, "grad_rel_l2": err_grad},
+        "e2e": {"value": world * dof_steps / (e2e * 1e-3), "unit": UNIT, "ms": e2e,
+                "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": (1 + n * n) * 8},
+        "gpu_launches": 8 * args.steps,
+        "roofline": roof,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        if args.cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def roofline(kind_ms: dict, stats: dict, w: dict, N_free: int, args) -> dict:
+    """Roofline entry of the dominant kernel (largest share of the step).
+
+    The stepper keeps every CG vector of a slice on chip (registers and shared memory of one
+    thread-block cluster), so its compulsory HBM traffic per fine DOF-step is the FP64 history
+    (8 B written in the primal pass, 16 B read in the adjoint pass: T_j and T_{j-1}) plus the
+    warm-start and slice-end states; the figure below counts the history bytes only.
+    """
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    dom = max((k for k in kind_ms if k != "assemble"), key=lambda k: kind_ms[k])
+    Nt, Ntau = w["Nt"], w["Ntau"]
+    nn = (w["n"] + 1) ** 2
+    bytes_per_launch = {
+        "fine_primal": 8.0 * nn * Nt + 16.0 * nn * Ntau,          # history write + start/end states
+        "fine_adjoint": 16.0 * nn * Nt + 16.0 * nn * Ntau,        # T_j, T_{j-1} reads + states
+        "coarse_primal": 16.0 * nn * Ntau,
+        "coarse_adjoint": 32.0 * nn * Ntau,
+        "correct_primal": 40.0 * nn * Ntau,
+        "correct_adjoint": 56.0 * nn * Ntau,
+    }[dom]
+    achieved = bytes_per_launch / (kind_ms[dom] * 1e-3) / 1e9
+    return {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+            "note": "on-chip CG: compulsory FP64 history/state bytes only; the kernel is bound by cluster "
+                    "synchronisation latency, not HBM"}
+
+
+# ---------------------------------------------------------------------------- CPU oracle arms
+
+ORACLE_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import workloads as W
+from oracle import Material, Operator, Problem
+from oracle.parareal import F_pri, F_adj
+w = W.workload('oneshot128')
+n = w['n']; h = w['h']
+prob = Problem(nx=n, ny=n, h=h, material=Material(**w['material']), Nt=w['Nt'], dt=w['dt'], Ntau=w['Ntau'],
+               p=w['p'], dirichlet=W.dirichlet_left_centre(n, n, h))
+rho = W.rho_warm_perturb(W.rho_uniform(n, n, 0, 0.2, 0.8), seed=1000, amp=0.01)
+budget = {budget}
+t0 = time.perf_counter()
+op = Operator(prob, rho)
+op._factor(prob.dt)
+T = np.zeros(prob.Nn); theta = 0.0
+steps = 0
+s = 0
+hist = np.zeros((prob.M + 1, prob.Nn))
+while time.perf_counter() - t0 < budget and s < prob.Ntau:
+    Tn, theta, inter = F_pri(op, s, T, theta)           # fine primal slice
+    hist[0] = T; hist[1:] = inter
+    full = np.zeros((prob.Nt + 1, prob.Nn)); full[prob.M * s: prob.M * (s + 1) + 1] = hist
+    F_adj(op, s, np.zeros(prob.Nn), np.zeros(prob.Ne), full, max(theta, 1e-3))   # fine adjoint slice
+    steps += 2 * prob.M
+    T = Tn; s += 1
+dt_s = time.perf_counter() - t0
+nfree = int(op.free.sum())
+print(json.dumps({{'value': nfree * steps / dt_s, 'seconds': dt_s, 'slices': s, 'fine_steps': steps}}))
+"""
+
+
+def cpu_baseline(budget_s: float) -> dict:
+    """The oracle (as it stands) on one host core: fine primal + adjoint slices of the same
+    workload until the time budget is spent; DOF*steps/s of that sample."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ORACLE_SNIPPET.format(root=ROOT, budget=budget_s)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=budget_s * 10 + 120)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{d['slices']} fine primal + adjoint slices (M=32 steps each, {d['fine_steps']} fine solves) "
+                      f"of the 128x128 workload, banded Cholesky, {d['seconds']:.1f} s, BLAS threads = 1"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_baseline(budget)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(budget))
+    wall = time.perf_counter() - t0
+    v = float(np.mean([x["value"] for x in vals if x["value"]])) if vals else None
+    ms = wall / max(1, args.steps) * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: 128x128 grid, Nt=1024, Ntau=32; bounded sample per step "
+                                   f"({budget:.0f} s of fine primal+adjoint slices)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": vals[0]["sample"] if vals else None},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="fp32_refine", choices=["fp32_refine", "fp64"])
+    ap.add_argument("--rtol", type=float, default=1e-10)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,248 @@
+/*
+ * ptg.h -- C ABI of the GB300 (sm_103a) one-shot Parareal topology-optimisation pass
+ * for transient heat conduction (Appel & Alexandersen, arXiv 2411.19030).
+ *
+ * The library computes, for one design rho, the per-design-iteration state / adjoint /
+ * sensitivity pass of the paper's one-shot Parareal method (Algorithm 3, lines 5-12):
+ *
+ *   a1  ptg_fe_assemble_operator   SIMP coefficients and element weights      Sec. 2.1-2.2, Eq. 2.5-2.7
+ *   a2  ptg_fine_propagate_slices  F_pri of every slice (modified Parareal)   Alg. 1, Sec. 4.3-4.4
+ *   a3  ptg_coarse_sweep           G_pri / G_adj of every slice (batched)     Alg. 1-2 substitutions, Sec. 4.4
+ *   a4  ptg_parareal_correct       sequential correction sweep                Eq. 4.9 (forward), Eq. 4.14 (reverse)
+ *   a5  ptg_adjoint_sweep          F_adj of every slice                        Alg. 2, Sec. 4.4
+ *   a6  ptg_sensitivities          sum_j lambda_j^T dR_j/drho_e reduction      Eq. 4.7
+ *
+ * Discretisation (Sec. 2.2): nx*ny square bilinear elements of side h, depth 1; nodes
+ * row-major (node = iy*(nx+1) + ix), elements row-major (e = ey*nx + ex); element-wise
+ * constant k, c, q; backward Euler  C (T_j - T_{j-1})/dt + K T_j = q_j; Dirichlet nodes
+ * (T = lambda = 0) are removed from the unknowns.  Objective (Eq. 2.11):
+ *   Theta = ( sum_{j=1..Nt} ||T_j||_p^p / (Nt Ne) )^(1/p),  p even.
+ * Parareal indexing (Sec. 4.2-4.4): M = Nt/Ntau, slice s = 0..Ntau-1 spans fine steps
+ * j = M s + 1 .. M (s+1); primal states u_n = (T_{Mn}, theta_{Mn}); adjoint states
+ * v_n = (lambda_{Mn+1}, g_{Mn+1}) with v_Ntau = 0.
+ *
+ * Conventions for every call
+ *  - Ownership: the caller owns every array argument (device memory unless stated,
+ *    contiguous, FP64, row-major with the shapes given).  The library owns only the
+ *    opaque ptg_op and the device workspace it allocates in ptg_op_create.
+ *  - Execution: every compute call is asynchronous on `stream` (a cudaStream_t; 0 is the
+ *    legacy default stream) and performs no host synchronisation.  Calls on one op must
+ *    not overlap on the GPU (they share the op's workspace).
+ *  - Errors: every call returns PTG_OK or a negative code.  Argument errors are detected
+ *    on the host before anything is launched (PTG_EINVAL).  Conditions found on the
+ *    device (non-finite or out-of-range design values, a solve that hit its iteration
+ *    limit, a non-finite solution) are recorded in the op's device status word and
+ *    reported by ptg_get_stats, which synchronises the stream.  No call traps or aborts.
+ *  - No C++ exception crosses this boundary.  Calls on distinct ops are independent.
+ */
+#ifndef PTG_H
+#define PTG_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+#define PTG_OK          0
+#define PTG_EINVAL     -1   /* invalid argument (host check) or invalid design value (device) */
+#define PTG_ENOCONV    -2   /* a linear solve stopped at its iteration limit */
+#define PTG_ENONFINITE -3   /* a non-finite value appeared in a solution or an objective */
+#define PTG_ETIMEOUT   -4   /* a bounded device wait gave up */
+#define PTG_ECUDA      -5   /* a CUDA runtime call failed (see ptg_last_error) */
+#define PTG_ENOMEM     -6   /* device allocation failed */
+
+/* precision of the fine-propagator CG (Sec. 2.2 solves; precision pattern of the port) */
+#define PTG_FP64         0  /* CG and every accumulation in FP64 */
+#define PTG_FP32_REFINE  1  /* CG in FP32, FP64 residuals and iterative refinement */
+
+/* slice scheduling of ptg_fine_propagate_slices / ptg_adjoint_sweep */
+#define PTG_SLICES_PARALLEL 0  /* every slice starts from its own given state (Parareal F) */
+#define PTG_SLICES_CHAINED  1  /* one sequential run: slice s starts where slice s-1 ended */
+
+#define PTG_PRIMAL   1
+#define PTG_ADJOINT -1
+
+/* ------------------------------------------------------------------ problem description */
+typedef struct {
+    int nx, ny;        /* elements per side, each >= 2 */
+    double h;          /* element side; the domain is [0, nx h] x [0, ny h] with depth 1 */
+} ptg_grid;
+
+typedef struct {       /* SIMP interpolation, Eq. 2.5-2.6 */
+    double k0, kmin, pk;   /* k = kmin + (k0 - kmin) rho^pk */
+    double c0, cmin, pc;   /* c = cmin + (c0 - cmin) rho^pc */
+} ptg_material;
+
+typedef struct {
+    int Nt;            /* fine steps, t_j = j dt */
+    int Ntau;          /* Parareal slices; must divide Nt (Sec. 4.2) */
+    double dt;         /* fine step; the coarse step is dtau = (Nt/Ntau) dt */
+    double p;          /* power-mean exponent, an even integer >= 2 (Eq. 2.11) */
+} ptg_time;
+
+typedef struct {
+    int precision;     /* PTG_FP64 or PTG_FP32_REFINE */
+    double rtol;       /* stop when ||b - A x||_2 <= rtol ||b||_2 (FP64 residual) */
+    double inner_rtol; /* FP32_REFINE: relative residual reduction of each FP32 CG */
+    int cg_iters_max;  /* iteration limit of one CG */
+    int refine_max;    /* limit of refinement sweeps of one solve */
+} ptg_solve;
+
+typedef struct {
+    int status;             /* PTG_OK or the first device-side error code recorded */
+    int fail_kind;          /* who recorded status: 1 assemble; 10 + task kind for the stepper
+                               (10 fine primal, 11 coarse primal, 12 correct primal,
+                                13 fine adjoint, 14 coarse adjoint, 15 correct adjoint) */
+    int fail_step;          /* fine time index j of the failing step (or -1) */
+    int reserved;
+    long long solves;       /* linear solves since the last reset */
+    long long cg_iters;     /* CG iterations since the last reset */
+    long long refinements;  /* refinement sweeps (FP32_REFINE) since the last reset */
+    long long max_cg_iters; /* largest CG iteration count of one solve */
+} ptg_stats;
+
+typedef struct ptg_op ptg_op;   /* opaque: operator coefficients, launch plan, workspace */
+
+/* Library version string ("ptg <major>.<minor> sm_103a"). */
+const char* ptg_version(void);
+
+/* Text of the last CUDA error seen by this thread's calls (static storage). */
+const char* ptg_last_error(void);
+
+/*
+ * Create an operator for one problem (Sec. 2-3).  Allocates the device workspace and
+ * chooses the launch plan; assembles nothing yet.
+ *   dirichlet_h  HOST uint8 [Nn]: 1 marks a Dirichlet node (T = 0, Eq. 2.1c), copied.
+ *   q_elem_h     HOST FP64 [Ne] element source density, or NULL for q_e = 1; copied.
+ *   q_time_h     HOST FP64 [Nt+1] time factor of the source at t_0..t_Nt, or NULL for 1;
+ *                the load vector at t_j is q_time[j] * sum_e q_e int N_i (copied).
+ *   device       CUDA device ordinal the op lives on.
+ * Errors: PTG_EINVAL (Ntau does not divide Nt, p not even, sizes out of range, grid too
+ * large for one thread-block cluster), PTG_ENOMEM, PTG_ECUDA.  *out is NULL on error.
+ */
+int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time* time,
+                  const ptg_solve* solve, const uint8_t* dirichlet_h, const double* q_elem_h,
+                  const double* q_time_h, int device, ptg_op** out);
+
+/* Release the op and its workspace (waits for the device).  NULL is ignored. */
+void ptg_op_destroy(ptg_op* op);
+
+/* Sizes of the op: Nn, Ne, Nt, Ntau, M (any pointer may be NULL). */
+int ptg_op_sizes(const ptg_op* op, int* Nn, int* Ne, int* Nt, int* Ntau, int* M);
+
+/*
+ * Launch plan of the cluster stepper.  Every solve runs on one thread-block cluster of
+ * `cs` CTAs (1, 2, 4, 8 or 16) that split the node rows; each CTA has `nthreads` threads
+ * holding `npt` nodes each.  kind: 0 fine primal, 1 coarse primal, 2 primal correction,
+ * 3 fine adjoint, 4 coarse adjoint, 5 adjoint correction.
+ * ptg_op_get_plan reports the plan used for `ntasks` concurrent clusters (chosen for the
+ * fewest waves, then the largest cluster).  ptg_op_set_plan forces a plan for a kind
+ * (cs = 0 removes the override); PTG_EINVAL if the plan does not fit the grid or device.
+ */
+int ptg_op_get_plan(ptg_op* op, int kind, int ntasks, int* cs, int* nthreads, int* npt, int* max_active_clusters);
+int ptg_op_set_plan(ptg_op* op, int kind, int cs, int nthreads, int npt);
+
+/*
+ * a1 -- Sec. 2.1-2.2, Eq. 2.5-2.6: evaluate the SIMP coefficients k_e, c_e, dk_e/drho,
+ * dc_e/drho of the design rho_d (device FP64 [Ne], rho in [0,1]) and the element weights
+ * of C/dt + K and C/dtau + K used by every solve.  The op keeps the results until the
+ * next call.  A value of rho outside [0,1] or non-finite records PTG_EINVAL on the
+ * device.  Must precede every other compute call for that design.
+ */
+int ptg_fe_assemble_operator(ptg_op* op, const double* rho_d, cudaStream_t stream);
+
+/*
+ * a2 -- Alg. 1 and Sec. 4.3: the fine primal propagator F_pri of slices s0..s0+ns-1.
+ *   schedule   PTG_SLICES_PARALLEL: slice s starts from (U_T[s], U_theta[s]) and all
+ *              slices run concurrently (the parallel part of Parareal).
+ *              PTG_SLICES_CHAINED: one sequential run from (U_T[s0], U_theta[s0]); slice s
+ *              starts from the end of slice s-1 (sequential time stepping, Alg. 3 line 6).
+ *   U_T        [Ntau+1][Nn], U_theta [Ntau+1]: start states (only rows s0.. are read).
+ *   T_hist     history window or NULL: row r holds T_{hist_j0 + r}, hist_rows rows.  Every
+ *              computed T_j, j = M s + 1 .. M (s+1), is written to its row (the last one
+ *              is the uncorrected slice end).  Rows outside the window are not written;
+ *              the window must cover every written row or PTG_EINVAL is returned.
+ *   F_T        [Ntau][Nn], F_theta [Ntau]: slice-end states (T_{M(s+1)}, theta_{M(s+1)}).
+ */
+int ptg_fine_propagate_slices(ptg_op* op, int schedule, int s0, int ns,
+                              const double* U_T, const double* U_theta,
+                              double* T_hist, int hist_j0, int hist_rows,
+                              double* F_T, double* F_theta, cudaStream_t stream);
+
+/*
+ * a3 -- Sec. 4.4: the coarse propagators of slices s = 0..Ntau-1, evaluated for all slices
+ * concurrently, on the guess states X (the G(u_n^k) terms of the correction).
+ *   direction PTG_PRIMAL: G_pri(s, u_s) = one step of size dtau ending at t_{M(s+1)} with the
+ *             load q_{M(s+1)}, and theta += ||T||_p^p/(Ntau Ne) in the power-mean recursion.
+ *             X_field = U_T [Ntau+1][Nn], X_aux = U_theta [Ntau+1]; outputs
+ *             G_field [Ntau][Nn], G_aux [Ntau].  T_hist and Theta_d are unused (may be NULL).
+ *   direction PTG_ADJOINT: G_adj(s, v_{s+1}) = one reverse step of size dtau solving for
+ *             lambda_k, k = M s + 1, from lambda_{k+M}, with the source Theta^(1-p)/Ne T_k^(p-1)
+ *             and g -= (1/Ntau) lambda^T(dC/drho (T_k - T_{k-M})/dtau + dK/drho T_k), where
+ *             T_{k-M} is read as T_0 for s = 0.  X_field = V_lam [Ntau+1][Nn],
+ *             X_aux = V_g [Ntau+1][Ne] (rows s+1 are read); outputs G_field [Ntau][Nn],
+ *             G_aux [Ntau][Ne].  T_hist is the full history [Nt+1][Nn]; Theta_d points to Theta.
+ */
+int ptg_coarse_sweep(ptg_op* op, int direction, const double* X_field, const double* X_aux,
+                     const double* T_hist, const double* Theta_d,
+                     double* G_field, double* G_aux, cudaStream_t stream);
+
+/*
+ * a4 -- Eq. 4.9 / 4.14: the sequential correction sweep of one Parareal iteration.
+ *   PTG_PRIMAL: X_new[0] (U_T[0], U_theta[0]) holds u_0 on entry; for s = 0..Ntau-1,
+ *      u_{s+1} = G_pri(s, u_s) + F[s] - G_old[s], and the corrected T_{M(s+1)} is written to
+ *      T_hist row M(s+1) (T_hist may be NULL).  Theta = X_aux[Ntau] afterwards.
+ *   PTG_ADJOINT: v_Ntau = 0 is written; for s = Ntau-1..0,
+ *      v_s = G_adj(s, v_{s+1}) + F[s] - G_old[s]; the gradient is X_aux row 0 (g_1).
+ *      T_hist (full, read only) and Theta_d are required.
+ *   F_field/F_aux are the fine results of a2/a5 and G_field/G_aux the coarse results of a3
+ *   on the same guess; X_field/X_aux have the state shapes of ptg_coarse_sweep.
+ */
+int ptg_parareal_correct(ptg_op* op, int direction,
+                         const double* F_field, const double* F_aux,
+                         const double* G_field, const double* G_aux,
+                         double* X_field, double* X_aux,
+                         double* T_hist, const double* Theta_d, cudaStream_t stream);
+
+/*
+ * a5 -- Alg. 2 and Sec. 4.4: the fine adjoint propagator F_adj of slices s0..s0+ns-1, each
+ * from v_{s+1} = (V_lam[s+1], V_g[s+1]) backwards through j = M(s+1) .. M s + 1:
+ *   solve (C/dt + K) lambda_j = C/dt lambda_{j+1} + Theta^(1-p)/Ne T_j^(p-1),
+ *   g_j = g_{j+1} - (1/Nt) lambda_j^T (dC/drho (T_j - T_{j-1})/dt + dK/drho T_j).
+ *   schedule  PTG_SLICES_PARALLEL (all slices concurrently from their own v_{s+1}) or
+ *             PTG_SLICES_CHAINED (one reverse sequential run from v_{s0+ns}).
+ *   T_hist    history window: row r holds T_{hist_j0 + r}; rows M s .. M(s+1) of every slice
+ *             processed must lie inside it (else PTG_EINVAL).
+ *   Theta_d   device pointer to Theta (the corrected theta_Nt of the same pass).
+ *   F_lam [Ntau][Nn], F_g [Ntau][Ne]: slice-end states (lambda_{Ms+1}, g_{Ms+1}).
+ */
+int ptg_adjoint_sweep(ptg_op* op, int schedule, int s0, int ns,
+                      const double* T_hist, int hist_j0, int hist_rows, const double* Theta_d,
+                      const double* V_lam, const double* V_g,
+                      double* F_lam, double* F_g, cudaStream_t stream);
+
+/*
+ * a6 -- Eq. 4.7: grad_e += -(1/Nt) sum_{j=j0..j1} lambda_j^T (dc_e Me (T_j - T_{j-1})/dt
+ *                                                           + dk_e Ke T_j)|_e
+ * for every element e, from an adjoint history lam_hist [j1-j0+1][Nn] (row r = lambda_{j0+r})
+ * and a temperature window T_hist (row r = T_{hist_j0+r}) that covers j0-1 .. j1.
+ * 1 <= j0 <= j1 <= Nt.  grad_d [Ne] is accumulated into (not overwritten).
+ */
+int ptg_sensitivities(ptg_op* op, const double* lam_hist, int j0, int j1,
+                      const double* T_hist, int hist_j0, int hist_rows,
+                      double* grad_d, cudaStream_t stream);
+
+/* Copy the device status and counters into *out (synchronises the op's last stream). */
+int ptg_get_stats(ptg_op* op, ptg_stats* out);
+
+/* Clear the device status word and the counters (asynchronous on stream). */
+int ptg_reset_stats(ptg_op* op, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PTG_H */

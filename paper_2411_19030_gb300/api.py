@@ -1,0 +1,256 @@
+"""Python layer over the C ABI: an ``Operator`` handle with one method per entry point,
+and the composition of those calls into the sequential pass, the one-shot pass
+(Algorithm 3) and k-iteration Parareal.
+
+Every method marshals torch CUDA tensors (FP64, contiguous) into pointers and calls the
+library; nothing here computes any step of the method.  Row slices of a tensor are
+passed as pointer offsets, so outputs land directly in the caller's state arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _ffi
+from ._ffi import (PTG_ADJOINT, PTG_FP32_REFINE, PTG_FP64, PTG_PRIMAL, PTG_SLICES_CHAINED,
+                   PTG_SLICES_PARALLEL)
+
+KIND_NAMES = ("fine_primal", "coarse_primal", "correct_primal", "fine_adjoint", "coarse_adjoint", "correct_adjoint")
+
+
+class PTGError(RuntimeError):
+    def __init__(self, code: int, what: str, detail: str = ""):
+        self.code = code
+        super().__init__(f"{what} failed with {_ffi.ERROR_NAMES.get(code, code)}" + (f": {detail}" if detail else ""))
+
+
+def _lib():
+    return _ffi.load()
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise PTGError(rc, what, _lib().ptg_last_error().decode())
+
+
+def _ptr(t: torch.Tensor | None, device: torch.device | None = None) -> int | None:
+    if t is None:
+        return None
+    if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("arrays must be contiguous CUDA float64 tensors")
+    if device is not None and t.device != device:
+        raise ValueError(f"array on {t.device}, operator on {device}")
+    return t.data_ptr()
+
+
+@dataclass
+class SolveConfig:
+    precision: str = "fp64"          # "fp64" or "fp32_refine"
+    rtol: float = 1e-13
+    inner_rtol: float = 1e-4
+    cg_iters_max: int = 2000
+    refine_max: int = 8
+
+
+class Operator:
+    """One problem (grid, materials, time grid, slices, objective, sink, source) on one GPU.
+
+    material: dict with k0, kmin, pk, c0, cmin, pc (Eq. 2.5-2.6).
+    dirichlet: uint8 array [Nn] marking the sink nodes.
+    q_elem / q_time: separable source (element density [Ne], time factor [Nt+1]).
+    """
+
+    def __init__(self, nx: int, ny: int, h: float, material: dict, Nt: int, Ntau: int, dt: float, p: float,
+                 dirichlet: np.ndarray, q_elem: np.ndarray | None = None, q_time: np.ndarray | None = None,
+                 solve: SolveConfig | None = None, device: int | torch.device | None = None):
+        lib = _lib()
+        solve = solve or SolveConfig()
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else
+                           (device.index if isinstance(device, torch.device) else device))
+        self.device = dev
+        self.nx, self.ny, self.h = nx, ny, h
+        self.Nt, self.Ntau, self.dt, self.p = Nt, Ntau, dt, p
+        self.material = dict(material)
+        self.solve = solve
+        self.Nn, self.Ne = (nx + 1) * (ny + 1), nx * ny
+        if Nt % Ntau:
+            raise ValueError("Ntau must divide Nt")
+        self.M = Nt // Ntau
+        g = _ffi.ptg_grid(nx, ny, h)
+        m = _ffi.ptg_material(material["k0"], material["kmin"], material["pk"],
+                              material["c0"], material["cmin"], material["pc"])
+        t = _ffi.ptg_time(Nt, Ntau, dt, p)
+        prec = {"fp64": PTG_FP64, "fp32_refine": PTG_FP32_REFINE}[solve.precision]
+        s = _ffi.ptg_solve(prec, solve.rtol, solve.inner_rtol, solve.cg_iters_max, solve.refine_max)
+        self._dir = np.ascontiguousarray(dirichlet, dtype=np.uint8).reshape(-1)
+        if self._dir.size != self.Nn:
+            raise ValueError("dirichlet mask must have (nx+1)(ny+1) entries")
+        self._qe = None if q_elem is None else np.ascontiguousarray(q_elem, dtype=np.float64)
+        self._qt = None if q_time is None else np.ascontiguousarray(q_time, dtype=np.float64)
+        if self._qe is not None and self._qe.size != self.Ne:
+            raise ValueError("q_elem must have nx*ny entries")
+        if self._qt is not None and self._qt.size != Nt + 1:
+            raise ValueError("q_time must have Nt+1 entries")
+        handle = ctypes.c_void_p()
+        with torch.cuda.device(dev):
+            rc = lib.ptg_op_create(ctypes.byref(g), ctypes.byref(m), ctypes.byref(t), ctypes.byref(s),
+                                   self._dir.ctypes.data,
+                                   None if self._qe is None else self._qe.ctypes.data,
+                                   None if self._qt is None else self._qt.ctypes.data,
+                                   dev.index, ctypes.byref(handle))
+        _check(rc, "ptg_op_create")
+        self._h = handle
+
+    # ------------------------------------------------------------------ lifecycle
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().ptg_op_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self, stream=None) -> int:
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        return s.cuda_stream
+
+    def zeros(self, *shape) -> torch.Tensor:
+        return torch.zeros(*shape, dtype=torch.float64, device=self.device)
+
+    # ------------------------------------------------------------------ entry points
+    def assemble(self, rho: torch.Tensor, stream=None):
+        """a1: SIMP coefficients and element weights of the design rho [Ne]."""
+        if rho.numel() != self.Ne:
+            raise ValueError("rho must have nx*ny entries")
+        _check(_lib().ptg_fe_assemble_operator(self._h, _ptr(rho, self.device), self._stream(stream)),
+               "ptg_fe_assemble_operator")
+
+    def fine_propagate_slices(self, U_T, U_theta, F_T, F_theta, T_hist=None, hist_j0=0, schedule=PTG_SLICES_PARALLEL,
+                              s0=0, ns=None, stream=None):
+        """a2: F_pri of slices s0..s0+ns-1 (see include/ptg.h)."""
+        ns = self.Ntau - s0 if ns is None else ns
+        rows = 0 if T_hist is None else T_hist.shape[0]
+        _check(_lib().ptg_fine_propagate_slices(self._h, schedule, s0, ns, _ptr(U_T, self.device),
+                                                _ptr(U_theta, self.device), _ptr(T_hist, self.device), hist_j0, rows,
+                                                _ptr(F_T, self.device), _ptr(F_theta, self.device),
+                                                self._stream(stream)), "ptg_fine_propagate_slices")
+
+    def coarse_sweep(self, direction, X_field, X_aux, G_field, G_aux, T_hist=None, Theta=None, stream=None):
+        """a3: G of every slice on the guess states X."""
+        _check(_lib().ptg_coarse_sweep(self._h, direction, _ptr(X_field, self.device), _ptr(X_aux, self.device),
+                                       _ptr(T_hist, self.device), _ptr(Theta, self.device),
+                                       _ptr(G_field, self.device), _ptr(G_aux, self.device), self._stream(stream)),
+               "ptg_coarse_sweep")
+
+    def parareal_correct(self, direction, F_field, F_aux, G_field, G_aux, X_field, X_aux, T_hist=None, Theta=None,
+                         stream=None):
+        """a4: the sequential correction sweep (forward or reverse)."""
+        _check(_lib().ptg_parareal_correct(self._h, direction, _ptr(F_field, self.device), _ptr(F_aux, self.device),
+                                           _ptr(G_field, self.device), _ptr(G_aux, self.device),
+                                           _ptr(X_field, self.device), _ptr(X_aux, self.device),
+                                           _ptr(T_hist, self.device), _ptr(Theta, self.device),
+                                           self._stream(stream)), "ptg_parareal_correct")
+
+    def adjoint_sweep(self, T_hist, Theta, V_lam, V_g, F_lam, F_g, hist_j0=0, schedule=PTG_SLICES_PARALLEL, s0=0,
+                      ns=None, stream=None):
+        """a5: F_adj of slices s0..s0+ns-1."""
+        ns = self.Ntau - s0 if ns is None else ns
+        _check(_lib().ptg_adjoint_sweep(self._h, schedule, s0, ns, _ptr(T_hist, self.device), hist_j0,
+                                        T_hist.shape[0], _ptr(Theta, self.device), _ptr(V_lam, self.device),
+                                        _ptr(V_g, self.device), _ptr(F_lam, self.device), _ptr(F_g, self.device),
+                                        self._stream(stream)), "ptg_adjoint_sweep")
+
+    def sensitivities(self, lam_hist, j0, j1, T_hist, grad, hist_j0=0, stream=None):
+        """a6: grad += -(1/Nt) sum_j lambda_j^T dR_j/drho (Eq. 4.7)."""
+        _check(_lib().ptg_sensitivities(self._h, _ptr(lam_hist, self.device), j0, j1, _ptr(T_hist, self.device),
+                                        hist_j0, T_hist.shape[0], _ptr(grad, self.device), self._stream(stream)),
+               "ptg_sensitivities")
+
+    def stats(self) -> dict:
+        st = _ffi.ptg_stats()
+        _check(_lib().ptg_get_stats(self._h, ctypes.byref(st)), "ptg_get_stats")
+        return {k: getattr(st, k) for k, _ in _ffi.ptg_stats._fields_ if k != "reserved"}
+
+    def reset_stats(self, stream=None):
+        _check(_lib().ptg_reset_stats(self._h, self._stream(stream)), "ptg_reset_stats")
+
+    def plan(self, kind: int, ntasks: int) -> dict:
+        cs, nt, npt, mac = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib().ptg_op_get_plan(self._h, kind, ntasks, ctypes.byref(cs), ctypes.byref(nt), ctypes.byref(npt),
+                                      ctypes.byref(mac)), "ptg_op_get_plan")
+        return dict(cs=cs.value, nthreads=nt.value, npt=npt.value, max_active_clusters=mac.value)
+
+    def set_plan(self, kind: int, cs: int, nthreads: int = 256, npt: int = 4):
+        _check(_lib().ptg_op_set_plan(self._h, kind, cs, nthreads, npt), "ptg_op_set_plan")
+
+
+# ---------------------------------------------------------------------- state buffers
+
+class PassBuffers:
+    """Device arrays of one pass: the history, the fine / coarse slice results and the
+    coarse states of the warm start (old) and of the result (new)."""
+
+    def __init__(self, op: Operator, with_history: bool = True):
+        Nt, Ntau, Nn, Ne = op.Nt, op.Ntau, op.Nn, op.Ne
+        z = op.zeros
+        self.T_hist = z(Nt + 1, Nn) if with_history else None
+        self.F_T, self.F_th, self.G_T, self.G_th = z(Ntau, Nn), z(Ntau), z(Ntau, Nn), z(Ntau)
+        self.F_l, self.F_g, self.G_l, self.G_g = z(Ntau, Nn), z(Ntau, Ne), z(Ntau, Nn), z(Ntau, Ne)
+        self.U_T, self.U_th = z(Ntau + 1, Nn), z(Ntau + 1)          # current coarse states
+        self.V_l, self.V_g = z(Ntau + 1, Nn), z(Ntau + 1, Ne)
+        self.U_T_new, self.U_th_new = z(Ntau + 1, Nn), z(Ntau + 1)
+        self.V_l_new, self.V_g_new = z(Ntau + 1, Nn), z(Ntau + 1, Ne)
+
+    def swap(self):
+        """Make the pass result the warm start of the next pass."""
+        self.U_T, self.U_T_new = self.U_T_new, self.U_T
+        self.U_th, self.U_th_new = self.U_th_new, self.U_th
+        self.V_l, self.V_l_new = self.V_l_new, self.V_l
+        self.V_g, self.V_g_new = self.V_g_new, self.V_g
+
+
+def sequential_pass(op: Operator, buf: PassBuffers, T0: torch.Tensor | None = None, stream=None):
+    """Alg. 3 lines 6-7: sequential primal (H_pri applied Nt times, full history) and
+    sequential adjoint (H_adj applied Nt times), with the coarse checkpoints of both.
+    On return buf.U_* / buf.V_* hold (T_{Mn}, theta_{Mn}) and (lambda_{Mn+1}, g_{Mn+1}),
+    Theta is buf.U_th[Ntau] and the gradient g_1 is buf.V_g[0]."""
+    if T0 is None:
+        buf.U_T[0].zero_()
+    else:
+        buf.U_T[0].copy_(T0)
+    buf.U_th[0].zero_()
+    op.fine_propagate_slices(buf.U_T, buf.U_th, buf.U_T[1:], buf.U_th[1:], T_hist=buf.T_hist,
+                             schedule=PTG_SLICES_CHAINED, stream=stream)
+    Theta = buf.U_th[op.Ntau:op.Ntau + 1]
+    buf.V_l[op.Ntau].zero_()
+    buf.V_g[op.Ntau].zero_()
+    op.adjoint_sweep(buf.T_hist, Theta, buf.V_l, buf.V_g, buf.V_l, buf.V_g, schedule=PTG_SLICES_CHAINED,
+                     stream=stream)
+    return Theta, buf.V_g[0]
+
+
+def oneshot_pass(op: Operator, buf: PassBuffers, stream=None, plt: bool = False):
+    """Alg. 3 lines 9-12: one modified forward Parareal iteration and one reverse vanilla
+    Parareal iteration from the warm start (buf.U_*, buf.V_*).  The corrected states go to
+    buf.U_*_new / buf.V_*_new, the history to buf.T_hist; returns (Theta, grad) views."""
+    Ntau = op.Ntau
+    # primal: F and G of every slice on the guess, then the sequential correction
+    op.fine_propagate_slices(buf.U_T, buf.U_th, buf.F_T, buf.F_th, T_hist=buf.T_hist, stream=stream)
+    op.coarse_sweep(PTG_PRIMAL, buf.U_T, buf.U_th, buf.G_T, buf.G_th, stream=stream)
+    buf.U_T_new[0].copy_(buf.U_T[0])
+    buf.U_th_new[0].copy_(buf.U_th[0])
+    op.parareal_correct(PTG_PRIMAL, buf.F_T, buf.F_th, buf.G_T, buf.G_th, buf.U_T_new, buf.U_th_new,
+                        T_hist=buf.T_hist, stream=stream)
+    Theta = buf.U_th_new[Ntau:Ntau + 1]
+    # adjoint: F and G of every slice on the guess, then the reverse correction
+    op.adjoint_sweep(buf.T_hist, Theta, buf.V_l, buf.V_g, buf.F_l, buf.F_g, stream=stream)
+    op.coarse_sweep(PTG_ADJOINT, buf.V_l, buf.V_g, buf.G_l, buf.G_g, T_hist=buf.T_hist, Theta=Theta, stream=stream)
+    op.parareal_correct(PTG_ADJOINT, buf.F_l, buf.F_g, buf.G_l, buf.G_g, buf.V_l_new, buf.V_g_new,
+                        T_hist=buf.T_hist, Theta=Theta, stream=stream)
+    return Theta, buf.V_g_new[0]

@@ -1,0 +1,98 @@
+"""Build the CUDA library ``libptg.so`` (sm_103a) in-tree.
+
+The stepper is compiled once per (precision, task kind) pair so the translation units
+build in parallel; the objects are linked with the assembly kernels and the C ABI layer
+into ``paper_2411_19030_gb300/libptg.so``.  Objects go to ``paper_2411_19030_gb300/_build``.
+A rebuild happens only when a source or header is newer than the library.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+BUILD = os.path.join(PKG, "_build")
+LIB = os.path.join(PKG, "libptg.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+
+
+def _nvcc() -> str:
+    for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found: the CUDA library cannot be built")
+
+
+def _units() -> list[tuple[str, list[str], str]]:
+    """(source, extra flags, object name) for every translation unit."""
+    units = []
+    for tag, real in (("f32", "float"), ("f64", "double")):
+        for kind in range(6):
+            units.append((os.path.join(CSRC, "stepper_inst.cu"),
+                          [f"-DPTG_REAL={real}", f"-DPTG_TAG={tag}", f"-DPTG_KIND={kind}"],
+                          f"stepper_{tag}_k{kind}.o"))
+    for name in ("plan.cu", "assemble.cu", "api.cu"):
+        units.append((os.path.join(CSRC, name), [], name.replace(".cu", ".o")))
+    return units
+
+
+def _inputs() -> list[str]:
+    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
+    files.append(os.path.join(ROOT, "include", "ptg.h"))
+    files.append(os.path.abspath(__file__))
+    return files
+
+
+def needs_build() -> bool:
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    return any(os.path.getmtime(f) > t for f in _inputs())
+
+
+def build_library(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
+    """Compile and link libptg.so; returns its path."""
+    if not force and not needs_build():
+        return LIB
+    nvcc = _nvcc()
+    os.makedirs(BUILD, exist_ok=True)
+    inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
+    extra = ["-Xptxas", "-v"] if verbose else []
+
+    def compile_one(u):
+        src, flags, obj = u
+        out = os.path.join(BUILD, obj)
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *inc, *flags, *extra, "-c", src, "-o", out]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {obj}:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+        return out, r.stderr
+
+    units = _units()
+    jobs = jobs or min(len(units), max(1, os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
+        results = list(ex.map(compile_one, units))
+    if verbose:
+        for _, log in results:
+            sys.stderr.write(log)
+    objs = [o for o, _ in results]
+    tmp = LIB + ".tmp"
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    import time
+    t0 = time.time()
+    path = build_library(force="--force" in sys.argv, verbose="-v" in sys.argv)
+    print(f"built {path} in {time.time() - t0:.1f} s")

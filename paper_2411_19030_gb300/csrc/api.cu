@@ -1,0 +1,462 @@
+// api.cu -- the C ABI (include/ptg.h): op lifecycle, argument checks, plan choice, launches.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include "ptg_internal.h"
+#include "stepper_launch.cuh"
+
+using namespace ptg;
+
+struct ptg_op {
+  int device = 0;
+  ptg_grid g{};
+  ptg_material mat{};
+  ptg_time tm{};
+  ptg_solve sv{};
+  int Nn = 0, Ne = 0, M = 0, p_int = 0, has_dc = 0;
+  double dtau = 0.0;
+  // device workspace
+  double *k = nullptr, *c = nullptr, *dk = nullptr, *dc = nullptr;
+  double *wAf = nullptr, *wAc = nullptr, *mass = nullptr, *fload = nullptr;
+  double *q_elem = nullptr, *q_time = nullptr;
+  uint8_t* dirichlet = nullptr;
+  double* sens_partial = nullptr;
+  int sens_chunks = 0;
+  DevStats* stats = nullptr;
+  cudaStream_t last_stream = nullptr;
+  std::mutex mu;
+  std::map<std::tuple<int, int, int>, Plan> plans;   // (precision, kind, ntasks) -> plan
+  std::map<int, Plan> plan_override;                   // kind -> forced plan
+};
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+int cuda_fail(cudaError_t e, const char* what) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
+  return PTG_ECUDA;
+}
+
+#define PTG_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Choose cluster size, threads and slots for `ntasks` concurrent clusters: fewest waves
+// first, then the largest cluster (least work per CTA per CG iteration).
+int choose_plan(ptg_op* op, int precision, int kind, int ntasks, Plan* out) {
+  std::lock_guard<std::mutex> lk(op->mu);
+  auto ov = op->plan_override.find(kind);
+  if (ov != op->plan_override.end()) {
+    *out = ov->second;
+    return PTG_OK;
+  }
+  auto key = std::make_tuple(precision, kind, ntasks);
+  auto it = op->plans.find(key);
+  if (it != op->plans.end()) {
+    *out = it->second;
+    return PTG_OK;
+  }
+  const int nx = op->g.nx, ny = op->g.ny;
+  Plan best;
+  long best_waves = -1;
+  for (int cs : {16, 8, 4, 2, 1}) {
+    const int rmax = (ny + 1 + cs - 1) / cs;
+    if (rmax < 2) continue;
+    const int nodes = rmax * (nx + 1);
+    int cfg = -1;
+    for (int i = 0; i < kNumStepConfigs; ++i) {
+      const int cap = kStepConfigs[i].nthreads * kStepConfigs[i].npt;
+      if (cap < nodes) continue;
+      if (cfg < 0 || cap < kStepConfigs[cfg].nthreads * kStepConfigs[cfg].npt) cfg = i;
+    }
+    if (cfg < 0) continue;
+    Plan p;
+    cudaError_t e = query_stepper_plan(nx, ny, precision, kind, cs, kStepConfigs[cfg].nthreads, kStepConfigs[cfg].npt, &p);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (p.max_active_clusters <= 0) continue;
+    const long waves = (ntasks + p.max_active_clusters - 1) / p.max_active_clusters;
+    if (best_waves < 0 || waves < best_waves) {   // clusters tried from largest: ties keep the larger
+      best = p;
+      best_waves = waves;
+    }
+  }
+  if (best_waves < 0) {
+    std::snprintf(g_last_error, sizeof(g_last_error), "no cluster plan fits a %dx%d grid", nx, ny);
+    return PTG_EINVAL;
+  }
+  op->plans[key] = best;
+  *out = best;
+  return PTG_OK;
+}
+
+void base_params(const ptg_op* op, StepParams& P) {
+  std::memset(&P, 0, sizeof(P));
+  P.nx = op->g.nx;
+  P.ny = op->g.ny;
+  P.Nn = op->Nn;
+  P.Ne = op->Ne;
+  P.Nt = op->tm.Nt;
+  P.Ntau = op->tm.Ntau;
+  P.M = op->M;
+  P.p_int = op->p_int;
+  P.h = op->g.h;
+  P.dt = op->tm.dt;
+  P.dtau = op->dtau;
+  P.p = op->tm.p;
+  P.has_dc = op->has_dc;
+  P.rtol = op->sv.rtol;
+  P.inner_rtol = op->sv.precision == PTG_FP32_REFINE ? op->sv.inner_rtol : 0.0;
+  P.itmax = op->sv.cg_iters_max;
+  P.refmax = op->sv.refine_max;
+  P.wA_fine = op->wAf;
+  P.wA_coarse = op->wAc;
+  P.mass = op->mass;
+  P.dk = op->dk;
+  P.dc = op->dc;
+  P.fload = op->fload;
+  P.q_time = op->q_time;
+  P.dirichlet = op->dirichlet;
+  P.stats = op->stats;
+  P.hist_rows = 0;
+}
+
+int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream) {
+  Plan plan;
+  int rc = choose_plan(op, op->sv.precision, P.kind, ntasks, &plan);
+  if (rc != PTG_OK) return rc;
+  P.cs = plan.cs;
+  P.rmax = plan.rmax;
+  op->last_stream = stream;
+  PTG_CUDA(launch_stepper(P, plan, op->sv.precision, ntasks, stream));
+  return PTG_OK;
+}
+
+bool window_covers(int j0, int rows, int lo, int hi) { return lo >= j0 && hi < j0 + rows; }
+
+void free_all(ptg_op* op) {
+  void* ptrs[] = {op->k, op->c, op->dk, op->dc, op->wAf, op->wAc, op->mass, op->fload,
+                  op->q_elem, op->q_time, op->dirichlet, op->sens_partial, op->stats};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ptg_version(void) { return "ptg 0.1 sm_103a"; }
+
+const char* ptg_last_error(void) { return g_last_error; }
+
+int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time* time, const ptg_solve* solve,
+                  const uint8_t* dirichlet_h, const double* q_elem_h, const double* q_time_h, int device,
+                  ptg_op** out) {
+  if (!out) return PTG_EINVAL;
+  *out = nullptr;
+  if (!grid || !mat || !time || !solve || !dirichlet_h) return PTG_EINVAL;
+  if (grid->nx < 2 || grid->ny < 2 || grid->nx > 4096 || grid->ny > 4096 || !(grid->h > 0.0)) return PTG_EINVAL;
+  if (time->Nt < 1 || time->Ntau < 1 || time->Nt % time->Ntau != 0 || !(time->dt > 0.0)) return PTG_EINVAL;
+  const double p = time->p;
+  if (!(p >= 2.0 && p <= 64.0) || p != (double)(int)p || ((int)p) % 2 != 0) return PTG_EINVAL;
+  if (solve->precision != PTG_FP64 && solve->precision != PTG_FP32_REFINE) return PTG_EINVAL;
+  if (!(solve->rtol > 0.0) || solve->cg_iters_max < 1 || solve->refine_max < 1 || !(solve->inner_rtol >= 0.0))
+    return PTG_EINVAL;
+  if (!(mat->k0 > 0.0) || !(mat->kmin > 0.0) || !(mat->c0 > 0.0) || !(mat->cmin > 0.0)) return PTG_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    std::snprintf(g_last_error, sizeof(g_last_error), "no CUDA device %d", device);
+    return PTG_ECUDA;
+  }
+  DeviceGuard dg(device);
+  ptg_op* op = new (std::nothrow) ptg_op();
+  if (!op) return PTG_ENOMEM;
+  op->device = device;
+  op->g = *grid;
+  op->mat = *mat;
+  op->tm = *time;
+  op->sv = *solve;
+  op->Nn = (grid->nx + 1) * (grid->ny + 1);
+  op->Ne = grid->nx * grid->ny;
+  op->M = time->Nt / time->Ntau;
+  op->dtau = op->M * time->dt;
+  op->p_int = (int)p;
+  op->has_dc = mat->c0 != mat->cmin;
+  const size_t PE = (size_t)(grid->ny + 2) * (grid->nx + 2);
+  const int blocks_e = (op->Ne + 255) / 256;
+  op->sens_chunks = std::max(1, std::min(64, (4 * 152 + blocks_e - 1) / blocks_e));
+  cudaError_t e = cudaSuccess;
+  auto A = [&](auto** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc((void**)p, bytes);
+  };
+  A(&op->k, op->Ne * sizeof(double));
+  A(&op->c, op->Ne * sizeof(double));
+  A(&op->dk, op->Ne * sizeof(double));
+  A(&op->dc, op->Ne * sizeof(double));
+  A(&op->wAf, 3 * PE * sizeof(double));
+  A(&op->wAc, 3 * PE * sizeof(double));
+  A(&op->mass, PE * sizeof(double));
+  A(&op->fload, op->Nn * sizeof(double));
+  A(&op->q_elem, op->Ne * sizeof(double));
+  A(&op->q_time, (time->Nt + 1) * sizeof(double));
+  A(&op->dirichlet, op->Nn);
+  A(&op->sens_partial, (size_t)op->sens_chunks * op->Ne * sizeof(double));
+  A(&op->stats, sizeof(DevStats));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_all(op);
+    delete op;
+    return PTG_ENOMEM;
+  }
+  double* tmp = new (std::nothrow) double[std::max(op->Ne, time->Nt + 1)];
+  if (!tmp) {
+    free_all(op);
+    delete op;
+    return PTG_ENOMEM;
+  }
+  for (int i = 0; i < op->Ne; ++i) tmp[i] = q_elem_h ? q_elem_h[i] : 1.0;
+  e = cudaMemcpy(op->q_elem, tmp, op->Ne * sizeof(double), cudaMemcpyHostToDevice);
+  for (int i = 0; i <= time->Nt; ++i) tmp[i] = q_time_h ? q_time_h[i] : 1.0;
+  if (e == cudaSuccess) e = cudaMemcpy(op->q_time, tmp, (time->Nt + 1) * sizeof(double), cudaMemcpyHostToDevice);
+  delete[] tmp;
+  if (e == cudaSuccess) e = cudaMemcpy(op->dirichlet, dirichlet_h, op->Nn, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(op->stats, 0, sizeof(DevStats));
+  if (e == cudaSuccess) e = cudaMemset(op->fload, 0, op->Nn * sizeof(double));
+  if (e != cudaSuccess) {
+    int rc = cuda_fail(e, "ptg_op_create");
+    free_all(op);
+    delete op;
+    return rc;
+  }
+  // the grid must fit one cluster for every kind and precision this op may run
+  Plan probe;
+  for (int kind = 0; kind < 6; ++kind) {
+    int rc = choose_plan(op, op->sv.precision, kind, 1, &probe);
+    if (rc != PTG_OK) {
+      free_all(op);
+      delete op;
+      return rc;
+    }
+  }
+  *out = op;
+  return PTG_OK;
+}
+
+void ptg_op_destroy(ptg_op* op) {
+  if (!op) return;
+  DeviceGuard dg(op->device);
+  cudaDeviceSynchronize();
+  free_all(op);
+  delete op;
+}
+
+int ptg_op_sizes(const ptg_op* op, int* Nn, int* Ne, int* Nt, int* Ntau, int* M) {
+  if (!op) return PTG_EINVAL;
+  if (Nn) *Nn = op->Nn;
+  if (Ne) *Ne = op->Ne;
+  if (Nt) *Nt = op->tm.Nt;
+  if (Ntau) *Ntau = op->tm.Ntau;
+  if (M) *M = op->M;
+  return PTG_OK;
+}
+
+int ptg_op_set_plan(ptg_op* op, int kind, int cs, int nthreads, int npt) {
+  if (!op || kind < 0 || kind > 5) return PTG_EINVAL;
+  DeviceGuard dg(op->device);
+  std::lock_guard<std::mutex> lk(op->mu);
+  if (cs == 0) {
+    op->plan_override.erase(kind);
+    return PTG_OK;
+  }
+  if (cs != 1 && cs != 2 && cs != 4 && cs != 8 && cs != 16) return PTG_EINVAL;
+  if ((op->g.ny + 1 + cs - 1) / cs < 2) return PTG_EINVAL;
+  Plan p;
+  cudaError_t e = query_stepper_plan(op->g.nx, op->g.ny, op->sv.precision, kind, cs, nthreads, npt, &p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return PTG_EINVAL;
+  }
+  if (p.max_active_clusters <= 0 || nthreads * npt < p.rmax * (op->g.nx + 1)) return PTG_EINVAL;
+  op->plan_override[kind] = p;
+  return PTG_OK;
+}
+
+int ptg_op_get_plan(ptg_op* op, int kind, int ntasks, int* cs, int* nthreads, int* npt, int* max_active_clusters) {
+  if (!op || kind < 0 || kind > 5 || ntasks < 1) return PTG_EINVAL;
+  DeviceGuard dg(op->device);
+  Plan p;
+  int rc = choose_plan(op, op->sv.precision, kind, ntasks, &p);
+  if (rc != PTG_OK) return rc;
+  if (cs) *cs = p.cs;
+  if (nthreads) *nthreads = p.nthreads;
+  if (npt) *npt = p.npt;
+  if (max_active_clusters) *max_active_clusters = p.max_active_clusters;
+  return PTG_OK;
+}
+
+int ptg_fe_assemble_operator(ptg_op* op, const double* rho_d, cudaStream_t stream) {
+  if (!op || !rho_d) return PTG_EINVAL;
+  DeviceGuard dg(op->device);
+  op->last_stream = stream;
+  PTG_CUDA(launch_assemble(op->g.nx, op->g.ny, op->g.h, op->mat, op->tm.dt, op->dtau, rho_d, op->q_elem,
+                           op->dirichlet, op->k, op->c, op->dk, op->dc, op->wAf, op->wAc, op->mass, op->fload,
+                           op->stats, stream));
+  return PTG_OK;
+}
+
+int ptg_fine_propagate_slices(ptg_op* op, int schedule, int s0, int ns, const double* U_T, const double* U_theta,
+                              double* T_hist, int hist_j0, int hist_rows, double* F_T, double* F_theta,
+                              cudaStream_t stream) {
+  if (!op || !U_T || !U_theta || !F_T || !F_theta) return PTG_EINVAL;
+  if (schedule != PTG_SLICES_PARALLEL && schedule != PTG_SLICES_CHAINED) return PTG_EINVAL;
+  if (s0 < 0 || ns < 1 || s0 + ns > op->tm.Ntau) return PTG_EINVAL;
+  if (T_hist && !window_covers(hist_j0, hist_rows, op->M * s0 + 1, op->M * (s0 + ns))) return PTG_EINVAL;
+  DeviceGuard dg(op->device);
+  StepParams P;
+  base_params(op, P);
+  P.kind = KIND_FINE_PRI;
+  P.s0 = s0;
+  P.ns = ns;
+  P.chained = schedule == PTG_SLICES_CHAINED;
+  P.in_field = U_T;
+  P.in_aux = U_theta;
+  P.out_field = F_T;
+  P.out_aux = F_theta;
+  P.hist = T_hist;
+  P.hist_j0 = hist_j0;
+  P.hist_rows = T_hist ? hist_rows : 0;
+  return run(op, P, P.chained ? 1 : ns, stream);
+}
+
+int ptg_coarse_sweep(ptg_op* op, int direction, const double* X_field, const double* X_aux, const double* T_hist,
+                     const double* Theta_d, double* G_field, double* G_aux, cudaStream_t stream) {
+  if (!op || !X_field || !X_aux || !G_field || !G_aux) return PTG_EINVAL;
+  if (direction != PTG_PRIMAL && direction != PTG_ADJOINT) return PTG_EINVAL;
+  if (direction == PTG_ADJOINT && (!T_hist || !Theta_d)) return PTG_EINVAL;
+  DeviceGuard dg(op->device);
+  StepParams P;
+  base_params(op, P);
+  P.kind = direction == PTG_PRIMAL ? KIND_COARSE_PRI : KIND_COARSE_ADJ;
+  P.s0 = 0;
+  P.ns = op->tm.Ntau;
+  P.in_field = X_field;
+  P.in_aux = X_aux;
+  P.out_field = G_field;
+  P.out_aux = G_aux;
+  P.hist = const_cast<double*>(T_hist);
+  P.hist_j0 = 0;
+  P.hist_rows = T_hist ? op->tm.Nt + 1 : 0;
+  P.Theta = Theta_d;
+  return run(op, P, op->tm.Ntau, stream);
+}
+
+int ptg_parareal_correct(ptg_op* op, int direction, const double* F_field, const double* F_aux, const double* G_field,
+                         const double* G_aux, double* X_field, double* X_aux, double* T_hist, const double* Theta_d,
+                         cudaStream_t stream) {
+  if (!op || !F_field || !F_aux || !G_field || !G_aux || !X_field || !X_aux) return PTG_EINVAL;
+  if (direction != PTG_PRIMAL && direction != PTG_ADJOINT) return PTG_EINVAL;
+  if (direction == PTG_ADJOINT && (!T_hist || !Theta_d)) return PTG_EINVAL;
+  DeviceGuard dg(op->device);
+  StepParams P;
+  base_params(op, P);
+  P.kind = direction == PTG_PRIMAL ? KIND_CORRECT_PRI : KIND_CORRECT_ADJ;
+  P.s0 = 0;
+  P.ns = op->tm.Ntau;
+  P.F_field = F_field;
+  P.F_aux = F_aux;
+  P.G_field = G_field;
+  P.G_aux = G_aux;
+  P.out_field = X_field;
+  P.out_aux = X_aux;
+  P.hist = T_hist;
+  P.hist_j0 = 0;
+  P.hist_rows = T_hist ? op->tm.Nt + 1 : 0;
+  P.Theta = Theta_d;
+  return run(op, P, 1, stream);
+}
+
+int ptg_adjoint_sweep(ptg_op* op, int schedule, int s0, int ns, const double* T_hist, int hist_j0, int hist_rows,
+                      const double* Theta_d, const double* V_lam, const double* V_g, double* F_lam, double* F_g,
+                      cudaStream_t stream) {
+  if (!op || !T_hist || !Theta_d || !V_lam || !V_g || !F_lam || !F_g) return PTG_EINVAL;
+  if (schedule != PTG_SLICES_PARALLEL && schedule != PTG_SLICES_CHAINED) return PTG_EINVAL;
+  if (s0 < 0 || ns < 1 || s0 + ns > op->tm.Ntau) return PTG_EINVAL;
+  if (!window_covers(hist_j0, hist_rows, op->M * s0, op->M * (s0 + ns))) return PTG_EINVAL;
+  DeviceGuard dg(op->device);
+  StepParams P;
+  base_params(op, P);
+  P.kind = KIND_FINE_ADJ;
+  P.s0 = s0;
+  P.ns = ns;
+  P.chained = schedule == PTG_SLICES_CHAINED;
+  P.in_field = V_lam;
+  P.in_aux = V_g;
+  P.out_field = F_lam;
+  P.out_aux = F_g;
+  P.hist = const_cast<double*>(T_hist);
+  P.hist_j0 = hist_j0;
+  P.hist_rows = hist_rows;
+  P.Theta = Theta_d;
+  return run(op, P, P.chained ? 1 : ns, stream);
+}
+
+int ptg_sensitivities(ptg_op* op, const double* lam_hist, int j0, int j1, const double* T_hist, int hist_j0,
+                      int hist_rows, double* grad_d, cudaStream_t stream) {
+  if (!op || !lam_hist || !T_hist || !grad_d) return PTG_EINVAL;
+  if (j0 < 1 || j1 < j0 || j1 > op->tm.Nt) return PTG_EINVAL;
+  if (!window_covers(hist_j0, hist_rows, j0 - 1, j1)) return PTG_EINVAL;
+  DeviceGuard dg(op->device);
+  op->last_stream = stream;
+  PTG_CUDA(launch_sensitivities(op->g.nx, op->g.ny, op->tm.Nt, op->g.h, op->tm.dt, op->has_dc, op->dk, op->dc,
+                                lam_hist, j0, j1, T_hist, hist_j0, op->sens_partial, op->sens_chunks, grad_d, stream));
+  return PTG_OK;
+}
+
+int ptg_get_stats(ptg_op* op, ptg_stats* out) {
+  if (!op || !out) return PTG_EINVAL;
+  DeviceGuard dg(op->device);
+  DevStats s;
+  PTG_CUDA(cudaStreamSynchronize(op->last_stream));
+  PTG_CUDA(cudaMemcpy(&s, op->stats, sizeof(s), cudaMemcpyDeviceToHost));
+  out->status = s.status;
+  out->fail_kind = s.fail_kind;
+  out->fail_step = s.fail_step;
+  out->reserved = 0;
+  out->solves = (long long)s.solves;
+  out->cg_iters = (long long)s.cg_iters;
+  out->refinements = (long long)s.refinements;
+  out->max_cg_iters = (long long)s.max_cg_iters;
+  return PTG_OK;
+}
+
+int ptg_reset_stats(ptg_op* op, cudaStream_t stream) {
+  if (!op) return PTG_EINVAL;
+  DeviceGuard dg(op->device);
+  op->last_stream = stream;
+  PTG_CUDA(cudaMemsetAsync(op->stats, 0, sizeof(DevStats), stream));
+  return PTG_OK;
+}
+
+}  // extern "C"

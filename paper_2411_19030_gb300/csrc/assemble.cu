@@ -1,0 +1,162 @@
+// assemble.cu -- a1 (SIMP coefficients and element weights) and a6 (sensitivity reduction).
+#include <cstdint>
+#include "ptg_device.cuh"
+#include "ptg_internal.h"
+
+namespace ptg {
+
+__device__ __forceinline__ void assemble_error(DevStats* st, int code) {
+  if (atomicCAS(&st->status, 0, code) == 0) {
+    st->fail_kind = 1;
+    st->fail_step = -1;
+  }
+}
+
+// a1, Sec. 2.1 Eq. 2.5-2.6 and Sec. 2.2: one thread per element of the zero-padded
+// (ny+2) x (nx+2) element grid.  Interior elements get the SIMP coefficients and the
+// (D, S, T) weights of C/dt + K and C/dtau + K; the padding ring gets zeros.
+__global__ void assemble_kernel(int nx, int ny, double h, ptg_material m, double dt, double dtau,
+                                const double* __restrict__ rho, double* __restrict__ k_out, double* __restrict__ c_out,
+                                double* __restrict__ dk_out, double* __restrict__ dc_out, double* __restrict__ wAf,
+                                double* __restrict__ wAc, double* __restrict__ mass, DevStats* st) {
+  const int EW = nx + 2, PE = (ny + 2) * EW;
+  const int pe = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pe >= PE) return;
+  const int ey = pe / EW - 1, ex = pe % EW - 1;
+  double wf[3] = {0.0, 0.0, 0.0}, wc[3] = {0.0, 0.0, 0.0}, mm = 0.0;
+  if (ey >= 0 && ey < ny && ex >= 0 && ex < nx) {
+    const int e = ey * nx + ex;
+    double r = rho[e];
+    if (!(r >= 0.0 && r <= 1.0)) {        // also catches NaN
+      assemble_error(st, PTG_EINVAL);
+      r = 0.0;
+    }
+    const double kk = m.kmin + (m.k0 - m.kmin) * pow(r, m.pk);
+    const double cc = m.cmin + (m.c0 - m.cmin) * pow(r, m.pc);
+    const double dk = (m.k0 == m.kmin) ? 0.0 : m.pk * (m.k0 - m.kmin) * pow(r, m.pk - 1.0);
+    const double dc = (m.c0 == m.cmin) ? 0.0 : m.pc * (m.c0 - m.cmin) * pow(r, m.pc - 1.0);
+    k_out[e] = kk;
+    c_out[e] = cc;
+    dk_out[e] = dk;
+    dc_out[e] = dc;
+    mm = cc * h * h / 36.0;                // consistent mass: Me = (h^2/36)[4 2 1 2; ...]
+    // K_e = (k/6)[4 -1 -2 -1; ...]: D = 4k/6, S = -k/6, T = -2k/6
+    const double kd = 4.0 * kk / 6.0, ks = -kk / 6.0, kt = -2.0 * kk / 6.0;
+    const double mf = mm / dt, mc = mm / dtau;
+    wf[0] = kd + 4.0 * mf;
+    wf[1] = ks + 2.0 * mf;
+    wf[2] = kt + mf;
+    wc[0] = kd + 4.0 * mc;
+    wc[1] = ks + 2.0 * mc;
+    wc[2] = kt + mc;
+  }
+  mass[pe] = mm;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    wAf[i * PE + pe] = wf[i];
+    wAc[i * PE + pe] = wc[i];
+  }
+}
+
+// Unit-time load vector f_i = sum_e q_e int N_i = sum over the elements around node i of
+// q_e h^2 / 4 (Sec. 2.2, element-wise constant q); zero on Dirichlet nodes.
+__global__ void load_kernel(int nx, int ny, double h, const double* __restrict__ q_elem,
+                            const uint8_t* __restrict__ dirichlet, double* __restrict__ fload) {
+  const int nn = nx + 1;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nn * (ny + 1)) return;
+  const int iy = i / nn, ix = i % nn;
+  double s = 0.0;
+  for (int dy = -1; dy <= 0; ++dy)
+    for (int dx = -1; dx <= 0; ++dx) {
+      const int ey = iy + dy, ex = ix + dx;
+      if (ey >= 0 && ey < ny && ex >= 0 && ex < nx) s += q_elem[ey * nx + ex];
+    }
+  fload[i] = dirichlet[i] ? 0.0 : s * h * h / 4.0;
+}
+
+cudaError_t launch_assemble(int nx, int ny, double h, const ptg_material& m, double dt, double dtau, const double* rho,
+                            const double* q_elem, const uint8_t* dirichlet, double* k, double* c, double* dk, double* dc,
+                            double* wAf, double* wAc, double* mass, double* fload, DevStats* st, cudaStream_t stream) {
+  const int PE = (ny + 2) * (nx + 2);
+  assemble_kernel<<<(PE + 255) / 256, 256, 0, stream>>>(nx, ny, h, m, dt, dtau, rho, k, c, dk, dc, wAf, wAc, mass, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int Nn = (nx + 1) * (ny + 1);
+  load_kernel<<<(Nn + 255) / 256, 256, 0, stream>>>(nx, ny, h, q_elem, dirichlet, fload);
+  return cudaGetLastError();
+}
+
+// a6, Eq. 4.7: per element e and time chunk, sum over j of
+//   lambda_j,e^T ( dk_e Ke T_j,e + dc_e/dt Me (T_j - T_{j-1})_e ).
+// One thread per element; blockIdx.y selects a contiguous chunk of time steps.  T_{j-1} is
+// carried in registers from the previous step, so each step reads lambda_j and T_j once.
+__global__ void sens_kernel(int nx, int ny, double h, double dt, int has_dc, const double* __restrict__ dk,
+                            const double* __restrict__ dc, const double* __restrict__ lam, int j0, int j1,
+                            const double* __restrict__ T, int hist_j0, int steps_per_chunk,
+                            double* __restrict__ partial) {
+  const int Ne = nx * ny, nn = nx + 1, Nn = nn * (ny + 1);
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Ne) return;
+  const int chunk = blockIdx.y;
+  const int ja = j0 + chunk * steps_per_chunk;
+  const int jb = min(j1, ja + steps_per_chunk - 1);
+  const int ey = e / nx, ex = e % nx;
+  const int g0 = ey * nn + ex;
+  const double h2 = h * h / 36.0;
+  const double dke = dk[e], dce = has_dc ? dc[e] / dt : 0.0;
+  double acc = 0.0;
+  if (ja <= jb) {
+    const double* Tp = T + (size_t)(ja - 1 - hist_j0) * Nn;
+    double psw = Tp[g0], pse = Tp[g0 + 1], pne = Tp[g0 + nn + 1], pnw = Tp[g0 + nn];
+    for (int j = ja; j <= jb; ++j) {
+      const double* Tj = T + (size_t)(j - hist_j0) * Nn;
+      const double* Lj = lam + (size_t)(j - j0) * Nn;
+      const double tsw = Tj[g0], tse = Tj[g0 + 1], tne = Tj[g0 + nn + 1], tnw = Tj[g0 + nn];
+      const double lsw = Lj[g0], lse = Lj[g0 + 1], lne = Lj[g0 + nn + 1], lnw = Lj[g0 + nn];
+      const double ksw = 4.0 * tsw - tse - 2.0 * tne - tnw;
+      const double kse = -tsw + 4.0 * tse - tne - 2.0 * tnw;
+      const double kne = -2.0 * tsw - tse + 4.0 * tne - tnw;
+      const double knw = -tsw - 2.0 * tse - tne + 4.0 * tnw;
+      double term = dke * (lsw * ksw + lse * kse + lne * kne + lnw * knw) / 6.0;
+      if (has_dc) {
+        const double dsw = tsw - psw, dse = tse - pse, dne = tne - pne, dnw = tnw - pnw;
+        const double msw = 4.0 * dsw + 2.0 * dse + dne + 2.0 * dnw;
+        const double mse = 2.0 * dsw + 4.0 * dse + 2.0 * dne + dnw;
+        const double mne = dsw + 2.0 * dse + 4.0 * dne + 2.0 * dnw;
+        const double mnw = 2.0 * dsw + dse + 2.0 * dne + 4.0 * dnw;
+        term += dce * (lsw * msw + lse * mse + lne * mne + lnw * mnw) * h2;
+      }
+      acc += term;
+      psw = tsw; pse = tse; pne = tne; pnw = tnw;
+    }
+  }
+  partial[(size_t)chunk * Ne + e] = acc;
+}
+
+// grad_e += -(1/Nt) sum over chunks (fixed order) of the partial sums.
+__global__ void sens_reduce_kernel(int Ne, int nchunks, double inv_nt, const double* __restrict__ partial,
+                                   double* __restrict__ grad) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Ne) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunks; ++c) s += partial[(size_t)c * Ne + e];
+  grad[e] -= inv_nt * s;
+}
+
+cudaError_t launch_sensitivities(int nx, int ny, int Nt, double h, double dt, int has_dc, const double* dk,
+                                 const double* dc, const double* lam, int j0, int j1, const double* T, int hist_j0,
+                                 double* partial, int nchunks, double* grad, cudaStream_t stream) {
+  const int Ne = nx * ny;
+  const int nsteps = j1 - j0 + 1;
+  const int spc = (nsteps + nchunks - 1) / nchunks;
+  const int used = (nsteps + spc - 1) / spc;
+  dim3 grid((Ne + 255) / 256, used);
+  sens_kernel<<<grid, 256, 0, stream>>>(nx, ny, h, dt, has_dc, dk, dc, lam, j0, j1, T, hist_j0, spc, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  sens_reduce_kernel<<<(Ne + 255) / 256, 256, 0, stream>>>(Ne, used, 1.0 / Nt, partial, grad);
+  return cudaGetLastError();
+}
+
+}  // namespace ptg
