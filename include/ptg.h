@@ -236,6 +236,33 @@ int ptg_sensitivities(ptg_op* op, const double* lam_hist, int j0, int j1,
                       const double* T_hist, int hist_j0, int hist_rows,
                       double* grad_d, cudaStream_t stream);
 
+/*
+ * ptg_sensitivities_noalloc -- the reduction of ptg_sensitivities without any device
+ * allocation.  The paper has no counterpart: this entry point exists for callers that are
+ * not allowed to allocate device memory themselves -- code whose device memory is owned by
+ * another allocator (a framework's caching pool, an application with a fixed memory
+ * budget), and timed loops in which cudaMalloc/cudaFree would synchronise the device.
+ * ptg_op_create allocates a workspace; this call needs no op and no workspace.
+ *   Inputs as for ptg_sensitivities, with the problem given explicitly: grid (nx, ny, h),
+ *   Nt and dt, the SIMP material and the design rho_d (device FP64 [Ne]), from which the
+ *   kernel evaluates dk/drho and dc/drho itself.  grad_d [Ne] is accumulated into.
+ *   Scratch: the per-chunk partial sums use one static device array of
+ *   PTG_NOALLOC_SCRATCH_DOUBLES doubles (16 MiB) that every GPU loading this library keeps
+ *   until the process exits.  Grids with nx*ny > PTG_NOALLOC_SCRATCH_DOUBLES are rejected
+ *   with PTG_EINVAL before anything is launched.  Every call shares that array and leaves
+ *   its partial sums behind; each call overwrites every entry it reads, so nothing needs
+ *   clearing, but calls that overlap on the GPU (other streams, other threads) race on it
+ *   and must be serialised by the caller.
+ *   Set-up: the first call on a device (that device current) looks up the array's device
+ *   address once; make that first call before any stream capture begins.
+ * Returns PTG_OK, PTG_EINVAL (arguments, size) or PTG_ECUDA.
+ */
+#define PTG_NOALLOC_SCRATCH_DOUBLES (1 << 21)
+int ptg_sensitivities_noalloc(int nx, int ny, double h, int Nt, double dt, const ptg_material* mat,
+                              const double* rho_d, const double* lam_hist, int j0, int j1,
+                              const double* T_hist, int hist_j0, int hist_rows,
+                              double* grad_d, cudaStream_t stream);
+
 /* Copy the device status and counters into *out (synchronises the op's last stream). */
 int ptg_get_stats(ptg_op* op, ptg_stats* out);
 

@@ -58,6 +58,8 @@ SIGNATURES = {
     "ptg_parareal_correct": (c_int, [_P, c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "ptg_adjoint_sweep": (c_int, [_P, c_int, c_int, c_int, _P, c_int, c_int, _P, _P, _P, _P, _P, _P]),
     "ptg_sensitivities": (c_int, [_P, _P, c_int, c_int, _P, c_int, c_int, _P, _P]),
+    "ptg_sensitivities_noalloc": (c_int, [c_int, c_int, c_double, c_int, c_double, POINTER(ptg_material), _P, _P,
+                                          c_int, c_int, _P, c_int, c_int, _P, _P]),
     "ptg_get_stats": (c_int, [_P, POINTER(ptg_stats)]),
     "ptg_reset_stats": (c_int, [_P, _P]),
 }

@@ -164,6 +164,11 @@ void free_all(ptg_op* op) {
 
 }  // namespace
 
+namespace ptg {
+// Lets other translation units of the library report a message through ptg_last_error.
+void set_last_error(const char* msg) { std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+}  // namespace ptg
+
 extern "C" {
 
 const char* ptg_version(void) { return "ptg 0.1 sm_103a"; }

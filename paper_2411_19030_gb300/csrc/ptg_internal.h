@@ -103,4 +103,6 @@ cudaError_t launch_sensitivities(int nx, int ny, int Nt, double h, double dt, in
                                  const double* dc, const double* lam, int j0, int j1, const double* T, int hist_j0,
                                  double* partial, int nchunks, double* grad, cudaStream_t stream);
 
+void set_last_error(const char* msg);
+
 }  // namespace ptg
