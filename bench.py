@@ -46,6 +46,23 @@ def problem_arrays(name=WORKLOAD):
     return w, rho_old, rho, sink
 
 
+def slowest_rank_ms(ms: float, device) -> float:
+    """Max over all ranks of the per-rank step time (every rank receives it).  With one process,
+    or without an initialised process group, returns ms unchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank_step: float, world: int, ms: float) -> float:
+    """Whole-job throughput: the units all replicas processed per step over the slowest rank's time."""
+    return world * units_per_rank_step / (ms * 1e-3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -200,12 +217,9 @@ def run_gpu(args):
         step_ms.append(ev[0].elapsed_time(ev[7]))
     ms = float(np.sum(step_ms)) / args.steps
     stats = op.stats()
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = slowest_rank_ms(ms, device)
     dof_steps = 2.0 * N_free * Nt
-    value = world * dof_steps / (ms * 1e-3)
+    value = job_throughput(dof_steps, world, ms)
     kind_ms = {k: float(v / args.steps) for k, v in zip(kinds, per_kind)}
 
     # end to end through the public API with host buffers: H2D of rho, D2H of Theta and grad
@@ -258,7 +272,10 @@ def run_gpu(args):
                    "wall_s": wall},
         "per_kernel_ms": kind_ms,
         "cg": {"solves": stats["solves"], "cg_iters": stats["cg_iters"], "refinements": stats["refinements"],
-               "mean_cg_per_solve": stats["cg_iters"] / max(1, stats["solves"])},
+               "mean_cg_per_solve": stats["cg_iters"] / max(1, stats["solves"]),
+               "by_kind": {k: {"cg_per_solve": v["cg_iters"] / max(1, v["solves"]),
+                               "refine_per_solve": v["refinements"] / max(1, v["solves"])}
+                           for k, v in stats["by_kind"].items() if v["solves"]}},
         "comparator_sequential_fp64": {"ms": seq_ms, "value": dof_steps / (seq_ms * 1e-3), "unit": UNIT,
                                        "speedup_of_oneshot": seq_ms / ms,
                                        "cg_iters": seq_stats["cg_iters"], "solves": seq_stats["solves"]},

@@ -103,6 +103,9 @@ typedef struct {
     long long cg_iters;     /* CG iterations since the last reset */
     long long refinements;  /* refinement sweeps (FP32_REFINE) since the last reset */
     long long max_cg_iters; /* largest CG iteration count of one solve */
+    long long kind_solves[6];      /* the same counters per stepper task kind (see ptg_op_get_plan) */
+    long long kind_cg_iters[6];
+    long long kind_refinements[6];
 } ptg_stats;
 
 typedef struct ptg_op ptg_op;   /* opaque: operator coefficients, launch plan, workspace */
@@ -136,15 +139,15 @@ int ptg_op_sizes(const ptg_op* op, int* Nn, int* Ne, int* Nt, int* Ntau, int* M)
 
 /*
  * Launch plan of the cluster stepper.  Every solve runs on one thread-block cluster of
- * `cs` CTAs (1, 2, 4, 8 or 16) that split the node rows; each CTA has `nthreads` threads
- * holding `npt` nodes each.  kind: 0 fine primal, 1 coarse primal, 2 primal correction,
- * 3 fine adjoint, 4 coarse adjoint, 5 adjoint correction.
+ * `cs` CTAs (1, 2, 4, 8 or 16) that split the node rows; each CTA has `nthreads` (256)
+ * threads, each holding `ng` aligned groups of 4 nodes (1..6).  kind: 0 fine primal,
+ * 1 coarse primal, 2 primal correction, 3 fine adjoint, 4 coarse adjoint, 5 adjoint correction.
  * ptg_op_get_plan reports the plan used for `ntasks` concurrent clusters (chosen for the
  * fewest waves, then the largest cluster).  ptg_op_set_plan forces a plan for a kind
  * (cs = 0 removes the override); PTG_EINVAL if the plan does not fit the grid or device.
  */
-int ptg_op_get_plan(ptg_op* op, int kind, int ntasks, int* cs, int* nthreads, int* npt, int* max_active_clusters);
-int ptg_op_set_plan(ptg_op* op, int kind, int cs, int nthreads, int npt);
+int ptg_op_get_plan(ptg_op* op, int kind, int ntasks, int* cs, int* nthreads, int* ng, int* max_active_clusters);
+int ptg_op_set_plan(ptg_op* op, int kind, int cs, int ng);
 
 /*
  * a1 -- Sec. 2.1-2.2, Eq. 2.5-2.6: evaluate the SIMP coefficients k_e, c_e, dk_e/drho,

@@ -38,7 +38,8 @@ class ptg_solve(ctypes.Structure):
 class ptg_stats(ctypes.Structure):
     _fields_ = [("status", c_int), ("fail_kind", c_int), ("fail_step", c_int), ("reserved", c_int),
                 ("solves", c_longlong), ("cg_iters", c_longlong), ("refinements", c_longlong),
-                ("max_cg_iters", c_longlong)]
+                ("max_cg_iters", c_longlong), ("kind_solves", c_longlong * 6), ("kind_cg_iters", c_longlong * 6),
+                ("kind_refinements", c_longlong * 6)]
 
 
 _P = c_void_p   # device / host pointers and cudaStream_t are passed as addresses
@@ -51,7 +52,7 @@ SIGNATURES = {
     "ptg_op_destroy": (None, [_P]),
     "ptg_op_sizes": (c_int, [_P, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "ptg_op_get_plan": (c_int, [_P, c_int, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
-    "ptg_op_set_plan": (c_int, [_P, c_int, c_int, c_int, c_int]),
+    "ptg_op_set_plan": (c_int, [_P, c_int, c_int, c_int]),
     "ptg_fe_assemble_operator": (c_int, [_P, _P, _P]),
     "ptg_fine_propagate_slices": (c_int, [_P, c_int, c_int, c_int, _P, _P, _P, c_int, c_int, _P, _P, _P]),
     "ptg_coarse_sweep": (c_int, [_P, c_int, _P, _P, _P, _P, _P, _P, _P]),

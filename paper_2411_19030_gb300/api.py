@@ -175,19 +175,28 @@ class Operator:
     def stats(self) -> dict:
         st = _ffi.ptg_stats()
         _check(_lib().ptg_get_stats(self._h, ctypes.byref(st)), "ptg_get_stats")
-        return {k: getattr(st, k) for k, _ in _ffi.ptg_stats._fields_ if k != "reserved"}
+        out = {}
+        for k, _ in _ffi.ptg_stats._fields_:
+            if k == "reserved":
+                continue
+            v = getattr(st, k)
+            out[k] = list(v) if k.startswith("kind_") else v
+        out["by_kind"] = {name: dict(solves=out["kind_solves"][i], cg_iters=out["kind_cg_iters"][i],
+                                     refinements=out["kind_refinements"][i]) for i, name in enumerate(KIND_NAMES)}
+        return out
 
     def reset_stats(self, stream=None):
         _check(_lib().ptg_reset_stats(self._h, self._stream(stream)), "ptg_reset_stats")
 
     def plan(self, kind: int, ntasks: int) -> dict:
-        cs, nt, npt, mac = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        _check(_lib().ptg_op_get_plan(self._h, kind, ntasks, ctypes.byref(cs), ctypes.byref(nt), ctypes.byref(npt),
+        cs, nt, ng, mac = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib().ptg_op_get_plan(self._h, kind, ntasks, ctypes.byref(cs), ctypes.byref(nt), ctypes.byref(ng),
                                       ctypes.byref(mac)), "ptg_op_get_plan")
-        return dict(cs=cs.value, nthreads=nt.value, npt=npt.value, max_active_clusters=mac.value)
+        return dict(cs=cs.value, nthreads=nt.value, ng=ng.value, max_active_clusters=mac.value)
 
-    def set_plan(self, kind: int, cs: int, nthreads: int = 256, npt: int = 4):
-        _check(_lib().ptg_op_set_plan(self._h, kind, cs, nthreads, npt), "ptg_op_set_plan")
+    def set_plan(self, kind: int, cs: int, ng: int = 1):
+        """Force the cluster size and groups per thread of one task kind (cs = 0 clears it)."""
+        _check(_lib().ptg_op_set_plan(self._h, kind, cs, ng), "ptg_op_set_plan")
 
 
 # ---------------------------------------------------------------------- state buffers

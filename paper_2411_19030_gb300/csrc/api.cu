@@ -19,9 +19,12 @@ struct ptg_op {
   ptg_solve sv{};
   int Nn = 0, Ne = 0, M = 0, p_int = 0, has_dc = 0;
   double dtau = 0.0;
+  int W = 0;               // padded row width
   // device workspace
   double *k = nullptr, *c = nullptr, *dk = nullptr, *dc = nullptr;
-  double *wAf = nullptr, *wAc = nullptr, *mass = nullptr, *fload = nullptr;
+  double* wE = nullptr;     // [2][3][PEe]: element (D, S, T) weights for dt and dtau (padded)
+  double* nodew = nullptr;  // [15][PN]: per-node weights of C/dt + K, C/dtau + K and C (padded)
+  double* fload = nullptr;
   double *q_elem = nullptr, *q_time = nullptr;
   uint8_t* dirichlet = nullptr;
   double* sens_partial = nullptr;
@@ -76,30 +79,30 @@ int choose_plan(ptg_op* op, int precision, int kind, int ntasks, Plan* out) {
     return PTG_OK;
   }
   const int nx = op->g.nx, ny = op->g.ny;
+  const int G = op->W / kGroup;
+  // candidates: every cluster size and groups-per-thread count whose block fits 512 threads;
+  // best = fewest waves, then the shortest per-thread work (ng), then the largest cluster
   Plan best;
   long best_waves = -1;
   for (int cs : {16, 8, 4, 2, 1}) {
     const int rmax = (ny + 1 + cs - 1) / cs;
     if (rmax < 2) continue;
-    const int nodes = rmax * (nx + 1);
-    int cfg = -1;
-    for (int i = 0; i < kNumStepConfigs; ++i) {
-      const int cap = kStepConfigs[i].nthreads * kStepConfigs[i].npt;
-      if (cap < nodes) continue;
-      if (cfg < 0 || cap < kStepConfigs[cfg].nthreads * kStepConfigs[cfg].npt) cfg = i;
-    }
-    if (cfg < 0) continue;
-    Plan p;
-    cudaError_t e = query_stepper_plan(nx, ny, precision, kind, cs, kStepConfigs[cfg].nthreads, kStepConfigs[cfg].npt, &p);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      continue;
-    }
-    if (p.max_active_clusters <= 0) continue;
-    const long waves = (ntasks + p.max_active_clusters - 1) / p.max_active_clusters;
-    if (best_waves < 0 || waves < best_waves) {   // clusters tried from largest: ties keep the larger
-      best = p;
-      best_waves = waves;
+    const int groups = rmax * G;
+    for (int ng : kStepNG) {
+      const int nthreads = ((groups + ng - 1) / ng + 31) / 32 * 32;
+      if (nthreads > kStepMaxThreadsHost) continue;
+      Plan p;
+      cudaError_t e = query_stepper_plan(nx, ny, precision, kind, cs, ng, nthreads, &p);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      if (p.max_active_clusters <= 0) continue;
+      const long waves = (ntasks + p.max_active_clusters - 1) / p.max_active_clusters;
+      if (best_waves < 0 || waves < best_waves || (waves == best_waves && ng < best.ng)) {
+        best = p;
+        best_waves = waves;
+      }
     }
   }
   if (best_waves < 0) {
@@ -130,9 +133,23 @@ void base_params(const ptg_op* op, StepParams& P) {
   P.inner_rtol = op->sv.precision == PTG_FP32_REFINE ? op->sv.inner_rtol : 0.0;
   P.itmax = op->sv.cg_iters_max;
   P.refmax = op->sv.refine_max;
-  P.wA_fine = op->wAf;
-  P.wA_coarse = op->wAc;
-  P.mass = op->mass;
+  P.W = op->W;
+  const size_t PEe = (size_t)(op->g.ny + 2) * op->W + 2 * kSlack;
+  const size_t PN = (size_t)(op->g.ny + 3) * op->W + 2 * kSlack;
+  P.wE_fine = op->wE + kSlack;
+  P.wE_coarse = op->wE + 3 * PEe + kSlack;
+  auto nw = [&](int base) {
+    NodeWeights w;
+    w.C = op->nodew + (base + 0) * PN + kSlack;
+    w.E = op->nodew + (base + 1) * PN + kSlack;
+    w.N = op->nodew + (base + 2) * PN + kSlack;
+    w.NE = op->nodew + (base + 3) * PN + kSlack;
+    w.NW = op->nodew + (base + 4) * PN + kSlack;
+    return w;
+  };
+  P.A_fine = nw(0);
+  P.A_coarse = nw(5);
+  P.mass = nw(10);
   P.dk = op->dk;
   P.dc = op->dc;
   P.fload = op->fload;
@@ -156,7 +173,7 @@ int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream) {
 bool window_covers(int j0, int rows, int lo, int hi) { return lo >= j0 && hi < j0 + rows; }
 
 void free_all(ptg_op* op) {
-  void* ptrs[] = {op->k, op->c, op->dk, op->dc, op->wAf, op->wAc, op->mass, op->fload,
+  void* ptrs[] = {op->k, op->c, op->dk, op->dc, op->wE, op->nodew, op->fload,
                   op->q_elem, op->q_time, op->dirichlet, op->sens_partial, op->stats};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -209,7 +226,9 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
   op->dtau = op->M * time->dt;
   op->p_int = (int)p;
   op->has_dc = mat->c0 != mat->cmin;
-  const size_t PE = (size_t)(grid->ny + 2) * (grid->nx + 2);
+  op->W = padded_width(grid->nx);
+  const size_t PEe = (size_t)(grid->ny + 2) * op->W + 2 * kSlack;
+  const size_t PN = (size_t)(grid->ny + 3) * op->W + 2 * kSlack;
   const int blocks_e = (op->Ne + 255) / 256;
   op->sens_chunks = std::max(1, std::min(64, (4 * 152 + blocks_e - 1) / blocks_e));
   cudaError_t e = cudaSuccess;
@@ -220,9 +239,8 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
   A(&op->c, op->Ne * sizeof(double));
   A(&op->dk, op->Ne * sizeof(double));
   A(&op->dc, op->Ne * sizeof(double));
-  A(&op->wAf, 3 * PE * sizeof(double));
-  A(&op->wAc, 3 * PE * sizeof(double));
-  A(&op->mass, PE * sizeof(double));
+  A(&op->wE, 6 * PEe * sizeof(double));
+  A(&op->nodew, 15 * PN * sizeof(double));
   A(&op->fload, op->Nn * sizeof(double));
   A(&op->q_elem, op->Ne * sizeof(double));
   A(&op->q_time, (time->Nt + 1) * sizeof(double));
@@ -249,6 +267,8 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
   if (e == cudaSuccess) e = cudaMemcpy(op->dirichlet, dirichlet_h, op->Nn, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(op->stats, 0, sizeof(DevStats));
   if (e == cudaSuccess) e = cudaMemset(op->fload, 0, op->Nn * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(op->wE, 0, 6 * PEe * sizeof(double));          // slack stays zero
+  if (e == cudaSuccess) e = cudaMemset(op->nodew, 0, 15 * PN * sizeof(double));
   if (e != cudaSuccess) {
     int rc = cuda_fail(e, "ptg_op_create");
     free_all(op);
@@ -287,7 +307,7 @@ int ptg_op_sizes(const ptg_op* op, int* Nn, int* Ne, int* Nt, int* Ntau, int* M)
   return PTG_OK;
 }
 
-int ptg_op_set_plan(ptg_op* op, int kind, int cs, int nthreads, int npt) {
+int ptg_op_set_plan(ptg_op* op, int kind, int cs, int ng) {
   if (!op || kind < 0 || kind > 5) return PTG_EINVAL;
   DeviceGuard dg(op->device);
   std::lock_guard<std::mutex> lk(op->mu);
@@ -296,19 +316,24 @@ int ptg_op_set_plan(ptg_op* op, int kind, int cs, int nthreads, int npt) {
     return PTG_OK;
   }
   if (cs != 1 && cs != 2 && cs != 4 && cs != 8 && cs != 16) return PTG_EINVAL;
-  if ((op->g.ny + 1 + cs - 1) / cs < 2) return PTG_EINVAL;
+  const int rmax = (op->g.ny + 1 + cs - 1) / cs;
+  if (rmax < 2) return PTG_EINVAL;
+  const int groups = rmax * (op->W / kGroup);
+  if (ng < 1 || ng > kStepNG[kNumStepNG - 1]) return PTG_EINVAL;
+  const int nthreads = ((groups + ng - 1) / ng + 31) / 32 * 32;
+  if (nthreads > kStepMaxThreadsHost) return PTG_EINVAL;
   Plan p;
-  cudaError_t e = query_stepper_plan(op->g.nx, op->g.ny, op->sv.precision, kind, cs, nthreads, npt, &p);
+  cudaError_t e = query_stepper_plan(op->g.nx, op->g.ny, op->sv.precision, kind, cs, ng, nthreads, &p);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return PTG_EINVAL;
   }
-  if (p.max_active_clusters <= 0 || nthreads * npt < p.rmax * (op->g.nx + 1)) return PTG_EINVAL;
+  if (p.max_active_clusters <= 0) return PTG_EINVAL;
   op->plan_override[kind] = p;
   return PTG_OK;
 }
 
-int ptg_op_get_plan(ptg_op* op, int kind, int ntasks, int* cs, int* nthreads, int* npt, int* max_active_clusters) {
+int ptg_op_get_plan(ptg_op* op, int kind, int ntasks, int* cs, int* nthreads, int* ng, int* max_active_clusters) {
   if (!op || kind < 0 || kind > 5 || ntasks < 1) return PTG_EINVAL;
   DeviceGuard dg(op->device);
   Plan p;
@@ -316,7 +341,7 @@ int ptg_op_get_plan(ptg_op* op, int kind, int ntasks, int* cs, int* nthreads, in
   if (rc != PTG_OK) return rc;
   if (cs) *cs = p.cs;
   if (nthreads) *nthreads = p.nthreads;
-  if (npt) *npt = p.npt;
+  if (ng) *ng = p.ng;
   if (max_active_clusters) *max_active_clusters = p.max_active_clusters;
   return PTG_OK;
 }
@@ -325,9 +350,19 @@ int ptg_fe_assemble_operator(ptg_op* op, const double* rho_d, cudaStream_t strea
   if (!op || !rho_d) return PTG_EINVAL;
   DeviceGuard dg(op->device);
   op->last_stream = stream;
+  AssembleOut out;
+  out.k = op->k;
+  out.c = op->c;
+  out.dk = op->dk;
+  out.dc = op->dc;
+  const size_t PEe = (size_t)(op->g.ny + 2) * op->W + 2 * kSlack;
+  const size_t PN = (size_t)(op->g.ny + 3) * op->W + 2 * kSlack;
+  out.wEf = op->wE + kSlack;
+  out.wEc = op->wE + 3 * PEe + kSlack;
+  for (int i = 0; i < 15; ++i) out.node[i] = op->nodew + i * PN + kSlack;
+  out.fload = op->fload;
   PTG_CUDA(launch_assemble(op->g.nx, op->g.ny, op->g.h, op->mat, op->tm.dt, op->dtau, rho_d, op->q_elem,
-                           op->dirichlet, op->k, op->c, op->dk, op->dc, op->wAf, op->wAc, op->mass, op->fload,
-                           op->stats, stream));
+                           op->dirichlet, out, op->stats, stream));
   return PTG_OK;
 }
 
@@ -453,6 +488,11 @@ int ptg_get_stats(ptg_op* op, ptg_stats* out) {
   out->cg_iters = (long long)s.cg_iters;
   out->refinements = (long long)s.refinements;
   out->max_cg_iters = (long long)s.max_cg_iters;
+  for (int k = 0; k < 6; ++k) {
+    out->kind_solves[k] = (long long)s.kind_solves[k];
+    out->kind_cg_iters[k] = (long long)s.kind_cg_iters[k];
+    out->kind_refinements[k] = (long long)s.kind_refinements[k];
+  }
   return PTG_OK;
 }
 

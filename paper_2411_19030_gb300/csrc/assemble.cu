@@ -5,6 +5,10 @@
 
 namespace ptg {
 
+struct NodeOut {
+  double* p[15];
+};
+
 __device__ __forceinline__ void assemble_error(DevStats* st, int code) {
   if (atomicCAS(&st->status, 0, code) == 0) {
     st->fail_kind = 1;
@@ -12,18 +16,18 @@ __device__ __forceinline__ void assemble_error(DevStats* st, int code) {
   }
 }
 
-// a1, Sec. 2.1 Eq. 2.5-2.6 and Sec. 2.2: one thread per element of the zero-padded
-// (ny+2) x (nx+2) element grid.  Interior elements get the SIMP coefficients and the
-// (D, S, T) weights of C/dt + K and C/dtau + K; the padding ring gets zeros.
-__global__ void assemble_kernel(int nx, int ny, double h, ptg_material m, double dt, double dtau,
-                                const double* __restrict__ rho, double* __restrict__ k_out, double* __restrict__ c_out,
-                                double* __restrict__ dk_out, double* __restrict__ dc_out, double* __restrict__ wAf,
-                                double* __restrict__ wAc, double* __restrict__ mass, DevStats* st) {
-  const int EW = nx + 2, PE = (ny + 2) * EW;
+// a1, Sec. 2.1 Eq. 2.5-2.6 and Sec. 2.2: one thread per element of the padded element grid
+// (rows ey = -1..ny, columns ex = -1..W-2, row-major with stride W).  Interior elements get
+// the SIMP coefficients and the (D, S, T) weights of C/dt + K and C/dtau + K; the padding
+// gets zeros.  wEf / wEc each hold three arrays (D, S, T) spaced PE apart.
+__global__ void assemble_elements(int nx, int ny, int W, int PE, double h, ptg_material m, double dt, double dtau,
+                                  const double* __restrict__ rho, double* __restrict__ k_out,
+                                  double* __restrict__ c_out, double* __restrict__ dk_out, double* __restrict__ dc_out,
+                                  double* __restrict__ wEf, double* __restrict__ wEc, DevStats* st) {
   const int pe = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pe >= PE) return;
-  const int ey = pe / EW - 1, ex = pe % EW - 1;
-  double wf[3] = {0.0, 0.0, 0.0}, wc[3] = {0.0, 0.0, 0.0}, mm = 0.0;
+  if (pe >= (ny + 2) * W) return;
+  const int ey = pe / W - 1, ex = pe % W - 1;
+  double wf[3] = {0.0, 0.0, 0.0}, wc[3] = {0.0, 0.0, 0.0};
   if (ey >= 0 && ey < ny && ex >= 0 && ex < nx) {
     const int e = ey * nx + ex;
     double r = rho[e];
@@ -39,7 +43,7 @@ __global__ void assemble_kernel(int nx, int ny, double h, ptg_material m, double
     c_out[e] = cc;
     dk_out[e] = dk;
     dc_out[e] = dc;
-    mm = cc * h * h / 36.0;                // consistent mass: Me = (h^2/36)[4 2 1 2; ...]
+    const double mm = cc * h * h / 36.0;   // consistent mass: Me = (h^2/36)[4 2 1 2; ...]
     // K_e = (k/6)[4 -1 -2 -1; ...]: D = 4k/6, S = -k/6, T = -2k/6
     const double kd = 4.0 * kk / 6.0, ks = -kk / 6.0, kt = -2.0 * kk / 6.0;
     const double mf = mm / dt, mc = mm / dtau;
@@ -50,12 +54,54 @@ __global__ void assemble_kernel(int nx, int ny, double h, ptg_material m, double
     wc[1] = ks + 2.0 * mc;
     wc[2] = kt + mc;
   }
-  mass[pe] = mm;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    wAf[i * PE + pe] = wf[i];
-    wAc[i * PE + pe] = wc[i];
+    wEf[i * PE + pe] = wf[i];
+    wEc[i * PE + pe] = wc[i];
   }
+}
+
+// Per-node FP64 weights of C/dt + K, C/dtau + K and C: one thread per node of the padded node
+// grid (rows iy = -1..ny+1, stride W).  For a node with elements a = (iy-1, ix-1),
+// b = (iy-1, ix), c = (iy, ix-1), d = (iy, ix):
+//   centre = (Da + Db) + (Dc + Dd),  east = Sb + Sd,  north = Sc + Sd,  north-east = Td,
+//   north-west = Tc  (the other four couplings are those of the neighbours).
+// node[0..4]: C/dt + K, node[5..9]: C/dtau + K, node[10..14]: C, each (C, E, N, NE, NW).
+__global__ void assemble_nodes(int nx, int ny, int W, int PE, double h, const double* __restrict__ wEf,
+                               const double* __restrict__ wEc, const double* __restrict__ c_elem,
+                               NodeOut out) {
+  const int pn = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pn >= (ny + 3) * W) return;
+  const int iy = pn / W - 1, ix = pn % W - 1;
+  double v[15];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) v[i] = 0.0;
+  if (iy >= 0 && iy <= ny && ix >= 0 && ix <= nx) {
+    // padded element index of element (ey, ex) is (ey + 1) * W + ex + 1
+    const int ea = iy * W + ix, eb = iy * W + ix + 1, ec = (iy + 1) * W + ix, ed = (iy + 1) * W + ix + 1;
+    const double* wsrc[2] = {wEf, wEc};
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const double* D = wsrc[t];
+      const double* S = wsrc[t] + PE;
+      const double* T = wsrc[t] + 2 * PE;
+      v[5 * t + 0] = (D[ea] + D[eb]) + (D[ec] + D[ed]);
+      v[5 * t + 1] = S[eb] + S[ed];
+      v[5 * t + 2] = S[ec] + S[ed];
+      v[5 * t + 3] = T[ed];
+      v[5 * t + 4] = T[ec];
+    }
+    const double h2 = h * h / 36.0;
+    auto me = [&](int ey, int ex) { return (ey >= 0 && ey < ny && ex >= 0 && ex < nx) ? c_elem[ey * nx + ex] * h2 : 0.0; };
+    const double ma = me(iy - 1, ix - 1), mb = me(iy - 1, ix), mc = me(iy, ix - 1), md = me(iy, ix);
+    v[10] = 4.0 * ((ma + mb) + (mc + md));
+    v[11] = 2.0 * (mb + md);
+    v[12] = 2.0 * (mc + md);
+    v[13] = md;
+    v[14] = mc;
+  }
+#pragma unroll
+  for (int i = 0; i < 15; ++i) out.p[i][pn] = v[i];
 }
 
 // Unit-time load vector f_i = sum_e q_e int N_i = sum over the elements around node i of
@@ -76,14 +122,23 @@ __global__ void load_kernel(int nx, int ny, double h, const double* __restrict__
 }
 
 cudaError_t launch_assemble(int nx, int ny, double h, const ptg_material& m, double dt, double dtau, const double* rho,
-                            const double* q_elem, const uint8_t* dirichlet, double* k, double* c, double* dk, double* dc,
-                            double* wAf, double* wAc, double* mass, double* fload, DevStats* st, cudaStream_t stream) {
-  const int PE = (ny + 2) * (nx + 2);
-  assemble_kernel<<<(PE + 255) / 256, 256, 0, stream>>>(nx, ny, h, m, dt, dtau, rho, k, c, dk, dc, wAf, wAc, mass, st);
+                            const double* q_elem, const uint8_t* dirichlet, const AssembleOut& out, DevStats* st,
+                            cudaStream_t stream) {
+  const int W = padded_width(nx);
+  const int PEe = (ny + 2) * W + 2 * kSlack;        // spacing of the D, S, T element arrays
+  const int ne_pad = (ny + 2) * W;
+  assemble_elements<<<(ne_pad + 255) / 256, 256, 0, stream>>>(nx, ny, W, PEe, h, m, dt, dtau, rho, out.k, out.c, out.dk,
+                                                             out.dc, out.wEf, out.wEc, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  NodeOut no;
+  for (int i = 0; i < 15; ++i) no.p[i] = out.node[i];
+  const int nn_pad = (ny + 3) * W;
+  assemble_nodes<<<(nn_pad + 255) / 256, 256, 0, stream>>>(nx, ny, W, PEe, h, out.wEf, out.wEc, out.c, no);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   const int Nn = (nx + 1) * (ny + 1);
-  load_kernel<<<(Nn + 255) / 256, 256, 0, stream>>>(nx, ny, h, q_elem, dirichlet, fload);
+  load_kernel<<<(Nn + 255) / 256, 256, 0, stream>>>(nx, ny, h, q_elem, dirichlet, out.fload);
   return cudaGetLastError();
 }
 

@@ -26,7 +26,7 @@ static void cluster_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, i
 }
 
 cudaError_t launch_stepper(const StepParams& P, const Plan& plan, int precision, int ntasks, cudaStream_t stream) {
-  StepKernel k = stepper_kernel_for(precision, P.kind, plan.npt, plan.nthreads);
+  StepKernel k = stepper_kernel_for(precision, P.kind, plan.ng);
   if (!k) return cudaErrorInvalidConfiguration;
   cudaError_t e = configure(k, plan.cs, plan.smem);
   if (e != cudaSuccess) return e;
@@ -36,14 +36,14 @@ cudaError_t launch_stepper(const StepParams& P, const Plan& plan, int precision,
   return cudaLaunchKernelEx(&cfg, k, P);
 }
 
-cudaError_t query_stepper_plan(int nx, int ny, int precision, int kind, int cs, int nthreads, int npt, Plan* plan) {
-  StepKernel k = stepper_kernel_for(precision, kind, npt, nthreads);
-  if (!k) return cudaErrorInvalidConfiguration;
+cudaError_t query_stepper_plan(int nx, int ny, int precision, int kind, int cs, int ng, int nthreads, Plan* plan) {
+  StepKernel k = stepper_kernel_for(precision, kind, ng);
+  if (!k || nthreads < 32 || nthreads > kStepMaxThreadsHost || nthreads % 32) return cudaErrorInvalidConfiguration;
   plan->cs = cs;
   plan->nthreads = nthreads;
-  plan->npt = npt;
+  plan->ng = ng;
   plan->rmax = (ny + 1 + cs - 1) / cs;
-  plan->smem = stepper_smem_bytes(nx, plan->rmax, precision == PTG_FP32_REFINE ? 4 : 8, nthreads);
+  plan->smem = stepper_smem_bytes(nx, plan->rmax, precision == PTG_FP32_REFINE ? 4 : 8);
   plan->max_active_clusters = 0;
   if (plan->smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = configure(k, cs, plan->smem);

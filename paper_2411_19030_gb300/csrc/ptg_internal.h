@@ -26,12 +26,37 @@ struct DevStats {
   unsigned long long cg_iters;
   unsigned long long refinements;
   unsigned long long max_cg_iters;
+  unsigned long long kind_solves[6];       // per task kind (Kind)
+  unsigned long long kind_cg_iters[6];
+  unsigned long long kind_refinements[6];
+};
+
+// Padded row layout shared by every grid-shaped array of the stepper (host and device):
+// a row holds columns ix = -1 .. W-2 at offsets ix+1, W = roundup(nx + 3, 4), so rows are
+// 16-byte aligned and split into W/4 aligned groups of 4 nodes; out-of-domain entries are 0.
+// Every such array starts kSlack entries after its base so that a group's neighbours
+// (offsets -1 and +4) are always inside the allocation.
+constexpr int kGroup = 4;
+constexpr int kSlack = 4;
+inline __host__ __device__ int padded_width(int nx) { return ((nx + 3 + kGroup - 1) / kGroup) * kGroup; }
+
+// Per-node FP64 weights of a symmetric 9-point operator (padded node grid, rows iy = -1..ny+1):
+// centre, east, north, north-east and north-west couplings of each node; the west, south,
+// south-west and south-east couplings are the east/north/north-east/north-west weights of the
+// neighbour on the other side.
+struct NodeWeights {
+  const double* C;
+  const double* E;
+  const double* N;
+  const double* NE;
+  const double* NW;
 };
 
 // Everything one stepper launch needs (passed by value in parameter space).
 struct StepParams {
   // problem
   int nx, ny, Nn, Ne, Nt, Ntau, M;
+  int W;                     // padded row width
   int p_int;                 // even integer power-mean exponent
   double h, dt, dtau, p;
   int has_dc;                // capacity depends on rho (dC/drho != 0)
@@ -45,10 +70,12 @@ struct StepParams {
   // solver
   double rtol, inner_rtol;
   int itmax, refmax;
-  // op data (device, FP64)
-  const double* wA_fine;     // [3][(ny+2)(nx+2)] padded (D, S, T) of C/dt + K
-  const double* wA_coarse;   // [3][(ny+2)(nx+2)] padded (D, S, T) of C/dtau + K
-  const double* mass;        // [(ny+2)(nx+2)] padded c_e h^2/36
+  // op data (device, FP64, padded layouts; pointers at the first non-slack entry)
+  const double* wE_fine;     // [3][(ny+2) W] element (D, S, T) weights of C/dt + K
+  const double* wE_coarse;   // [3][(ny+2) W] element (D, S, T) weights of C/dtau + K
+  NodeWeights A_fine;        // per-node weights of C/dt + K
+  NodeWeights A_coarse;      // per-node weights of C/dtau + K
+  NodeWeights mass;          // per-node weights of C
   const double* dk;          // [Ne]
   const double* dc;          // [Ne]
   const double* fload;       // [Nn] unit-time load, zero on Dirichlet nodes
@@ -69,35 +96,42 @@ struct StepParams {
   DevStats* stats;
 };
 
-// Shared-memory footprint (bytes) of one CTA of the stepper for a given plan.
-inline size_t stepper_smem_bytes(int nx, int rmax, int real_bytes, int nthreads) {
-  const size_t W = (size_t)nx + 3, EW = (size_t)nx + 2;
-  const size_t nodes_halo = (size_t)(rmax + 2) * W;
-  const size_t elems = (size_t)(rmax + 1) * EW;
-  const size_t nown_cap = (size_t)rmax * (nx + 1);
+// Shared-memory footprint (bytes) of one CTA of the stepper.
+inline size_t stepper_smem_bytes(int nx, int rmax, int real_bytes) {
+  const size_t W = (size_t)padded_width(nx);
+  const size_t halo = (size_t)(rmax + 2) * W + 2 * kSlack;   // rows -1..R
+  const size_t own = (size_t)rmax * W + 2 * kSlack;          // rows 0..R-1
+  const size_t elems = (size_t)(rmax + 1) * W + 2 * kSlack;  // element rows -1..R-1
   size_t b = 0;
-  b += nodes_halo * sizeof(double);            // x64: FP64 state with halos
-  b += nown_cap * sizeof(double);              // b64: FP64 right-hand side of owned nodes
-  b += nodes_halo * real_bytes;                // zbuf: preconditioned residual with halos
-  b += 3 * elems * real_bytes;                 // (D, S, T) element weights in CG precision
-  b = (b + 15) & ~size_t(15);
-  (void)nthreads;
-  return b;
+  b += halo * sizeof(double);                  // x64: FP64 state with halos
+  b += own * sizeof(double);                   // b64: FP64 right-hand side
+  b += own * sizeof(double);                   // ax64: A x of the last residual evaluation
+  b += halo * real_bytes;                      // zbuf: CG stencil operand with halos
+  b += own * real_bytes;                       // dinv: Jacobi inverse diagonal (0 off the unknowns)
+  if (real_bytes == 4) b += 3 * elems * 4;     // (D, S, T) element weights for the FP32 CG
+  return (b + 15) & ~size_t(15);
 }
 
 // Host entry points of the kernel translation units.
 struct Plan {
-  int cs = 0, nthreads = 0, npt = 0, rmax = 0;
+  int cs = 0, nthreads = 0, ng = 0, rmax = 0;
   size_t smem = 0;
   int max_active_clusters = 0;
 };
 
 cudaError_t launch_stepper(const StepParams& P, const Plan& plan, int precision, int ntasks, cudaStream_t stream);
-cudaError_t query_stepper_plan(int nx, int ny, int precision, int kind, int cs, int nthreads, int npt, Plan* plan);
+cudaError_t query_stepper_plan(int nx, int ny, int precision, int kind, int cs, int ng, int nthreads, Plan* plan);
 
+// Device arrays written by the assembly (see ptg_op in api.cu for their shapes).
+struct AssembleOut {
+  double *k, *c, *dk, *dc;            // [Ne]
+  double *wEf, *wEc;                  // [3][(ny+2) W] element (D, S, T) weights
+  double* node[15];                   // per-node weights: A_fine C,E,N,NE,NW; A_coarse ...; mass ...
+  double* fload;                      // [Nn]
+};
 cudaError_t launch_assemble(int nx, int ny, double h, const ptg_material& m, double dt, double dtau, const double* rho,
-                            const double* q_elem, const uint8_t* dirichlet, double* k, double* c, double* dk, double* dc,
-                            double* wAf, double* wAc, double* mass, double* fload, DevStats* st, cudaStream_t stream);
+                            const double* q_elem, const uint8_t* dirichlet, const AssembleOut& out, DevStats* st,
+                            cudaStream_t stream);
 
 cudaError_t launch_sensitivities(int nx, int ny, int Nt, double h, double dt, int has_dc, const double* dk,
                                  const double* dc, const double* lam, int j0, int j1, const double* T, int hist_j0,

@@ -2,14 +2,16 @@
 //
 // One thread-block cluster owns one independent time-stepping system (one Parareal slice,
 // one coarse step, or the sequential correction sweep).  Its CTAs split the node rows into
-// slabs held on chip (ptg_device.cuh).  Each solve of (C/dt + K) x = b (Eq. 2.7 / 4.4) is a
-// Jacobi-preconditioned CG in precision Real, wrapped in an FP64 residual loop:
-//     r = b - A x            (FP64, from the FP64 element weights)
-//     while ||r|| > rtol ||b||:   CG:  A d = r  (Real),  x += d,  r = b - A x
-// With Real = double the first CG already meets the tolerance (plain FP64 PCG); with
-// Real = float this is iterative refinement with FP64 residuals.  CG uses the recurrence
-// q_{k+1} = A z_{k+1} + beta q_k (q = A p) so each iteration has two cluster reductions and
-// the z halo exchange rides on the second one.
+// slabs held on chip (ptg_device.cuh); each thread owns NG aligned groups of 4 consecutive
+// nodes of a row.  Each solve of (C/dt + K) x = b (Eq. 2.7 / 4.4) is a Jacobi-preconditioned
+// CG in precision Real inside an FP64 residual loop:
+//     r = b - A x            (FP64, per-node FP64 weights: 9 FMAs per node)
+//     while ||r|| > rtol ||b||:   CG on A d = r / ||r||  (Real),  x += ||r|| d,  r = b - A x
+// With Real = double the first CG already meets the tolerance (plain FP64 PCG on the same
+// per-node weights); with Real = float the CG uses FP32 element weights held in shared memory
+// and this is iterative refinement with FP64 residuals.  CG carries q = A p by the recurrence
+// q_{k+1} = A z_{k+1} + beta q_k, so each iteration has two cluster reductions and the halo
+// exchange of z, the only stencil operand, rides on the second one.
 //
 // Task kinds (StepParams::kind), one task per cluster:
 //   FINE_PRI    Alg. 1 repeated M times from u_s (or chained over slices), history written.
@@ -32,7 +34,111 @@ __device__ __forceinline__ void record_error(DevStats* st, int code, int kind, i
   }
 }
 
-template <class Real, int NPT>
+// 6-entry window of a row around a group: w[0] = offset b-1, w[1..4] = b..b+3, w[5] = b+4
+// (b a multiple of 4).  One 16-byte load for the centre in float, two in double.
+template <class T>
+__device__ __forceinline__ void load_window(const T* __restrict__ x, int b, T (&w)[6]) {
+  w[0] = x[b - 1];
+  if constexpr (sizeof(T) == 4) {
+    const float4 c = *reinterpret_cast<const float4*>(x + b);
+    w[1] = c.x; w[2] = c.y; w[3] = c.z; w[4] = c.w;
+  } else {
+    const double2 c0 = *reinterpret_cast<const double2*>(x + b);
+    const double2 c1 = *reinterpret_cast<const double2*>(x + b + 2);
+    w[1] = c0.x; w[2] = c0.y; w[3] = c1.x; w[4] = c1.y;
+  }
+  w[5] = x[b + 4];
+}
+
+// 5-entry window of an element row: e[0] = offset b-1, e[1..4] = b..b+3 (b a multiple of 4).
+__device__ __forceinline__ void load_ewindow(const float* __restrict__ w, int b, float (&e)[5]) {
+  e[0] = w[b - 1];
+  const float4 c = *reinterpret_cast<const float4*>(w + b);
+  e[1] = c.x; e[2] = c.y; e[3] = c.z; e[4] = c.w;
+}
+
+__device__ __forceinline__ void load4(const double* __restrict__ p, double (&v)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+// y = A x for the 4 nodes of a group, FP64 per-node weights (global memory).
+// x: node buffer (rows -1..R); loc0: offset of the group's first node in x;
+// go: offset of the same node in the padded global node arrays; W: row width.
+template <class T>
+__device__ __forceinline__ void stencil_node64(const T* __restrict__ x, int loc0, const NodeWeights& nw, int go, int W,
+                                               double (&y)[4]) {
+  T xl[6], xm[6], xh[6];
+  load_window(x, loc0 - W, xl);
+  load_window(x, loc0, xm);
+  load_window(x, loc0 + W, xh);
+  double C[4], No[4], Nb[4], NEo[4], NWo[4];
+  load4(nw.C + go, C);
+  load4(nw.N + go, No);
+  load4(nw.N + go - W, Nb);
+  load4(nw.NE + go, NEo);
+  load4(nw.NW + go, NWo);
+  double E[5];
+  E[0] = nw.E[go - 1];
+  {
+    double e4[4];
+    load4(nw.E + go, e4);
+    E[1] = e4[0]; E[2] = e4[1]; E[3] = e4[2]; E[4] = e4[3];
+  }
+  const double* neb = nw.NE + go - W - 1;      // NE weights of the row below, shifted left
+  const double* nwb = nw.NW + go - W + 1;      // NW weights of the row below, shifted right
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    double a = C[j] * (double)xm[j + 1];
+    a = fma(E[j + 1], (double)xm[j + 2], a);   // east
+    a = fma(E[j], (double)xm[j], a);           // west  = east weight of the west neighbour
+    a = fma(No[j], (double)xh[j + 1], a);      // north
+    a = fma(Nb[j], (double)xl[j + 1], a);      // south = north weight of the south neighbour
+    a = fma(NEo[j], (double)xh[j + 2], a);     // north-east
+    a = fma(neb[j], (double)xl[j], a);         // south-west = NE weight of the SW neighbour
+    a = fma(NWo[j], (double)xh[j], a);         // north-west
+    a = fma(nwb[j], (double)xl[j + 2], a);     // south-east = NW weight of the SE neighbour
+    y[j] = a;
+  }
+}
+
+// y = A z for the 4 nodes of a group, FP32 element weights (D, S, T) in shared memory.
+// For the node at window position c = j+1: elements a, b below-left / below-right and c, d
+// above-left / above-right, i.e. element windows lower[j], lower[j+1], upper[j], upper[j+1].
+__device__ __forceinline__ void stencil_elem32(const float* __restrict__ z, const float* __restrict__ wd,
+                                               const float* __restrict__ ws, const float* __restrict__ wt, int loc0,
+                                               int W, float (&y)[4]) {
+  float zl[6], zm[6], zh[6];
+  load_window(z, loc0 - W, zl);
+  load_window(z, loc0, zm);
+  load_window(z, loc0 + W, zh);
+  float dl[5], sl[5], tl[5], du[5], su[5], tu[5];
+  const int el = loc0 - W, eu = loc0;   // element windows share the node buffers' row offsets
+  load_ewindow(wd, el, dl);
+  load_ewindow(ws, el, sl);
+  load_ewindow(wt, el, tl);
+  load_ewindow(wd, eu, du);
+  load_ewindow(ws, eu, su);
+  load_ewindow(wt, eu, tu);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float Da = dl[j], Db = dl[j + 1], Dc = du[j], Dd = du[j + 1];
+    const float Sa = sl[j], Sb = sl[j + 1], Sc = su[j], Sd = su[j + 1];
+    float a = ((Da + Db) + (Dc + Dd)) * zm[j + 1];
+    a = fmaf(Sa + Sc, zm[j], a);           // west:  shared by a, c
+    a = fmaf(Sb + Sd, zm[j + 2], a);       // east:  shared by b, d
+    a = fmaf(Sa + Sb, zl[j + 1], a);       // south: shared by a, b
+    a = fmaf(Sc + Sd, zh[j + 1], a);       // north: shared by c, d
+    a = fmaf(tl[j], zl[j], a);             // south-west corner of a
+    a = fmaf(tl[j + 1], zl[j + 2], a);     // south-east corner of b
+    a = fmaf(tu[j], zh[j], a);             // north-west corner of c
+    a = fmaf(tu[j + 1], zh[j + 2], a);     // north-east corner of d
+    y[j] = a;
+  }
+}
+
+template <class Real, int NG>
 struct Stepper {
   static constexpr bool kMixed = std::is_same<Real, float>::value;
 
@@ -41,24 +147,22 @@ struct Stepper {
   RedSmem& rs;
   Slab sb;
   int phase = 0;
-  // shared memory
-  double* x64;      // FP64 state, own rows + halos
-  double* b64;      // FP64 right-hand side, owned nodes (linear index)
-  Real* zbuf;       // CG operand with halos
-  Real* wd;         // element weights in CG precision
-  Real* ws;
-  Real* wt;
-  // per-thread node slots: node i = threadIdx.x + k*blockDim.x of the slab
-  int lrow[NPT];
-  Real invd[NPT];
-  unsigned freemask = 0;
-  // current operator (FP64 element weights in global memory, offset to this slab)
-  const double* gwd = nullptr;
-  const double* gws = nullptr;
-  const double* gwt = nullptr;
+  // shared memory (each pointer at the first non-slack entry)
+  double* x64;      // FP64 state, rows -1..R
+  double* b64;      // FP64 right-hand side, rows 0..R-1
+  Real* zbuf;       // CG stencil operand, rows -1..R
+  Real* dinv;       // Jacobi inverse diagonal, rows 0..R-1 (0 on Dirichlet and pad nodes)
+  float* wd;        // FP32 element weights (D, S, T), element rows r0-1..r0+R-1 (FP32 CG only)
+  float* ws;
+  float* wt;
+  // per-thread groups: loc0[k] = offset of the group's first node in the halo buffers, -1 if none
+  int loc0[NG];
+  NodeWeights A;    // per-node FP64 weights of the current operator
   double step_dt = 0.0;
-  // per-solve counters (meaningful in thread 0)
-  long long it_total = 0;
+  double inv_dt = 0.0;
+  int gshift = 0;   // offset from a halo-buffer node to the same node of the global padded arrays
+  double* ax64;     // A x64 from the last residual evaluation, rows 0..R-1 (reused by the next step)
+  bool ax_valid = false;
 
   __device__ Stepper(const StepParams& P_, cg::cluster_group& cl, RedSmem& rs_, unsigned char* dyn)
       : P(P_), cluster(cl), rs(rs_) {
@@ -67,85 +171,103 @@ struct Stepper {
     sb.cs = P.cs;
     sb.rank = (int)cluster.block_rank();
     slab_rows(P.ny + 1, P.cs, sb.rank, sb.r0, sb.R);
-    sb.W = P.nx + 3;
-    sb.EW = P.nx + 2;
-    sb.nown = sb.R * (P.nx + 1);
-    const int nodes_halo = (P.rmax + 2) * sb.W;
-    const int elems = (P.rmax + 1) * sb.EW;
-    x64 = reinterpret_cast<double*>(dyn);
-    b64 = x64 + nodes_halo;
-    zbuf = reinterpret_cast<Real*>(b64 + P.rmax * (P.nx + 1));
-    wd = zbuf + nodes_halo;
-    ws = wd + elems;
-    wt = ws + elems;
-    // zero every buffer: pads, halos outside the domain and unused rows stay zero
-    for (int i = threadIdx.x; i < nodes_halo; i += blockDim.x) {
-      x64[i] = 0.0;
-      zbuf[i] = Real(0);
+    sb.W = P.W;
+    sb.G = P.W / kGroup;
+    sb.ngroups = sb.R * sb.G;
+    const int W = sb.W;
+    const int halo = (P.rmax + 2) * W + 2 * kSlack;
+    const int own = P.rmax * W + 2 * kSlack;
+    const int elems = (P.rmax + 1) * W + 2 * kSlack;
+    unsigned char* p = dyn;
+    double* x64b = reinterpret_cast<double*>(p);  p += sizeof(double) * halo;
+    double* b64b = reinterpret_cast<double*>(p);  p += sizeof(double) * own;
+    double* axb = reinterpret_cast<double*>(p);   p += sizeof(double) * own;
+    Real* zb = reinterpret_cast<Real*>(p);        p += sizeof(Real) * halo;
+    Real* db = reinterpret_cast<Real*>(p);        p += sizeof(Real) * own;
+    float* eb = reinterpret_cast<float*>(p);
+    for (int i = threadIdx.x; i < halo; i += blockDim.x) {
+      x64b[i] = 0.0;
+      zb[i] = Real(0);
     }
-    for (int i = threadIdx.x; i < P.rmax * (P.nx + 1); i += blockDim.x) b64[i] = 0.0;
-    for (int i = threadIdx.x; i < elems; i += blockDim.x) {
-      wd[i] = Real(0);
-      ws[i] = Real(0);
-      wt[i] = Real(0);
+    for (int i = threadIdx.x; i < own; i += blockDim.x) {
+      b64b[i] = 0.0;
+      axb[i] = 0.0;
+      db[i] = Real(0);
     }
+    if constexpr (kMixed) {
+      for (int i = threadIdx.x; i < 3 * elems; i += blockDim.x) eb[i] = 0.f;
+    }
+    x64 = x64b + kSlack;
+    b64 = b64b + kSlack - W;   // b64[loc] for loc in own rows (loc >= W)
+    ax64 = axb + kSlack - W;
+    zbuf = zb + kSlack;
+    dinv = db + kSlack - W;    // dinv[loc] likewise
+    wd = eb + kSlack;
+    ws = eb + elems + kSlack;
+    wt = eb + 2 * elems + kSlack;
 #pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-      const int i = threadIdx.x + k * blockDim.x;
-      lrow[k] = i < sb.nown ? i / (P.nx + 1) : 0;
-      if (i < sb.nown && P.dirichlet[sb.r0 * (P.nx + 1) + i] == 0) freemask |= 1u << k;
-      invd[k] = Real(0);
-    }
-  }
-
-  __device__ __forceinline__ bool own(int k, int& i) const {
-    i = threadIdx.x + k * blockDim.x;
-    return i < sb.nown;
-  }
-  __device__ __forceinline__ bool is_free(int k) const { return (freemask >> k) & 1u; }
-  __device__ __forceinline__ int loc_of(int k, int i) const { return i + 2 * lrow[k] + sb.W + 1; }
-  __device__ __forceinline__ int eloc_of(int k, int i) const { return i + lrow[k] + sb.EW + 1; }
-  __device__ __forceinline__ int gnode(int i) const { return sb.r0 * (P.nx + 1) + i; }
-
-  template <int NV>
-  __device__ __forceinline__ void allreduce(double (&v)[NV]) {
-    cluster_allreduce<NV>(v, rs, phase, cluster, sb.cs);
-  }
-
-  // Select the operator C/dt + K (fine) or C/dtau + K (coarse): copy its element weights
-  // for this slab into shared memory in CG precision and form the Jacobi inverse diagonal.
-  __device__ void set_operator(bool coarse) {
-    const int PE = (P.ny + 2) * (P.nx + 2);
-    const double* wA = coarse ? P.wA_coarse : P.wA_fine;
-    step_dt = coarse ? P.dtau : P.dt;
-    const int off = sb.r0 * sb.EW;  // padded element row r0 holds element row r0 - 1
-    gwd = wA + off;
-    gws = wA + PE + off;
-    gwt = wA + 2 * PE + off;
-    const int n = (sb.R + 1) * sb.EW;
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      wd[i] = (Real)gwd[i];
-      ws[i] = (Real)gws[i];
-      wt[i] = (Real)gwt[i];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-      int i;
-      if (own(k, i) && is_free(k)) {
-        const int e = eloc_of(k, i);
-        const Real dg = (wd[e - sb.EW - 1] + wd[e - sb.EW]) + (wd[e - 1] + wd[e]);
-        invd[k] = Real(1) / dg;
-      } else {
-        invd[k] = Real(0);
+    for (int k = 0; k < NG; ++k) {
+      const int gi = threadIdx.x + k * blockDim.x;
+      loc0[k] = -1;
+      if (gi < sb.ngroups) {
+        const int lr = gi / sb.G, g = gi - lr * sb.G;
+        loc0[k] = (lr + 1) * W + kGroup * g;
       }
     }
+    gshift = sb.r0 * W;
+  }
+
+  // global node index of node j of a group, or -1 for a pad node
+  __device__ __forceinline__ int gnode(int l0, int j) const {
+    const int lr = l0 / sb.W - 1;
+    const int ix = (l0 - (lr + 1) * sb.W) + j - 1;
+    return (ix >= 0 && ix <= P.nx) ? (sb.r0 + lr) * (P.nx + 1) + ix : -1;
+  }
+
+  template <class T, int NV, int NX = 0, class Post = NoPost>
+  __device__ __forceinline__ void allreduce(T (&v)[NV + NX], Post post = Post()) {
+    cluster_allreduce<T, NV, NX, Post>(v, rs, phase, cluster, sb.cs, post);
+  }
+
+  // Select the operator C/dt + K (fine) or C/dtau + K (coarse): per-node FP64 weights for the
+  // residual (and the FP64 CG), FP32 element weights in shared memory for the FP32 CG, and
+  // the Jacobi inverse diagonal (zero on Dirichlet and pad nodes).
+  __device__ void set_operator(bool coarse) {
+    A = coarse ? P.A_coarse : P.A_fine;
+    step_dt = coarse ? P.dtau : P.dt;
+    inv_dt = 1.0 / step_dt;
+    ax_valid = false;
+    const int W = sb.W;
+    __syncthreads();
+    if constexpr (kMixed) {
+      const double* wE = coarse ? P.wE_coarse : P.wE_fine;
+      const int PE = (P.ny + 2) * W + 2 * kSlack;      // one element array incl. slack
+      const int n = (sb.R + 1) * W;
+      const double* src = wE + sb.r0 * W;               // padded element row r0 = element row r0 - 1
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        wd[i] = (float)src[i];
+        ws[i] = (float)src[PE + i];
+        wt[i] = (float)src[2 * PE + i];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+      if (l0 < 0) continue;
+      for (int j = 0; j < kGroup; ++j) {
+        const int g = gnode(l0, j);
+        Real v = Real(0);
+        if (g >= 0 && P.dirichlet[g] == 0) v = Real(1) / (Real)A.C[l0 + gshift + j];
+        dinv[l0 + j] = v;
+      }
+    }
+    __syncthreads();
   }
 
   // Load a node vector from global memory into x64: owned rows and both halo rows
   // (Dirichlet nodes forced to zero).  Ends with __syncthreads.
   __device__ void load_x64(const double* __restrict__ src) {
+    ax_valid = false;
     __syncthreads();
     const int nn = P.nx + 1;
     const int rows = sb.R + 2;
@@ -161,176 +283,237 @@ struct Stepper {
   }
 
   __device__ void zero_x64() {
+    ax_valid = false;
     __syncthreads();
     for (int i = threadIdx.x; i < (P.rmax + 2) * sb.W; i += blockDim.x) x64[i] = 0.0;
     __syncthreads();
   }
 
-  // Store the owned rows of x64 to a global node vector.
+  // Store the owned nodes of x64 to a global node vector.
   __device__ void store_x64(double* __restrict__ dst) const {
 #pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-      int i;
-      if (own(k, i)) dst[gnode(i)] = x64[loc_of(k, i)];
-    }
-  }
-
-  // Refresh every CTA's halo rows of x64 from the neighbours' owned rows.
-  __device__ void exchange_x64() {
-    __syncthreads();
-    push_halos(x64, sb, cluster);
-    cluster_sync_all();
-  }
-
-  // b64 = (C/dt) x64 + src, with src supplied per owned node by the functor.
-  template <class Src>
-  __device__ void build_rhs(Src src) {
-    const double inv_dt = 1.0 / step_dt;
-    const double* gm = P.mass + sb.r0 * sb.EW;
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+      if (l0 < 0) continue;
 #pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-      int i;
-      if (own(k, i)) {
-        double b = 0.0;
-        if (is_free(k)) b = mass9(x64, gm, loc_of(k, i), eloc_of(k, i), sb.W, sb.EW) * inv_dt + src(gnode(i));
-        b64[i] = b;
+      for (int j = 0; j < kGroup; ++j) {
+        const int g = gnode(l0, j);
+        if (g >= 0) dst[g] = x64[l0 + j];
       }
     }
   }
 
-  // r = b - A x64 on owned free nodes (FP64).
-  __device__ __forceinline__ double residual(int k, int i) const {
-    double ax;
-    if constexpr (kMixed) {
-      ax = stencil9<double, double>(x64, gwd, gws, gwt, loc_of(k, i), eloc_of(k, i), sb.W, sb.EW);
-    } else {
-      ax = stencil9<double, Real>(x64, wd, ws, wt, loc_of(k, i), eloc_of(k, i), sb.W, sb.EW);
+  // Refresh every CTA's halo rows of a buffer from the neighbours' owned rows.
+  template <class T>
+  __device__ void exchange(T* buf) {
+    __syncthreads();
+    push_halos(buf, sb, cluster);
+    cluster_sync_all();
+  }
+  __device__ void exchange_x64() { exchange(x64); }
+
+  // b64 = (C/dt) x64 + src, with src(global node) supplied per owned free node.
+  template <class Src>
+  __device__ void build_rhs(Src src) {
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+      if (l0 < 0) continue;
+      double y[4];
+      stencil_node64<double>(x64, l0, P.mass, l0 + gshift, sb.W, y);
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) {
+        const bool free_node = dinv[l0 + j] != Real(0);
+        b64[l0 + j] = free_node ? fma(y[j], inv_dt, src(gnode(l0, j))) : 0.0;
+      }
     }
-    return b64[i] - ax;
   }
 
-  // CG in precision Real on A d = r (r given per slot), d accumulated into x64.
-  // Returns the iteration count.  Target: ||r_k||^2 <= target2.
-  __device__ int cg_correct(Real (&r)[NPT], double rr0, double target2) {
-    Real d[NPT], p[NPT], q[NPT];
-    double rz;
-    {
-      double v[2] = {0.0, 0.0};
+  // r64 = b - A x64 on the owned groups (0 off the unknowns); returns the local sum of r^2.
+  __device__ __forceinline__ double residual(double (&r64)[NG][4]) const {
+    double rr = 0.0;
 #pragma unroll
-      for (int k = 0; k < NPT; ++k) {
-        int i;
-        d[k] = Real(0);
-        p[k] = Real(0);
-        q[k] = Real(0);
-        if (own(k, i)) {
-          const Real z = invd[k] * r[k];
-          zbuf[loc_of(k, i)] = z;
-          v[0] += (double)(r[k] * z);
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) r64[k][j] = 0.0;
+      if (l0 < 0) continue;
+      double y[4];
+      stencil_node64<double>(x64, l0, A, l0 + gshift, sb.W, y);
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) {
+        ax64[l0 + j] = y[j];
+        if (dinv[l0 + j] != Real(0)) {
+          r64[k][j] = b64[l0 + j] - y[j];
+          rr = fma(r64[k][j], r64[k][j], rr);
+        }
+      }
+    }
+    return rr;
+  }
+
+  // r64 = b - (A x64 saved by the last residual evaluation); valid while x64 is unchanged.
+  __device__ __forceinline__ double residual_saved(double (&r64)[NG][4]) const {
+    double rr = 0.0;
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) r64[k][j] = 0.0;
+      if (l0 < 0) continue;
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) {
+        if (dinv[l0 + j] != Real(0)) {
+          r64[k][j] = b64[l0 + j] - ax64[l0 + j];
+          rr = fma(r64[k][j], r64[k][j], rr);
+        }
+      }
+    }
+    return rr;
+  }
+
+  __device__ __forceinline__ void apply_A(const Real* z, int l0, Real (&w)[4]) const {
+    if constexpr (kMixed) {
+      stencil_elem32(z, wd, ws, wt, l0, sb.W, w);
+    } else {
+      double y[4];
+      stencil_node64<double>(z, l0, A, l0 + gshift, sb.W, y);
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) w[j] = y[j];
+    }
+  }
+
+  // Jacobi-preconditioned CG in precision Real on A d = r, where r (given per node) is the FP64
+  // residual scaled to unit 2-norm; on return x64 += unscale * d.  Stops when ||r||^2 <= target2
+  // (scaled units) or at the iteration limit; returns the iteration count.  All CG scalars and
+  // dot products are in precision Real.
+  __device__ int cg_correct(Real (&r)[NG][4], Real target2, double unscale) {
+    Real d[NG][4], p[NG][4], q[NG][4];
+    Real rz;
+    {
+      Real v[1] = {Real(0)};
+#pragma unroll
+      for (int k = 0; k < NG; ++k) {
+        const int l0 = loc0[k];
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j) { d[k][j] = Real(0); p[k][j] = Real(0); q[k][j] = Real(0); }
+        if (l0 < 0) continue;
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j) {
+          const Real z = dinv[l0 + j] * r[k][j];
+          zbuf[l0 + j] = z;
+          v[0] = fma(r[k][j], z, v[0]);
         }
       }
       __syncthreads();
       push_halos(zbuf, sb, cluster);
-      double w[1] = {v[0]};
-      allreduce<1>(w);
-      rz = w[0];
+      allreduce<Real, 1>(v);
+      rz = v[0];
     }
     int it = 0;
     Real beta = Real(0);
-    bool done = !(rr0 > target2);
+    bool done = !(Real(1) > target2);
     while (!done && it < P.itmax) {
-      // q = A z + beta q, p = z + beta p, (p, q)
-      double pq[1] = {0.0};
+      // q = A z + beta q, p = z + beta p, (p, q); alpha = rz / (p, q)
+      Real pq[1] = {Real(0)};
 #pragma unroll
-      for (int k = 0; k < NPT; ++k) {
-        int i;
-        if (own(k, i)) {
-          const int loc = loc_of(k, i);
-          Real w = stencil9<Real, Real>(zbuf, wd, ws, wt, loc, eloc_of(k, i), sb.W, sb.EW);
-          if (!is_free(k)) w = Real(0);
-          const Real z = zbuf[loc];
-          p[k] = fma(beta, p[k], z);
-          q[k] = fma(beta, q[k], w);
-          pq[0] += (double)(p[k] * q[k]);
+      for (int k = 0; k < NG; ++k) {
+        const int l0 = loc0[k];
+        if (l0 < 0) continue;
+        Real w[4];
+        apply_A(zbuf, l0, w);
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j) {
+          const Real di = dinv[l0 + j];
+          const Real wj = di != Real(0) ? w[j] : Real(0);
+          const Real z = zbuf[l0 + j];
+          p[k][j] = fma(beta, p[k][j], z);
+          q[k][j] = fma(beta, q[k][j], wj);
+          pq[0] = fma(p[k][j], q[k][j], pq[0]);
         }
       }
-      allreduce<1>(pq);
-      const Real alpha = (Real)(rz / pq[0]);
-      double v[2] = {0.0, 0.0};
+      const Real rz_c = rz;
+      allreduce<Real, 1>(pq, [rz_c](Real* t) { t[0] = rz_c / t[0]; });
+      const Real alpha = pq[0];
+      // d += alpha p, r -= alpha q, z = D^-1 r; (r, z), (r, r) and beta = (r, z)_new / (r, z)
+      Real v[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
-      for (int k = 0; k < NPT; ++k) {
-        int i;
-        if (own(k, i)) {
-          d[k] = fma(alpha, p[k], d[k]);
-          r[k] = fma(-alpha, q[k], r[k]);
-          const Real z = invd[k] * r[k];
-          zbuf[loc_of(k, i)] = z;
-          v[0] += (double)(r[k] * z);
-          v[1] += (double)(r[k] * r[k]);
+      for (int k = 0; k < NG; ++k) {
+        const int l0 = loc0[k];
+        if (l0 < 0) continue;
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j) {
+          d[k][j] = fma(alpha, p[k][j], d[k][j]);
+          r[k][j] = fma(-alpha, q[k][j], r[k][j]);
+          const Real z = dinv[l0 + j] * r[k][j];
+          zbuf[l0 + j] = z;
+          v[0] = fma(r[k][j], z, v[0]);
+          v[1] = fma(r[k][j], r[k][j], v[1]);
         }
       }
       __syncthreads();
       push_halos(zbuf, sb, cluster);
-      allreduce<2>(v);
+      allreduce<Real, 2, 1>(v, [rz_c](Real* t) { t[2] = t[0] / rz_c; });
       ++it;
       if (!(v[1] > target2)) done = true;  // NaN keeps iterating until the limit
-      beta = (Real)(v[0] / rz);
+      beta = v[2];
       rz = v[0];
     }
-    // x64 += d on owned nodes
 #pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-      int i;
-      if (own(k, i)) x64[loc_of(k, i)] += (double)d[k];
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+      if (l0 < 0) continue;
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) x64[l0 + j] = fma((double)d[k][j], unscale, x64[l0 + j]);
     }
     return it;
   }
 
   // Solve (C/dt + K) x = b64 with x64 (owned + halos) as initial guess; on return x64 holds
   // the solution with valid halos in every CTA.  `step` is the fine index for error reports.
-  __device__ void solve(int step) {
+  // `reuse_ax`: x64 is the previous solution of the same operator, so the A x64 saved by that
+  // solve's final residual check gives the first residual without another stencil.
+  __device__ void solve(int step, bool reuse_ax = false) {
+    double r64[NG][4];
     double bb_rr[2] = {0.0, 0.0};
-    Real r[NPT];
-    double r64[NPT];
+    bb_rr[1] = (reuse_ax && ax_valid) ? residual_saved(r64) : residual(r64);
 #pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-      int i;
-      r64[k] = 0.0;
-      if (own(k, i) && is_free(k)) {
-        r64[k] = residual(k, i);
-        bb_rr[0] += b64[i] * b64[i];
-        bb_rr[1] += r64[k] * r64[k];
-      }
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+      if (l0 < 0) continue;
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) bb_rr[0] = fma(b64[l0 + j], b64[l0 + j], bb_rr[0]);
     }
-    allreduce<2>(bb_rr);
+    allreduce<double, 2>(bb_rr);
     const double bb = bb_rr[0];
     double rr = bb_rr[1];
     const double tol2 = P.rtol * P.rtol * bb;
     int sweeps = 0, its = 0;
     while (rr > tol2 && sweeps < P.refmax) {
+      // scale the residual to unit norm so the Real-precision CG works on O(1) values
+      const double nrm = sqrt(rr), scale = 1.0 / nrm;
+      Real r[NG][4];
 #pragma unroll
-      for (int k = 0; k < NPT; ++k) r[k] = (Real)r64[k];
-      const double target2 = fmax(P.inner_rtol * P.inner_rtol * rr, 0.25 * tol2);
-      its += cg_correct(r, rr, target2);
+      for (int k = 0; k < NG; ++k)
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j) r[k][j] = (Real)(r64[k][j] * scale);
+      const Real target2 = (Real)fmax(P.inner_rtol * P.inner_rtol, 0.25 * tol2 / rr);
+      its += cg_correct(r, target2, nrm);
       ++sweeps;
       exchange_x64();
-      double v[1] = {0.0};
-#pragma unroll
-      for (int k = 0; k < NPT; ++k) {
-        int i;
-        r64[k] = 0.0;
-        if (own(k, i) && is_free(k)) {
-          r64[k] = residual(k, i);
-          v[0] += r64[k] * r64[k];
-        }
-      }
-      allreduce<1>(v);
+      double v[1] = {residual(r64)};
+      allreduce<double, 1>(v);
       rr = v[0];
     }
+    ax_valid = true;
     if (threadIdx.x == 0 && sb.rank == 0) {
       atomicAdd(&P.stats->solves, 1ull);
       atomicAdd(&P.stats->cg_iters, (unsigned long long)its);
       atomicAdd(&P.stats->refinements, (unsigned long long)sweeps);
       atomicMax(&P.stats->max_cg_iters, (unsigned long long)its);
+      atomicAdd(&P.stats->kind_solves[P.kind], 1ull);
+      atomicAdd(&P.stats->kind_cg_iters[P.kind], (unsigned long long)its);
+      atomicAdd(&P.stats->kind_refinements[P.kind], (unsigned long long)sweeps);
       if (!(rr == rr) || !(bb == bb) || isinf(rr)) {
         record_error(P.stats, PTG_ENONFINITE, P.kind, step);
       } else if (rr > tol2) {
@@ -343,16 +526,20 @@ struct Stepper {
   __device__ double pnorm_p() {
     double v[1] = {0.0};
 #pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-      int i;
-      if (own(k, i) && is_free(k)) v[0] += ipow(x64[loc_of(k, i)], P.p_int);
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+      if (l0 < 0) continue;
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j)
+        if (dinv[l0 + j] != Real(0)) v[0] += ipow(x64[l0 + j], P.p_int);
     }
-    allreduce<1>(v);
+    allreduce<double, 1>(v);
     return v[0];
   }
 
   // Element term of Eq. 4.7 for the owned elements:
-  //   g[e] -= (1/nnorm) * ( dk_e lambda_e^T Ke T_j,e + dc_e/dt lambda_e^T Me (T_j - T_jm)_e )
+  //   g[e] = gsrc[e] - (1/nnorm) * ( dk_e lambda_e^T Ke T_j,e + dc_e/dt lambda_e^T Me (T_j - T_jm)_e )
+  //          (+ addF[e] - subG[e] when given)
   // lambda is x64 (valid halos), T_j / T_jm are full global node vectors.
   __device__ void accumulate_g(const double* __restrict__ Tj, const double* __restrict__ Tjm, double dt_step,
                                double nnorm, const double* __restrict__ gsrc, double* __restrict__ gdst,
@@ -365,7 +552,7 @@ struct Stepper {
       const int ler = t / nx, ex = t - ler * nx;
       const int ey = sb.r0 + ler;
       const int e = ey * nx + ex;
-      const int l0 = (ler + 1) * sb.W + ex + 1;   // SW in x64
+      const int l0 = (ler + 1) * sb.W + ex + 1;   // SW node in x64
       const double lsw = x64[l0], lse = x64[l0 + 1], lne = x64[l0 + sb.W + 1], lnw = x64[l0 + sb.W];
       const int g0 = ey * nn + ex;
       const double tsw = Tj[g0], tse = Tj[g0 + 1], tne = Tj[g0 + nn + 1], tnw = Tj[g0 + nn];
@@ -398,6 +585,26 @@ struct Stepper {
     return P.hist + (size_t)r * P.Nn;
   }
 
+  // correction x64 = x64 + F - G on the owned nodes, written to X (and Y if given)
+  __device__ void apply_correction(const double* __restrict__ Fs, const double* __restrict__ Gs, double* __restrict__ X,
+                                   double* __restrict__ Y) {
+    ax_valid = false;
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+      if (l0 < 0) continue;
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) {
+        const int g = gnode(l0, j);
+        if (g < 0) continue;
+        const double t = dinv[l0 + j] != Real(0) ? (x64[l0 + j] + Fs[g]) - Gs[g] : 0.0;
+        x64[l0 + j] = t;
+        X[g] = t;
+        if (Y) Y[g] = t;
+      }
+    }
+  }
+
   // ------------------------------------------------------------------ task bodies
   __device__ void fine_primal(int task) {
     const int sa = P.chained ? P.s0 : P.s0 + task;
@@ -414,9 +621,9 @@ struct Stepper {
       for (int j = M * s + 1; j <= M * (s + 1); ++j) {
         const double qj = P.q_time[j];
         build_rhs([&](int g) { return qj * P.fload[g]; });
-        solve(j);
+        solve(j, true);
         const double sp = pnorm_p();
-        theta = pow(ipow(theta, P.p_int) + sp * inv_norm, 1.0 / P.p);
+        if (threadIdx.x == 0) theta = pow(ipow(theta, P.p_int) + sp * inv_norm, 1.0 / P.p);  // used by thread 0 only
         if (double* row = hist_row(j)) store_x64(row);
       }
       store_x64(P.out_field + (size_t)s * P.Nn);
@@ -434,9 +641,9 @@ struct Stepper {
     build_rhs([&](int g) { return qj * P.fload[g]; });
     solve(j);
     const double sp = pnorm_p();
-    const double theta = pow(ipow(theta0, P.p_int) + sp / ((double)P.Ntau * (double)P.Ne), 1.0 / P.p);
     store_x64(P.out_field + (size_t)s * P.Nn);
-    if (threadIdx.x == 0 && sb.rank == 0) P.out_aux[s] = theta;
+    if (threadIdx.x == 0 && sb.rank == 0)
+      P.out_aux[s] = pow(ipow(theta0, P.p_int) + sp / ((double)P.Ntau * (double)P.Ne), 1.0 / P.p);
   }
 
   __device__ void correct_primal() {
@@ -451,25 +658,13 @@ struct Stepper {
       load_x64(P.G_field + (size_t)s * P.Nn);   // initial guess G(u_s^old)
       solve(j);
       const double sp = pnorm_p();
-      const double theta_g = pow(ipow(theta, P.p_int) + sp / ((double)P.Ntau * (double)P.Ne), 1.0 / P.p);
-      const double* Fs = P.F_field + (size_t)s * P.Nn;
-      const double* Gs = P.G_field + (size_t)s * P.Nn;
-      double* Xn = P.out_field + (size_t)(s + 1) * P.Nn;
-      double* hrow = hist_row(j);
-#pragma unroll
-      for (int k = 0; k < NPT; ++k) {
-        int i;
-        if (own(k, i)) {
-          const int g = gnode(i);
-          const int loc = loc_of(k, i);
-          const double t = is_free(k) ? (x64[loc] + Fs[g]) - Gs[g] : 0.0;
-          x64[loc] = t;
-          Xn[g] = t;
-          if (hrow) hrow[g] = t;
-        }
+      apply_correction(P.F_field + (size_t)s * P.Nn, P.G_field + (size_t)s * P.Nn,
+                       P.out_field + (size_t)(s + 1) * P.Nn, hist_row(j));
+      if (threadIdx.x == 0) {                    // theta is needed by thread 0 only
+        const double theta_g = pow(ipow(theta, P.p_int) + sp / ((double)P.Ntau * (double)P.Ne), 1.0 / P.p);
+        theta = (theta_g + P.F_aux[s]) - P.G_aux[s];
+        if (sb.rank == 0) P.out_aux[s + 1] = theta;
       }
-      theta = (theta_g + P.F_aux[s]) - P.G_aux[s];
-      if (threadIdx.x == 0 && sb.rank == 0) P.out_aux[s + 1] = theta;
       exchange_x64();
     }
   }
@@ -493,7 +688,7 @@ struct Stepper {
           return;
         }
         build_rhs([&](int g) { return scale * ipow(Tj[g], P.p_int - 1); });
-        solve(j);
+        solve(j, true);
         accumulate_g(Tj, Tjm, P.dt, (double)P.Nt, gsrc, gdst, nullptr, nullptr);
         gsrc = gdst;
         __syncthreads();
@@ -527,9 +722,13 @@ struct Stepper {
     {
       double* Xl = P.out_field + (size_t)P.Ntau * P.Nn;
 #pragma unroll
-      for (int k = 0; k < NPT; ++k) {
-        int i;
-        if (own(k, i)) Xl[gnode(i)] = 0.0;
+      for (int k = 0; k < NG; ++k) {
+        const int l0 = loc0[k];
+        if (l0 < 0) continue;
+        for (int j = 0; j < kGroup; ++j) {
+          const int g = gnode(l0, j);
+          if (g >= 0) Xl[g] = 0.0;
+        }
       }
       const int er = min(sb.R, P.ny - sb.r0);
       double* Xg = P.out_aux + (size_t)P.Ntau * P.Ne;
@@ -548,34 +747,24 @@ struct Stepper {
       accumulate_g(Tk, Tkm, P.dtau, (double)P.Ntau, P.out_aux + (size_t)(s + 1) * P.Ne, P.out_aux + (size_t)s * P.Ne,
                    P.F_aux + (size_t)s * P.Ne, P.G_aux + (size_t)s * P.Ne);
       cluster_sync_all();                       // every CTA is done reading lambda_G halos
-      const double* Fs = P.F_field + (size_t)s * P.Nn;
-      const double* Gs = P.G_field + (size_t)s * P.Nn;
-      double* Xn = P.out_field + (size_t)s * P.Nn;
-#pragma unroll
-      for (int k = 0; k < NPT; ++k) {
-        int i;
-        if (own(k, i)) {
-          const int g = gnode(i);
-          const int loc = loc_of(k, i);
-          const double t = is_free(k) ? (x64[loc] + Fs[g]) - Gs[g] : 0.0;
-          x64[loc] = t;
-          Xn[g] = t;
-        }
-      }
+      apply_correction(P.F_field + (size_t)s * P.Nn, P.G_field + (size_t)s * P.Nn, P.out_field + (size_t)s * P.Nn,
+                       nullptr);
       exchange_x64();
     }
   }
 };
 
-// One kernel per (precision, slots per thread, threads per CTA, task kind): each kernel
-// inlines a single task body, which keeps register pressure and compile time down.
-// MINB = 2 CTAs per SM caps the kernel at 128 registers per thread for 256 threads.
-template <class Real, int NPT, int NTHREADS, int KIND>
-__global__ void __launch_bounds__(NTHREADS, (NTHREADS <= 256 ? 2 : 1)) stepper_kernel(const __grid_constant__ StepParams P) {
+// One kernel per (precision, groups per thread, task kind); each kernel inlines a single task
+// body, which keeps register pressure and compile time down.  Up to 512 threads per CTA (the
+// plan picks the block size), at most 128 registers per thread.
+constexpr int kStepMaxThreads = 512;
+
+template <class Real, int NG, int KIND>
+__global__ void __launch_bounds__(kStepMaxThreads) stepper_kernel(const __grid_constant__ StepParams P) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   __shared__ RedSmem rs;
   cg::cluster_group cluster = cg::this_cluster();
-  Stepper<Real, NPT> st(P, cluster, rs, dyn_smem);
+  Stepper<Real, NG> st(P, cluster, rs, dyn_smem);
   // every CTA of the cluster has initialised its shared memory before any DSMEM traffic
   cluster_sync_all();
   const int task = (int)(blockIdx.x / (unsigned)P.cs);

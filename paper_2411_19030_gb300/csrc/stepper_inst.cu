@@ -19,17 +19,16 @@
 
 namespace ptg {
 
-StepKernel PTG_SELECT_NAME(PTG_TAG, PTG_KIND)(int npt, int nthreads) {
-#define PTG_TRY(NT_, NPT_) \
-  if (npt == NPT_ && nthreads == NT_) return &stepper_kernel<PTG_REAL, NPT_, NT_, PTG_KIND>;
-  PTG_TRY(256, 2)
-  PTG_TRY(256, 4)
-  PTG_TRY(256, 6)
-  PTG_TRY(256, 10)
-  PTG_TRY(256, 12)
-  PTG_TRY(512, 10)
-#undef PTG_TRY
-  return nullptr;
+StepKernel PTG_SELECT_NAME(PTG_TAG, PTG_KIND)(int ng) {
+  switch (ng) {
+    case 1: return &stepper_kernel<PTG_REAL, 1, PTG_KIND>;
+    case 2: return &stepper_kernel<PTG_REAL, 2, PTG_KIND>;
+    case 3: return &stepper_kernel<PTG_REAL, 3, PTG_KIND>;
+    case 4: return &stepper_kernel<PTG_REAL, 4, PTG_KIND>;
+    case 5: return &stepper_kernel<PTG_REAL, 5, PTG_KIND>;
+    case 6: return &stepper_kernel<PTG_REAL, 6, PTG_KIND>;
+    default: return nullptr;
+  }
 }
 
 }  // namespace ptg
