@@ -1,13 +1,27 @@
-// plan.cu -- launch of the cluster stepper and occupancy queries for plan selection.
+// plan.cu -- launches of the cluster stepper (single task set and persistent multi-design) and
+// occupancy queries for plan selection.
+#include <mutex>
+#include <unordered_map>
 #include "stepper_launch.cuh"
 
 namespace ptg {
 
-static cudaError_t configure(StepKernel k, int cs, size_t smem) {
+// Function attributes are set once per kernel (and raised when a larger shared-memory
+// footprint is requested), so launches made after a warm-up call no attribute API and can be
+// captured into a CUDA graph.
+static cudaError_t configure(const void* k, int cs, size_t smem) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> done;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = done.find(k);
+  if (it != done.end() && it->second >= smem) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (cs > 8) e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  return e;
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  done[k] = smem;
+  (void)cs;
+  return cudaSuccess;
 }
 
 static void cluster_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int nclusters, int cs, int nthreads,
@@ -28,12 +42,35 @@ static void cluster_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, i
 cudaError_t launch_stepper(const StepParams& P, const Plan& plan, int precision, int ntasks, cudaStream_t stream) {
   StepKernel k = stepper_kernel_for(precision, P.kind, plan.ng);
   if (!k) return cudaErrorInvalidConfiguration;
-  cudaError_t e = configure(k, plan.cs, plan.smem);
+  cudaError_t e = configure((const void*)k, plan.cs, plan.smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
   cluster_config(cfg, attr, ntasks, plan.cs, plan.nthreads, plan.smem, stream);
   return cudaLaunchKernelEx(&cfg, k, P);
+}
+
+cudaError_t launch_stepper_batch(int precision, int kind, const Plan& plan, const StepParams* table, const int2* tasks,
+                                 int ntasks, int* queue, int nclusters, cudaStream_t stream) {
+  BatchKernel k = stepper_kernels_for(precision, kind, plan.ng).batch;
+  if (!k) return cudaErrorInvalidConfiguration;
+  cudaError_t e = configure((const void*)k, plan.cs, plan.smem);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(queue, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  cluster_config(cfg, attr, nclusters, plan.cs, plan.nthreads, plan.smem, stream);
+  return cudaLaunchKernelEx(&cfg, k, table, tasks, ntasks, queue);
+}
+
+static cudaError_t occupancy(const void* k, int cs, int nthreads, size_t smem, int* out) {
+  cudaError_t e = configure(k, cs, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  cluster_config(cfg, attr, 64, cs, nthreads, smem, 0);
+  return cudaOccupancyMaxActiveClusters(out, k, &cfg);
 }
 
 cudaError_t query_stepper_plan(int nx, int ny, int precision, int kind, int cs, int ng, int nthreads, Plan* plan) {
@@ -46,15 +83,17 @@ cudaError_t query_stepper_plan(int nx, int ny, int precision, int kind, int cs, 
   plan->smem = stepper_smem_bytes(nx, plan->rmax, precision == PTG_FP32_REFINE ? 4 : 8);
   plan->max_active_clusters = 0;
   if (plan->smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t e = configure(k, cs, plan->smem);
-  if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg;
-  cudaLaunchAttribute attr[1];
-  cluster_config(cfg, attr, 64, cs, nthreads, plan->smem, 0);
   int n = 0;
-  e = cudaOccupancyMaxActiveClusters(&n, k, &cfg);
+  cudaError_t e = occupancy((const void*)k, cs, nthreads, plan->smem, &n);
   plan->max_active_clusters = n;
   return e;
+}
+
+cudaError_t query_batch_occupancy(int precision, int kind, int cs, int ng, int nthreads, size_t smem, int* nclusters) {
+  BatchKernel k = stepper_kernels_for(precision, kind, ng).batch;
+  if (!k || nthreads < 32 || nthreads > kStepMaxThreadsHost || nthreads % 32 || smem > 227 * 1024)
+    return cudaErrorInvalidConfiguration;
+  return occupancy((const void*)k, cs, nthreads, smem, nclusters);
 }
 
 }  // namespace ptg

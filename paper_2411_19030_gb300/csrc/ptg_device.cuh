@@ -57,9 +57,10 @@ struct NoPost {
 // the dot products).  Every thread of every CTA of the cluster must call it the same number of
 // times; the result is bitwise identical in every thread of every CTA: the warp butterfly
 // combines the same pairs in every lane, lanes of warp 0 sum the warp partials in warp order,
-// every CTA writes its partial into every CTA's slot array and the slots are summed in rank
-// order.  In float every thread sums the slots and applies `post` itself.  In double (1/58 of
-// the float rate on this chip) thread 0 does that and broadcasts through shared memory.
+// and every CTA writes its partial into every CTA's slot array.  In float every warp sums the
+// slots with a second butterfly (lane r holds rank r) and applies `post` itself.  In double
+// (1/58 of the float rate on this chip) thread 0 sums them in rank order, applies `post` and
+// broadcasts through shared memory.
 // One __syncthreads and one cluster barrier per call (two __syncthreads in double); the
 // cluster barrier also publishes every DSMEM store made before the call.
 template <class T, int NV, int NX = 0, class Post = NoPost>
@@ -91,10 +92,12 @@ __device__ __forceinline__ void cluster_allreduce(T (&v)[NV + NX], RedSmem& rs, 
   }
   cluster_sync_all();
   if constexpr (sizeof(T) == 4) {
+    // lane r loads rank r's partial; the same butterfly in every warp of every CTA
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
-      T t = rb.slot[phase][0][i];
-      for (int r = 1; r < cs; ++r) t += rb.slot[phase][r][i];
+      T t = lane < cs ? rb.slot[phase][lane][i] : T(0);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
       v[i] = t;
     }
     post(v);

@@ -120,6 +120,9 @@ struct Plan {
 };
 
 cudaError_t launch_stepper(const StepParams& P, const Plan& plan, int precision, int ntasks, cudaStream_t stream);
+cudaError_t launch_stepper_batch(int precision, int kind, const Plan& plan, const StepParams* table, const int2* tasks,
+                                 int ntasks, int* queue, int nclusters, cudaStream_t stream);
+cudaError_t query_batch_occupancy(int precision, int kind, int cs, int ng, int nthreads, size_t smem, int* nclusters);
 cudaError_t query_stepper_plan(int nx, int ny, int precision, int kind, int cs, int ng, int nthreads, Plan* plan);
 
 // Device arrays written by the assembly (see ptg_op in api.cu for their shapes).

@@ -648,8 +648,16 @@ struct Stepper {
 
   __device__ void correct_primal() {
     set_operator(true);
-    load_x64(P.out_field);                      // u_0
-    double theta = P.out_aux[0];
+    double theta;
+    if (P.in_field) {                           // u_0 taken from the guess states, copied to X[0]
+      load_x64(P.in_field);
+      store_x64(P.out_field);
+      theta = P.in_aux[0];
+      if (threadIdx.x == 0 && sb.rank == 0) P.out_aux[0] = theta;
+    } else {                                    // u_0 given in X[0]
+      load_x64(P.out_field);
+      theta = P.out_aux[0];
+    }
     if (double* row = hist_row(0)) store_x64(row);
     for (int s = 0; s < P.Ntau; ++s) {
       const int j = P.M * (s + 1);
@@ -760,6 +768,16 @@ struct Stepper {
 constexpr int kStepMaxThreads = 512;
 
 template <class Real, int NG, int KIND>
+__device__ __forceinline__ void run_task(Stepper<Real, NG>& st, int task) {
+  if constexpr (KIND == KIND_FINE_PRI) st.fine_primal(task);
+  if constexpr (KIND == KIND_COARSE_PRI) st.coarse_primal(task);
+  if constexpr (KIND == KIND_CORRECT_PRI) st.correct_primal();
+  if constexpr (KIND == KIND_FINE_ADJ) st.fine_adjoint(task);
+  if constexpr (KIND == KIND_COARSE_ADJ) st.coarse_adjoint(task);
+  if constexpr (KIND == KIND_CORRECT_ADJ) st.correct_adjoint();
+}
+
+template <class Real, int NG, int KIND>
 __global__ void __launch_bounds__(kStepMaxThreads) stepper_kernel(const __grid_constant__ StepParams P) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   __shared__ RedSmem rs;
@@ -767,15 +785,42 @@ __global__ void __launch_bounds__(kStepMaxThreads) stepper_kernel(const __grid_c
   Stepper<Real, NG> st(P, cluster, rs, dyn_smem);
   // every CTA of the cluster has initialised its shared memory before any DSMEM traffic
   cluster_sync_all();
-  const int task = (int)(blockIdx.x / (unsigned)P.cs);
-  if constexpr (KIND == KIND_FINE_PRI) st.fine_primal(task);
-  if constexpr (KIND == KIND_COARSE_PRI) st.coarse_primal(task);
-  if constexpr (KIND == KIND_CORRECT_PRI) st.correct_primal();
-  if constexpr (KIND == KIND_FINE_ADJ) st.fine_adjoint(task);
-  if constexpr (KIND == KIND_COARSE_ADJ) st.coarse_adjoint(task);
-  if constexpr (KIND == KIND_CORRECT_ADJ) st.correct_adjoint();
+  run_task<Real, NG, KIND>(st, (int)(blockIdx.x / (unsigned)P.cs));
   // no CTA leaves while another may still read or write its shared memory
   cluster_sync_all();
+}
+
+// Persistent multi-design variant: `tasks` lists (design, task) pairs, largest designs first;
+// every cluster claims the next pair from the work queue until the list is exhausted, and
+// runs it with that design's parameters (table[design]).  All designs share the precision,
+// the cluster size, the block size and NG; shared memory is carved per task for the design's
+// geometry from the largest footprint that the launch reserves.
+template <class Real, int NG, int KIND>
+__global__ void __launch_bounds__(kStepMaxThreads) stepper_batch_kernel(const StepParams* __restrict__ table,
+                                                                       const int2* __restrict__ tasks, int ntasks,
+                                                                       int* __restrict__ queue) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  __shared__ RedSmem rs;
+  __shared__ int s_task;
+  cg::cluster_group cluster = cg::this_cluster();
+  const unsigned rank = cluster.block_rank();
+  cluster_sync_all();                          // all CTAs running before any DSMEM store
+  for (;;) {
+    // rank 0 claims the next task and writes it into every CTA of the cluster; the barrier
+    // publishes it (and orders it after the previous task's last shared-memory access)
+    if (rank == 0 && threadIdx.x == 0) {
+      const int t = atomicAdd(queue, 1);
+      for (unsigned r = 0; r < cluster.num_blocks(); ++r) *cluster.map_shared_rank(&s_task, r) = t;
+    }
+    cluster_sync_all();
+    const int t = s_task;                      // identical in every CTA: the loop is uniform
+    if (t >= ntasks) break;
+    const int2 tk = tasks[t];
+    Stepper<Real, NG> st(table[tk.x], cluster, rs, dyn_smem);
+    cluster_sync_all();
+    run_task<Real, NG, KIND>(st, tk.y);
+    cluster_sync_all();
+  }
 }
 
 }  // namespace ptg

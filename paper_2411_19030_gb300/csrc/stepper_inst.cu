@@ -19,16 +19,19 @@
 
 namespace ptg {
 
-StepKernel PTG_SELECT_NAME(PTG_TAG, PTG_KIND)(int ng) {
+StepKernels PTG_SELECT_NAME(PTG_TAG, PTG_KIND)(int ng) {
+#define PTG_PAIR(NG_) \
+  StepKernels{&stepper_kernel<PTG_REAL, NG_, PTG_KIND>, &stepper_batch_kernel<PTG_REAL, NG_, PTG_KIND>}
   switch (ng) {
-    case 1: return &stepper_kernel<PTG_REAL, 1, PTG_KIND>;
-    case 2: return &stepper_kernel<PTG_REAL, 2, PTG_KIND>;
-    case 3: return &stepper_kernel<PTG_REAL, 3, PTG_KIND>;
-    case 4: return &stepper_kernel<PTG_REAL, 4, PTG_KIND>;
-    case 5: return &stepper_kernel<PTG_REAL, 5, PTG_KIND>;
-    case 6: return &stepper_kernel<PTG_REAL, 6, PTG_KIND>;
-    default: return nullptr;
+    case 1: return PTG_PAIR(1);
+    case 2: return PTG_PAIR(2);
+    case 3: return PTG_PAIR(3);
+    case 4: return PTG_PAIR(4);
+    case 5: return PTG_PAIR(5);
+    case 6: return PTG_PAIR(6);
+    default: return StepKernels{nullptr, nullptr};
   }
+#undef PTG_PAIR
 }
 
 }  // namespace ptg
