@@ -266,6 +266,49 @@ int ptg_sensitivities_noalloc(int nx, int ny, double h, int Nt, double dt, const
                               const double* T_hist, int hist_j0, int hist_rows,
                               double* grad_d, cudaStream_t stream);
 
+/* ------------------------------------------------------------------ batches of designs
+ * A batch advances several designs (ops of the same precision on the same device, grid sizes
+ * may differ) together: each phase of a pass is ONE persistent launch in which every
+ * thread-block cluster takes (design, slice) tasks from a work queue, largest designs first.
+ * The batch owns each design's pass buffers (ptg_pass_buffers); the caller fills rho (and,
+ * if it wants, the warm start) through the pointers returned by ptg_batch_buffers.
+ * Phases: 0 fine primal, 1 coarse primal, 2 primal correction, 3 fine adjoint, 4 coarse
+ * adjoint, 5 adjoint correction (the one-shot pass, Alg. 3 lines 9-12); 6 sequential primal,
+ * 7 sequential adjoint (Alg. 3 lines 6-7, writing the warm start U/V).
+ * Every call is asynchronous on `stream`; after a first call of each phase (which uploads the
+ * plan) the launch sequence can be captured into a CUDA graph.
+ */
+typedef struct {
+    double *T_hist;                              /* [Nt+1][Nn] */
+    double *U_T, *U_theta, *V_lam, *V_g;         /* warm start: [Ntau+1][Nn], [Ntau+1], [Ntau+1][Nn], [Ntau+1][Ne] */
+    double *U_T_new, *U_theta_new, *V_lam_new, *V_g_new;   /* result of the one-shot pass, same shapes */
+    double *F_T, *F_theta, *G_T, *G_theta;       /* slice results of the primal: [Ntau][Nn], [Ntau] */
+    double *F_lam, *F_g, *G_lam, *G_g;           /* slice results of the adjoint: [Ntau][Nn], [Ntau][Ne] */
+    double *rho;                                 /* [Ne] the design, read by ptg_batch_assemble */
+} ptg_pass_buffers;
+
+typedef struct ptg_batch ptg_batch;
+
+int ptg_batch_create(ptg_op* const* ops, int nops, ptg_batch** out);
+void ptg_batch_destroy(ptg_batch* b);
+int ptg_batch_buffers(ptg_batch* b, int design, ptg_pass_buffers* out);
+/* a1 for every design from its buffers' rho. */
+int ptg_batch_assemble(ptg_batch* b, cudaStream_t stream);
+/* Alg. 3 lines 6-7 for every design: sequential primal and adjoint, writing U/V and T_hist;
+ * Theta = U_theta[Ntau], gradient = V_g row 0. */
+int ptg_batch_sequential_pass(ptg_batch* b, cudaStream_t stream);
+/* Alg. 3 lines 9-12 for every design from the warm start U/V: writes *_new and T_hist;
+ * Theta = U_theta_new[Ntau], gradient = V_g_new row 0. */
+int ptg_batch_oneshot_pass(ptg_batch* b, cudaStream_t stream);
+/* Copy the one-shot result (*_new) into the warm start for the next design iteration. */
+int ptg_batch_commit(ptg_batch* b, cudaStream_t stream);
+/* One phase alone (its inputs must be current), e.g. to time it. */
+int ptg_batch_run_phase(ptg_batch* b, int phase, cudaStream_t stream);
+/* Plan of a phase: cluster size (2..16), groups per thread (1..6), threads per CTA (32..512,
+ * multiple of 32); PTG_EINVAL if it does not fit every design or the device. */
+int ptg_batch_set_plan(ptg_batch* b, int phase, int cs, int ng, int nthreads);
+int ptg_batch_get_plan(ptg_batch* b, int phase, int* cs, int* ng, int* nthreads, int* nclusters);
+
 /* Copy the device status and counters into *out (synchronises the op's last stream). */
 int ptg_get_stats(ptg_op* op, ptg_stats* out);
 

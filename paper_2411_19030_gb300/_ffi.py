@@ -42,6 +42,12 @@ class ptg_stats(ctypes.Structure):
                 ("kind_refinements", c_longlong * 6)]
 
 
+class ptg_pass_buffers(ctypes.Structure):
+    _fields_ = [(n, c_void_p) for n in ("T_hist", "U_T", "U_theta", "V_lam", "V_g", "U_T_new", "U_theta_new",
+                                        "V_lam_new", "V_g_new", "F_T", "F_theta", "G_T", "G_theta", "F_lam",
+                                        "F_g", "G_lam", "G_g", "rho")]
+
+
 _P = c_void_p   # device / host pointers and cudaStream_t are passed as addresses
 
 SIGNATURES = {
@@ -61,6 +67,16 @@ SIGNATURES = {
     "ptg_sensitivities": (c_int, [_P, _P, c_int, c_int, _P, c_int, c_int, _P, _P]),
     "ptg_sensitivities_noalloc": (c_int, [c_int, c_int, c_double, c_int, c_double, POINTER(ptg_material), _P, _P,
                                           c_int, c_int, _P, c_int, c_int, _P, _P]),
+    "ptg_batch_create": (c_int, [POINTER(c_void_p), c_int, POINTER(c_void_p)]),
+    "ptg_batch_destroy": (None, [_P]),
+    "ptg_batch_buffers": (c_int, [_P, c_int, POINTER(ptg_pass_buffers)]),
+    "ptg_batch_assemble": (c_int, [_P, _P]),
+    "ptg_batch_sequential_pass": (c_int, [_P, _P]),
+    "ptg_batch_oneshot_pass": (c_int, [_P, _P]),
+    "ptg_batch_commit": (c_int, [_P, _P]),
+    "ptg_batch_run_phase": (c_int, [_P, c_int, _P]),
+    "ptg_batch_set_plan": (c_int, [_P, c_int, c_int, c_int, c_int]),
+    "ptg_batch_get_plan": (c_int, [_P, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "ptg_get_stats": (c_int, [_P, POINTER(ptg_stats)]),
     "ptg_reset_stats": (c_int, [_P, _P]),
 }

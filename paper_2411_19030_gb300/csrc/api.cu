@@ -6,6 +6,7 @@
 #include <mutex>
 #include <new>
 #include <tuple>
+#include <vector>
 #include "ptg_internal.h"
 #include "stepper_launch.cuh"
 
@@ -501,6 +502,351 @@ int ptg_reset_stats(ptg_op* op, cudaStream_t stream) {
   DeviceGuard dg(op->device);
   op->last_stream = stream;
   PTG_CUDA(cudaMemsetAsync(op->stats, 0, sizeof(DevStats), stream));
+  return PTG_OK;
+}
+
+}  // extern "C"
+
+// =========================================================================== batches
+// Several designs (ops, possibly of different grid sizes) advanced together: one persistent
+// multi-design launch per phase of the pass, every cluster taking (design, task) pairs from a
+// work queue, largest designs first.
+
+namespace {
+
+constexpr int kPhases = 8;   // 0..5: one-shot kinds; 6: sequential primal; 7: sequential adjoint
+
+struct BatchBuf {
+  double *T_hist, *U_T, *U_th, *V_l, *V_g, *U_T_new, *U_th_new, *V_l_new, *V_g_new;
+  double *F_T, *F_th, *G_T, *G_th, *F_l, *F_g, *G_l, *G_g, *rho;
+};
+
+struct PhasePlan {
+  Plan plan;
+  int nclusters = 0;
+  int ntasks = 0;
+  StepParams* table = nullptr;   // device, one per design
+  int2* tasks = nullptr;         // device
+  bool ready = false;
+};
+
+int phase_kind(int ph) { return ph < 6 ? ph : (ph == 6 ? KIND_FINE_PRI : KIND_FINE_ADJ); }
+
+}  // namespace
+
+struct ptg_batch {
+  int device = 0;
+  int precision = 0;
+  std::vector<ptg_op*> ops;
+  std::vector<BatchBuf> bufs;
+  std::vector<void*> allocs;
+  std::vector<int> order;        // design indices, largest first
+  PhasePlan ph[kPhases];
+  int* queue = nullptr;          // [kPhases]
+  std::mutex mu;
+};
+
+namespace {
+
+void batch_free(ptg_batch* b) {
+  for (void* p : b->allocs)
+    if (p) cudaFree(p);
+  b->allocs.clear();
+  for (auto& p : b->ph) {
+    if (p.table) cudaFree(p.table);
+    if (p.tasks) cudaFree(p.tasks);
+    p.table = nullptr;
+    p.tasks = nullptr;
+  }
+  if (b->queue) cudaFree(b->queue);
+  b->queue = nullptr;
+}
+
+// Per-design parameters of one phase with cluster size cs.
+StepParams phase_params(const ptg_batch* b, int d, int ph, int cs) {
+  const ptg_op* op = b->ops[d];
+  const BatchBuf& B = b->bufs[d];
+  StepParams P;
+  base_params(op, P);
+  P.cs = cs;
+  P.rmax = (op->g.ny + 1 + cs - 1) / cs;
+  P.kind = phase_kind(ph);
+  P.s0 = 0;
+  P.ns = op->tm.Ntau;
+  P.hist = B.T_hist;
+  P.hist_j0 = 0;
+  P.hist_rows = op->tm.Nt + 1;
+  const int Ntau = op->tm.Ntau;
+  switch (ph) {
+    case 0:  P.in_field = B.U_T; P.in_aux = B.U_th; P.out_field = B.F_T; P.out_aux = B.F_th; break;
+    case 1:  P.in_field = B.U_T; P.in_aux = B.U_th; P.out_field = B.G_T; P.out_aux = B.G_th; break;
+    case 2:
+      P.in_field = B.U_T; P.in_aux = B.U_th; P.out_field = B.U_T_new; P.out_aux = B.U_th_new;
+      P.F_field = B.F_T; P.F_aux = B.F_th; P.G_field = B.G_T; P.G_aux = B.G_th;
+      break;
+    case 3:
+      P.in_field = B.V_l; P.in_aux = B.V_g; P.out_field = B.F_l; P.out_aux = B.F_g; P.Theta = B.U_th_new + Ntau;
+      break;
+    case 4:
+      P.in_field = B.V_l; P.in_aux = B.V_g; P.out_field = B.G_l; P.out_aux = B.G_g; P.Theta = B.U_th_new + Ntau;
+      break;
+    case 5:
+      P.out_field = B.V_l_new; P.out_aux = B.V_g_new; P.F_field = B.F_l; P.F_aux = B.F_g; P.G_field = B.G_l;
+      P.G_aux = B.G_g; P.Theta = B.U_th_new + Ntau;
+      break;
+    case 6:   // sequential primal: u_0 in U[0], checkpoints into U[1..]
+      P.chained = 1; P.in_field = B.U_T; P.in_aux = B.U_th; P.out_field = B.U_T + op->Nn; P.out_aux = B.U_th + 1;
+      break;
+    case 7:   // sequential adjoint: v_Ntau = 0 in V[Ntau], checkpoints into V[0..Ntau-1]
+      P.chained = 1; P.in_field = B.V_l; P.in_aux = B.V_g; P.out_field = B.V_l; P.out_aux = B.V_g;
+      P.Theta = B.U_th + Ntau;
+      break;
+  }
+  return P;
+}
+
+// Tasks of a phase: (design, slice) for the parallel kinds, (design, 0) for the sweeps and the
+// chained runs, largest designs first.
+std::vector<int2> phase_tasks(const ptg_batch* b, int ph) {
+  std::vector<int2> t;
+  const bool per_slice = ph == 0 || ph == 1 || ph == 3 || ph == 4;
+  for (int d : b->order) {
+    const int n = per_slice ? b->ops[d]->tm.Ntau : 1;
+    for (int s = 0; s < n; ++s) t.push_back(make_int2(d, s));
+  }
+  return t;
+}
+
+// Install a plan for a phase: validate it for every design, upload the parameter table and
+// the task list, and size the persistent grid.
+int batch_install(ptg_batch* b, int ph, int cs, int ng, int nthreads) {
+  const int kind = phase_kind(ph);
+  size_t smem = 0;
+  for (ptg_op* op : b->ops) {
+    const int rmax = (op->g.ny + 1 + cs - 1) / cs;
+    if (rmax < 2) return PTG_EINVAL;
+    const int groups = rmax * (op->W / kGroup);
+    if (groups > ng * nthreads) return PTG_EINVAL;
+    smem = std::max(smem, stepper_smem_bytes(op->g.nx, rmax, b->precision == PTG_FP32_REFINE ? 4 : 8));
+  }
+  int nclusters = 0;
+  if (query_batch_occupancy(b->precision, kind, cs, ng, nthreads, smem, &nclusters) != cudaSuccess || nclusters <= 0) {
+    cudaGetLastError();
+    return PTG_EINVAL;
+  }
+  std::vector<StepParams> table;
+  for (int d = 0; d < (int)b->ops.size(); ++d) table.push_back(phase_params(b, d, ph, cs));
+  std::vector<int2> tasks = phase_tasks(b, ph);
+  PhasePlan& pp = b->ph[ph];
+  if (!pp.table) PTG_CUDA(cudaMalloc(&pp.table, sizeof(StepParams) * table.size()));
+  if (!pp.tasks) PTG_CUDA(cudaMalloc(&pp.tasks, sizeof(int2) * tasks.size()));
+  PTG_CUDA(cudaMemcpy(pp.table, table.data(), sizeof(StepParams) * table.size(), cudaMemcpyHostToDevice));
+  PTG_CUDA(cudaMemcpy(pp.tasks, tasks.data(), sizeof(int2) * tasks.size(), cudaMemcpyHostToDevice));
+  pp.plan.cs = cs;
+  pp.plan.ng = ng;
+  pp.plan.nthreads = nthreads;
+  pp.plan.smem = smem;
+  pp.plan.max_active_clusters = nclusters;
+  pp.ntasks = (int)tasks.size();
+  pp.nclusters = std::min(nclusters, pp.ntasks);
+  pp.ready = true;
+  return PTG_OK;
+}
+
+// Default plan of a phase: fewest waves, then the fewest groups per thread, then the largest
+// cluster (the autotuner may replace it).
+int batch_default(ptg_batch* b, int ph) {
+  int best_cs = 0, best_ng = 0, best_nt = 0;
+  long best_waves = -1;
+  const int ntasks = (int)phase_tasks(b, ph).size();
+  for (int cs : {16, 8, 4, 2}) {
+    for (int ng : kStepNG) {
+      int nt = 32;
+      bool ok = true;
+      size_t smem = 0;
+      for (ptg_op* op : b->ops) {
+        const int rmax = (op->g.ny + 1 + cs - 1) / cs;
+        if (rmax < 2) { ok = false; break; }
+        const int groups = rmax * (op->W / kGroup);
+        nt = std::max(nt, ((groups + ng - 1) / ng + 31) / 32 * 32);
+        smem = std::max(smem, stepper_smem_bytes(op->g.nx, rmax, b->precision == PTG_FP32_REFINE ? 4 : 8));
+      }
+      if (!ok || nt > kStepMaxThreadsHost) continue;
+      int ncl = 0;
+      if (query_batch_occupancy(b->precision, phase_kind(ph), cs, ng, nt, smem, &ncl) != cudaSuccess || ncl <= 0) {
+        cudaGetLastError();
+        continue;
+      }
+      const long waves = (ntasks + ncl - 1) / ncl;
+      if (best_waves < 0 || waves < best_waves || (waves == best_waves && ng < best_ng)) {
+        best_waves = waves;
+        best_cs = cs;
+        best_ng = ng;
+        best_nt = nt;
+      }
+    }
+  }
+  if (best_waves < 0) return PTG_EINVAL;
+  return batch_install(b, ph, best_cs, best_ng, best_nt);
+}
+
+int batch_run(ptg_batch* b, int ph, cudaStream_t stream) {
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (!b->ph[ph].ready) {
+    int rc = batch_default(b, ph);
+    if (rc != PTG_OK) return rc;
+  }
+  const PhasePlan& pp = b->ph[ph];
+  for (ptg_op* op : b->ops) op->last_stream = stream;
+  PTG_CUDA(launch_stepper_batch(b->precision, phase_kind(ph), pp.plan, pp.table, pp.tasks, pp.ntasks,
+                                b->queue + ph, pp.nclusters, stream));
+  return PTG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ptg_batch_create(ptg_op* const* ops, int nops, ptg_batch** out) {
+  if (!out) return PTG_EINVAL;
+  *out = nullptr;
+  if (!ops || nops < 1) return PTG_EINVAL;
+  for (int d = 0; d < nops; ++d) {
+    if (!ops[d]) return PTG_EINVAL;
+    if (ops[d]->device != ops[0]->device || ops[d]->sv.precision != ops[0]->sv.precision) return PTG_EINVAL;
+  }
+  DeviceGuard dg(ops[0]->device);
+  ptg_batch* b = new (std::nothrow) ptg_batch();
+  if (!b) return PTG_ENOMEM;
+  b->device = ops[0]->device;
+  b->precision = ops[0]->sv.precision;
+  b->ops.assign(ops, ops + nops);
+  cudaError_t e = cudaSuccess;
+  auto A = [&](double** p, size_t n) {
+    *p = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc((void**)p, n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(*p, 0, n * sizeof(double));
+    b->allocs.push_back(*p);
+  };
+  for (ptg_op* op : b->ops) {
+    const size_t Nn = op->Nn, Ne = op->Ne, Nt = op->tm.Nt, T = op->tm.Ntau;
+    BatchBuf B;
+    A(&B.T_hist, (Nt + 1) * Nn);
+    A(&B.U_T, (T + 1) * Nn); A(&B.U_th, T + 1); A(&B.V_l, (T + 1) * Nn); A(&B.V_g, (T + 1) * Ne);
+    A(&B.U_T_new, (T + 1) * Nn); A(&B.U_th_new, T + 1); A(&B.V_l_new, (T + 1) * Nn); A(&B.V_g_new, (T + 1) * Ne);
+    A(&B.F_T, T * Nn); A(&B.F_th, T); A(&B.G_T, T * Nn); A(&B.G_th, T);
+    A(&B.F_l, T * Nn); A(&B.F_g, T * Ne); A(&B.G_l, T * Nn); A(&B.G_g, T * Ne);
+    A(&B.rho, Ne);
+    b->bufs.push_back(B);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&b->queue, kPhases * sizeof(int));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    batch_free(b);
+    delete b;
+    return PTG_ENOMEM;
+  }
+  b->order.resize(nops);
+  for (int d = 0; d < nops; ++d) b->order[d] = d;
+  std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
+    const long wx = (long)b->ops[x]->Nn * b->ops[x]->tm.Nt, wy = (long)b->ops[y]->Nn * b->ops[y]->tm.Nt;
+    return wx > wy;
+  });
+  *out = b;
+  return PTG_OK;
+}
+
+void ptg_batch_destroy(ptg_batch* b) {
+  if (!b) return;
+  DeviceGuard dg(b->device);
+  cudaDeviceSynchronize();
+  batch_free(b);
+  delete b;
+}
+
+int ptg_batch_buffers(ptg_batch* b, int d, ptg_pass_buffers* out) {
+  if (!b || !out || d < 0 || d >= (int)b->ops.size()) return PTG_EINVAL;
+  const BatchBuf& B = b->bufs[d];
+  out->T_hist = B.T_hist;
+  out->U_T = B.U_T; out->U_theta = B.U_th; out->V_lam = B.V_l; out->V_g = B.V_g;
+  out->U_T_new = B.U_T_new; out->U_theta_new = B.U_th_new; out->V_lam_new = B.V_l_new; out->V_g_new = B.V_g_new;
+  out->F_T = B.F_T; out->F_theta = B.F_th; out->G_T = B.G_T; out->G_theta = B.G_th;
+  out->F_lam = B.F_l; out->F_g = B.F_g; out->G_lam = B.G_l; out->G_g = B.G_g;
+  out->rho = B.rho;
+  return PTG_OK;
+}
+
+int ptg_batch_assemble(ptg_batch* b, cudaStream_t stream) {
+  if (!b) return PTG_EINVAL;
+  for (int d = 0; d < (int)b->ops.size(); ++d) {
+    int rc = ptg_fe_assemble_operator(b->ops[d], b->bufs[d].rho, stream);
+    if (rc != PTG_OK) return rc;
+  }
+  return PTG_OK;
+}
+
+int ptg_batch_sequential_pass(ptg_batch* b, cudaStream_t stream) {
+  if (!b) return PTG_EINVAL;
+  DeviceGuard dg(b->device);
+  int rc = batch_run(b, 6, stream);
+  if (rc == PTG_OK) rc = batch_run(b, 7, stream);
+  return rc;
+}
+
+int ptg_batch_oneshot_pass(ptg_batch* b, cudaStream_t stream) {
+  if (!b) return PTG_EINVAL;
+  DeviceGuard dg(b->device);
+  for (int ph = 0; ph < 6; ++ph) {
+    int rc = batch_run(b, ph, stream);
+    if (rc != PTG_OK) return rc;
+  }
+  return PTG_OK;
+}
+
+int ptg_batch_commit(ptg_batch* b, cudaStream_t stream) {
+  if (!b) return PTG_EINVAL;
+  DeviceGuard dg(b->device);
+  for (int d = 0; d < (int)b->ops.size(); ++d) {
+    const ptg_op* op = b->ops[d];
+    const BatchBuf& B = b->bufs[d];
+    const size_t T1 = op->tm.Ntau + 1;
+    PTG_CUDA(cudaMemcpyAsync(B.U_T, B.U_T_new, T1 * op->Nn * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    PTG_CUDA(cudaMemcpyAsync(B.U_th, B.U_th_new, T1 * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    PTG_CUDA(cudaMemcpyAsync(B.V_l, B.V_l_new, T1 * op->Nn * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    PTG_CUDA(cudaMemcpyAsync(B.V_g, B.V_g_new, T1 * op->Ne * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  }
+  return PTG_OK;
+}
+
+int ptg_batch_run_phase(ptg_batch* b, int phase, cudaStream_t stream) {
+  if (!b || phase < 0 || phase >= kPhases) return PTG_EINVAL;
+  DeviceGuard dg(b->device);
+  return batch_run(b, phase, stream);
+}
+
+int ptg_batch_set_plan(ptg_batch* b, int phase, int cs, int ng, int nthreads) {
+  if (!b || phase < 0 || phase >= kPhases) return PTG_EINVAL;
+  if (cs != 2 && cs != 4 && cs != 8 && cs != 16) return PTG_EINVAL;
+  if (ng < 1 || ng > kStepNG[kNumStepNG - 1] || nthreads < 32 || nthreads > kStepMaxThreadsHost || nthreads % 32)
+    return PTG_EINVAL;
+  DeviceGuard dg(b->device);
+  std::lock_guard<std::mutex> lk(b->mu);
+  return batch_install(b, phase, cs, ng, nthreads);
+}
+
+int ptg_batch_get_plan(ptg_batch* b, int phase, int* cs, int* ng, int* nthreads, int* nclusters) {
+  if (!b || phase < 0 || phase >= kPhases) return PTG_EINVAL;
+  DeviceGuard dg(b->device);
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (!b->ph[phase].ready) {
+    int rc = batch_default(b, phase);
+    if (rc != PTG_OK) return rc;
+  }
+  const PhasePlan& pp = b->ph[phase];
+  if (cs) *cs = pp.plan.cs;
+  if (ng) *ng = pp.plan.ng;
+  if (nthreads) *nthreads = pp.plan.nthreads;
+  if (nclusters) *nclusters = pp.nclusters;
   return PTG_OK;
 }
 
