@@ -1,5 +1,5 @@
 #!/usr/bin/env python3
-"""Benchmark of the one-shot Parareal pass (one design iteration of Algorithm 3, lines 5-12).
+"""Benchmark of the one-shot Parareal pass (one design iteration of Algorithm 3).
 
 Workload (one "step"): 128x128 bilinear grid (16 641 nodes, 13 Dirichlet), Nt = 1024 fine
 backward-Euler steps in N_tau = 32 slices (M = 32), SIMP k = 1e-3 + (1 - 1e-3) rho^3, unit
@@ -143,7 +143,8 @@ def run_gpu(args):
     w, rho_old_np, rho_np, sink = problem_arrays()
     n, Nt, Ntau, dt, p = w["n"], w["Nt"], w["Ntau"], w["dt"], w["p"]
     N_free = (n + 1) ** 2 - int(sink.sum())
-    solve = SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=2000, refine_max=8)
+    solve = SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=2000, refine_max=8,
+                        twolevel=args.twolevel)
     op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink, solve=solve, device=local)
     seq_op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink,
                       solve=SolveConfig("fp64", rtol=1e-13, cg_iters_max=4000, refine_max=8), device=local)
@@ -287,7 +288,7 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": f"{WORKLOAD}: 128x128 grid, Nt=1024, Ntau=32 (M=32), p=8, SIMP k, warm start from "
                                "the sequential coarse states of a design 1% away",
-                   "precision": args.precision, "rtol": args.rtol, "l2": "flushed between steps (256 MB write)",
+                   "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "wall_s": wall},
         "per_kernel_ms": kind_ms,
@@ -443,6 +444,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="fp32_refine", choices=["fp32_refine", "fp64"])
     ap.add_argument("--rtol", type=float, default=1e-10)
+    ap.add_argument("--no-twolevel", dest="twolevel", action="store_false",
+                    help="Jacobi only on the coarse-step solves (default: two-level preconditioner)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()

@@ -3,7 +3,7 @@
  * for transient heat conduction (Appel & Alexandersen, arXiv 2411.19030).
  *
  * The library computes, for one design rho, the per-design-iteration state / adjoint /
- * sensitivity pass of the paper's one-shot Parareal method (Algorithm 3, lines 5-12):
+ * sensitivity pass of the paper's one-shot Parareal method (Algorithm 3):
  *
  *   a1  ptg_fe_assemble_operator   SIMP coefficients and element weights      Sec. 2.1-2.2, Eq. 2.5-2.7
  *   a2  ptg_fine_propagate_slices  F_pri of every slice (modified Parareal)   Alg. 1, Sec. 4.3-4.4
@@ -90,6 +90,10 @@ typedef struct {
     double inner_rtol; /* FP32_REFINE: relative residual reduction of each FP32 CG */
     int cg_iters_max;  /* iteration limit of one CG */
     int refine_max;    /* limit of refinement sweeps of one solve */
+    int twolevel;      /* FP32_REFINE: precondition the coarse-step solves (C/dtau + K) with
+                          D^-1 + P Ac^-1 P^T, P bilinear from a coarse grid of spacing m h (m the
+                          smallest divisor >= 2 of both sides giving <= 17 coarse nodes per side;
+                          off if none).  0: Jacobi everywhere. */
 } ptg_solve;
 
 typedef struct {
@@ -163,7 +167,7 @@ int ptg_fe_assemble_operator(ptg_op* op, const double* rho_d, cudaStream_t strea
  *   schedule   PTG_SLICES_PARALLEL: slice s starts from (U_T[s], U_theta[s]) and all
  *              slices run concurrently (the parallel part of Parareal).
  *              PTG_SLICES_CHAINED: one sequential run from (U_T[s0], U_theta[s0]); slice s
- *              starts from the end of slice s-1 (sequential time stepping, Alg. 3 line 6).
+ *              starts from the end of slice s-1 (sequential time stepping, the initialisation of Alg. 3).
  *   U_T        [Ntau+1][Nn], U_theta [Ntau+1]: start states (only rows s0.. are read).
  *   T_hist     history window or NULL: row r holds T_{hist_j0 + r}, hist_rows rows.  Every
  *              computed T_j, j = M s + 1 .. M (s+1), is written to its row (the last one
@@ -273,8 +277,8 @@ int ptg_sensitivities_noalloc(int nx, int ny, double h, int Nt, double dt, const
  * The batch owns each design's pass buffers (ptg_pass_buffers); the caller fills rho (and,
  * if it wants, the warm start) through the pointers returned by ptg_batch_buffers.
  * Phases: 0 fine primal, 1 coarse primal, 2 primal correction, 3 fine adjoint, 4 coarse
- * adjoint, 5 adjoint correction (the one-shot pass, Alg. 3 lines 9-12); 6 sequential primal,
- * 7 sequential adjoint (Alg. 3 lines 6-7, writing the warm start U/V).
+ * adjoint, 5 adjoint correction (the one-shot pass, the iteration body of Alg. 3); 6 sequential primal,
+ * 7 sequential adjoint (the initialisation of Alg. 3, writing the warm start U/V).
  * Every call is asynchronous on `stream`; after a first call of each phase (which uploads the
  * plan) the launch sequence can be captured into a CUDA graph.
  */
@@ -294,10 +298,10 @@ void ptg_batch_destroy(ptg_batch* b);
 int ptg_batch_buffers(ptg_batch* b, int design, ptg_pass_buffers* out);
 /* a1 for every design from its buffers' rho. */
 int ptg_batch_assemble(ptg_batch* b, cudaStream_t stream);
-/* Alg. 3 lines 6-7 for every design: sequential primal and adjoint, writing U/V and T_hist;
+/* The initialisation of Alg. 3 for every design: sequential primal and adjoint, writing U/V and T_hist;
  * Theta = U_theta[Ntau], gradient = V_g row 0. */
 int ptg_batch_sequential_pass(ptg_batch* b, cudaStream_t stream);
-/* Alg. 3 lines 9-12 for every design from the warm start U/V: writes *_new and T_hist;
+/* The iteration body of Alg. 3 for every design from the warm start U/V: writes *_new and T_hist;
  * Theta = U_theta_new[Ntau], gradient = V_g_new row 0. */
 int ptg_batch_oneshot_pass(ptg_batch* b, cudaStream_t stream);
 /* Copy the one-shot result (*_new) into the warm start for the next design iteration. */

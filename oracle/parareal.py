@@ -155,7 +155,7 @@ def adjoint_iteration(op: Operator, V_old, T_hist: np.ndarray, Theta: float, plt
 
 
 def oneshot_pass(op: Operator, U_old, V_old, plt: bool = False) -> dict:
-    """Lines 9-12 of Alg. 3: one modified forward Parareal iteration and one reverse
+    """The iteration body of Alg. 3: one modified forward Parareal iteration and one reverse
     vanilla Parareal iteration, each warm-started from the previous design iteration's
     coarse states; Theta = theta_Nt and grad = g_1 (Sec. 4.4, four-step procedure)."""
     pri = primal_iteration(op, U_old, plt=plt)

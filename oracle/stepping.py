@@ -129,7 +129,7 @@ def sequential_adjoint(op: Operator, T_hist: np.ndarray, Theta: float):
 
 
 def sequential_pass(op: Operator) -> dict:
-    """Sequential reference (Alg. 3, lines 6-7): state, objective, adjoint, gradient."""
+    """Sequential reference (the initialisation of Alg. 3): state, objective, adjoint, gradient."""
     T_hist, theta = sequential_primal(op)
     Theta = theta[-1]
     lam, g = sequential_adjoint(op, T_hist, Theta)

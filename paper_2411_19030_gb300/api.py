@@ -53,6 +53,7 @@ class SolveConfig:
     inner_rtol: float = 1e-4
     cg_iters_max: int = 2000
     refine_max: int = 8
+    twolevel: bool = True            # two-level preconditioner of the coarse-step solves (fp32_refine)
 
 
 class Operator:
@@ -84,7 +85,8 @@ class Operator:
                               material["c0"], material["cmin"], material["pc"])
         t = _ffi.ptg_time(Nt, Ntau, dt, p)
         prec = {"fp64": PTG_FP64, "fp32_refine": PTG_FP32_REFINE}[solve.precision]
-        s = _ffi.ptg_solve(prec, solve.rtol, solve.inner_rtol, solve.cg_iters_max, solve.refine_max)
+        s = _ffi.ptg_solve(prec, solve.rtol, solve.inner_rtol, solve.cg_iters_max, solve.refine_max,
+                           int(solve.twolevel))
         self._dir = np.ascontiguousarray(dirichlet, dtype=np.uint8).reshape(-1)
         if self._dir.size != self.Nn:
             raise ValueError("dirichlet mask must have (nx+1)(ny+1) entries")
@@ -225,7 +227,7 @@ class PassBuffers:
 
 
 def sequential_pass(op: Operator, buf: PassBuffers, T0: torch.Tensor | None = None, stream=None):
-    """Alg. 3 lines 6-7: sequential primal (H_pri applied Nt times, full history) and
+    """Initialisation of Alg. 3: sequential primal (H_pri applied Nt times, full history) and
     sequential adjoint (H_adj applied Nt times), with the coarse checkpoints of both.
     On return buf.U_* / buf.V_* hold (T_{Mn}, theta_{Mn}) and (lambda_{Mn+1}, g_{Mn+1}),
     Theta is buf.U_th[Ntau] and the gradient g_1 is buf.V_g[0]."""
@@ -245,7 +247,7 @@ def sequential_pass(op: Operator, buf: PassBuffers, T0: torch.Tensor | None = No
 
 
 def oneshot_pass(op: Operator, buf: PassBuffers, stream=None, plt: bool = False):
-    """Alg. 3 lines 9-12: one modified forward Parareal iteration and one reverse vanilla
+    """Iteration body of Alg. 3: one modified forward Parareal iteration and one reverse vanilla
     Parareal iteration from the warm start (buf.U_*, buf.V_*).  The corrected states go to
     buf.U_*_new / buf.V_*_new, the history to buf.T_hist; returns (Theta, grad) views."""
     Ntau = op.Ntau

@@ -21,6 +21,10 @@ struct ptg_op {
   int Nn = 0, Ne = 0, M = 0, p_int = 0, has_dc = 0;
   double dtau = 0.0;
   int W = 0;               // padded row width
+  // two-level preconditioner of the coarse-step solves (FP32 CG); tl_m == 0: disabled
+  int tl_m = 0, tl_nax = 0, tl_nay = 0;
+  double* tl_Ac = nullptr;
+  float *tl_band = nullptr, *tl_X = nullptr, *tl_Ainv = nullptr;
   // device workspace
   double *k = nullptr, *c = nullptr, *dk = nullptr, *dc = nullptr;
   double* wE = nullptr;     // [2][3][PEe]: element (D, S, T) weights for dt and dtau (padded)
@@ -64,8 +68,78 @@ struct DeviceGuard {
   }
 };
 
-// Choose cluster size, threads and slots for `ntasks` concurrent clusters: fewest waves
-// first, then the largest cluster (least work per CTA per CG iteration).
+bool coarse_kind(int kind) {
+  return kind == KIND_COARSE_PRI || kind == KIND_CORRECT_PRI || kind == KIND_COARSE_ADJ || kind == KIND_CORRECT_ADJ;
+}
+
+// Aggregate rows reserved per CTA for cluster size cs (the largest over the ranks), 0 if the
+// two-level preconditioner is off for this op, precision, kind or plan.
+int twolevel_rows(const ptg_op* op, int precision, int kind, int cs, bool use = true) {
+  if (!use || op->tl_m == 0 || precision != PTG_FP32_REFINE || !coarse_kind(kind)) return 0;
+  int best = 0;
+  for (int q = 0; q < cs; ++q) {
+    int r0, R, lo, hi;
+    const int rows = op->g.ny + 1, base = rows / cs, rem = rows % cs;
+    r0 = q * base + (q < rem ? q : rem);
+    R = base + (q < rem ? 1 : 0);
+    coarse_rows_of_slab(r0, R, op->tl_m, op->tl_nay, lo, hi);
+    best = std::max(best, hi - lo + 1);
+  }
+  return best;
+}
+
+size_t twolevel_bytes(const ptg_op* op, int precision, int kind, int cs, bool use = true) {
+  const int ncj = twolevel_rows(op, precision, kind, cs, use);
+  if (ncj == 0) return 0;
+  const int rmax = (op->g.ny + 1 + cs - 1) / cs;
+  return twolevel_smem_bytes(op->W, rmax, cs, op->tl_nax, op->tl_nay, ncj);
+}
+
+void twolevel_params(const ptg_op* op, int precision, StepParams& P, bool use) {
+  P.tl_naj = twolevel_rows(op, precision, P.kind, P.cs, use);
+  if (P.tl_naj == 0) return;
+  P.Ainv = op->tl_Ainv;
+  P.cm = op->tl_m;
+  P.nax = op->tl_nax;
+  P.nay = op->tl_nay;
+}
+
+// Best plan for `ntasks` concurrent clusters with or without the two-level preconditioner:
+// fewest waves, then the shortest per-thread work (ng), then the largest cluster.  Returns
+// the number of waves, or -1 if nothing fits.
+long best_plan(ptg_op* op, int precision, int kind, int ntasks, bool tl, Plan* out) {
+  const int nx = op->g.nx, ny = op->g.ny;
+  const int G = op->W / kGroup;
+  long best_waves = -1;
+  for (int cs : {16, 8, 4, 2, 1}) {
+    const int rmax = (ny + 1 + cs - 1) / cs;
+    if (rmax < 2) continue;
+    const int groups = rmax * G;
+    for (int ng : kStepNG) {
+      const int nthreads = ((groups + ng - 1) / ng + 31) / 32 * 32;
+      if (nthreads > kStepMaxThreadsHost) continue;
+      Plan p;
+      cudaError_t e = query_stepper_plan(nx, ny, precision, kind, cs, ng, nthreads,
+                                         twolevel_bytes(op, precision, kind, cs, tl), &p);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      if (p.max_active_clusters <= 0) continue;
+      const long waves = (ntasks + p.max_active_clusters - 1) / p.max_active_clusters;
+      if (best_waves < 0 || waves < best_waves || (waves == best_waves && ng < out->ng)) {
+        p.twolevel = tl && twolevel_rows(op, precision, kind, cs) > 0;
+        *out = p;
+        best_waves = waves;
+      }
+    }
+  }
+  return best_waves;
+}
+
+// Choose the plan of a task kind for `ntasks` concurrent clusters.  The two-level
+// preconditioner (coarse kinds, FP32 CG) cuts the CG iterations about threefold for a
+// shared-memory cost; it is used unless its plan needs more waves than Jacobi's.
 int choose_plan(ptg_op* op, int precision, int kind, int ntasks, Plan* out) {
   std::lock_guard<std::mutex> lk(op->mu);
   auto ov = op->plan_override.find(kind);
@@ -79,37 +153,14 @@ int choose_plan(ptg_op* op, int precision, int kind, int ntasks, Plan* out) {
     *out = it->second;
     return PTG_OK;
   }
-  const int nx = op->g.nx, ny = op->g.ny;
-  const int G = op->W / kGroup;
-  // candidates: every cluster size and groups-per-thread count whose block fits 512 threads;
-  // best = fewest waves, then the shortest per-thread work (ng), then the largest cluster
-  Plan best;
-  long best_waves = -1;
-  for (int cs : {16, 8, 4, 2, 1}) {
-    const int rmax = (ny + 1 + cs - 1) / cs;
-    if (rmax < 2) continue;
-    const int groups = rmax * G;
-    for (int ng : kStepNG) {
-      const int nthreads = ((groups + ng - 1) / ng + 31) / 32 * 32;
-      if (nthreads > kStepMaxThreadsHost) continue;
-      Plan p;
-      cudaError_t e = query_stepper_plan(nx, ny, precision, kind, cs, ng, nthreads, &p);
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        continue;
-      }
-      if (p.max_active_clusters <= 0) continue;
-      const long waves = (ntasks + p.max_active_clusters - 1) / p.max_active_clusters;
-      if (best_waves < 0 || waves < best_waves || (waves == best_waves && ng < best.ng)) {
-        best = p;
-        best_waves = waves;
-      }
-    }
-  }
-  if (best_waves < 0) {
-    std::snprintf(g_last_error, sizeof(g_last_error), "no cluster plan fits a %dx%d grid", nx, ny);
+  Plan jac, two;
+  const long wj = best_plan(op, precision, kind, ntasks, false, &jac);
+  const long wt = twolevel_rows(op, precision, kind, 1) > 0 ? best_plan(op, precision, kind, ntasks, true, &two) : -1;
+  if (wj < 0 && wt < 0) {
+    std::snprintf(g_last_error, sizeof(g_last_error), "no cluster plan fits a %dx%d grid", op->g.nx, op->g.ny);
     return PTG_EINVAL;
   }
+  const Plan best = (wt >= 0 && (wj < 0 || wt <= wj)) ? two : jac;
   op->plans[key] = best;
   *out = best;
   return PTG_OK;
@@ -166,6 +217,7 @@ int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream) {
   if (rc != PTG_OK) return rc;
   P.cs = plan.cs;
   P.rmax = plan.rmax;
+  twolevel_params(op, op->sv.precision, P, plan.twolevel);
   op->last_stream = stream;
   PTG_CUDA(launch_stepper(P, plan, op->sv.precision, ntasks, stream));
   return PTG_OK;
@@ -175,7 +227,8 @@ bool window_covers(int j0, int rows, int lo, int hi) { return lo >= j0 && hi < j
 
 void free_all(ptg_op* op) {
   void* ptrs[] = {op->k, op->c, op->dk, op->dc, op->wE, op->nodew, op->fload,
-                  op->q_elem, op->q_time, op->dirichlet, op->sens_partial, op->stats};
+                  op->q_elem, op->q_time, op->dirichlet, op->sens_partial, op->stats,
+                  op->tl_Ac, op->tl_band, op->tl_X, op->tl_Ainv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -247,6 +300,21 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
   A(&op->q_time, (time->Nt + 1) * sizeof(double));
   A(&op->dirichlet, op->Nn);
   A(&op->sens_partial, (size_t)op->sens_chunks * op->Ne * sizeof(double));
+  // two-level preconditioner: aggregates of m x m nodes, m the smallest multiple of 4 giving
+  // at most kCoarseMaxAgg aggregates per direction (FP32 CG only)
+  if (solve->precision == PTG_FP32_REFINE && solve->twolevel) {
+    int m = 4;
+    while ((grid->nx + 1) / m > kCoarseMaxAgg || (grid->ny + 1) / m > kCoarseMaxAgg) m += 4;
+    op->tl_m = m;
+    op->tl_nax = coarse_aggregates(grid->nx, m);
+    op->tl_nay = coarse_aggregates(grid->ny, m);
+    const size_t nc = (size_t)op->tl_nax * op->tl_nay;
+    A(&op->tl_Ac, nc * nc * sizeof(double));
+    A(&op->tl_band, nc * (op->tl_nax + 2) * sizeof(float));
+    const size_t ncp = (size_t)coarse_row_stride(op->tl_nax) * op->tl_nay;
+    A(&op->tl_X, nc * nc * sizeof(float));
+    A(&op->tl_Ainv, ncp * ncp * sizeof(float));
+  }
   A(&op->stats, sizeof(DevStats));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -323,15 +391,22 @@ int ptg_op_set_plan(ptg_op* op, int kind, int cs, int ng) {
   if (ng < 1 || ng > kStepNG[kNumStepNG - 1]) return PTG_EINVAL;
   const int nthreads = ((groups + ng - 1) / ng + 31) / 32 * 32;
   if (nthreads > kStepMaxThreadsHost) return PTG_EINVAL;
-  Plan p;
-  cudaError_t e = query_stepper_plan(op->g.nx, op->g.ny, op->sv.precision, kind, cs, ng, nthreads, &p);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return PTG_EINVAL;
+  // with the two-level preconditioner where it applies and fits, else with Jacobi
+  for (bool tl : {true, false}) {
+    if (tl && twolevel_rows(op, op->sv.precision, kind, cs) == 0) continue;
+    Plan p;
+    cudaError_t e = query_stepper_plan(op->g.nx, op->g.ny, op->sv.precision, kind, cs, ng, nthreads,
+                                       twolevel_bytes(op, op->sv.precision, kind, cs, tl), &p);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (p.max_active_clusters <= 0) continue;
+    p.twolevel = tl;
+    op->plan_override[kind] = p;
+    return PTG_OK;
   }
-  if (p.max_active_clusters <= 0) return PTG_EINVAL;
-  op->plan_override[kind] = p;
-  return PTG_OK;
+  return PTG_EINVAL;
 }
 
 int ptg_op_get_plan(ptg_op* op, int kind, int ntasks, int* cs, int* nthreads, int* ng, int* max_active_clusters) {
@@ -364,6 +439,16 @@ int ptg_fe_assemble_operator(ptg_op* op, const double* rho_d, cudaStream_t strea
   out.fload = op->fload;
   PTG_CUDA(launch_assemble(op->g.nx, op->g.ny, op->g.h, op->mat, op->tm.dt, op->dtau, rho_d, op->q_elem,
                            op->dirichlet, out, op->stats, stream));
+  if (op->tl_m) {
+    NodeWeights Ac;
+    Ac.C = out.node[5];
+    Ac.E = out.node[6];
+    Ac.N = out.node[7];
+    Ac.NE = out.node[8];
+    Ac.NW = out.node[9];
+    PTG_CUDA(launch_coarse_setup(op->g.nx, op->g.ny, op->W, op->tl_m, Ac, op->dirichlet, op->tl_Ac, op->tl_band,
+                                 op->tl_X, op->tl_Ainv, stream));
+  }
   return PTG_OK;
 }
 
@@ -563,7 +648,7 @@ void batch_free(ptg_batch* b) {
 }
 
 // Per-design parameters of one phase with cluster size cs.
-StepParams phase_params(const ptg_batch* b, int d, int ph, int cs) {
+StepParams phase_params(const ptg_batch* b, int d, int ph, int cs, bool tl) {
   const ptg_op* op = b->ops[d];
   const BatchBuf& B = b->bufs[d];
   StepParams P;
@@ -576,6 +661,7 @@ StepParams phase_params(const ptg_batch* b, int d, int ph, int cs) {
   P.hist = B.T_hist;
   P.hist_j0 = 0;
   P.hist_rows = op->tm.Nt + 1;
+  twolevel_params(op, b->precision, P, tl);
   const int Ntau = op->tm.Ntau;
   switch (ph) {
     case 0:  P.in_field = B.U_T; P.in_aux = B.U_th; P.out_field = B.F_T; P.out_aux = B.F_th; break;
@@ -618,8 +704,8 @@ std::vector<int2> phase_tasks(const ptg_batch* b, int ph) {
 }
 
 // Install a plan for a phase: validate it for every design, upload the parameter table and
-// the task list, and size the persistent grid.
-int batch_install(ptg_batch* b, int ph, int cs, int ng, int nthreads) {
+// the task list, and size the persistent grid.  tl: two-level preconditioner where it applies.
+int batch_install(ptg_batch* b, int ph, int cs, int ng, int nthreads, bool tl) {
   const int kind = phase_kind(ph);
   size_t smem = 0;
   for (ptg_op* op : b->ops) {
@@ -627,7 +713,8 @@ int batch_install(ptg_batch* b, int ph, int cs, int ng, int nthreads) {
     if (rmax < 2) return PTG_EINVAL;
     const int groups = rmax * (op->W / kGroup);
     if (groups > ng * nthreads) return PTG_EINVAL;
-    smem = std::max(smem, stepper_smem_bytes(op->g.nx, rmax, b->precision == PTG_FP32_REFINE ? 4 : 8));
+    smem = std::max(smem, stepper_smem_bytes(op->g.nx, rmax, b->precision == PTG_FP32_REFINE ? 4 : 8) +
+                              twolevel_bytes(op, b->precision, kind, cs, tl));
   }
   int nclusters = 0;
   if (query_batch_occupancy(b->precision, kind, cs, ng, nthreads, smem, &nclusters) != cudaSuccess || nclusters <= 0) {
@@ -635,7 +722,7 @@ int batch_install(ptg_batch* b, int ph, int cs, int ng, int nthreads) {
     return PTG_EINVAL;
   }
   std::vector<StepParams> table;
-  for (int d = 0; d < (int)b->ops.size(); ++d) table.push_back(phase_params(b, d, ph, cs));
+  for (int d = 0; d < (int)b->ops.size(); ++d) table.push_back(phase_params(b, d, ph, cs, tl));
   std::vector<int2> tasks = phase_tasks(b, ph);
   PhasePlan& pp = b->ph[ph];
   if (!pp.table) PTG_CUDA(cudaMalloc(&pp.table, sizeof(StepParams) * table.size()));
@@ -647,6 +734,7 @@ int batch_install(ptg_batch* b, int ph, int cs, int ng, int nthreads) {
   pp.plan.nthreads = nthreads;
   pp.plan.smem = smem;
   pp.plan.max_active_clusters = nclusters;
+  pp.plan.twolevel = tl;
   pp.ntasks = (int)tasks.size();
   pp.nclusters = std::min(nclusters, pp.ntasks);
   pp.ready = true;
@@ -654,11 +742,10 @@ int batch_install(ptg_batch* b, int ph, int cs, int ng, int nthreads) {
 }
 
 // Default plan of a phase: fewest waves, then the fewest groups per thread, then the largest
-// cluster (the autotuner may replace it).
-int batch_default(ptg_batch* b, int ph) {
-  int best_cs = 0, best_ng = 0, best_nt = 0;
+// cluster; the two-level preconditioner unless it needs more waves (the autotuner may replace
+// the plan).
+long batch_best(ptg_batch* b, int ph, bool tl, int ntasks, int* best_cs, int* best_ng, int* best_nt) {
   long best_waves = -1;
-  const int ntasks = (int)phase_tasks(b, ph).size();
   for (int cs : {16, 8, 4, 2}) {
     for (int ng : kStepNG) {
       int nt = 32;
@@ -669,7 +756,8 @@ int batch_default(ptg_batch* b, int ph) {
         if (rmax < 2) { ok = false; break; }
         const int groups = rmax * (op->W / kGroup);
         nt = std::max(nt, ((groups + ng - 1) / ng + 31) / 32 * 32);
-        smem = std::max(smem, stepper_smem_bytes(op->g.nx, rmax, b->precision == PTG_FP32_REFINE ? 4 : 8));
+        smem = std::max(smem, stepper_smem_bytes(op->g.nx, rmax, b->precision == PTG_FP32_REFINE ? 4 : 8) +
+                                  twolevel_bytes(op, b->precision, phase_kind(ph), cs, tl));
       }
       if (!ok || nt > kStepMaxThreadsHost) continue;
       int ncl = 0;
@@ -678,16 +766,31 @@ int batch_default(ptg_batch* b, int ph) {
         continue;
       }
       const long waves = (ntasks + ncl - 1) / ncl;
-      if (best_waves < 0 || waves < best_waves || (waves == best_waves && ng < best_ng)) {
+      if (best_waves < 0 || waves < best_waves || (waves == best_waves && ng < *best_ng)) {
         best_waves = waves;
-        best_cs = cs;
-        best_ng = ng;
-        best_nt = nt;
+        *best_cs = cs;
+        *best_ng = ng;
+        *best_nt = nt;
       }
     }
   }
-  if (best_waves < 0) return PTG_EINVAL;
-  return batch_install(b, ph, best_cs, best_ng, best_nt);
+  return best_waves;
+}
+
+bool batch_has_twolevel(const ptg_batch* b, int ph) {
+  for (const ptg_op* op : b->ops)
+    if (twolevel_rows(op, b->precision, phase_kind(ph), 1) > 0) return true;
+  return false;
+}
+
+int batch_default(ptg_batch* b, int ph) {
+  const int ntasks = (int)phase_tasks(b, ph).size();
+  int jc = 0, jg = 0, jt = 0, tc = 0, tg = 0, tt = 0;
+  const long wj = batch_best(b, ph, false, ntasks, &jc, &jg, &jt);
+  const long wt = batch_has_twolevel(b, ph) ? batch_best(b, ph, true, ntasks, &tc, &tg, &tt) : -1;
+  if (wj < 0 && wt < 0) return PTG_EINVAL;
+  if (wt >= 0 && (wj < 0 || wt <= wj)) return batch_install(b, ph, tc, tg, tt, true);
+  return batch_install(b, ph, jc, jg, jt, false);
 }
 
 int batch_run(ptg_batch* b, int ph, cudaStream_t stream) {
@@ -831,7 +934,9 @@ int ptg_batch_set_plan(ptg_batch* b, int phase, int cs, int ng, int nthreads) {
     return PTG_EINVAL;
   DeviceGuard dg(b->device);
   std::lock_guard<std::mutex> lk(b->mu);
-  return batch_install(b, phase, cs, ng, nthreads);
+  // with the two-level preconditioner where it applies and fits, else with Jacobi
+  if (batch_has_twolevel(b, phase) && batch_install(b, phase, cs, ng, nthreads, true) == PTG_OK) return PTG_OK;
+  return batch_install(b, phase, cs, ng, nthreads, false);
 }
 
 int ptg_batch_get_plan(ptg_batch* b, int phase, int* cs, int* ng, int* nthreads, int* nclusters) {

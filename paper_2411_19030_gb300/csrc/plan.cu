@@ -1,27 +1,37 @@
 // plan.cu -- launches of the cluster stepper (single task set and persistent multi-design) and
 // occupancy queries for plan selection.
+#include <map>
 #include <mutex>
 #include <unordered_map>
 #include "stepper_launch.cuh"
 
 namespace ptg {
 
-// Function attributes are set once per kernel (and raised when a larger shared-memory
+// Function attributes are set once per (device, kernel) (and raised when a larger shared-memory
 // footprint is requested), so launches made after a warm-up call no attribute API and can be
 // captured into a CUDA graph.
-static cudaError_t configure(const void* k, int cs, size_t smem) {
+cudaError_t configure_kernel(const void* k, size_t smem, bool cluster) {
   static std::mutex mu;
-  static std::unordered_map<const void*, size_t> done;
+  static std::map<std::pair<int, const void*>, size_t> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lk(mu);
-  auto it = done.find(k);
+  auto it = done.find({dev, k});
   if (it != done.end() && it->second >= smem) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  if (e != cudaSuccess) return e;
-  done[k] = smem;
-  (void)cs;
+  if (cluster) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  done[{dev, k}] = smem;
   return cudaSuccess;
+}
+
+static cudaError_t configure(const void* k, int cs, size_t smem) {
+  (void)cs;
+  return configure_kernel(k, smem, true);
 }
 
 static void cluster_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int nclusters, int cs, int nthreads,
@@ -73,14 +83,15 @@ static cudaError_t occupancy(const void* k, int cs, int nthreads, size_t smem, i
   return cudaOccupancyMaxActiveClusters(out, k, &cfg);
 }
 
-cudaError_t query_stepper_plan(int nx, int ny, int precision, int kind, int cs, int ng, int nthreads, Plan* plan) {
+cudaError_t query_stepper_plan(int nx, int ny, int precision, int kind, int cs, int ng, int nthreads, size_t extra_smem,
+                               Plan* plan) {
   StepKernel k = stepper_kernel_for(precision, kind, ng);
   if (!k || nthreads < 32 || nthreads > kStepMaxThreadsHost || nthreads % 32) return cudaErrorInvalidConfiguration;
   plan->cs = cs;
   plan->nthreads = nthreads;
   plan->ng = ng;
   plan->rmax = (ny + 1 + cs - 1) / cs;
-  plan->smem = stepper_smem_bytes(nx, plan->rmax, precision == PTG_FP32_REFINE ? 4 : 8);
+  plan->smem = stepper_smem_bytes(nx, plan->rmax, precision == PTG_FP32_REFINE ? 4 : 8) + extra_smem;
   plan->max_active_clusters = 0;
   if (plan->smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   int n = 0;

@@ -94,7 +94,54 @@ struct StepParams {
   int hist_j0, hist_rows;
   const double* Theta;       // device scalar (adjoint kinds)
   DevStats* stats;
+  // two-level preconditioner of the coarse-step solves (FP32 CG only; Ainv == null: Jacobi)
+  const float* Ainv;         // [ncp][ncp] inverse of the Galerkin coarse matrix (padded layout)
+  int cm, nax, nay;          // aggregate size m and aggregate counts per direction
+  int tl_naj;                // aggregate rows reserved per CTA (0: two-level disabled for this launch)
 };
+
+// Two-level preconditioner of the coarse-step solves: aggregates of m x m nodes (m a multiple
+// of 4, so every aligned group of 4 nodes lies in one aggregate), at most kCoarseMaxAgg per
+// direction; the last aggregate of a direction absorbs the remainder.
+constexpr int kCoarseMaxAgg = 16;
+inline __host__ __device__ int coarse_aggregates(int n_elems, int m) {
+  const int a = (n_elems + 1) / m;
+  return a < 1 ? 1 : a;
+}
+// aggregate row of node row iy
+inline __host__ __device__ int coarse_agg_y(int iy, int m, int nay) {
+  const int a = iy / m;
+  return a < nay - 1 ? a : nay - 1;
+}
+// aggregate column of the group g (nodes 4g-1 .. 4g+2)
+inline __host__ __device__ int coarse_agg_x(int g, int m, int nax) {
+  const int a = g / (m / 4);
+  return a < nax - 1 ? a : nax - 1;
+}
+// aggregate rows [jlo, jhi] touched by the node rows r0 .. r0+R-1 of a slab
+inline __host__ __device__ void coarse_rows_of_slab(int r0, int R, int m, int nay, int& jlo, int& jhi) {
+  jlo = coarse_agg_y(r0, m, nay);
+  jhi = coarse_agg_y(r0 + R - 1, m, nay);
+}
+// Coarse vectors index aggregate (ay, ax) as L = ay * naxp + ax with naxp = nax rounded up to
+// a multiple of 4 (16-byte chunks never straddle two aggregate rows); ncp = nay * naxp is the
+// padded length of a coarse vector and of a row of the dense inverse (zero in the padding).
+inline __host__ __device__ int coarse_row_stride(int nax) { return (nax + 3) / 4 * 4; }
+
+// Shared-memory bytes of the two-level preconditioner for one CTA (naj aggregate rows).
+inline size_t twolevel_smem_bytes(int W, int rmax, int cs, int nax, int nay, int naj) {
+  const size_t naxp = (size_t)coarse_row_stride(nax), ncp = naxp * nay;
+  const size_t groups = (size_t)rmax * (W / kGroup);
+  size_t b = 0;
+  b += (size_t)naj * naxp * ncp * 4;        // rows of Ainv for the CTA's aggregates
+  b += (size_t)cs * ncp * 4;                // restricted partials of every rank
+  b += ncp * 4;                             // their sum over the covering ranks
+  b += (size_t)naj * naxp * 4;              // coarse correction of the CTA's aggregates
+  b += groups * 4;                          // group sums of the restricted vector
+  b += groups * 4;                          // local aggregate of every group
+  b += (size_t)nay * 2 * 4;                 // covering rank range per aggregate row
+  return (b + 15) & ~size_t(15);
+}
 
 // Shared-memory footprint (bytes) of one CTA of the stepper.
 inline size_t stepper_smem_bytes(int nx, int rmax, int real_bytes) {
@@ -117,13 +164,20 @@ struct Plan {
   int cs = 0, nthreads = 0, ng = 0, rmax = 0;
   size_t smem = 0;
   int max_active_clusters = 0;
+  bool twolevel = false;     // coarse kinds: two-level preconditioner (its shared memory is in smem)
 };
 
 cudaError_t launch_stepper(const StepParams& P, const Plan& plan, int precision, int ntasks, cudaStream_t stream);
 cudaError_t launch_stepper_batch(int precision, int kind, const Plan& plan, const StepParams* table, const int2* tasks,
                                  int ntasks, int* queue, int nclusters, cudaStream_t stream);
 cudaError_t query_batch_occupancy(int precision, int kind, int cs, int ng, int nthreads, size_t smem, int* nclusters);
-cudaError_t query_stepper_plan(int nx, int ny, int precision, int kind, int cs, int ng, int nthreads, Plan* plan);
+cudaError_t launch_coarse_setup(int nx, int ny, int W, int m, const NodeWeights& A, const uint8_t* dirichlet,
+                                double* Ac, float* band, float* X, float* Ainv, cudaStream_t stream);
+// Raise a kernel's dynamic shared-memory limit (and allow non-portable cluster sizes) once per
+// device; later calls with no larger footprint make no attribute call.
+cudaError_t configure_kernel(const void* k, size_t smem, bool cluster);
+cudaError_t query_stepper_plan(int nx, int ny, int precision, int kind, int cs, int ng, int nthreads, size_t extra_smem,
+                               Plan* plan);
 
 // Device arrays written by the assembly (see ptg_op in api.cu for their shapes).
 struct AssembleOut {

@@ -163,6 +163,17 @@ struct Stepper {
   int gshift = 0;   // offset from a halo-buffer node to the same node of the global padded arrays
   double* ax64;     // A x64 from the last residual evaluation, rows 0..R-1 (reused by the next step)
   bool ax_valid = false;
+  // two-level preconditioner of the coarse-step solves (FP32 CG): see coarse_restrict_push
+  bool tl = false;
+  bool tl_loaded = false;
+  int aj0 = 0, naj = 0;      // this CTA's aggregate rows [aj0, aj0 + naj)
+  float* tl_ainv = nullptr;  // rows of Ainv for the CTA's aggregates, [naj * naxp][ncp]
+  float* tl_slot = nullptr;  // restricted partials of every rank, [cs][ncp]
+  float* tl_qc = nullptr;    // restricted vector summed over the covering ranks, [ncp]
+  float* tl_ec = nullptr;    // coarse correction Ac^-1 P^T r on the CTA's aggregates, [naj * naxp]
+  float* tl_gs = nullptr;    // group sums of the vector being restricted, [R * G]
+  int* tl_gagg = nullptr;    // local aggregate (row-major in [naj][nax]) of every group, [R * G]
+  int* tl_cov = nullptr;     // first / last rank covering each aggregate row, [nay][2]
 
   __device__ Stepper(const StepParams& P_, cg::cluster_group& cl, RedSmem& rs_, unsigned char* dyn)
       : P(P_), cluster(cl), rs(rs_) {
@@ -196,6 +207,42 @@ struct Stepper {
     }
     if constexpr (kMixed) {
       for (int i = threadIdx.x; i < 3 * elems; i += blockDim.x) eb[i] = 0.f;
+    }
+    if constexpr (kMixed) {
+      if (P.tl_naj > 0) {
+        const int naxp = coarse_row_stride(P.nax), ncp = naxp * P.nay;
+        const int groups = P.rmax * (W / kGroup);
+        float* t = eb + 3 * elems;   // 16-byte aligned: every earlier array is a multiple of 4 words
+        tl_ainv = t;  t += P.tl_naj * naxp * ncp;
+        tl_slot = t;  t += P.cs * ncp;
+        tl_qc = t;    t += ncp;
+        tl_ec = t;    t += P.tl_naj * naxp;
+        tl_gs = t;    t += groups;
+        tl_gagg = reinterpret_cast<int*>(t);  t += groups;
+        tl_cov = reinterpret_cast<int*>(t);
+        int ajhi;
+        coarse_rows_of_slab(sb.r0, sb.R, P.cm, P.nay, aj0, ajhi);
+        naj = ajhi - aj0 + 1;
+        for (int gi = threadIdx.x; gi < sb.ngroups; gi += blockDim.x) {
+          const int lr = gi / sb.G, g = gi - lr * sb.G;
+          tl_gagg[gi] = (coarse_agg_y(sb.r0 + lr, P.cm, P.nay) - aj0) * coarse_row_stride(P.nax) +
+                        coarse_agg_x(g, P.cm, P.nax);
+        }
+        for (int J = threadIdx.x; J < P.nay; J += blockDim.x) {
+          int lo = -1, hi = -1;
+          for (int q = 0; q < P.cs; ++q) {
+            int r0q, Rq, a, bq;
+            slab_rows(P.ny + 1, P.cs, q, r0q, Rq);
+            coarse_rows_of_slab(r0q, Rq, P.cm, P.nay, a, bq);
+            if (J >= a && J <= bq) {
+              if (lo < 0) lo = q;
+              hi = q;
+            }
+          }
+          tl_cov[2 * J] = lo;
+          tl_cov[2 * J + 1] = hi;
+        }
+      }
     }
     x64 = x64b + kSlack;
     b64 = b64b + kSlack - W;   // b64[loc] for loc in own rows (loc >= W)
@@ -237,6 +284,15 @@ struct Stepper {
     step_dt = coarse ? P.dtau : P.dt;
     inv_dt = 1.0 / step_dt;
     ax_valid = false;
+    tl = kMixed && coarse && P.tl_naj > 0 && P.Ainv != nullptr;
+    if (tl && !tl_loaded) {        // rows of the aggregate rows aj0 .. aj0+naj-1 of Ainv, 16-byte copies
+      const int naxp = coarse_row_stride(P.nax), ncp = naxp * P.nay;
+      const int n4 = naj * naxp * ncp / 4;
+      const float4* src = reinterpret_cast<const float4*>(P.Ainv + (size_t)aj0 * naxp * ncp);
+      float4* dst = reinterpret_cast<float4*>(tl_ainv);
+      for (int i = threadIdx.x; i < n4; i += blockDim.x) dst[i] = src[i];
+      tl_loaded = true;
+    }
     const int W = sb.W;
     __syncthreads();
     if constexpr (kMixed) {
@@ -383,6 +439,119 @@ struct Stepper {
     }
   }
 
+  // Two-level preconditioner M^-1 = D^-1 + P Ac^-1 P^T of the coarse-step solves (FP32 CG);
+  // P is piecewise constant on aggregates of m x m nodes aligned to the 4-node groups, so the
+  // restriction P^T v is a sum of group sums and the prolongation adds one value per group.
+  // Every CTA sends its partial sums for the aggregates its slab touches to every CTA of the
+  // cluster (16-byte stores of 4 aggregates); the next cluster barrier (the one of the
+  // following all-reduce) makes them visible.  coarse_gather then adds, chunk by chunk, the
+  // partials of the covering ranks in rank order and multiplies by the CTA's rows of Ac^-1.
+  // In the CG loop the coarse correction follows r by the same recurrence as r,
+  // ec -= alpha Ac^-1 P^T q, so restricting q needs no cluster barrier of its own.
+  __device__ void coarse_restrict_push(const Real (&v)[NG][4]) {
+    const int G = sb.G, m4 = P.cm / 4, nax = P.nax, naxp = coarse_row_stride(nax), ncp = naxp * P.nay;
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      if (loc0[k] < 0) continue;
+      tl_gs[threadIdx.x + k * blockDim.x] = (float)((v[k][0] + v[k][1]) + (v[k][2] + v[k][3]));
+    }
+    __syncthreads();
+    // 4 lanes per local aggregate (16 lanes per chunk of 4 aggregates), each summing every
+    // 4th node row; padding aggregates (ax >= nax) sum to 0
+    const int items = naj * naxp, padded = ((4 * items + 31) / 32) * 32;
+    const int rlast = sb.r0 + sb.R - 1;
+    const int lane = threadIdx.x & 31;
+    for (int t = threadIdx.x; t < padded; t += blockDim.x) {
+      const int item = t >> 2, part = t & 3;
+      const int ajl = item / naxp, ax = item - ajl * naxp;
+      const int ay = aj0 + ajl;
+      float acc = 0.f;
+      if (item < items && ax < nax) {
+        const int y0 = max(ay * P.cm, sb.r0), y1 = min(ay == P.nay - 1 ? P.ny : ay * P.cm + P.cm - 1, rlast);
+        const int g0 = ax * m4, g1 = ax == nax - 1 ? G - 1 : g0 + m4 - 1;
+        for (int iy = y0 + part; iy <= y1; iy += 4) {
+          const float* row = tl_gs + (iy - sb.r0) * G;
+          for (int g = g0; g <= g1; ++g) acc += row[g];
+        }
+      }
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      // the 16 lanes of a chunk: lane (c, p) holds aggregate c's sum; collect all four
+      const int base = lane & 16;
+      float4 chunk;
+      chunk.x = __shfl_sync(0xffffffffu, acc, base + 0);
+      chunk.y = __shfl_sync(0xffffffffu, acc, base + 4);
+      chunk.z = __shfl_sync(0xffffffffu, acc, base + 8);
+      chunk.w = __shfl_sync(0xffffffffu, acc, base + 12);
+      const int item0 = (t & ~15) >> 2;              // first aggregate of the chunk
+      if (item0 < items) {
+        const int ajl0 = item0 / naxp, ax0 = item0 - ajl0 * naxp;
+        const int dst = sb.rank * ncp + (aj0 + ajl0) * naxp + ax0;
+        for (int q = lane & 15; q < sb.cs; q += 16)
+          *reinterpret_cast<float4*>(cluster.map_shared_rank(tl_slot + dst, (unsigned)q)) = chunk;
+      }
+    }
+  }
+
+  // After the cluster barrier that follows coarse_restrict_push: qc = sum over the covering
+  // ranks of the partials (in rank order), then ec = Ac^-1 qc (first == true) or
+  // ec -= alpha Ac^-1 qc on the CTA's aggregate rows (8 lanes per row of Ac^-1, 16-byte loads).
+  __device__ void coarse_gather(bool first, float alpha) {
+    const int naxp = coarse_row_stride(P.nax), ncp = naxp * P.nay;
+    for (int L = threadIdx.x; L < ncp; L += blockDim.x) {
+      const int J = L / naxp;
+      float acc = 0.f;
+      for (int q = tl_cov[2 * J]; q <= tl_cov[2 * J + 1]; ++q) acc += tl_slot[q * ncp + L];
+      tl_qc[L] = acc;
+    }
+    __syncthreads();
+    const int nrows = naj * naxp, n4 = ncp / 4;
+    const int padded = ((8 * nrows + 31) / 32) * 32;
+    const float4* q4 = reinterpret_cast<const float4*>(tl_qc);
+    for (int t = threadIdx.x; t < padded; t += blockDim.x) {
+      const int row = t >> 3, part = t & 7;
+      float acc = 0.f;
+      if (row < nrows) {
+        const float4* a4 = reinterpret_cast<const float4*>(tl_ainv + (size_t)row * ncp);
+        float ax = 0.f, ay = 0.f, az = 0.f, aw = 0.f;
+#pragma unroll 4
+        for (int L = part; L < n4; L += 8) {
+          const float4 a = a4[L], r = q4[L];
+          ax = fmaf(a.x, r.x, ax);
+          ay = fmaf(a.y, r.y, ay);
+          az = fmaf(a.z, r.z, az);
+          aw = fmaf(a.w, r.w, aw);
+        }
+        acc = (ax + ay) + (az + aw);
+      }
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+      if (part == 0 && row < nrows) tl_ec[row] = first ? acc : fmaf(-alpha, acc, tl_ec[row]);
+    }
+    __syncthreads();
+  }
+
+  // z = D^-1 r + P ec on the owned nodes (0 off the unknowns), written to zbuf; returns the
+  // local part of (r, z).
+  __device__ Real prolong_precondition(const Real (&r)[NG][4]) {
+    Real rz = Real(0);
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+      if (l0 < 0) continue;
+      const Real e = (Real)tl_ec[tl_gagg[threadIdx.x + k * blockDim.x]];
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) {
+        const Real di = dinv[l0 + j];
+        const Real z = di != Real(0) ? fma(di, r[k][j], e) : Real(0);
+        zbuf[l0 + j] = z;
+        rz = fma(r[k][j], z, rz);
+      }
+    }
+    return rz;
+  }
+
   // Jacobi-preconditioned CG in precision Real on A d = r, where r (given per node) is the FP64
   // residual scaled to unit 2-norm; on return x64 += unscale * d.  Stops when ||r||^2 <= target2
   // (scaled units) or at the iteration limit; returns the iteration count.  All CG scalars and
@@ -397,12 +566,20 @@ struct Stepper {
         const int l0 = loc0[k];
 #pragma unroll
         for (int j = 0; j < kGroup; ++j) { d[k][j] = Real(0); p[k][j] = Real(0); q[k][j] = Real(0); }
-        if (l0 < 0) continue;
+        if (l0 < 0 || tl) continue;
 #pragma unroll
         for (int j = 0; j < kGroup; ++j) {
           const Real z = dinv[l0 + j] * r[k][j];
           zbuf[l0 + j] = z;
           v[0] = fma(r[k][j], z, v[0]);
+        }
+      }
+      if constexpr (kMixed) {
+        if (tl) {
+          coarse_restrict_push(r);
+          cluster_sync_all();
+          coarse_gather(true, 0.f);
+          v[0] = prolong_precondition(r);
         }
       }
       __syncthreads();
@@ -432,9 +609,15 @@ struct Stepper {
           pq[0] = fma(p[k][j], q[k][j], pq[0]);
         }
       }
+      if constexpr (kMixed) {
+        if (tl) coarse_restrict_push(q);     // visible after the all-reduce's cluster barrier
+      }
       const Real rz_c = rz;
       allreduce<Real, 1>(pq, [rz_c](Real* t) { t[0] = rz_c / t[0]; });
       const Real alpha = pq[0];
+      if constexpr (kMixed) {
+        if (tl) coarse_gather(false, alpha);
+      }
       // d += alpha p, r -= alpha q, z = D^-1 r; (r, z), (r, r) and beta = (r, z)_new / (r, z)
       Real v[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
@@ -445,11 +628,16 @@ struct Stepper {
         for (int j = 0; j < kGroup; ++j) {
           d[k][j] = fma(alpha, p[k][j], d[k][j]);
           r[k][j] = fma(-alpha, q[k][j], r[k][j]);
-          const Real z = dinv[l0 + j] * r[k][j];
-          zbuf[l0 + j] = z;
-          v[0] = fma(r[k][j], z, v[0]);
           v[1] = fma(r[k][j], r[k][j], v[1]);
+          if (!tl) {
+            const Real z = dinv[l0 + j] * r[k][j];
+            zbuf[l0 + j] = z;
+            v[0] = fma(r[k][j], z, v[0]);
+          }
         }
+      }
+      if constexpr (kMixed) {
+        if (tl) v[0] = prolong_precondition(r);
       }
       __syncthreads();
       push_halos(zbuf, sb, cluster);
@@ -778,7 +966,7 @@ __device__ __forceinline__ void run_task(Stepper<Real, NG>& st, int task) {
 }
 
 template <class Real, int NG, int KIND>
-__global__ void __launch_bounds__(kStepMaxThreads) stepper_kernel(const __grid_constant__ StepParams P) {
+__global__ void __launch_bounds__(kStepMaxThreads, 1) stepper_kernel(const __grid_constant__ StepParams P) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   __shared__ RedSmem rs;
   cg::cluster_group cluster = cg::this_cluster();
@@ -796,7 +984,7 @@ __global__ void __launch_bounds__(kStepMaxThreads) stepper_kernel(const __grid_c
 // the cluster size, the block size and NG; shared memory is carved per task for the design's
 // geometry from the largest footprint that the launch reserves.
 template <class Real, int NG, int KIND>
-__global__ void __launch_bounds__(kStepMaxThreads) stepper_batch_kernel(const StepParams* __restrict__ table,
+__global__ void __launch_bounds__(kStepMaxThreads, 1) stepper_batch_kernel(const StepParams* __restrict__ table,
                                                                        const int2* __restrict__ tasks, int ntasks,
                                                                        int* __restrict__ queue) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];

@@ -52,7 +52,7 @@ CASES = ["ragged_table1", "plain32", "paper_p20", "m1", "one_slice", "tiny"]
 
 @pytest.mark.parametrize("name", CASES)
 def test_sequential_pass_fp64(name):
-    """Alg. 3 lines 6-7 (chained F_pri and F_adj) vs the oracle's sequential pass."""
+    """Initialisation of Alg. 3 (chained F_pri and F_adj) vs the oracle's sequential pass."""
     prob, rho = case_problem(name)
     oop = OracleOp(prob, rho)
     seq = o_sequential(oop)
@@ -106,7 +106,7 @@ def _oneshot_compare(name, precision, tol_t, tol_g, **solve_kw):
 
 @pytest.mark.parametrize("name", CASES)
 def test_oneshot_pass_fp64(name):
-    """Alg. 3 lines 9-12 from a warm start of a nearby design: every intermediate of a2-a6."""
+    """Iteration body of Alg. 3 from a warm start of a nearby design: every intermediate of a2-a6."""
     _oneshot_compare(name, "fp64", FP64_TOL, FP64_TOL)
 
 

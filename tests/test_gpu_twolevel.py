@@ -1,0 +1,84 @@
+"""Two-level preconditioner of the coarse-step solves (FP32 CG, aggregation coarse space):
+the one-shot pass with it matches the oracle for every cluster size (the restricted residual
+is summed across the CTAs of a cluster whose slabs split aggregate rows differently), and it
+needs fewer CG iterations than Jacobi alone on the coarse and correction solves."""
+from __future__ import annotations
+
+import pytest
+import torch
+
+import workloads as W
+from oracle import Operator as OracleOp
+from oracle import coarse_states_from_sequential, oneshot_pass as o_oneshot
+from paper_2411_19030_gb300 import PassBuffers, oneshot_pass
+from tests.gpu_helpers import MIXED_G_TOL, MIXED_T_TOL, assert_close, dev, ensure_built, gpu_operator, host
+from tests.problems import make_problem
+
+pytestmark = pytest.mark.gpu
+
+COARSE_KINDS = (1, 2, 4, 5)   # coarse_primal, correct_primal, coarse_adjoint, correct_adjoint
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+@pytest.fixture(scope="module")
+def case():
+    """64 x 48 elements (16 x 12 aggregates of 4 x 4 nodes, the last ones larger), 64 steps in
+    8 slices, warm start of a nearby design."""
+    prob = make_problem(64, 48, Nt=64, Ntau=8, dt=1 / 64)
+    rho = W.rho_uniform(64, 48, 11, 0.05, 0.95)
+    rho_old = W.rho_warm_perturb(rho, seed=12, amp=0.05)
+    U_old, V_old, _ = coarse_states_from_sequential(OracleOp(prob, rho_old))
+    ref = o_oneshot(OracleOp(prob, rho), U_old, V_old)
+    return prob, rho, U_old, V_old, ref
+
+
+def run_pass(case, twolevel, cs=0):
+    prob, rho, U_old, V_old, _ = case
+    op = gpu_operator(prob, "fp32_refine", rtol=1e-10, twolevel=twolevel)
+    if cs:
+        for kind in COARSE_KINDS:
+            op.set_plan(kind, cs, 1 if cs >= 8 else 2)
+    buf = PassBuffers(op)
+    buf.U_T.copy_(dev(U_old[0])); buf.U_th.copy_(dev(U_old[1]))
+    buf.V_l.copy_(dev(V_old[0])); buf.V_g.copy_(dev(V_old[1]))
+    op.assemble(dev(rho))
+    Theta, grad = oneshot_pass(op, buf)
+    torch.cuda.synchronize()
+    return op, buf, Theta, grad
+
+
+def check(case, op, buf, Theta, grad):
+    ref = case[4]
+    assert_close("G_T", host(buf.G_T), ref["G_pri_old"][0], MIXED_T_TOL)
+    assert_close("U_new", host(buf.U_T_new), ref["U"][0], MIXED_T_TOL)
+    assert_close("T_hist", host(buf.T_hist), ref["T_hist"], MIXED_T_TOL)
+    assert_close("Theta", host(Theta), [ref["Theta"]], MIXED_T_TOL)
+    assert_close("G_lam", host(buf.G_l), ref["G_adj_old"][0], MIXED_G_TOL)
+    assert_close("V_lam", host(buf.V_l_new), ref["V"][0], MIXED_G_TOL)
+    assert_close("grad", host(grad), ref["grad"], MIXED_G_TOL)
+    assert op.stats()["status"] == 0
+
+
+@pytest.mark.parametrize("cs", [2, 4, 8, 16])
+def test_twolevel_pass_matches_oracle_for_every_cluster_size(case, cs):
+    op, buf, Theta, grad = run_pass(case, True, cs)
+    assert op.plan(1, 1)["cs"] == cs
+    check(case, op, buf, Theta, grad)
+
+
+def test_twolevel_reduces_coarse_iterations(case):
+    on = run_pass(case, True)
+    off = run_pass(case, False)
+    check(case, *on)
+    check(case, *off)
+    k_on, k_off = on[0].stats()["by_kind"], off[0].stats()["by_kind"]
+    for name in ("coarse_primal", "correct_primal", "coarse_adjoint", "correct_adjoint"):
+        assert k_on[name]["solves"] == k_off[name]["solves"] > 0
+        assert k_on[name]["cg_iters"] < 0.8 * k_off[name]["cg_iters"], (name, k_on[name], k_off[name])
+    for name in ("fine_primal", "fine_adjoint"):      # fine solves keep Jacobi (the adjoint
+        assert k_on[name]["solves"] == k_off[name]["solves"]  # source moves with Theta's rounding)
+        assert abs(k_on[name]["cg_iters"] - k_off[name]["cg_iters"]) <= 0.01 * k_off[name]["cg_iters"]
