@@ -24,17 +24,21 @@ Pins (``tests/test_oracle_*.py``, run with ``-m "not gpu"``): the separable-eige
 closed form, the discrete energy balance, the dense all-at-once solve, central
 finite differences of the gradient, Parareal's exactness after N_tau iterations,
 the M = 1 and N_tau = 1 degenerate cases, the one-shot fixed point, mirror symmetry,
-the constant-field objective identity and the homogeneity of Theta in q.
+the constant-field objective identity and the homogeneity of Theta in q; for the
+modified objective of Sec. 7.1, Theta~ = Theta^p and the gradient identity
+grad Theta = Theta^(1-p)/p grad Theta~; for PLT (G = 0, Sec. 7), its fixed point and its
+exactness after N_tau iterations.
 The one-shot estimate for a design that differs from the warm-start design has
 no closed form: beyond the fixed point it is "parity unpinned" (it is the literal
 algorithm, checked only for consistency with the pinned pieces it is made of).
 """
 from .fem import Material, Problem, element_matrices, simp, assemble
-from .stepping import Operator, objective, sequential_primal, sequential_adjoint, sequential_pass, sensitivity_term
+from .stepping import (Operator, objective, objective_from_modified, sequential_primal, sequential_adjoint,
+                       sequential_pass, sensitivity_term)
 from .parareal import (F_pri, G_pri, F_adj, G_adj, oneshot_pass, parareal, coarse_states_from_sequential)
 
 __all__ = [
     "Material", "Problem", "element_matrices", "simp", "assemble",
-    "Operator", "objective", "sequential_primal", "sequential_adjoint", "sequential_pass", "sensitivity_term",
+    "Operator", "objective", "objective_from_modified", "sequential_primal", "sequential_adjoint", "sequential_pass", "sensitivity_term",
     "F_pri", "G_pri", "F_adj", "G_adj", "oneshot_pass", "parareal", "coarse_states_from_sequential",
 ]

@@ -43,6 +43,9 @@ class Problem:
              q_time[j] * (sum over elements of q_e * int N_i)
     q_time   time factor of the source at t_0..t_Nt
     T0       initial temperature (length Nn), zero by default (Eq. 2.1b)
+    modified_objective  False: the power mean Theta of Eq. 2.11.  True: the modified
+             objective Theta~ = Theta^p of Sec. 7.1, a plain sum over the steps, whose
+             adjoint source is p/Ne T^(p-1) (the form the PLT comparison uses)
     """
     nx: int
     ny: int
@@ -56,6 +59,7 @@ class Problem:
     q_elem: np.ndarray | None = None
     q_time: np.ndarray | None = None
     T0: np.ndarray | None = None
+    modified_objective: bool = False
     extra: dict = field(default_factory=dict)
 
     @property

@@ -28,7 +28,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .stepping import Operator, pnorm_p, sensitivity_term, sequential_pass
+from .stepping import Operator, accumulate_theta, sensitivity_term, sequential_pass
 
 
 # ------------------------------------------------------------------ propagators
@@ -37,13 +37,13 @@ def F_pri(op: Operator, s: int, T: np.ndarray, theta: float):
     """Fine primal propagator over slice s.  Returns (T_end, theta_end, inter) where
     inter[i] is T_{Ms+1+i}, i = 0..M-1 (the last one equals T_end)."""
     prob = op.prob
-    M, p = prob.M, prob.p
+    M = prob.M
     inter = np.zeros((M, prob.Nn))
     T = np.asarray(T, dtype=np.float64).copy()
     for i in range(M):
         j = M * s + 1 + i
         T = op.step_primal(T, j, prob.dt)
-        theta = (theta ** p + pnorm_p(T, p) / (prob.Nt * prob.Ne)) ** (1.0 / p)
+        theta = accumulate_theta(prob, theta, T, prob.Nt)
         inter[i] = T
     return T, theta, inter
 
@@ -51,10 +51,9 @@ def F_pri(op: Operator, s: int, T: np.ndarray, theta: float):
 def G_pri(op: Operator, s: int, T: np.ndarray, theta: float):
     """Coarse primal propagator over slice s: one step of size dtau."""
     prob = op.prob
-    p = prob.p
     j_end = prob.M * (s + 1)
     T_new = op.step_primal(np.asarray(T, dtype=np.float64), j_end, prob.dtau)
-    theta_new = (theta ** p + pnorm_p(T_new, p) / (prob.Ntau * prob.Ne)) ** (1.0 / p)
+    theta_new = accumulate_theta(prob, theta, T_new, prob.Ntau)
     return T_new, theta_new
 
 

@@ -5,9 +5,13 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 Primal (Eq. 2.7):   C (T_j - T_{j-1}) / dt + K T_j = q_j,  j = 1..Nt,  T_0 given.
 Objective (Eq. 2.11): Theta = ( sum_j ||T_j||_p^p / (Nt Ne) )^(1/p); the p-norm runs
                     over every node (Dirichlet nodes contribute 0) and the divisor
-                    is the element count, exactly as printed.
+                    is the element count, exactly as printed.  The cumulative objective
+                    theta_j = (theta_{j-1}^p + ||T_j||_p^p / (Nt Ne))^(1/p) (Sec. 4.4).
+                    Modified objective (Sec. 7.1): Theta~ = Theta^p = sum_j ||T_j||_p^p / (Nt Ne),
+                    cumulative theta~_j = theta~_{j-1} + ||T_j||_p^p / (Nt Ne).
 Adjoint (Eq. 4.4-4.6): lambda_{Nt+1} = 0,
-                    C (lambda_j - lambda_{j+1}) / dt + K lambda_j = Theta^(1-p)/Ne T_j^(p-1).
+                    C (lambda_j - lambda_{j+1}) / dt + K lambda_j = Theta^(1-p)/Ne T_j^(p-1);
+                    for Theta~ the source is p/Ne T_j^(p-1) (Sec. 7.1).
 Gradient (Eq. 4.7): dTheta/drho = -(1/Nt) sum_j lambda_j^T (dC/drho (T_j - T_{j-1})/dt + dK/drho T_j).
 
 Linear solves: the free-node block of (C/dt + K) is factored once per step size
@@ -67,9 +71,30 @@ class Operator:
 
     def step_adjoint(self, lam_next: np.ndarray, T_j: np.ndarray, Theta: float, dt: float) -> np.ndarray:
         """One reverse adjoint solve (Alg. 2, first line)."""
-        p = self.prob.p
-        src = Theta ** (1.0 - p) / self.prob.Ne * T_j ** (p - 1.0)
+        src = adjoint_source_scale(self.prob, Theta) * T_j ** (self.prob.p - 1.0)
         return self.solve(dt, self.C @ lam_next / dt + src)
+
+
+def accumulate_theta(prob: Problem, theta_prev: float, T: np.ndarray, N: int) -> float:
+    """One update of the cumulative objective with the divisor N Ne (N = Nt for H and F,
+    N_tau for G): the power mean of Sec. 4.4, or the plain sum of Sec. 7.1 for Theta~."""
+    inc = pnorm_p(T, prob.p) / (N * prob.Ne)
+    if prob.modified_objective:
+        return theta_prev + inc
+    return (theta_prev ** prob.p + inc) ** (1.0 / prob.p)
+
+
+def adjoint_source_scale(prob: Problem, Theta: float) -> float:
+    """Factor of T_j^(p-1) in the adjoint source: Theta^(1-p)/Ne (Eq. 4.6) or p/Ne (Sec. 7.1)."""
+    if prob.modified_objective:
+        return prob.p / prob.Ne
+    return Theta ** (1.0 - prob.p) / prob.Ne
+
+
+def objective_from_modified(Theta_mod: float, grad_mod: np.ndarray, p: float):
+    """Sec. 7.1: Theta = Theta~^(1/p) and grad Theta = Theta^(1-p)/p grad Theta~."""
+    Theta = Theta_mod ** (1.0 / p)
+    return Theta, Theta ** (1.0 - p) / p * np.asarray(grad_mod, dtype=np.float64)
 
 
 def pnorm_p(T: np.ndarray, p: float) -> float:
@@ -78,9 +103,9 @@ def pnorm_p(T: np.ndarray, p: float) -> float:
 
 
 def objective(T_hist: np.ndarray, prob: Problem) -> float:
-    """Eq. 2.11 on a history T_hist[0..Nt]; T_0 is not part of the sum."""
-    s = sum(pnorm_p(T_hist[j], prob.p) for j in range(1, prob.Nt + 1))
-    return (s / (prob.Nt * prob.Ne)) ** (1.0 / prob.p)
+    """Eq. 2.11 (or Theta~ of Sec. 7.1) on a history T_hist[0..Nt]; T_0 is not part of the sum."""
+    s = sum(pnorm_p(T_hist[j], prob.p) for j in range(1, prob.Nt + 1)) / (prob.Nt * prob.Ne)
+    return s if prob.modified_objective else s ** (1.0 / prob.p)
 
 
 def sensitivity_term(op: Operator, lam: np.ndarray, T_j: np.ndarray, T_jm1: np.ndarray, dt: float) -> np.ndarray:
@@ -100,14 +125,14 @@ def sensitivity_term(op: Operator, lam: np.ndarray, T_j: np.ndarray, T_jm1: np.n
 def sequential_primal(op: Operator):
     """Alg. 1 applied Nt times from T_0: returns (T_hist[Nt+1, Nn], theta[Nt+1])."""
     prob = op.prob
-    Nt, p = prob.Nt, prob.p
+    Nt = prob.Nt
     T = np.zeros(prob.Nn) if prob.T0 is None else np.asarray(prob.T0, dtype=np.float64).copy()
     T_hist = np.zeros((Nt + 1, prob.Nn))
     theta = np.zeros(Nt + 1)
     T_hist[0] = T
     for j in range(1, Nt + 1):
         T = op.step_primal(T, j, prob.dt)
-        theta[j] = (theta[j - 1] ** p + pnorm_p(T, p) / (Nt * prob.Ne)) ** (1.0 / p)
+        theta[j] = accumulate_theta(prob, theta[j - 1], T, Nt)
         T_hist[j] = T
     return T_hist, theta
 

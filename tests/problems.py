@@ -8,7 +8,7 @@ from oracle import Material, Problem
 
 
 def make_problem(nx, ny=None, *, Nt, Ntau=1, dt=None, p=8.0, material="simp_k", sink="left",
-                 q_elem=None, q_time=None, T0=None, h=None) -> Problem:
+                 q_elem=None, q_time=None, T0=None, h=None, modified_objective=False) -> Problem:
     ny = nx if ny is None else ny
     h = 1.0 / max(nx, ny) if h is None else h
     dt = 1.0 / Nt if dt is None else dt
@@ -26,7 +26,8 @@ def make_problem(nx, ny=None, *, Nt, Ntau=1, dt=None, p=8.0, material="simp_k", 
     else:
         raise ValueError(sink)
     return Problem(nx=nx, ny=ny, h=h, material=mat, Nt=Nt, dt=dt, Ntau=Ntau, p=p,
-                   dirichlet=dir_mask, q_elem=q_elem, q_time=q_time, T0=T0)
+                   dirichlet=dir_mask, q_elem=q_elem, q_time=q_time, T0=T0,
+                   modified_objective=modified_objective)
 
 
 def workload_problem(name: str, Ntau=None) -> tuple[Problem, np.ndarray]:
