@@ -86,7 +86,7 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -223,62 +223,86 @@ def run_gpu(args):
     value = job_throughput(dof_steps, world, ms)
     kind_ms = {k: float(v / args.steps) for k, v in zip(kinds, per_kind)}
 
-    # end to end through the public API with host buffers: H2D of rho, D2H of Theta and grad
-    rho_host = torch.from_numpy(rho_np).pin_memory()
-    out_host = torch.empty(1 + n * n, dtype=torch.float64).pin_memory()
-    e2e_ms = []
-    for _ in range(max(2, min(args.steps, 5))):
-        flush.fill_(1.0)
+    if args.extras:
+        # end to end through the public API with host buffers: H2D of rho, D2H of Theta and grad
+        rho_host = torch.from_numpy(rho_np).pin_memory()
+        out_host = torch.empty(1 + n * n, dtype=torch.float64).pin_memory()
+        e2e_ms = []
+        for _ in range(max(2, min(args.steps, 5))):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rho.copy_(rho_host, non_blocking=True)
+            op.assemble(rho)
+            Theta, grad = oneshot_pass(op, buf)
+            out_host[:1].copy_(Theta, non_blocking=True)
+            out_host[1:].copy_(grad, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            e2e_ms.append(a.elapsed_time(b))
+        e2e = float(np.mean(e2e_ms))
+
+        # comparator: sequential FP64 GPU time stepping of the same design (bounded repetitions)
+        seq_buf = PassBuffers(seq_op)
+        seq_op.assemble(rho)
+        seq_op.reset_stats()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        rho.copy_(rho_host, non_blocking=True)
-        op.assemble(rho)
-        Theta, grad = oneshot_pass(op, buf)
-        out_host[:1].copy_(Theta, non_blocking=True)
-        out_host[1:].copy_(grad, non_blocking=True)
+        Theta_seq, grad_seq = sequential_pass(seq_op, seq_buf)
         b.record(stream)
         b.synchronize()
-        e2e_ms.append(a.elapsed_time(b))
-    e2e = float(np.mean(e2e_ms))
+        seq_ms = a.elapsed_time(b)
+        seq_stats = seq_op.stats()
+        # accuracy of the one-shot estimate and of the mixed arithmetic against sequential FP64
+        Theta_os = float(buf.U_th_new[Ntau].item())
+        g_os = buf.V_g_new[0]
+        err_theta = abs(Theta_os - float(Theta_seq.item())) / abs(float(Theta_seq.item()))
+        err_grad = float(torch.linalg.norm(g_os - grad_seq) / torch.linalg.norm(grad_seq))
+        # error of the precision pattern: the same one-shot pass in FP64 (CG and all sums FP64,
+        # rtol 1e-13; this path matches the CPU oracle to 1e-10 in the parity tests), untimed
+        prec = {}
+        if args.precision != "fp64":
+            f64_op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink,
+                              solve=SolveConfig("fp64", rtol=1e-13, cg_iters_max=8000, refine_max=8), device=local)
+            f64_buf = PassBuffers(f64_op)
+            for a_, b_ in ((f64_buf.U_T, buf.U_T), (f64_buf.U_th, buf.U_th), (f64_buf.V_l, buf.V_l), (f64_buf.V_g, buf.V_g)):
+                a_.copy_(b_)
+            f64_op.assemble(rho)
+            Th64, g64 = oneshot_pass(f64_op, f64_buf)
+            torch.cuda.synchronize()
 
-    # comparator: sequential FP64 GPU time stepping of the same design (bounded repetitions)
-    seq_buf = PassBuffers(seq_op)
-    seq_op.assemble(rho)
-    seq_op.reset_stats()
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    Theta_seq, grad_seq = sequential_pass(seq_op, seq_buf)
-    b.record(stream)
-    b.synchronize()
-    seq_ms = a.elapsed_time(b)
-    seq_stats = seq_op.stats()
-    # accuracy of the one-shot estimate and of the mixed arithmetic against sequential FP64
-    Theta_os = float(buf.U_th_new[Ntau].item())
-    g_os = buf.V_g_new[0]
-    err_theta = abs(Theta_os - float(Theta_seq.item())) / abs(float(Theta_seq.item()))
-    err_grad = float(torch.linalg.norm(g_os - grad_seq) / torch.linalg.norm(grad_seq))
-    # error of the precision pattern: the same one-shot pass in FP64 (CG and all sums FP64,
-    # rtol 1e-13; this path matches the CPU oracle to 1e-10 in the parity tests), untimed
-    prec = {}
-    if args.precision != "fp64":
-        f64_op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink,
-                          solve=SolveConfig("fp64", rtol=1e-13, cg_iters_max=8000, refine_max=8), device=local)
-        f64_buf = PassBuffers(f64_op)
-        for a_, b_ in ((f64_buf.U_T, buf.U_T), (f64_buf.U_th, buf.U_th), (f64_buf.V_l, buf.V_l), (f64_buf.V_g, buf.V_g)):
-            a_.copy_(b_)
-        f64_op.assemble(rho)
-        Th64, g64 = oneshot_pass(f64_op, f64_buf)
-        torch.cuda.synchronize()
+            def relmax(a, b):
+                return float((a - b).abs().max() / b.abs().max())
+            prec = {"T_hist_rel_max": relmax(buf.T_hist, f64_buf.T_hist),
+                    "Theta_rel": abs(Theta_os - float(Th64.item())) / abs(float(Th64.item())),
+                    "grad_rel_max": relmax(g_os, g64),
+                    "targets": {"temperature": 1e-6, "sensitivity": 1e-5}}
+            del f64_buf
 
-        def relmax(a, b):
-            return float((a - b).abs().max() / b.abs().max())
-        prec = {"T_hist_rel_max": relmax(buf.T_hist, f64_buf.T_hist),
-                "Theta_rel": abs(Theta_os - float(Th64.item())) / abs(float(Th64.item())),
-                "grad_rel_max": relmax(g_os, g64),
-                "targets": {"temperature": 1e-6, "sensitivity": 1e-5}}
-        del f64_buf
+        # Sec. 7.3 bottleneck probe: the same pass with the coarse propagators identically zero
+        # (G_pri = G_adj = 0, the corrections copy F), timed like the main steps
+        g0_ms = []
+        for i in range(args.warmup + args.steps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            op.assemble(rho)
+            oneshot_pass(op, buf, plt=True)
+            b.record(stream)
+            b.synchronize()
+            if i >= args.warmup:
+                g0_ms.append(a.elapsed_time(b))
+        g0 = slowest_rank_ms(float(np.mean(g0_ms)), device)
+        probe = {"what": "Sec. 7.3: the one-shot pass with G_pri = G_adj = 0 (PLT-style corrections) at N_tau = 32",
+                 "oneshot_ms": ms, "g_zero_ms": g0, "sequential_fp64_ms": seq_ms,
+                 "speedup_oneshot": seq_ms / ms, "speedup_g_zero": seq_ms / g0,
+                 "paper_context": "MATLAB on 32 CPU threads: 3.81x (one-shot) vs 10.8x (G = 0) over its sequential run"}
+    else:
+        e2e = seq_ms = None
+        seq_stats, prec, probe = {}, {}, None
+        err_theta = err_grad = None
 
     roof = roofline(kind_ms, stats, w, N_free, args)
     line = {
@@ -297,16 +321,18 @@ def run_gpu(args):
                "by_kind": {k: {"cg_per_solve": v["cg_iters"] / max(1, v["solves"]),
                                "refine_per_solve": v["refinements"] / max(1, v["solves"])}
                            for k, v in stats["by_kind"].items() if v["solves"]}},
-        "comparator_sequential_fp64": {"ms": seq_ms, "value": dof_steps / (seq_ms * 1e-3), "unit": UNIT,
-                                       "speedup_of_oneshot": seq_ms / ms,
-                                       "cg_iters": seq_stats["cg_iters"], "solves": seq_stats["solves"]},
+        "comparator_sequential_fp64": None if seq_ms is None else {
+            "ms": seq_ms, "value": dof_steps / (seq_ms * 1e-3), "unit": UNIT, "speedup_of_oneshot": seq_ms / ms,
+            "cg_iters": seq_stats["cg_iters"], "solves": seq_stats["solves"]},
         "accuracy_vs_sequential_fp64": {"Theta_rel": err_theta, "grad_rel_l2": err_grad,
                                         "note": "one-shot estimate (warm start from a design 1% away) vs the exact "
                                                 "sequential result of the current design"},
         "accuracy_mixed_vs_fp64_oneshot": prec,
-        "e2e": {"value": world * dof_steps / (e2e * 1e-3), "unit": UNIT, "ms": e2e,
-                "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": (1 + n * n) * 8},
-        "gpu_launches": 9 * args.steps,   # assembly 3 kernels + 6 stepper launches per pass
+        "bottleneck_probe": probe,
+        "e2e": None if e2e is None else {"value": world * dof_steps / (e2e * 1e-3), "unit": UNIT, "ms": e2e,
+                                         "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": (1 + n * n) * 8},
+        # per pass: assembly 3 kernels (+ 4 for the two-level coarse set-up) + 6 stepper launches
+        "gpu_launches": (9 + (4 if args.precision == "fp32_refine" and args.twolevel else 0)) * args.steps,
         "roofline": roof,
         "clocks": clk.summary(),
     }
@@ -319,9 +345,10 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-# DRAM bytes per launch from the committed ncu capture
+# DRAM bytes per launch (read + write) from the committed ncu capture of the 128x128 pass
 # (profiles/stepper_fine_and_correct_oneshot128.md); a kernel changed since has no entry.
-NCU_TRAFFIC_BYTES = {"fine_primal": 6.446848e6 + 80.372480e6, "correct_primal": 10.695168e6}
+NCU_TRAFFIC_BYTES = {"fine_primal": 7.166720e6 + 80.248320e6, "correct_primal": 10.990080e6 + 0.0,
+                     "correct_adjoint": 23.498496e6 + 0.007424e6}
 
 
 def roofline(kind_ms: dict, stats: dict, w: dict, N_free: int, args) -> dict:
@@ -439,7 +466,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="fp32_refine", choices=["fp32_refine", "fp64"])
@@ -447,6 +474,9 @@ def main():
     ap.add_argument("--no-twolevel", dest="twolevel", action="store_false",
                     help="Jacobi only on the coarse-step solves (default: two-level preconditioner)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="time the passes only: no end-to-end run, comparator, accuracy checks or G = 0 probe "
+                         "(for profiling the launch sequence of the timed steps)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     if args.impl == "reference":

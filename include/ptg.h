@@ -66,6 +66,10 @@ extern "C" {
 #define PTG_PRIMAL   1
 #define PTG_ADJOINT -1
 
+/* objectives (ptg_time.objective) */
+#define PTG_OBJ_POWER_MEAN 0   /* Theta of Eq. 2.11 with the cumulative power mean of Sec. 4.4 */
+#define PTG_OBJ_MODIFIED   1   /* Theta~ = Theta^p of Sec. 7.1: cumulative plain sum, adjoint source p/Ne T^(p-1) */
+
 /* ------------------------------------------------------------------ problem description */
 typedef struct {
     int nx, ny;        /* elements per side, each >= 2 */
@@ -82,6 +86,8 @@ typedef struct {
     int Ntau;          /* Parareal slices; must divide Nt (Sec. 4.2) */
     double dt;         /* fine step; the coarse step is dtau = (Nt/Ntau) dt */
     double p;          /* power-mean exponent, an even integer >= 2 (Eq. 2.11) */
+    int objective;     /* PTG_OBJ_POWER_MEAN or PTG_OBJ_MODIFIED; every theta / g quantity of the
+                          passes then refers to that objective */
 } ptg_time;
 
 typedef struct {
@@ -200,6 +206,8 @@ int ptg_coarse_sweep(ptg_op* op, int direction, const double* X_field, const dou
 
 /*
  * a4 -- Eq. 4.9 / 4.14: the sequential correction sweep of one Parareal iteration.
+ *   G_field == G_aux == NULL selects the PLT variant of Sec. 7 (coarse propagators identically
+ *   zero, Eq. 7.1-7.2): u_{s+1} = F[s] and v_s = F[s], a copy with no solve.
  *   PTG_PRIMAL: X_new[0] (U_T[0], U_theta[0]) holds u_0 on entry; for s = 0..Ntau-1,
  *      u_{s+1} = G_pri(s, u_s) + F[s] - G_old[s], and the corrected T_{M(s+1)} is written to
  *      T_hist row M(s+1) (T_hist may be NULL).  Theta = X_aux[Ntau] afterwards.
@@ -214,6 +222,15 @@ int ptg_parareal_correct(ptg_op* op, int direction,
                          const double* G_field, const double* G_aux,
                          double* X_field, double* X_aux,
                          double* T_hist, const double* Theta_d, cudaStream_t stream);
+
+/*
+ * Sec. 7.1: the power-mean objective and its gradient from the modified objective's,
+ *   Theta = Theta~^(1/p),  grad_e = Theta^(1-p)/p grad~_e,  e = 0..Ne-1.
+ * Theta_mod_d, Theta_d: device scalars; grad_mod_d, grad_d: [Ne] device arrays.  The outputs
+ * may alias the inputs.  Theta~ must be positive (a zero objective has no power-mean gradient).
+ */
+int ptg_objective_from_modified(ptg_op* op, const double* Theta_mod_d, const double* grad_mod_d,
+                                double* Theta_d, double* grad_d, cudaStream_t stream);
 
 /*
  * a5 -- Alg. 2 and Sec. 4.4: the fine adjoint propagator F_adj of slices s0..s0+ns-1, each
@@ -278,7 +295,8 @@ int ptg_sensitivities_noalloc(int nx, int ny, double h, int Nt, double dt, const
  * if it wants, the warm start) through the pointers returned by ptg_batch_buffers.
  * Phases: 0 fine primal, 1 coarse primal, 2 primal correction, 3 fine adjoint, 4 coarse
  * adjoint, 5 adjoint correction (the one-shot pass, the iteration body of Alg. 3); 6 sequential primal,
- * 7 sequential adjoint (the initialisation of Alg. 3, writing the warm start U/V).
+ * 7 sequential adjoint (the initialisation of Alg. 3, writing the warm start U/V); 8 and 9 the
+ * primal and adjoint corrections of the PLT variant (G = 0, Sec. 7).
  * Every call is asynchronous on `stream`; after a first call of each phase (which uploads the
  * plan) the launch sequence can be captured into a CUDA graph.
  */
@@ -302,8 +320,11 @@ int ptg_batch_assemble(ptg_batch* b, cudaStream_t stream);
  * Theta = U_theta[Ntau], gradient = V_g row 0. */
 int ptg_batch_sequential_pass(ptg_batch* b, cudaStream_t stream);
 /* The iteration body of Alg. 3 for every design from the warm start U/V: writes *_new and T_hist;
- * Theta = U_theta_new[Ntau], gradient = V_g_new row 0. */
-int ptg_batch_oneshot_pass(ptg_batch* b, cudaStream_t stream);
+ * Theta = U_theta_new[Ntau], gradient = V_g_new row 0.  variant PTG_PARAREAL, or PTG_PLT for
+ * coarse propagators identically zero (Sec. 7: the corrections copy F, G_* are not written). */
+#define PTG_PARAREAL 0
+#define PTG_PLT      1
+int ptg_batch_oneshot_pass(ptg_batch* b, int variant, cudaStream_t stream);
 /* Copy the one-shot result (*_new) into the warm start for the next design iteration. */
 int ptg_batch_commit(ptg_batch* b, cudaStream_t stream);
 /* One phase alone (its inputs must be current), e.g. to time it. */

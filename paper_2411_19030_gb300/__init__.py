@@ -7,10 +7,11 @@ fallback: every step of the pass runs in the library's CUDA kernels.
 """
 from .api import (KIND_NAMES, Operator, PassBuffers, PTGError, SolveConfig, oneshot_pass,
                   sequential_pass)
-from ._ffi import (PTG_ADJOINT, PTG_FP32_REFINE, PTG_FP64, PTG_PRIMAL, PTG_SLICES_CHAINED,
-                   PTG_SLICES_PARALLEL)
+from ._ffi import (PTG_ADJOINT, PTG_FP32_REFINE, PTG_FP64, PTG_OBJ_MODIFIED, PTG_OBJ_POWER_MEAN, PTG_PARAREAL,
+                   PTG_PLT, PTG_PRIMAL, PTG_SLICES_CHAINED, PTG_SLICES_PARALLEL)
 
 __all__ = [
     "KIND_NAMES", "Operator", "PassBuffers", "PTGError", "SolveConfig", "oneshot_pass", "sequential_pass",
-    "PTG_ADJOINT", "PTG_FP32_REFINE", "PTG_FP64", "PTG_PRIMAL", "PTG_SLICES_CHAINED", "PTG_SLICES_PARALLEL",
+    "PTG_ADJOINT", "PTG_FP32_REFINE", "PTG_FP64", "PTG_OBJ_MODIFIED", "PTG_OBJ_POWER_MEAN", "PTG_PARAREAL",
+    "PTG_PLT", "PTG_PRIMAL", "PTG_SLICES_CHAINED", "PTG_SLICES_PARALLEL",
 ]

@@ -12,6 +12,8 @@ PTG_OK, PTG_EINVAL, PTG_ENOCONV, PTG_ENONFINITE, PTG_ETIMEOUT, PTG_ECUDA, PTG_EN
 PTG_FP64, PTG_FP32_REFINE = 0, 1
 PTG_SLICES_PARALLEL, PTG_SLICES_CHAINED = 0, 1
 PTG_PRIMAL, PTG_ADJOINT = 1, -1
+PTG_OBJ_POWER_MEAN, PTG_OBJ_MODIFIED = 0, 1
+PTG_PARAREAL, PTG_PLT = 0, 1
 
 ERROR_NAMES = {0: "PTG_OK", -1: "PTG_EINVAL", -2: "PTG_ENOCONV", -3: "PTG_ENONFINITE",
                -4: "PTG_ETIMEOUT", -5: "PTG_ECUDA", -6: "PTG_ENOMEM"}
@@ -27,7 +29,7 @@ class ptg_material(ctypes.Structure):
 
 
 class ptg_time(ctypes.Structure):
-    _fields_ = [("Nt", c_int), ("Ntau", c_int), ("dt", c_double), ("p", c_double)]
+    _fields_ = [("Nt", c_int), ("Ntau", c_int), ("dt", c_double), ("p", c_double), ("objective", c_int)]
 
 
 class ptg_solve(ctypes.Structure):
@@ -63,6 +65,7 @@ SIGNATURES = {
     "ptg_fine_propagate_slices": (c_int, [_P, c_int, c_int, c_int, _P, _P, _P, c_int, c_int, _P, _P, _P]),
     "ptg_coarse_sweep": (c_int, [_P, c_int, _P, _P, _P, _P, _P, _P, _P]),
     "ptg_parareal_correct": (c_int, [_P, c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "ptg_objective_from_modified": (c_int, [_P, _P, _P, _P, _P, _P]),
     "ptg_adjoint_sweep": (c_int, [_P, c_int, c_int, c_int, _P, c_int, c_int, _P, _P, _P, _P, _P, _P]),
     "ptg_sensitivities": (c_int, [_P, _P, c_int, c_int, _P, c_int, c_int, _P, _P]),
     "ptg_sensitivities_noalloc": (c_int, [c_int, c_int, c_double, c_int, c_double, POINTER(ptg_material), _P, _P,
@@ -72,7 +75,7 @@ SIGNATURES = {
     "ptg_batch_buffers": (c_int, [_P, c_int, POINTER(ptg_pass_buffers)]),
     "ptg_batch_assemble": (c_int, [_P, _P]),
     "ptg_batch_sequential_pass": (c_int, [_P, _P]),
-    "ptg_batch_oneshot_pass": (c_int, [_P, _P]),
+    "ptg_batch_oneshot_pass": (c_int, [_P, c_int, _P]),
     "ptg_batch_commit": (c_int, [_P, _P]),
     "ptg_batch_run_phase": (c_int, [_P, c_int, _P]),
     "ptg_batch_set_plan": (c_int, [_P, c_int, c_int, c_int, c_int]),

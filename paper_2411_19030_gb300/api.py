@@ -15,8 +15,8 @@ import numpy as np
 import torch
 
 from . import _ffi
-from ._ffi import (PTG_ADJOINT, PTG_FP32_REFINE, PTG_FP64, PTG_PRIMAL, PTG_SLICES_CHAINED,
-                   PTG_SLICES_PARALLEL)
+from ._ffi import (PTG_ADJOINT, PTG_FP32_REFINE, PTG_FP64, PTG_OBJ_MODIFIED, PTG_OBJ_POWER_MEAN, PTG_PRIMAL,
+                   PTG_SLICES_CHAINED, PTG_SLICES_PARALLEL)
 
 KIND_NAMES = ("fine_primal", "coarse_primal", "correct_primal", "fine_adjoint", "coarse_adjoint", "correct_adjoint")
 
@@ -62,11 +62,14 @@ class Operator:
     material: dict with k0, kmin, pk, c0, cmin, pc (Eq. 2.5-2.6).
     dirichlet: uint8 array [Nn] marking the sink nodes.
     q_elem / q_time: separable source (element density [Ne], time factor [Nt+1]).
+    objective: "power_mean" (Theta, Eq. 2.11) or "modified" (Theta~ = Theta^p, Sec. 7.1); every
+    theta / g quantity of the passes refers to it (objective_from_modified converts back).
     """
 
     def __init__(self, nx: int, ny: int, h: float, material: dict, Nt: int, Ntau: int, dt: float, p: float,
                  dirichlet: np.ndarray, q_elem: np.ndarray | None = None, q_time: np.ndarray | None = None,
-                 solve: SolveConfig | None = None, device: int | torch.device | None = None):
+                 solve: SolveConfig | None = None, device: int | torch.device | None = None,
+                 objective: str = "power_mean"):
         lib = _lib()
         solve = solve or SolveConfig()
         dev = torch.device("cuda", torch.cuda.current_device() if device is None else
@@ -83,7 +86,8 @@ class Operator:
         g = _ffi.ptg_grid(nx, ny, h)
         m = _ffi.ptg_material(material["k0"], material["kmin"], material["pk"],
                               material["c0"], material["cmin"], material["pc"])
-        t = _ffi.ptg_time(Nt, Ntau, dt, p)
+        self.objective = objective
+        t = _ffi.ptg_time(Nt, Ntau, dt, p, {"power_mean": PTG_OBJ_POWER_MEAN, "modified": PTG_OBJ_MODIFIED}[objective])
         prec = {"fp64": PTG_FP64, "fp32_refine": PTG_FP32_REFINE}[solve.precision]
         s = _ffi.ptg_solve(prec, solve.rtol, solve.inner_rtol, solve.cg_iters_max, solve.refine_max,
                            int(solve.twolevel))
@@ -152,7 +156,8 @@ class Operator:
 
     def parareal_correct(self, direction, F_field, F_aux, G_field, G_aux, X_field, X_aux, T_hist=None, Theta=None,
                          stream=None):
-        """a4: the sequential correction sweep (forward or reverse)."""
+        """a4: the sequential correction sweep (forward or reverse); G_field = G_aux = None is the
+        PLT variant (coarse propagators identically zero, Sec. 7)."""
         _check(_lib().ptg_parareal_correct(self._h, direction, _ptr(F_field, self.device), _ptr(F_aux, self.device),
                                            _ptr(G_field, self.device), _ptr(G_aux, self.device),
                                            _ptr(X_field, self.device), _ptr(X_aux, self.device),
@@ -167,6 +172,12 @@ class Operator:
                                         T_hist.shape[0], _ptr(Theta, self.device), _ptr(V_lam, self.device),
                                         _ptr(V_g, self.device), _ptr(F_lam, self.device), _ptr(F_g, self.device),
                                         self._stream(stream)), "ptg_adjoint_sweep")
+
+    def objective_from_modified(self, Theta_mod, grad_mod, Theta, grad, stream=None):
+        """Sec. 7.1: Theta = Theta~^(1/p), grad = Theta^(1-p)/p grad~ (outputs may alias inputs)."""
+        _check(_lib().ptg_objective_from_modified(self._h, _ptr(Theta_mod, self.device), _ptr(grad_mod, self.device),
+                                                  _ptr(Theta, self.device), _ptr(grad, self.device),
+                                                  self._stream(stream)), "ptg_objective_from_modified")
 
     def sensitivities(self, lam_hist, j0, j1, T_hist, grad, hist_j0=0, stream=None):
         """a6: grad += -(1/Nt) sum_j lambda_j^T dR_j/drho (Eq. 4.7)."""
@@ -249,19 +260,24 @@ def sequential_pass(op: Operator, buf: PassBuffers, T0: torch.Tensor | None = No
 def oneshot_pass(op: Operator, buf: PassBuffers, stream=None, plt: bool = False):
     """Iteration body of Alg. 3: one modified forward Parareal iteration and one reverse vanilla
     Parareal iteration from the warm start (buf.U_*, buf.V_*).  The corrected states go to
-    buf.U_*_new / buf.V_*_new, the history to buf.T_hist; returns (Theta, grad) views."""
+    buf.U_*_new / buf.V_*_new, the history to buf.T_hist; returns (Theta, grad) views.
+    plt=True: the coarse propagators are identically zero (Sec. 7): no coarse sweep, and the
+    corrections copy the fine results (buf.G_* are left untouched)."""
     Ntau = op.Ntau
     # primal: F and G of every slice on the guess, then the sequential correction
     op.fine_propagate_slices(buf.U_T, buf.U_th, buf.F_T, buf.F_th, T_hist=buf.T_hist, stream=stream)
-    op.coarse_sweep(PTG_PRIMAL, buf.U_T, buf.U_th, buf.G_T, buf.G_th, stream=stream)
+    if not plt:
+        op.coarse_sweep(PTG_PRIMAL, buf.U_T, buf.U_th, buf.G_T, buf.G_th, stream=stream)
     buf.U_T_new[0].copy_(buf.U_T[0])
     buf.U_th_new[0].copy_(buf.U_th[0])
-    op.parareal_correct(PTG_PRIMAL, buf.F_T, buf.F_th, buf.G_T, buf.G_th, buf.U_T_new, buf.U_th_new,
-                        T_hist=buf.T_hist, stream=stream)
+    op.parareal_correct(PTG_PRIMAL, buf.F_T, buf.F_th, None if plt else buf.G_T, None if plt else buf.G_th,
+                        buf.U_T_new, buf.U_th_new, T_hist=buf.T_hist, stream=stream)
     Theta = buf.U_th_new[Ntau:Ntau + 1]
     # adjoint: F and G of every slice on the guess, then the reverse correction
     op.adjoint_sweep(buf.T_hist, Theta, buf.V_l, buf.V_g, buf.F_l, buf.F_g, stream=stream)
-    op.coarse_sweep(PTG_ADJOINT, buf.V_l, buf.V_g, buf.G_l, buf.G_g, T_hist=buf.T_hist, Theta=Theta, stream=stream)
-    op.parareal_correct(PTG_ADJOINT, buf.F_l, buf.F_g, buf.G_l, buf.G_g, buf.V_l_new, buf.V_g_new,
-                        T_hist=buf.T_hist, Theta=Theta, stream=stream)
+    if not plt:
+        op.coarse_sweep(PTG_ADJOINT, buf.V_l, buf.V_g, buf.G_l, buf.G_g, T_hist=buf.T_hist, Theta=Theta,
+                        stream=stream)
+    op.parareal_correct(PTG_ADJOINT, buf.F_l, buf.F_g, None if plt else buf.G_l, None if plt else buf.G_g,
+                        buf.V_l_new, buf.V_g_new, T_hist=buf.T_hist, Theta=Theta, stream=stream)
     return Theta, buf.V_g_new[0]

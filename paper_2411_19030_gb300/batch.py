@@ -14,6 +14,7 @@ import ctypes
 import torch
 
 from . import _ffi
+from ._ffi import PTG_PARAREAL, PTG_PLT
 from .api import Operator, _check, _lib
 
 PHASES = ("fine_primal", "coarse_primal", "correct_primal", "fine_adjoint", "coarse_adjoint", "correct_adjoint",
@@ -85,8 +86,11 @@ class Batch:
     def sequential_pass(self, stream=None):
         _check(_lib().ptg_batch_sequential_pass(self._h, self._stream(stream)), "ptg_batch_sequential_pass")
 
-    def oneshot_pass(self, stream=None):
-        _check(_lib().ptg_batch_oneshot_pass(self._h, self._stream(stream)), "ptg_batch_oneshot_pass")
+    def oneshot_pass(self, stream=None, plt: bool = False):
+        """The iteration body of Alg. 3 for every design; plt=True: coarse propagators
+        identically zero (Sec. 7)."""
+        _check(_lib().ptg_batch_oneshot_pass(self._h, PTG_PLT if plt else PTG_PARAREAL, self._stream(stream)),
+               "ptg_batch_oneshot_pass")
 
     def commit(self, stream=None):
         _check(_lib().ptg_batch_commit(self._h, self._stream(stream)), "ptg_batch_commit")

@@ -33,6 +33,7 @@ struct ptg_op {
   double *q_elem = nullptr, *q_time = nullptr;
   uint8_t* dirichlet = nullptr;
   double* sens_partial = nullptr;
+  double* scratch = nullptr;   // [2] small device scalars
   int sens_chunks = 0;
   DevStats* stats = nullptr;
   cudaStream_t last_stream = nullptr;
@@ -208,6 +209,7 @@ void base_params(const ptg_op* op, StepParams& P) {
   P.q_time = op->q_time;
   P.dirichlet = op->dirichlet;
   P.stats = op->stats;
+  P.objective = op->tm.objective;
   P.hist_rows = 0;
 }
 
@@ -217,7 +219,7 @@ int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream) {
   if (rc != PTG_OK) return rc;
   P.cs = plan.cs;
   P.rmax = plan.rmax;
-  twolevel_params(op, op->sv.precision, P, plan.twolevel);
+  twolevel_params(op, op->sv.precision, P, plan.twolevel && !P.plt);
   op->last_stream = stream;
   PTG_CUDA(launch_stepper(P, plan, op->sv.precision, ntasks, stream));
   return PTG_OK;
@@ -227,7 +229,7 @@ bool window_covers(int j0, int rows, int lo, int hi) { return lo >= j0 && hi < j
 
 void free_all(ptg_op* op) {
   void* ptrs[] = {op->k, op->c, op->dk, op->dc, op->wE, op->nodew, op->fload,
-                  op->q_elem, op->q_time, op->dirichlet, op->sens_partial, op->stats,
+                  op->q_elem, op->q_time, op->dirichlet, op->sens_partial, op->scratch, op->stats,
                   op->tl_Ac, op->tl_band, op->tl_X, op->tl_Ainv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -256,6 +258,7 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
   if (time->Nt < 1 || time->Ntau < 1 || time->Nt % time->Ntau != 0 || !(time->dt > 0.0)) return PTG_EINVAL;
   const double p = time->p;
   if (!(p >= 2.0 && p <= 64.0) || p != (double)(int)p || ((int)p) % 2 != 0) return PTG_EINVAL;
+  if (time->objective != PTG_OBJ_POWER_MEAN && time->objective != PTG_OBJ_MODIFIED) return PTG_EINVAL;
   if (solve->precision != PTG_FP64 && solve->precision != PTG_FP32_REFINE) return PTG_EINVAL;
   if (!(solve->rtol > 0.0) || solve->cg_iters_max < 1 || solve->refine_max < 1 || !(solve->inner_rtol >= 0.0))
     return PTG_EINVAL;
@@ -315,6 +318,7 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
     A(&op->tl_X, nc * nc * sizeof(float));
     A(&op->tl_Ainv, ncp * ncp * sizeof(float));
   }
+  A(&op->scratch, 2 * sizeof(double));
   A(&op->stats, sizeof(DevStats));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -501,7 +505,8 @@ int ptg_coarse_sweep(ptg_op* op, int direction, const double* X_field, const dou
 int ptg_parareal_correct(ptg_op* op, int direction, const double* F_field, const double* F_aux, const double* G_field,
                          const double* G_aux, double* X_field, double* X_aux, double* T_hist, const double* Theta_d,
                          cudaStream_t stream) {
-  if (!op || !F_field || !F_aux || !G_field || !G_aux || !X_field || !X_aux) return PTG_EINVAL;
+  if (!op || !F_field || !F_aux || !X_field || !X_aux) return PTG_EINVAL;
+  if ((G_field == nullptr) != (G_aux == nullptr)) return PTG_EINVAL;   // both NULL: PLT (G = 0)
   if (direction != PTG_PRIMAL && direction != PTG_ADJOINT) return PTG_EINVAL;
   if (direction == PTG_ADJOINT && (!T_hist || !Theta_d)) return PTG_EINVAL;
   DeviceGuard dg(op->device);
@@ -514,6 +519,7 @@ int ptg_parareal_correct(ptg_op* op, int direction, const double* F_field, const
   P.F_aux = F_aux;
   P.G_field = G_field;
   P.G_aux = G_aux;
+  P.plt = G_field == nullptr;
   P.out_field = X_field;
   P.out_aux = X_aux;
   P.hist = T_hist;
@@ -521,6 +527,16 @@ int ptg_parareal_correct(ptg_op* op, int direction, const double* F_field, const
   P.hist_rows = T_hist ? op->tm.Nt + 1 : 0;
   P.Theta = Theta_d;
   return run(op, P, 1, stream);
+}
+
+int ptg_objective_from_modified(ptg_op* op, const double* Theta_mod_d, const double* grad_mod_d, double* Theta_d,
+                                double* grad_d, cudaStream_t stream) {
+  if (!op || !Theta_mod_d || !grad_mod_d || !Theta_d || !grad_d) return PTG_EINVAL;
+  DeviceGuard dg(op->device);
+  op->last_stream = stream;
+  PTG_CUDA(launch_objective_from_modified(op->Ne, op->tm.p, Theta_mod_d, grad_mod_d, Theta_d, grad_d, op->scratch,
+                                          stream));
+  return PTG_OK;
 }
 
 int ptg_adjoint_sweep(ptg_op* op, int schedule, int s0, int ns, const double* T_hist, int hist_j0, int hist_rows,
@@ -599,7 +615,9 @@ int ptg_reset_stats(ptg_op* op, cudaStream_t stream) {
 
 namespace {
 
-constexpr int kPhases = 8;   // 0..5: one-shot kinds; 6: sequential primal; 7: sequential adjoint
+// 0..5: one-shot kinds; 6: sequential primal; 7: sequential adjoint; 8, 9: primal and adjoint
+// corrections of the PLT variant (G = 0)
+constexpr int kPhases = 10;
 
 struct BatchBuf {
   double *T_hist, *U_T, *U_th, *V_l, *V_g, *U_T_new, *U_th_new, *V_l_new, *V_g_new;
@@ -615,7 +633,12 @@ struct PhasePlan {
   bool ready = false;
 };
 
-int phase_kind(int ph) { return ph < 6 ? ph : (ph == 6 ? KIND_FINE_PRI : KIND_FINE_ADJ); }
+int phase_kind(int ph) {
+  if (ph < 6) return ph;
+  if (ph == 6) return KIND_FINE_PRI;
+  if (ph == 7) return KIND_FINE_ADJ;
+  return ph == 8 ? KIND_CORRECT_PRI : KIND_CORRECT_ADJ;
+}
 
 }  // namespace
 
@@ -686,6 +709,14 @@ StepParams phase_params(const ptg_batch* b, int d, int ph, int cs, bool tl) {
     case 7:   // sequential adjoint: v_Ntau = 0 in V[Ntau], checkpoints into V[0..Ntau-1]
       P.chained = 1; P.in_field = B.V_l; P.in_aux = B.V_g; P.out_field = B.V_l; P.out_aux = B.V_g;
       P.Theta = B.U_th + Ntau;
+      break;
+    case 8:   // PLT primal correction: U_new[s+1] = F[s]
+      P.plt = 1; P.in_field = B.U_T; P.in_aux = B.U_th; P.out_field = B.U_T_new; P.out_aux = B.U_th_new;
+      P.F_field = B.F_T; P.F_aux = B.F_th;
+      break;
+    case 9:   // PLT adjoint correction: V_new[s] = F[s]
+      P.plt = 1; P.out_field = B.V_l_new; P.out_aux = B.V_g_new; P.F_field = B.F_l; P.F_aux = B.F_g;
+      P.Theta = B.U_th_new + Ntau;
       break;
   }
   return P;
@@ -778,6 +809,7 @@ long batch_best(ptg_batch* b, int ph, bool tl, int ntasks, int* best_cs, int* be
 }
 
 bool batch_has_twolevel(const ptg_batch* b, int ph) {
+  if (ph >= 8) return false;   // the PLT corrections solve nothing
   for (const ptg_op* op : b->ops)
     if (twolevel_rows(op, b->precision, phase_kind(ph), 1) > 0) return true;
   return false;
@@ -896,11 +928,15 @@ int ptg_batch_sequential_pass(ptg_batch* b, cudaStream_t stream) {
   return rc;
 }
 
-int ptg_batch_oneshot_pass(ptg_batch* b, cudaStream_t stream) {
-  if (!b) return PTG_EINVAL;
+int ptg_batch_oneshot_pass(ptg_batch* b, int variant, cudaStream_t stream) {
+  if (!b || (variant != PTG_PARAREAL && variant != PTG_PLT)) return PTG_EINVAL;
   DeviceGuard dg(b->device);
-  for (int ph = 0; ph < 6; ++ph) {
-    int rc = batch_run(b, ph, stream);
+  static const int parareal[] = {0, 1, 2, 3, 4, 5};
+  static const int plt[] = {0, 8, 3, 9};
+  const int* phases = variant == PTG_PLT ? plt : parareal;
+  const int n = variant == PTG_PLT ? 4 : 6;
+  for (int i = 0; i < n; ++i) {
+    int rc = batch_run(b, phases[i], stream);
     if (rc != PTG_OK) return rc;
   }
   return PTG_OK;

@@ -199,6 +199,32 @@ __global__ void sens_reduce_kernel(int Ne, int nchunks, double inv_nt, const dou
   grad[e] -= inv_nt * s;
 }
 
+// Sec. 7.1: Theta = Theta~^(1/p) and the factor Theta^(1-p)/p of the gradient (one thread;
+// the factor goes to scratch so that Theta may alias Theta~), then grad = factor * grad~.
+__global__ void modified_objective_scalar_kernel(double p, const double* __restrict__ Theta_mod, double* Theta,
+                                                 double* __restrict__ scratch) {
+  const double Tm = *Theta_mod;
+  const double T = pow(Tm, 1.0 / p);
+  scratch[0] = pow(T, 1.0 - p) / p;
+  *Theta = T;
+}
+
+__global__ void modified_objective_grad_kernel(int Ne, const double* __restrict__ scratch, const double* grad_mod,
+                                               double* grad) {
+  const double f = scratch[0];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Ne; e += gridDim.x * blockDim.x) grad[e] = f * grad_mod[e];
+}
+
+cudaError_t launch_objective_from_modified(int Ne, double p, const double* Theta_mod, const double* grad_mod,
+                                          double* Theta, double* grad, double* scratch, cudaStream_t stream) {
+  modified_objective_scalar_kernel<<<1, 1, 0, stream>>>(p, Theta_mod, Theta, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int blocks = (Ne + 255) / 256 < 1216 ? (Ne + 255) / 256 : 1216;
+  modified_objective_grad_kernel<<<blocks, 256, 0, stream>>>(Ne, scratch, grad_mod, grad);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sensitivities(int nx, int ny, int Nt, double h, double dt, int has_dc, const double* dk,
                                  const double* dc, const double* lam, int j0, int j1, const double* T, int hist_j0,
                                  double* partial, int nchunks, double* grad, cudaStream_t stream) {

@@ -94,6 +94,8 @@ struct StepParams {
   int hist_j0, hist_rows;
   const double* Theta;       // device scalar (adjoint kinds)
   DevStats* stats;
+  int objective;             // PTG_OBJ_POWER_MEAN or PTG_OBJ_MODIFIED
+  int plt;                   // correction kinds: coarse propagators identically zero (copy F)
   // two-level preconditioner of the coarse-step solves (FP32 CG only; Ainv == null: Jacobi)
   const float* Ainv;         // [ncp][ncp] inverse of the Galerkin coarse matrix (padded layout)
   int cm, nax, nay;          // aggregate size m and aggregate counts per direction
@@ -190,6 +192,8 @@ cudaError_t launch_assemble(int nx, int ny, double h, const ptg_material& m, dou
                             const double* q_elem, const uint8_t* dirichlet, const AssembleOut& out, DevStats* st,
                             cudaStream_t stream);
 
+cudaError_t launch_objective_from_modified(int Ne, double p, const double* Theta_mod, const double* grad_mod,
+                                          double* Theta, double* grad, double* scratch, cudaStream_t stream);
 cudaError_t launch_sensitivities(int nx, int ny, int Nt, double h, double dt, int has_dc, const double* dk,
                                  const double* dc, const double* lam, int j0, int j1, const double* T, int hist_j0,
                                  double* partial, int nchunks, double* grad, cudaStream_t stream);

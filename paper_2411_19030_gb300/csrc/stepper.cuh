@@ -793,6 +793,33 @@ struct Stepper {
     }
   }
 
+  // Cumulative objective update with increment sp / N (N Ne the divisor, sp = ||T||_p^p / Ne
+  // folded by the caller): the power mean of Sec. 4.4, or the plain sum of the modified
+  // objective Theta~ = Theta^p (Sec. 7.1).
+  __device__ __forceinline__ double accumulate_theta(double theta, double inc) const {
+    return P.objective == PTG_OBJ_MODIFIED ? theta + inc : pow(ipow(theta, P.p_int) + inc, 1.0 / P.p);
+  }
+  // Factor of T^(p-1) in the adjoint source: Theta^(1-p)/Ne (Eq. 4.6) or p/Ne (Sec. 7.1).
+  __device__ __forceinline__ double adjoint_scale(double Theta) const {
+    return (P.objective == PTG_OBJ_MODIFIED ? P.p : pow(Theta, 1.0 - P.p)) / (double)P.Ne;
+  }
+
+  // Copy the own rows of a node field (stride Nn) from src to dst (and to hist if given).
+  __device__ void copy_field(const double* src, double* dst, double* hist) {
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+      if (l0 < 0) continue;
+      for (int j = 0; j < kGroup; ++j) {
+        const int g = gnode(l0, j);
+        if (g < 0) continue;
+        const double v = src[g];
+        dst[g] = v;
+        if (hist) hist[g] = v;
+      }
+    }
+  }
+
   // ------------------------------------------------------------------ task bodies
   __device__ void fine_primal(int task) {
     const int sa = P.chained ? P.s0 : P.s0 + task;
@@ -811,7 +838,7 @@ struct Stepper {
         build_rhs([&](int g) { return qj * P.fload[g]; });
         solve(j, true);
         const double sp = pnorm_p();
-        if (threadIdx.x == 0) theta = pow(ipow(theta, P.p_int) + sp * inv_norm, 1.0 / P.p);  // used by thread 0 only
+        if (threadIdx.x == 0) theta = accumulate_theta(theta, sp * inv_norm);  // used by thread 0 only
         if (double* row = hist_row(j)) store_x64(row);
       }
       store_x64(P.out_field + (size_t)s * P.Nn);
@@ -830,12 +857,11 @@ struct Stepper {
     solve(j);
     const double sp = pnorm_p();
     store_x64(P.out_field + (size_t)s * P.Nn);
-    if (threadIdx.x == 0 && sb.rank == 0)
-      P.out_aux[s] = pow(ipow(theta0, P.p_int) + sp / ((double)P.Ntau * (double)P.Ne), 1.0 / P.p);
+    if (threadIdx.x == 0 && sb.rank == 0) P.out_aux[s] = accumulate_theta(theta0, sp / ((double)P.Ntau * (double)P.Ne));
   }
 
   __device__ void correct_primal() {
-    set_operator(true);
+    if (!P.plt) set_operator(true);
     double theta;
     if (P.in_field) {                           // u_0 taken from the guess states, copied to X[0]
       load_x64(P.in_field);
@@ -847,6 +873,13 @@ struct Stepper {
       theta = P.out_aux[0];
     }
     if (double* row = hist_row(0)) store_x64(row);
+    if (P.plt) {                                // G = 0 (Sec. 7, Eq. 7.2): u_{s+1} = F(u_s^old)
+      for (int s = 0; s < P.Ntau; ++s) {
+        copy_field(P.F_field + (size_t)s * P.Nn, P.out_field + (size_t)(s + 1) * P.Nn, hist_row(P.M * (s + 1)));
+        if (threadIdx.x == 0 && sb.rank == 0) P.out_aux[s + 1] = P.F_aux[s];
+      }
+      return;
+    }
     for (int s = 0; s < P.Ntau; ++s) {
       const int j = P.M * (s + 1);
       const double qj = P.q_time[j];
@@ -857,7 +890,7 @@ struct Stepper {
       apply_correction(P.F_field + (size_t)s * P.Nn, P.G_field + (size_t)s * P.Nn,
                        P.out_field + (size_t)(s + 1) * P.Nn, hist_row(j));
       if (threadIdx.x == 0) {                    // theta is needed by thread 0 only
-        const double theta_g = pow(ipow(theta, P.p_int) + sp / ((double)P.Ntau * (double)P.Ne), 1.0 / P.p);
+        const double theta_g = accumulate_theta(theta, sp / ((double)P.Ntau * (double)P.Ne));
         theta = (theta_g + P.F_aux[s]) - P.G_aux[s];
         if (sb.rank == 0) P.out_aux[s + 1] = theta;
       }
@@ -870,7 +903,7 @@ struct Stepper {
     const int s_hi = P.chained ? P.s0 + P.ns - 1 : s_lo;
     const int M = P.M;
     const double Theta = *P.Theta;
-    const double scale = pow(Theta, 1.0 - P.p) / (double)P.Ne;
+    const double scale = adjoint_scale(Theta);
     set_operator(false);
     load_x64(P.in_field + (size_t)(s_hi + 1) * P.Nn);
     const double* gsrc = P.in_aux + (size_t)(s_hi + 1) * P.Ne;
@@ -898,7 +931,7 @@ struct Stepper {
     const int kidx = P.M * s + 1;
     const int kprev = max(kidx - P.M, 0);
     const double Theta = *P.Theta;
-    const double scale = pow(Theta, 1.0 - P.p) / (double)P.Ne;
+    const double scale = adjoint_scale(Theta);
     const double* Tk = P.hist + (size_t)kidx * P.Nn;
     const double* Tkm = P.hist + (size_t)kprev * P.Nn;
     set_operator(true);
@@ -912,8 +945,8 @@ struct Stepper {
 
   __device__ void correct_adjoint() {
     const double Theta = *P.Theta;
-    const double scale = pow(Theta, 1.0 - P.p) / (double)P.Ne;
-    set_operator(true);
+    const double scale = adjoint_scale(Theta);
+    if (!P.plt) set_operator(true);
     // v_Ntau = 0
     {
       double* Xl = P.out_field + (size_t)P.Ntau * P.Nn;
@@ -929,6 +962,16 @@ struct Stepper {
       const int er = min(sb.R, P.ny - sb.r0);
       double* Xg = P.out_aux + (size_t)P.Ntau * P.Ne;
       for (int t = threadIdx.x; t < (er > 0 ? er * P.nx : 0); t += blockDim.x) Xg[sb.r0 * P.nx + t] = 0.0;
+    }
+    if (P.plt) {                                // G = 0 (Sec. 7, Eq. 7.2): v_s = F(v_{s+1}^old)
+      const int er = min(sb.R, P.ny - sb.r0);
+      for (int s = P.Ntau - 1; s >= 0; --s) {
+        copy_field(P.F_field + (size_t)s * P.Nn, P.out_field + (size_t)s * P.Nn, nullptr);
+        const double* Fg = P.F_aux + (size_t)s * P.Ne + sb.r0 * P.nx;
+        double* Xg = P.out_aux + (size_t)s * P.Ne + sb.r0 * P.nx;
+        for (int t = threadIdx.x; t < (er > 0 ? er * P.nx : 0); t += blockDim.x) Xg[t] = Fg[t];
+      }
+      return;
     }
     zero_x64();
     for (int s = P.Ntau - 1; s >= 0; --s) {

@@ -24,7 +24,8 @@ def gpu_operator(prob: Problem, precision: str = "fp64", **solve_kw) -> Operator
     return Operator(prob.nx, prob.ny, prob.h,
                     dict(k0=mat.k0, kmin=mat.kmin, pk=mat.pk, c0=mat.c0, cmin=mat.cmin, pc=mat.pc),
                     prob.Nt, prob.Ntau, prob.dt, prob.p, np.asarray(prob.dirichlet, np.uint8),
-                    q_elem=prob.q_elem, q_time=prob.q_time, solve=solve)
+                    q_elem=prob.q_elem, q_time=prob.q_time, solve=solve,
+                    objective="modified" if prob.modified_objective else "power_mean")
 
 
 def dev(a) -> torch.Tensor:

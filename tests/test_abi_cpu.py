@@ -53,7 +53,7 @@ def _args(nx=4, ny=4, Nt=4, Ntau=2, p=8.0, prec=0):
     return g, m, t, s, d
 
 
-@pytest.mark.parametrize("bad", ["ntau", "p_odd", "p_frac", "nx", "precision"])
+@pytest.mark.parametrize("bad", ["ntau", "p_odd", "p_frac", "nx", "precision", "objective"])
 def test_invalid_problem_rejected_on_host(lib, bad):
     g, m, t, s, d = _args()
     if bad == "ntau":
@@ -66,6 +66,8 @@ def test_invalid_problem_rejected_on_host(lib, bad):
         g.nx = 1
     elif bad == "precision":
         s.precision = 7
+    elif bad == "objective":
+        t.objective = 2
     h = ctypes.c_void_p()
     rc = lib.ptg_op_create(ctypes.byref(g), ctypes.byref(m), ctypes.byref(t), ctypes.byref(s), d.ctypes.data,
                            None, None, 0, ctypes.byref(h))
@@ -76,3 +78,6 @@ def test_null_op_rejected(lib):
     assert lib.ptg_fe_assemble_operator(None, None, None) == _ffi.PTG_EINVAL
     assert lib.ptg_fine_propagate_slices(None, 0, 0, 1, None, None, None, 0, 0, None, None, None) == _ffi.PTG_EINVAL
     assert lib.ptg_get_stats(None, None) == _ffi.PTG_EINVAL
+    assert lib.ptg_objective_from_modified(None, None, None, None, None, None) == _ffi.PTG_EINVAL
+    assert lib.ptg_parareal_correct(None, 1, None, None, None, None, None, None, None, None, None) == _ffi.PTG_EINVAL
+    assert lib.ptg_batch_oneshot_pass(None, 0, None) == _ffi.PTG_EINVAL
