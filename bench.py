@@ -275,11 +275,40 @@ def run_gpu(args):
 
             def relmax(a, b):
                 return float((a - b).abs().max() / b.abs().max())
-            prec = {"T_hist_rel_max": relmax(buf.T_hist, f64_buf.T_hist),
+            f64_T = f64_buf.T_hist
+            prec = {"T_hist_rel_max": relmax(buf.T_hist, f64_T),
                     "Theta_rel": abs(Theta_os - float(Th64.item())) / abs(float(Th64.item())),
                     "grad_rel_max": relmax(g_os, g64),
                     "targets": {"temperature": 1e-6, "sensitivity": 1e-5}}
-            del f64_buf
+
+        # the other mixed variant (every CG in FP32 when the headline keeps the coarse solves in
+        # FP64, and the reverse), timed like the main steps, with its error against FP64
+        variant = None
+        if args.precision != "fp64":
+            vname = "fp32_refine_all" if args.precision == "fp32_refine" else "fp32_refine"
+            v_op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink,
+                            solve=SolveConfig(vname, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=2000,
+                                              refine_max=8, twolevel=args.twolevel), device=local)
+            v_buf = PassBuffers(v_op)
+            for a_, b_ in ((v_buf.U_T, buf.U_T), (v_buf.U_th, buf.U_th), (v_buf.V_l, buf.V_l),
+                           (v_buf.V_g, buf.V_g)):
+                a_.copy_(b_)
+            v_ms = []
+            for i in range(args.warmup + args.steps):
+                flush.fill_(1.0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                v_op.assemble(rho)
+                Thv, gv = oneshot_pass(v_op, v_buf)
+                b.record(stream)
+                b.synchronize()
+                if i >= args.warmup:
+                    v_ms.append(a.elapsed_time(b))
+            vm = slowest_rank_ms(float(np.mean(v_ms)), device)
+            variant = {"precision": vname, "ms_per_step": vm, "value": job_throughput(dof_steps, world, vm),
+                       "unit": UNIT, "speedup_vs_sequential_fp64": seq_ms / vm,
+                       "T_hist_rel_max": relmax(v_buf.T_hist, f64_T), "grad_rel_max": relmax(gv, g64)}
+            del v_buf, f64_buf
 
         # Sec. 7.3 bottleneck probe: the same pass with the coarse propagators identically zero
         # (G_pri = G_adj = 0, the corrections copy F), timed like the main steps
@@ -301,14 +330,14 @@ def run_gpu(args):
                  "paper_context": "MATLAB on 32 CPU threads: 3.81x (one-shot) vs 10.8x (G = 0) over its sequential run"}
     else:
         e2e = seq_ms = None
-        seq_stats, prec, probe = {}, {}, None
+        seq_stats, prec, probe, variant = {}, {}, None, None
         err_theta = err_grad = None
 
     roof = roofline(kind_ms, stats, w, N_free, args)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "fp32_refine" else "f64",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic",
         "config": {"workload": f"{WORKLOAD}: 128x128 grid, Nt=1024, Ntau=32 (M=32), p=8, SIMP k, warm start from "
                                "the sequential coarse states of a design 1% away",
@@ -329,6 +358,7 @@ def run_gpu(args):
                                                 "sequential result of the current design"},
         "accuracy_mixed_vs_fp64_oneshot": prec,
         "bottleneck_probe": probe,
+        "precision_variant": variant,
         "e2e": None if e2e is None else {"value": world * dof_steps / (e2e * 1e-3), "unit": UNIT, "ms": e2e,
                                          "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": (1 + n * n) * 8},
         # per pass: assembly 3 kernels (+ 4 for the two-level coarse set-up) + 6 stepper launches
@@ -469,7 +499,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="fp32_refine", choices=["fp32_refine", "fp64"])
+    ap.add_argument("--precision", default="fp32_refine", choices=["fp32_refine", "fp32_refine_all", "fp64"],
+                    help="fp32_refine: fine-step CG in FP32 with FP64 refinement, coarse-step solves FP64; "
+                         "fp32_refine_all: every CG in FP32 with FP64 refinement")
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--no-twolevel", dest="twolevel", action="store_false",
                     help="Jacobi only on the coarse-step solves (default: two-level preconditioner)")

@@ -56,8 +56,10 @@ extern "C" {
 #define PTG_ENOMEM     -6   /* device allocation failed */
 
 /* precision of the fine-propagator CG (Sec. 2.2 solves; precision pattern of the port) */
-#define PTG_FP64         0  /* CG and every accumulation in FP64 */
-#define PTG_FP32_REFINE  1  /* CG in FP32, FP64 residuals and iterative refinement */
+#define PTG_FP64            0  /* CG and every accumulation in FP64 */
+#define PTG_FP32_REFINE     1  /* fine-step solves: CG in FP32 on the FP64 residual, refined in FP64;
+                                  coarse-step solves (G and the correction sweeps): FP64 CG */
+#define PTG_FP32_REFINE_ALL 2  /* every solve as the fine-step solves of PTG_FP32_REFINE */
 
 /* slice scheduling of ptg_fine_propagate_slices / ptg_adjoint_sweep */
 #define PTG_SLICES_PARALLEL 0  /* every slice starts from its own given state (Parareal F) */
@@ -91,15 +93,15 @@ typedef struct {
 } ptg_time;
 
 typedef struct {
-    int precision;     /* PTG_FP64 or PTG_FP32_REFINE */
+    int precision;     /* PTG_FP64, PTG_FP32_REFINE or PTG_FP32_REFINE_ALL */
     double rtol;       /* stop when ||b - A x||_2 <= rtol ||b||_2 (FP64 residual) */
-    double inner_rtol; /* FP32_REFINE: relative residual reduction of each FP32 CG */
+    double inner_rtol; /* relative residual reduction of each FP32 CG (FP32 solves only) */
     int cg_iters_max;  /* iteration limit of one CG */
     int refine_max;    /* limit of refinement sweeps of one solve */
-    int twolevel;      /* FP32_REFINE: precondition the coarse-step solves (C/dtau + K) with
-                          D^-1 + P Ac^-1 P^T, P bilinear from a coarse grid of spacing m h (m the
-                          smallest divisor >= 2 of both sides giving <= 17 coarse nodes per side;
-                          off if none).  0: Jacobi everywhere. */
+    int twolevel;      /* precondition the CG of the coarse-step solves (C/dtau + K) with
+                          D^-1 + P Ac^-1 P^T: P piecewise constant on aggregates of m x m nodes
+                          (m the smallest multiple of 4 giving <= 16 aggregates per direction),
+                          Ac = P^T A P, its inverse applied in FP32.  0: Jacobi everywhere. */
 } ptg_solve;
 
 typedef struct {

@@ -9,7 +9,7 @@ from ctypes import POINTER, c_char_p, c_double, c_int, c_longlong, c_void_p
 from .build import LIB
 
 PTG_OK, PTG_EINVAL, PTG_ENOCONV, PTG_ENONFINITE, PTG_ETIMEOUT, PTG_ECUDA, PTG_ENOMEM = 0, -1, -2, -3, -4, -5, -6
-PTG_FP64, PTG_FP32_REFINE = 0, 1
+PTG_FP64, PTG_FP32_REFINE, PTG_FP32_REFINE_ALL = 0, 1, 2
 PTG_SLICES_PARALLEL, PTG_SLICES_CHAINED = 0, 1
 PTG_PRIMAL, PTG_ADJOINT = 1, -1
 PTG_OBJ_POWER_MEAN, PTG_OBJ_MODIFIED = 0, 1

@@ -15,8 +15,8 @@ import numpy as np
 import torch
 
 from . import _ffi
-from ._ffi import (PTG_ADJOINT, PTG_FP32_REFINE, PTG_FP64, PTG_OBJ_MODIFIED, PTG_OBJ_POWER_MEAN, PTG_PRIMAL,
-                   PTG_SLICES_CHAINED, PTG_SLICES_PARALLEL)
+from ._ffi import (PTG_ADJOINT, PTG_FP32_REFINE, PTG_FP32_REFINE_ALL, PTG_FP64, PTG_OBJ_MODIFIED, PTG_OBJ_POWER_MEAN,
+                   PTG_PRIMAL, PTG_SLICES_CHAINED, PTG_SLICES_PARALLEL)
 
 KIND_NAMES = ("fine_primal", "coarse_primal", "correct_primal", "fine_adjoint", "coarse_adjoint", "correct_adjoint")
 
@@ -48,7 +48,8 @@ def _ptr(t: torch.Tensor | None, device: torch.device | None = None) -> int | No
 
 @dataclass
 class SolveConfig:
-    precision: str = "fp64"          # "fp64" or "fp32_refine"
+    precision: str = "fp64"          # "fp64"; "fp32_refine": fine-step CG in FP32 with FP64 refinement,
+    #                                  coarse-step solves in FP64; "fp32_refine_all": every CG in FP32
     rtol: float = 1e-13
     inner_rtol: float = 1e-4
     cg_iters_max: int = 2000
@@ -88,7 +89,8 @@ class Operator:
                               material["c0"], material["cmin"], material["pc"])
         self.objective = objective
         t = _ffi.ptg_time(Nt, Ntau, dt, p, {"power_mean": PTG_OBJ_POWER_MEAN, "modified": PTG_OBJ_MODIFIED}[objective])
-        prec = {"fp64": PTG_FP64, "fp32_refine": PTG_FP32_REFINE}[solve.precision]
+        prec = {"fp64": PTG_FP64, "fp32_refine": PTG_FP32_REFINE,
+                "fp32_refine_all": PTG_FP32_REFINE_ALL}[solve.precision]
         s = _ffi.ptg_solve(prec, solve.rtol, solve.inner_rtol, solve.cg_iters_max, solve.refine_max,
                            int(solve.twolevel))
         self._dir = np.ascontiguousarray(dirichlet, dtype=np.uint8).reshape(-1)

@@ -73,10 +73,21 @@ bool coarse_kind(int kind) {
   return kind == KIND_COARSE_PRI || kind == KIND_CORRECT_PRI || kind == KIND_COARSE_ADJ || kind == KIND_CORRECT_ADJ;
 }
 
+// Precision of the kernels of a task kind: PTG_FP32_REFINE keeps the coarse-step solves
+// (G and the correction sweeps) in FP64 and runs only the fine-step CG in FP32;
+// PTG_FP32_REFINE_ALL runs every CG in FP32.  Returns PTG_FP64 or PTG_FP32_REFINE (the two
+// kernel instantiations).
+int kind_precision(int solve_precision, int kind) {
+  if (solve_precision == PTG_FP64) return PTG_FP64;
+  if (solve_precision == PTG_FP32_REFINE_ALL) return PTG_FP32_REFINE;
+  return coarse_kind(kind) ? PTG_FP64 : PTG_FP32_REFINE;
+}
+
 // Aggregate rows reserved per CTA for cluster size cs (the largest over the ranks), 0 if the
-// two-level preconditioner is off for this op, precision, kind or plan.
+// two-level preconditioner is off for this op, kind or plan.
 int twolevel_rows(const ptg_op* op, int precision, int kind, int cs, bool use = true) {
-  if (!use || op->tl_m == 0 || precision != PTG_FP32_REFINE || !coarse_kind(kind)) return 0;
+  (void)precision;
+  if (!use || op->tl_m == 0 || !coarse_kind(kind)) return 0;
   int best = 0;
   for (int q = 0; q < cs; ++q) {
     int r0, R, lo, hi;
@@ -96,8 +107,16 @@ size_t twolevel_bytes(const ptg_op* op, int precision, int kind, int cs, bool us
   return twolevel_smem_bytes(op->W, rmax, cs, op->tl_nax, op->tl_nay, ncj);
 }
 
+// Inner tolerance of an FP64 CG with the two-level preconditioner: its coarse correction follows
+// the CG recurrence in FP32, whose rounding is relative to the residual the CG started from, so
+// each CG stops at this reduction and the FP64 residual loop restarts it from the exact residual.
+constexpr double kTwoLevelInnerFp64 = 1e-5;
+
 void twolevel_params(const ptg_op* op, int precision, StepParams& P, bool use) {
   P.tl_naj = twolevel_rows(op, precision, P.kind, P.cs, use);
+  // FP32 CG: the op's inner tolerance; FP64 CG: to the final tolerance in one go, or in
+  // kTwoLevelInnerFp64 steps with the two-level preconditioner
+  if (precision == PTG_FP64) P.inner_rtol = P.tl_naj > 0 ? kTwoLevelInnerFp64 : 0.0;
   if (P.tl_naj == 0) return;
   P.Ainv = op->tl_Ainv;
   P.cm = op->tl_m;
@@ -183,7 +202,7 @@ void base_params(const ptg_op* op, StepParams& P) {
   P.p = op->tm.p;
   P.has_dc = op->has_dc;
   P.rtol = op->sv.rtol;
-  P.inner_rtol = op->sv.precision == PTG_FP32_REFINE ? op->sv.inner_rtol : 0.0;
+  P.inner_rtol = op->sv.inner_rtol;   // used by the FP32 CG kernels only
   P.itmax = op->sv.cg_iters_max;
   P.refmax = op->sv.refine_max;
   P.W = op->W;
@@ -215,13 +234,14 @@ void base_params(const ptg_op* op, StepParams& P) {
 
 int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream) {
   Plan plan;
-  int rc = choose_plan(op, op->sv.precision, P.kind, ntasks, &plan);
+  const int prec = kind_precision(op->sv.precision, P.kind);
+  int rc = choose_plan(op, prec, P.kind, ntasks, &plan);
   if (rc != PTG_OK) return rc;
   P.cs = plan.cs;
   P.rmax = plan.rmax;
-  twolevel_params(op, op->sv.precision, P, plan.twolevel && !P.plt);
+  twolevel_params(op, prec, P, plan.twolevel && !P.plt);
   op->last_stream = stream;
-  PTG_CUDA(launch_stepper(P, plan, op->sv.precision, ntasks, stream));
+  PTG_CUDA(launch_stepper(P, plan, prec, ntasks, stream));
   return PTG_OK;
 }
 
@@ -259,7 +279,8 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
   const double p = time->p;
   if (!(p >= 2.0 && p <= 64.0) || p != (double)(int)p || ((int)p) % 2 != 0) return PTG_EINVAL;
   if (time->objective != PTG_OBJ_POWER_MEAN && time->objective != PTG_OBJ_MODIFIED) return PTG_EINVAL;
-  if (solve->precision != PTG_FP64 && solve->precision != PTG_FP32_REFINE) return PTG_EINVAL;
+  if (solve->precision != PTG_FP64 && solve->precision != PTG_FP32_REFINE && solve->precision != PTG_FP32_REFINE_ALL)
+    return PTG_EINVAL;
   if (!(solve->rtol > 0.0) || solve->cg_iters_max < 1 || solve->refine_max < 1 || !(solve->inner_rtol >= 0.0))
     return PTG_EINVAL;
   if (!(mat->k0 > 0.0) || !(mat->kmin > 0.0) || !(mat->c0 > 0.0) || !(mat->cmin > 0.0)) return PTG_EINVAL;
@@ -304,8 +325,8 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
   A(&op->dirichlet, op->Nn);
   A(&op->sens_partial, (size_t)op->sens_chunks * op->Ne * sizeof(double));
   // two-level preconditioner: aggregates of m x m nodes, m the smallest multiple of 4 giving
-  // at most kCoarseMaxAgg aggregates per direction (FP32 CG only)
-  if (solve->precision == PTG_FP32_REFINE && solve->twolevel) {
+  // at most kCoarseMaxAgg aggregates per direction
+  if (solve->twolevel) {
     int m = 4;
     while ((grid->nx + 1) / m > kCoarseMaxAgg || (grid->ny + 1) / m > kCoarseMaxAgg) m += 4;
     op->tl_m = m;
@@ -351,7 +372,7 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
   // the grid must fit one cluster for every kind and precision this op may run
   Plan probe;
   for (int kind = 0; kind < 6; ++kind) {
-    int rc = choose_plan(op, op->sv.precision, kind, 1, &probe);
+    int rc = choose_plan(op, kind_precision(op->sv.precision, kind), kind, 1, &probe);
     if (rc != PTG_OK) {
       free_all(op);
       delete op;
@@ -397,10 +418,11 @@ int ptg_op_set_plan(ptg_op* op, int kind, int cs, int ng) {
   if (nthreads > kStepMaxThreadsHost) return PTG_EINVAL;
   // with the two-level preconditioner where it applies and fits, else with Jacobi
   for (bool tl : {true, false}) {
-    if (tl && twolevel_rows(op, op->sv.precision, kind, cs) == 0) continue;
+    const int prec = kind_precision(op->sv.precision, kind);
+    if (tl && twolevel_rows(op, prec, kind, cs) == 0) continue;
     Plan p;
-    cudaError_t e = query_stepper_plan(op->g.nx, op->g.ny, op->sv.precision, kind, cs, ng, nthreads,
-                                       twolevel_bytes(op, op->sv.precision, kind, cs, tl), &p);
+    cudaError_t e = query_stepper_plan(op->g.nx, op->g.ny, prec, kind, cs, ng, nthreads,
+                                       twolevel_bytes(op, prec, kind, cs, tl), &p);
     if (e != cudaSuccess) {
       cudaGetLastError();
       continue;
@@ -417,7 +439,7 @@ int ptg_op_get_plan(ptg_op* op, int kind, int ntasks, int* cs, int* nthreads, in
   if (!op || kind < 0 || kind > 5 || ntasks < 1) return PTG_EINVAL;
   DeviceGuard dg(op->device);
   Plan p;
-  int rc = choose_plan(op, op->sv.precision, kind, ntasks, &p);
+  int rc = choose_plan(op, kind_precision(op->sv.precision, kind), kind, ntasks, &p);
   if (rc != PTG_OK) return rc;
   if (cs) *cs = p.cs;
   if (nthreads) *nthreads = p.nthreads;
@@ -684,7 +706,7 @@ StepParams phase_params(const ptg_batch* b, int d, int ph, int cs, bool tl) {
   P.hist = B.T_hist;
   P.hist_j0 = 0;
   P.hist_rows = op->tm.Nt + 1;
-  twolevel_params(op, b->precision, P, tl);
+  twolevel_params(op, kind_precision(b->precision, P.kind), P, tl);
   const int Ntau = op->tm.Ntau;
   switch (ph) {
     case 0:  P.in_field = B.U_T; P.in_aux = B.U_th; P.out_field = B.F_T; P.out_aux = B.F_th; break;
@@ -738,17 +760,18 @@ std::vector<int2> phase_tasks(const ptg_batch* b, int ph) {
 // the task list, and size the persistent grid.  tl: two-level preconditioner where it applies.
 int batch_install(ptg_batch* b, int ph, int cs, int ng, int nthreads, bool tl) {
   const int kind = phase_kind(ph);
+  const int prec = kind_precision(b->precision, kind);
   size_t smem = 0;
   for (ptg_op* op : b->ops) {
     const int rmax = (op->g.ny + 1 + cs - 1) / cs;
     if (rmax < 2) return PTG_EINVAL;
     const int groups = rmax * (op->W / kGroup);
     if (groups > ng * nthreads) return PTG_EINVAL;
-    smem = std::max(smem, stepper_smem_bytes(op->g.nx, rmax, b->precision == PTG_FP32_REFINE ? 4 : 8) +
-                              twolevel_bytes(op, b->precision, kind, cs, tl));
+    smem = std::max(smem, stepper_smem_bytes(op->g.nx, rmax, prec == PTG_FP32_REFINE ? 4 : 8) +
+                              twolevel_bytes(op, prec, kind, cs, tl));
   }
   int nclusters = 0;
-  if (query_batch_occupancy(b->precision, kind, cs, ng, nthreads, smem, &nclusters) != cudaSuccess || nclusters <= 0) {
+  if (query_batch_occupancy(prec, kind, cs, ng, nthreads, smem, &nclusters) != cudaSuccess || nclusters <= 0) {
     cudaGetLastError();
     return PTG_EINVAL;
   }
@@ -777,6 +800,7 @@ int batch_install(ptg_batch* b, int ph, int cs, int ng, int nthreads, bool tl) {
 // the plan).
 long batch_best(ptg_batch* b, int ph, bool tl, int ntasks, int* best_cs, int* best_ng, int* best_nt) {
   long best_waves = -1;
+  const int prec = kind_precision(b->precision, phase_kind(ph));
   for (int cs : {16, 8, 4, 2}) {
     for (int ng : kStepNG) {
       int nt = 32;
@@ -787,12 +811,12 @@ long batch_best(ptg_batch* b, int ph, bool tl, int ntasks, int* best_cs, int* be
         if (rmax < 2) { ok = false; break; }
         const int groups = rmax * (op->W / kGroup);
         nt = std::max(nt, ((groups + ng - 1) / ng + 31) / 32 * 32);
-        smem = std::max(smem, stepper_smem_bytes(op->g.nx, rmax, b->precision == PTG_FP32_REFINE ? 4 : 8) +
-                                  twolevel_bytes(op, b->precision, phase_kind(ph), cs, tl));
+        smem = std::max(smem, stepper_smem_bytes(op->g.nx, rmax, prec == PTG_FP32_REFINE ? 4 : 8) +
+                                  twolevel_bytes(op, prec, phase_kind(ph), cs, tl));
       }
       if (!ok || nt > kStepMaxThreadsHost) continue;
       int ncl = 0;
-      if (query_batch_occupancy(b->precision, phase_kind(ph), cs, ng, nt, smem, &ncl) != cudaSuccess || ncl <= 0) {
+      if (query_batch_occupancy(prec, phase_kind(ph), cs, ng, nt, smem, &ncl) != cudaSuccess || ncl <= 0) {
         cudaGetLastError();
         continue;
       }
@@ -833,7 +857,8 @@ int batch_run(ptg_batch* b, int ph, cudaStream_t stream) {
   }
   const PhasePlan& pp = b->ph[ph];
   for (ptg_op* op : b->ops) op->last_stream = stream;
-  PTG_CUDA(launch_stepper_batch(b->precision, phase_kind(ph), pp.plan, pp.table, pp.tasks, pp.ntasks,
+  PTG_CUDA(launch_stepper_batch(kind_precision(b->precision, phase_kind(ph)), phase_kind(ph), pp.plan, pp.table,
+                                pp.tasks, pp.ntasks,
                                 b->queue + ph, pp.nclusters, stream));
   return PTG_OK;
 }

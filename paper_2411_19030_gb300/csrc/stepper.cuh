@@ -163,7 +163,7 @@ struct Stepper {
   int gshift = 0;   // offset from a halo-buffer node to the same node of the global padded arrays
   double* ax64;     // A x64 from the last residual evaluation, rows 0..R-1 (reused by the next step)
   bool ax_valid = false;
-  // two-level preconditioner of the coarse-step solves (FP32 CG): see coarse_restrict_push
+  // two-level preconditioner of the coarse-step solves: see coarse_restrict_push
   bool tl = false;
   bool tl_loaded = false;
   int aj0 = 0, naj = 0;      // this CTA's aggregate rows [aj0, aj0 + naj)
@@ -208,11 +208,13 @@ struct Stepper {
     if constexpr (kMixed) {
       for (int i = threadIdx.x; i < 3 * elems; i += blockDim.x) eb[i] = 0.f;
     }
-    if constexpr (kMixed) {
+    {
       if (P.tl_naj > 0) {
         const int naxp = coarse_row_stride(P.nax), ncp = naxp * P.nay;
         const int groups = P.rmax * (W / kGroup);
-        float* t = eb + 3 * elems;   // 16-byte aligned: every earlier array is a multiple of 4 words
+        // after the element weights (FP32 CG only); 16-byte aligned: every earlier array is a
+        // multiple of 4 words
+        float* t = eb + (kMixed ? 3 * elems : 0);
         tl_ainv = t;  t += P.tl_naj * naxp * ncp;
         tl_slot = t;  t += P.cs * ncp;
         tl_qc = t;    t += ncp;
@@ -284,7 +286,7 @@ struct Stepper {
     step_dt = coarse ? P.dtau : P.dt;
     inv_dt = 1.0 / step_dt;
     ax_valid = false;
-    tl = kMixed && coarse && P.tl_naj > 0 && P.Ainv != nullptr;
+    tl = coarse && P.tl_naj > 0 && P.Ainv != nullptr;
     if (tl && !tl_loaded) {        // rows of the aggregate rows aj0 .. aj0+naj-1 of Ainv, 16-byte copies
       const int naxp = coarse_row_stride(P.nax), ncp = naxp * P.nay;
       const int n4 = naj * naxp * ncp / 4;
@@ -439,8 +441,9 @@ struct Stepper {
     }
   }
 
-  // Two-level preconditioner M^-1 = D^-1 + P Ac^-1 P^T of the coarse-step solves (FP32 CG);
-  // P is piecewise constant on aggregates of m x m nodes aligned to the 4-node groups, so the
+  // Two-level preconditioner M^-1 = D^-1 + P Ac^-1 P^T of the coarse-step solves (CG in either
+  // precision; the coarse part is applied in FP32, the FP64 residual loop around the CG fixes
+  // the accuracy); P is piecewise constant on aggregates of m x m nodes aligned to the 4-node groups, so the
   // restriction P^T v is a sum of group sums and the prolongation adds one value per group.
   // Every CTA sends its partial sums for the aggregates its slab touches to every CTA of the
   // cluster (16-byte stores of 4 aggregates); the next cluster barrier (the one of the
@@ -574,13 +577,11 @@ struct Stepper {
           v[0] = fma(r[k][j], z, v[0]);
         }
       }
-      if constexpr (kMixed) {
-        if (tl) {
-          coarse_restrict_push(r);
-          cluster_sync_all();
-          coarse_gather(true, 0.f);
-          v[0] = prolong_precondition(r);
-        }
+      if (tl) {
+        coarse_restrict_push(r);
+        cluster_sync_all();
+        coarse_gather(true, 0.f);
+        v[0] = prolong_precondition(r);
       }
       __syncthreads();
       push_halos(zbuf, sb, cluster);
@@ -609,15 +610,11 @@ struct Stepper {
           pq[0] = fma(p[k][j], q[k][j], pq[0]);
         }
       }
-      if constexpr (kMixed) {
-        if (tl) coarse_restrict_push(q);     // visible after the all-reduce's cluster barrier
-      }
+      if (tl) coarse_restrict_push(q);       // visible after the all-reduce's cluster barrier
       const Real rz_c = rz;
       allreduce<Real, 1>(pq, [rz_c](Real* t) { t[0] = rz_c / t[0]; });
       const Real alpha = pq[0];
-      if constexpr (kMixed) {
-        if (tl) coarse_gather(false, alpha);
-      }
+      if (tl) coarse_gather(false, (float)alpha);
       // d += alpha p, r -= alpha q, z = D^-1 r; (r, z), (r, r) and beta = (r, z)_new / (r, z)
       Real v[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
@@ -636,9 +633,7 @@ struct Stepper {
           }
         }
       }
-      if constexpr (kMixed) {
-        if (tl) v[0] = prolong_precondition(r);
-      }
+      if (tl) v[0] = prolong_precondition(r);
       __syncthreads();
       push_halos(zbuf, sb, cluster);
       allreduce<Real, 2, 1>(v, [rz_c](Real* t) { t[2] = t[0] / rz_c; });

@@ -59,7 +59,8 @@ def test_batched_sequential_pass_matches_oracle_per_design():
 
 
 @pytest.mark.parametrize("precision,tol_t,tol_g", [("fp64", FP64_TOL, FP64_TOL),
-                                                   ("fp32_refine", MIXED_T_TOL, MIXED_G_TOL)])
+                                                   ("fp32_refine", MIXED_T_TOL, MIXED_G_TOL),
+                                                   ("fp32_refine_all", MIXED_T_TOL, MIXED_G_TOL)])
 def test_batched_oneshot_pass_matches_oracle_per_design(precision, tol_t, tol_g):
     kw = {} if precision == "fp64" else {"rtol": 1e-10}
     ds, ops, batch = make_batch(precision, **kw)

@@ -110,10 +110,12 @@ def test_oneshot_pass_fp64(name):
     _oneshot_compare(name, "fp64", FP64_TOL, FP64_TOL)
 
 
+@pytest.mark.parametrize("precision", ["fp32_refine", "fp32_refine_all"])
 @pytest.mark.parametrize("name", ["ragged_table1", "plain32", "paper_p20", "m1"])
-def test_oneshot_pass_fp32_refine(name):
-    """FP32 CG with FP64 residual refinement, against the FP64 oracle."""
-    _oneshot_compare(name, "fp32_refine", MIXED_T_TOL, MIXED_G_TOL, rtol=1e-10)
+def test_oneshot_pass_fp32_refine(name, precision):
+    """FP32 CG with FP64 residual refinement for the fine-step solves (and, with
+    fp32_refine_all, for the coarse-step solves too), against the FP64 oracle."""
+    _oneshot_compare(name, precision, MIXED_T_TOL, MIXED_G_TOL, rtol=1e-10)
 
 
 @pytest.mark.parametrize("name", ["ragged_table1", "paper_p20"])

@@ -11,7 +11,7 @@ import workloads as W
 from oracle import Operator as OracleOp
 from oracle import coarse_states_from_sequential, oneshot_pass as o_oneshot
 from paper_2411_19030_gb300 import PassBuffers, oneshot_pass
-from tests.gpu_helpers import MIXED_G_TOL, MIXED_T_TOL, assert_close, dev, ensure_built, gpu_operator, host
+from tests.gpu_helpers import FP64_TOL, MIXED_G_TOL, MIXED_T_TOL, assert_close, dev, ensure_built, gpu_operator, host
 from tests.problems import make_problem
 
 pytestmark = pytest.mark.gpu
@@ -36,9 +36,9 @@ def case():
     return prob, rho, U_old, V_old, ref
 
 
-def run_pass(case, twolevel, cs=0):
+def run_pass(case, twolevel, cs=0, precision="fp32_refine"):
     prob, rho, U_old, V_old, _ = case
-    op = gpu_operator(prob, "fp32_refine", rtol=1e-10, twolevel=twolevel)
+    op = gpu_operator(prob, precision, rtol=1e-13 if precision == "fp64" else 1e-10, twolevel=twolevel)
     if cs:
         for kind in COARSE_KINDS:
             op.set_plan(kind, cs, 1 if cs >= 8 else 2)
@@ -51,28 +51,36 @@ def run_pass(case, twolevel, cs=0):
     return op, buf, Theta, grad
 
 
-def check(case, op, buf, Theta, grad):
+def check(case, op, buf, Theta, grad, tol_t=MIXED_T_TOL, tol_g=MIXED_G_TOL):
     ref = case[4]
-    assert_close("G_T", host(buf.G_T), ref["G_pri_old"][0], MIXED_T_TOL)
-    assert_close("U_new", host(buf.U_T_new), ref["U"][0], MIXED_T_TOL)
-    assert_close("T_hist", host(buf.T_hist), ref["T_hist"], MIXED_T_TOL)
-    assert_close("Theta", host(Theta), [ref["Theta"]], MIXED_T_TOL)
-    assert_close("G_lam", host(buf.G_l), ref["G_adj_old"][0], MIXED_G_TOL)
-    assert_close("V_lam", host(buf.V_l_new), ref["V"][0], MIXED_G_TOL)
-    assert_close("grad", host(grad), ref["grad"], MIXED_G_TOL)
+    assert_close("G_T", host(buf.G_T), ref["G_pri_old"][0], tol_t)
+    assert_close("U_new", host(buf.U_T_new), ref["U"][0], tol_t)
+    assert_close("T_hist", host(buf.T_hist), ref["T_hist"], tol_t)
+    assert_close("Theta", host(Theta), [ref["Theta"]], tol_t)
+    assert_close("G_lam", host(buf.G_l), ref["G_adj_old"][0], tol_g)
+    assert_close("V_lam", host(buf.V_l_new), ref["V"][0], tol_g)
+    assert_close("grad", host(grad), ref["grad"], tol_g)
     assert op.stats()["status"] == 0
 
 
+@pytest.mark.parametrize("precision", ["fp32_refine", "fp32_refine_all"])
 @pytest.mark.parametrize("cs", [2, 4, 8, 16])
-def test_twolevel_pass_matches_oracle_for_every_cluster_size(case, cs):
-    op, buf, Theta, grad = run_pass(case, True, cs)
+def test_twolevel_pass_matches_oracle_for_every_cluster_size(case, cs, precision):
+    op, buf, Theta, grad = run_pass(case, True, cs, precision)
     assert op.plan(1, 1)["cs"] == cs
     check(case, op, buf, Theta, grad)
 
 
-def test_twolevel_reduces_coarse_iterations(case):
-    on = run_pass(case, True)
-    off = run_pass(case, False)
+def test_twolevel_fp64_path_keeps_the_fp64_tolerance(case):
+    """FP64 CG with the two-level coarse correction (applied in FP32, refined in FP64)."""
+    op, buf, Theta, grad = run_pass(case, True, 0, "fp64")
+    check(case, op, buf, Theta, grad, FP64_TOL, FP64_TOL)
+
+
+@pytest.mark.parametrize("precision", ["fp32_refine", "fp32_refine_all"])
+def test_twolevel_reduces_coarse_iterations(case, precision):
+    on = run_pass(case, True, 0, precision)
+    off = run_pass(case, False, 0, precision)
     check(case, *on)
     check(case, *off)
     k_on, k_off = on[0].stats()["by_kind"], off[0].stats()["by_kind"]
