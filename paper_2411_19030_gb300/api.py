@@ -54,7 +54,9 @@ class SolveConfig:
     inner_rtol: float = 1e-4
     cg_iters_max: int = 2000
     refine_max: int = 8
-    twolevel: bool = True            # two-level preconditioner of the coarse-step solves (fp32_refine)
+    twolevel: bool = True            # two-level preconditioner of the coarse-step solves
+    grid_wide: int = 1               # single FP64 systems over every SM (cooperative grid):
+    #                                  0 never, 1 for large grids or when no cluster fits, 2 always
 
 
 class Operator:
@@ -92,7 +94,7 @@ class Operator:
         prec = {"fp64": PTG_FP64, "fp32_refine": PTG_FP32_REFINE,
                 "fp32_refine_all": PTG_FP32_REFINE_ALL}[solve.precision]
         s = _ffi.ptg_solve(prec, solve.rtol, solve.inner_rtol, solve.cg_iters_max, solve.refine_max,
-                           int(solve.twolevel))
+                           int(solve.twolevel), int(solve.grid_wide))
         self._dir = np.ascontiguousarray(dirichlet, dtype=np.uint8).reshape(-1)
         if self._dir.size != self.Nn:
             raise ValueError("dirichlet mask must have (nx+1)(ny+1) entries")

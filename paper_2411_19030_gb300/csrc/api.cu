@@ -34,6 +34,12 @@ struct ptg_op {
   uint8_t* dirichlet = nullptr;
   double* sens_partial = nullptr;
   double* scratch = nullptr;   // [2] small device scalars
+  // grid-wide launches (one system over every SM): reduction partials, barrier, halo rows,
+  // two-level partials
+  double* g_red = nullptr;
+  unsigned* g_bar = nullptr;
+  void* g_halo = nullptr;
+  float* g_tl = nullptr;
   int sens_chunks = 0;
   DevStats* stats = nullptr;
   cudaStream_t last_stream = nullptr;
@@ -100,11 +106,24 @@ int twolevel_rows(const ptg_op* op, int precision, int kind, int cs, bool use = 
   return best;
 }
 
-size_t twolevel_bytes(const ptg_op* op, int precision, int kind, int cs, bool use = true) {
+size_t twolevel_bytes(const ptg_op* op, int precision, int kind, int cs, bool use = true, bool slots = true) {
   const int ncj = twolevel_rows(op, precision, kind, cs, use);
   if (ncj == 0) return 0;
   const int rmax = (op->g.ny + 1 + cs - 1) / cs;
-  return twolevel_smem_bytes(op->W, rmax, cs, op->tl_nax, op->tl_nay, ncj);
+  return twolevel_smem_bytes(op->W, rmax, cs, op->tl_nax, op->tl_nay, ncj, slots);
+}
+
+// Node count from which a single FP64 system runs grid-wide (see choose_plan).
+constexpr int kWideMinNodes = 40000;
+
+// two-level bytes of a grid-wide launch of G CTAs (the partials live in global memory)
+struct WideCtx {
+  const ptg_op* op;
+  int precision, kind;
+};
+size_t wide_twolevel_bytes(const void* ctx, int G) {
+  const WideCtx* c = static_cast<const WideCtx*>(ctx);
+  return twolevel_bytes(c->op, c->precision, c->kind, G, true, false);
 }
 
 // Inner tolerance of an FP64 CG with the two-level preconditioner: its coarse correction follows
@@ -158,8 +177,9 @@ long best_plan(ptg_op* op, int precision, int kind, int ntasks, bool tl, Plan* o
 }
 
 // Choose the plan of a task kind for `ntasks` concurrent clusters.  The two-level
-// preconditioner (coarse kinds, FP32 CG) cuts the CG iterations about threefold for a
-// shared-memory cost; it is used unless its plan needs more waves than Jacobi's.
+// preconditioner (coarse kinds) cuts the CG iterations about threefold for a shared-memory
+// cost; with FP32 CG it is used unless its plan needs more waves than Jacobi's, with FP64 CG
+// whenever it fits.
 int choose_plan(ptg_op* op, int precision, int kind, int ntasks, Plan* out) {
   std::lock_guard<std::mutex> lk(op->mu);
   auto ov = op->plan_override.find(kind);
@@ -173,14 +193,35 @@ int choose_plan(ptg_op* op, int precision, int kind, int ntasks, Plan* out) {
     *out = it->second;
     return PTG_OK;
   }
+  // One FP64 system: a cluster runs its CG on 16 SMs, bound by their FP64 pipes; a grid-wide
+  // launch spreads the FP64 work over every SM, but each of its reductions costs a few
+  // microseconds of global-memory round trips against about one for a cluster.  Measured on
+  // GB300 the cluster wins at 128 x 128; the grid wins once the per-iteration FP64 work of 16
+  // SMs dominates (kWideMinNodes) or when no cluster plan fits (large grids in FP64).
+  // grid_wide: 0 never, 1 by that rule, 2 always.
   Plan jac, two;
   const long wj = best_plan(op, precision, kind, ntasks, false, &jac);
+  const bool want_wide = op->sv.grid_wide == 2 || (op->sv.grid_wide == 1 && (wj < 0 || op->Nn >= kWideMinNodes));
+  if (ntasks == 1 && precision == PTG_FP64 && want_wide) {
+    Plan w;
+    WideCtx ctx{op, precision, kind};
+    if (query_wide_plan(op->g.nx, op->g.ny, precision, kind, wide_twolevel_bytes, &ctx, &w) == cudaSuccess) {
+      w.twolevel = twolevel_rows(op, precision, kind, w.cs) > 0;
+      op->plans[key] = w;
+      *out = w;
+      return PTG_OK;
+    }
+    cudaGetLastError();
+  }
   const long wt = twolevel_rows(op, precision, kind, 1) > 0 ? best_plan(op, precision, kind, ntasks, true, &two) : -1;
   if (wj < 0 && wt < 0) {
     std::snprintf(g_last_error, sizeof(g_last_error), "no cluster plan fits a %dx%d grid", op->g.nx, op->g.ny);
     return PTG_EINVAL;
   }
-  const Plan best = (wt >= 0 && (wj < 0 || wt <= wj)) ? two : jac;
+  // FP64 CG on GB300 is bound by the FP64 pipe, so the cut in iterations outweighs extra
+  // waves; FP32 CG is bound by latency, so two-level must not add waves
+  const bool prefer_two = wt >= 0 && (wj < 0 || wt <= wj || precision == PTG_FP64);
+  const Plan best = prefer_two ? two : jac;
   op->plans[key] = best;
   *out = best;
   return PTG_OK;
@@ -239,6 +280,14 @@ int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream) {
   if (rc != PTG_OK) return rc;
   P.cs = plan.cs;
   P.rmax = plan.rmax;
+  if (plan.wide) {
+    P.wide = 1;
+    P.g_red = op->g_red;
+    P.g_bar = op->g_bar;
+    P.g_halo = op->g_halo;
+    P.g_halo_row_bytes = op->W * (int)sizeof(double);
+    P.g_tl = op->g_tl;
+  }
   twolevel_params(op, prec, P, plan.twolevel && !P.plt);
   op->last_stream = stream;
   PTG_CUDA(launch_stepper(P, plan, prec, ntasks, stream));
@@ -250,6 +299,7 @@ bool window_covers(int j0, int rows, int lo, int hi) { return lo >= j0 && hi < j
 void free_all(ptg_op* op) {
   void* ptrs[] = {op->k, op->c, op->dk, op->dc, op->wE, op->nodew, op->fload,
                   op->q_elem, op->q_time, op->dirichlet, op->sens_partial, op->scratch, op->stats,
+                  op->g_red, op->g_bar, op->g_halo, op->g_tl,
                   op->tl_Ac, op->tl_band, op->tl_X, op->tl_Ainv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -338,8 +388,12 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
     const size_t ncp = (size_t)coarse_row_stride(op->tl_nax) * op->tl_nay;
     A(&op->tl_X, nc * nc * sizeof(float));
     A(&op->tl_Ainv, ncp * ncp * sizeof(float));
+    A(&op->g_tl, (size_t)kMaxGrid * ncp * sizeof(float));
   }
   A(&op->scratch, 2 * sizeof(double));
+  A(&op->g_red, 2 * kMaxGrid * 4 * sizeof(double));
+  A(&op->g_bar, 64);
+  A(&op->g_halo, (size_t)kMaxGrid * 2 * op->W * sizeof(double));
   A(&op->stats, sizeof(DevStats));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -845,7 +899,8 @@ int batch_default(ptg_batch* b, int ph) {
   const long wj = batch_best(b, ph, false, ntasks, &jc, &jg, &jt);
   const long wt = batch_has_twolevel(b, ph) ? batch_best(b, ph, true, ntasks, &tc, &tg, &tt) : -1;
   if (wj < 0 && wt < 0) return PTG_EINVAL;
-  if (wt >= 0 && (wj < 0 || wt <= wj)) return batch_install(b, ph, tc, tg, tt, true);
+  const bool fp64 = kind_precision(b->precision, phase_kind(ph)) == PTG_FP64;
+  if (wt >= 0 && (wj < 0 || wt <= wj || fp64)) return batch_install(b, ph, tc, tg, tt, true);
   return batch_install(b, ph, jc, jg, jt, false);
 }
 

@@ -1,0 +1,230 @@
+// comm.cuh -- how the CTAs that share one linear system talk to each other.
+//
+// The stepper (stepper.cuh) needs four collective operations: an all-reduce of a few
+// scalars, the exchange of the first and last owned node rows with the neighbouring slabs
+// (halo rows), a barrier, and the broadcast of the two-level preconditioner's restricted
+// partials.  Two implementations:
+//
+//   ClusterComm  one thread-block cluster (up to 16 CTAs): distributed shared memory stores
+//                and the hardware cluster barrier.  Used wherever several independent
+//                systems run side by side (one cluster each).
+//   GridComm     one cooperative launch of G CTAs (up to kMaxGrid, one per SM): global memory
+//                and a counting grid barrier.  Used for a single system whose solves are
+//                bound by the FP64 pipe (1/58 of the FP32 rate on this chip): spreading it
+//                over every SM instead of one cluster multiplies the FP64 throughput.
+//
+// Both produce bitwise identical reductions in every CTA (fixed summation orders).
+#pragma once
+#include "ptg_device.cuh"
+
+namespace ptg {
+
+constexpr long kGridSpinLimit = 1L << 20; // polls of a grid barrier before it reports PTG_ETIMEOUT
+
+// ---------------------------------------------------------------------------- cluster
+struct ClusterComm {
+  cg::cluster_group cl;
+  RedSmem& rs;
+  int phase = 0;
+
+  __device__ ClusterComm(RedSmem& rs_) : cl(cg::this_cluster()), rs(rs_) {}
+  __device__ int rank() const { return (int)cl.block_rank(); }
+  __device__ void sync() { cluster_sync_all(); }
+
+  template <class T, int NV, int NX, class Post>
+  __device__ void allreduce(T (&v)[NV + NX], int cs, Post post) {
+    cluster_allreduce<T, NV, NX, Post>(v, rs, phase, cl, cs, post);
+  }
+  // own first / last rows into the neighbours' halo rows; visible after the next barrier
+  template <class T>
+  __device__ void push_halos(T* buf, const Slab& sb) {
+    ptg::push_halos(buf, sb, cl);
+  }
+  // a 16-byte chunk of restricted partials, written at offset dst of every rank's slot array;
+  // the 16 lanes `sub` = 0..15 of a half-warp share the destinations
+  __device__ void publish_tl(float* slot, int dst, const float4& chunk, int sub, int cs) {
+    for (int q = sub; q < cs; q += 16) *reinterpret_cast<float4*>(cl.map_shared_rank(slot + dst, (unsigned)q)) = chunk;
+  }
+  __device__ const float* tl_slots(const float* local) const { return local; }
+  __device__ float4 tl_load4(const float* slots, int idx) const {
+    return *reinterpret_cast<const float4*>(slots + idx);
+  }
+};
+
+// ---------------------------------------------------------------------------- grid
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+struct GridComm {
+  const StepParams& P;
+  RedSmem& rs;
+  int phase = 0;
+  // halo rows published by push_halos and pulled in after the next barrier
+  unsigned char* pending = nullptr;
+  int pending_bytes = 0;         // bytes of one row
+  int R = 0, W = 0;
+
+  __device__ GridComm(const StepParams& P_, RedSmem& rs_) : P(P_), rs(rs_) {}
+  __device__ int rank() const { return (int)blockIdx.x; }
+
+  // Counting barrier over all CTAs of the launch (co-resident: cooperative launch).  Thread 0
+  // of each CTA makes the CTA's global writes visible, arrives, and waits for the generation
+  // to move on; the last arriver resets the count and releases the next generation.  A wait
+  // that exceeds kGridSpinLimit polls records PTG_ETIMEOUT and returns; once any CTA has
+  // recorded it (the launch's status word, P.g_bar[2]), every later wait returns at once, so a
+  // broken launch ends quickly with the error instead of waiting out every barrier.
+  __device__ void barrier() {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned* count = P.g_bar;
+      unsigned* gen = P.g_bar + 1;
+      unsigned* broken = P.g_bar + 2;
+      const unsigned g0 = ld_acquire_gpu(gen);
+      __threadfence();
+      const unsigned arrived = atomicAdd(count, 1u);
+      if (arrived == gridDim.x - 1) {
+        atomicExch(count, 0u);
+        __threadfence();
+        st_release_gpu(gen, g0 + 1u);
+      } else {
+        long spins = 0;
+        while (ld_acquire_gpu(gen) == g0) {
+          if ((++spins & 255) == 0 && ld_acquire_gpu(broken) != 0u) break;
+          if (spins > kGridSpinLimit) {
+            record_error(P.stats, PTG_ETIMEOUT, P.kind, -1);
+            atomicExch(broken, 1u);
+            break;
+          }
+        }
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    pull_halos();
+  }
+  __device__ void sync() { barrier(); }
+
+  template <class T, int NV, int NX, class Post>
+  __device__ void allreduce(T (&v)[NV + NX], int G, Post post) {
+    RedBank<T>& rb = bank<T>(rs);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) rb.warp[warp][i] = v[i];
+    }
+    __syncthreads();
+    double* slots = P.g_red + (size_t)phase * kMaxGrid * 4;
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        T s = rb.warp[0][i];
+        for (int w = 1; w < nwarps; ++w) s += rb.warp[w][i];
+        slots[rank() * 4 + i] = (double)s;          // exact for T = float too
+      }
+    }
+    barrier();
+    if constexpr (sizeof(T) == 4) {
+      // every warp: lane-strided sums over the ranks, then the same butterfly
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        T t = T(0);
+        for (int r = lane; r < G; r += 32) t += (T)__ldcg(slots + r * 4 + i);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        v[i] = t;
+      }
+      post(v);
+    } else {
+      // warp 0 sums (lane-strided, then the butterfly), thread 0 applies `post` and
+      // broadcasts: one lane of FP64 work for the divisions instead of every thread
+      if (warp == 0) {
+        T t[NV + NX];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+          T a = T(0);
+          for (int r = lane; r < G; r += 32) a += (T)__ldcg(slots + r * 4 + i);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+          t[i] = a;
+        }
+        if (lane == 0) {
+#pragma unroll
+          for (int i = NV; i < NV + NX; ++i) t[i] = T(0);
+          post(t);
+#pragma unroll
+          for (int i = 0; i < NV + NX; ++i) rb.bcast[i] = t[i];
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < NV + NX; ++i) v[i] = rb.bcast[i];
+    }
+    phase ^= 1;
+  }
+
+  // Publish the own first and last rows (local rows 0 and R-1 of buf, which points at row -1)
+  // to this CTA's two global halo slots; the neighbours pull them after the next barrier.
+  template <class T>
+  __device__ void push_halos(T* buf, const Slab& sb) {
+    const int nb = sb.W * (int)sizeof(T);           // bytes per row, a multiple of 16
+    unsigned char* out = reinterpret_cast<unsigned char*>(P.g_halo) + (size_t)rank() * 2 * P.g_halo_row_bytes;
+    const uint4* s0 = reinterpret_cast<const uint4*>(buf + 1 * sb.W);
+    const uint4* s1 = reinterpret_cast<const uint4*>(buf + sb.R * sb.W);
+    uint4* d0 = reinterpret_cast<uint4*>(out);
+    uint4* d1 = reinterpret_cast<uint4*>(out + P.g_halo_row_bytes);
+    for (int i = threadIdx.x; i < nb / 16; i += blockDim.x) {
+      d0[i] = s0[i];
+      d1[i] = s1[i];
+    }
+    __threadfence();                                // each writer orders its own stores
+    pending = reinterpret_cast<unsigned char*>(buf);
+    pending_bytes = nb;
+    R = sb.R;
+    W = sb.W;
+  }
+  // After a barrier: the neighbours' last / first rows into the local halo rows -1 and R.
+  __device__ void pull_halos() {
+    if (!pending) return;
+    const unsigned char* base = reinterpret_cast<const unsigned char*>(P.g_halo);
+    const size_t rb = P.g_halo_row_bytes;
+    const int n16 = pending_bytes / 16;
+    uint4* lo = reinterpret_cast<uint4*>(pending);                                    // row -1
+    uint4* hi = reinterpret_cast<uint4*>(pending + (size_t)(R + 1) * pending_bytes);  // row R
+    const int r = rank();
+    if (r > 0) {
+      const uint4* src = reinterpret_cast<const uint4*>(base + (size_t)(r - 1) * 2 * rb + rb);
+      for (int i = threadIdx.x; i < n16; i += blockDim.x) lo[i] = __ldcg(src + i);
+    }
+    if (r < (int)gridDim.x - 1) {
+      const uint4* src = reinterpret_cast<const uint4*>(base + (size_t)(r + 1) * 2 * rb);
+      for (int i = threadIdx.x; i < n16; i += blockDim.x) hi[i] = __ldcg(src + i);
+    }
+    pending = nullptr;
+    __syncthreads();
+  }
+
+  // the partials live in one global array read by every CTA after the barrier
+  __device__ void publish_tl(float* /*slot*/, int dst, const float4& chunk, int sub, int /*cs*/) {
+    if (sub == 0) {
+      *reinterpret_cast<float4*>(P.g_tl + dst) = chunk;
+      __threadfence();
+    }
+  }
+  __device__ const float* tl_slots(const float* /*local*/) const { return P.g_tl; }
+  __device__ float4 tl_load4(const float* slots, int idx) const {
+    return __ldcg(reinterpret_cast<const float4*>(slots + idx));
+  }
+};
+
+}  // namespace ptg

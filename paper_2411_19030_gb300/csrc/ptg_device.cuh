@@ -27,6 +27,14 @@ namespace cg = cooperative_groups;
 constexpr int kMaxCluster = 16;
 constexpr int kMaxWarps = 32;
 
+// First device-side error wins: status code, the task kind and the time index.
+__device__ __forceinline__ void record_error(DevStats* st, int code, int kind, int step) {
+  if (atomicCAS(&st->status, 0, code) == 0) {
+    st->fail_kind = 10 + kind;
+    st->fail_step = step;
+  }
+}
+
 // ---------------------------------------------------------------------------- cluster sync
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");

@@ -96,10 +96,17 @@ struct StepParams {
   DevStats* stats;
   int objective;             // PTG_OBJ_POWER_MEAN or PTG_OBJ_MODIFIED
   int plt;                   // correction kinds: coarse propagators identically zero (copy F)
-  // two-level preconditioner of the coarse-step solves (FP32 CG only; Ainv == null: Jacobi)
+  // two-level preconditioner of the coarse-step solves (Ainv == null: Jacobi)
   const float* Ainv;         // [ncp][ncp] inverse of the Galerkin coarse matrix (padded layout)
   int cm, nax, nay;          // aggregate size m and aggregate counts per direction
   int tl_naj;                // aggregate rows reserved per CTA (0: two-level disabled for this launch)
+  // one system over a whole cooperative grid (GridComm): global scratch of the op
+  int wide;                  // 1: launched as stepper_wide_kernel, cs = gridDim.x
+  double* g_red;             // [2][kMaxGrid][4] reduction partials
+  unsigned* g_bar;           // [3] grid barrier: arrival count, generation, broken flag (zeroed per launch)
+  void* g_halo;              // [kMaxGrid][2] rows of g_halo_row_bytes: first / last owned row
+  int g_halo_row_bytes;      // W * 8 (a row of doubles; float rows use the first half)
+  float* g_tl;               // [kMaxGrid][ncp] restricted partials of the two-level preconditioner
 };
 
 // Two-level preconditioner of the coarse-step solves: aggregates of m x m nodes (m a multiple
@@ -130,13 +137,15 @@ inline __host__ __device__ void coarse_rows_of_slab(int r0, int R, int m, int na
 // padded length of a coarse vector and of a row of the dense inverse (zero in the padding).
 inline __host__ __device__ int coarse_row_stride(int nax) { return (nax + 3) / 4 * 4; }
 
-// Shared-memory bytes of the two-level preconditioner for one CTA (naj aggregate rows).
-inline size_t twolevel_smem_bytes(int W, int rmax, int cs, int nax, int nay, int naj) {
+// Shared-memory bytes of the two-level preconditioner for one CTA (naj aggregate rows); the
+// partials of every rank sit in shared memory for a cluster (slots = true), in global memory
+// for a grid-wide launch.
+inline size_t twolevel_smem_bytes(int W, int rmax, int cs, int nax, int nay, int naj, bool slots = true) {
   const size_t naxp = (size_t)coarse_row_stride(nax), ncp = naxp * nay;
   const size_t groups = (size_t)rmax * (W / kGroup);
   size_t b = 0;
   b += (size_t)naj * naxp * ncp * 4;        // rows of Ainv for the CTA's aggregates
-  b += (size_t)cs * ncp * 4;                // restricted partials of every rank
+  if (slots) b += (size_t)cs * ncp * 4;     // restricted partials of every rank
   b += ncp * 4;                             // their sum over the covering ranks
   b += (size_t)naj * naxp * 4;              // coarse correction of the CTA's aggregates
   b += groups * 4;                          // group sums of the restricted vector
@@ -167,7 +176,11 @@ struct Plan {
   size_t smem = 0;
   int max_active_clusters = 0;
   bool twolevel = false;     // coarse kinds: two-level preconditioner (its shared memory is in smem)
+  bool wide = false;         // one task over a cooperative grid of cs CTAs (GridComm), no clusters
 };
+
+// CTAs of a grid-wide launch at most (>= the SM count of the chip).
+constexpr int kMaxGrid = 160;
 
 cudaError_t launch_stepper(const StepParams& P, const Plan& plan, int precision, int ntasks, cudaStream_t stream);
 cudaError_t launch_stepper_batch(int precision, int kind, const Plan& plan, const StepParams* table, const int2* tasks,
@@ -180,6 +193,11 @@ cudaError_t launch_coarse_setup(int nx, int ny, int W, int m, const NodeWeights&
 cudaError_t configure_kernel(const void* k, size_t smem, bool cluster);
 cudaError_t query_stepper_plan(int nx, int ny, int precision, int kind, int cs, int ng, int nthreads, size_t extra_smem,
                                Plan* plan);
+// Plan of the grid-wide variant for one task: G CTAs (one per SM at most) of rmax >= 2 rows;
+// extra_smem(G) gives the two-level bytes for G.  cudaErrorInvalidConfiguration if the kernel
+// does not exist for (precision, kind) or nothing fits.
+cudaError_t query_wide_plan(int nx, int ny, int precision, int kind, size_t (*extra_smem)(const void*, int),
+                            const void* ctx, Plan* plan);
 
 // Device arrays written by the assembly (see ptg_op in api.cu for their shapes).
 struct AssembleOut {

@@ -22,17 +22,11 @@
 //   CORRECT_ADJ Eq. 4.14 reverse sweep: v_s = G(v_{s+1}) + F[s] - G_old[s], v_Ntau = 0.
 #pragma once
 #include <type_traits>
+#include "comm.cuh"
 #include "ptg_device.cuh"
 #include "ptg_internal.h"
 
 namespace ptg {
-
-__device__ __forceinline__ void record_error(DevStats* st, int code, int kind, int step) {
-  if (atomicCAS(&st->status, 0, code) == 0) {
-    st->fail_kind = 10 + kind;
-    st->fail_step = step;
-  }
-}
 
 // 6-entry window of a row around a group: w[0] = offset b-1, w[1..4] = b..b+3, w[5] = b+4
 // (b a multiple of 4).  One 16-byte load for the centre in float, two in double.
@@ -138,15 +132,13 @@ __device__ __forceinline__ void stencil_elem32(const float* __restrict__ z, cons
   }
 }
 
-template <class Real, int NG>
+template <class Real, int NG, class Comm>
 struct Stepper {
   static constexpr bool kMixed = std::is_same<Real, float>::value;
 
   const StepParams& P;
-  cg::cluster_group& cluster;
-  RedSmem& rs;
+  Comm& comm;
   Slab sb;
-  int phase = 0;
   // shared memory (each pointer at the first non-slack entry)
   double* x64;      // FP64 state, rows -1..R
   double* b64;      // FP64 right-hand side, rows 0..R-1
@@ -157,6 +149,7 @@ struct Stepper {
   float* wt;
   // per-thread groups: loc0[k] = offset of the group's first node in the halo buffers, -1 if none
   int loc0[NG];
+  unsigned fmask = 0;   // bit 4k+j: node j of group k is an unknown (free, not a pad)
   NodeWeights A;    // per-node FP64 weights of the current operator
   double step_dt = 0.0;
   double inv_dt = 0.0;
@@ -175,12 +168,11 @@ struct Stepper {
   int* tl_gagg = nullptr;    // local aggregate (row-major in [naj][nax]) of every group, [R * G]
   int* tl_cov = nullptr;     // first / last rank covering each aggregate row, [nay][2]
 
-  __device__ Stepper(const StepParams& P_, cg::cluster_group& cl, RedSmem& rs_, unsigned char* dyn)
-      : P(P_), cluster(cl), rs(rs_) {
+  __device__ Stepper(const StepParams& P_, Comm& comm_, unsigned char* dyn) : P(P_), comm(comm_) {
     sb.nx = P.nx;
     sb.ny = P.ny;
     sb.cs = P.cs;
-    sb.rank = (int)cluster.block_rank();
+    sb.rank = comm.rank();
     slab_rows(P.ny + 1, P.cs, sb.rank, sb.r0, sb.R);
     sb.W = P.W;
     sb.G = P.W / kGroup;
@@ -216,7 +208,7 @@ struct Stepper {
         // multiple of 4 words
         float* t = eb + (kMixed ? 3 * elems : 0);
         tl_ainv = t;  t += P.tl_naj * naxp * ncp;
-        tl_slot = t;  t += P.cs * ncp;
+        tl_slot = t;  t += P.wide ? 0 : P.cs * ncp;   // grid-wide: the partials are in global memory
         tl_qc = t;    t += ncp;
         tl_ec = t;    t += P.tl_naj * naxp;
         tl_gs = t;    t += groups;
@@ -275,7 +267,7 @@ struct Stepper {
 
   template <class T, int NV, int NX = 0, class Post = NoPost>
   __device__ __forceinline__ void allreduce(T (&v)[NV + NX], Post post = Post()) {
-    cluster_allreduce<T, NV, NX, Post>(v, rs, phase, cluster, sb.cs, post);
+    comm.template allreduce<T, NV, NX, Post>(v, sb.cs, post);
   }
 
   // Select the operator C/dt + K (fine) or C/dtau + K (coarse): per-node FP64 weights for the
@@ -308,19 +300,26 @@ struct Stepper {
         wt[i] = (float)src[2 * PE + i];
       }
     }
+    fmask = 0;
 #pragma unroll
     for (int k = 0; k < NG; ++k) {
       const int l0 = loc0[k];
       if (l0 < 0) continue;
+#pragma unroll
       for (int j = 0; j < kGroup; ++j) {
         const int g = gnode(l0, j);
         Real v = Real(0);
-        if (g >= 0 && P.dirichlet[g] == 0) v = Real(1) / (Real)A.C[l0 + gshift + j];
+        if (g >= 0 && P.dirichlet[g] == 0) {
+          v = Real(1) / (Real)A.C[l0 + gshift + j];
+          fmask |= 1u << (kGroup * k + j);
+        }
         dinv[l0 + j] = v;
       }
     }
     __syncthreads();
   }
+
+  __device__ __forceinline__ bool unknown(int k, int j) const { return (fmask >> (kGroup * k + j)) & 1u; }
 
   // Load a node vector from global memory into x64: owned rows and both halo rows
   // (Dirichlet nodes forced to zero).  Ends with __syncthreads.
@@ -365,8 +364,8 @@ struct Stepper {
   template <class T>
   __device__ void exchange(T* buf) {
     __syncthreads();
-    push_halos(buf, sb, cluster);
-    cluster_sync_all();
+    comm.push_halos(buf, sb);
+    comm.sync();
   }
   __device__ void exchange_x64() { exchange(x64); }
 
@@ -401,7 +400,7 @@ struct Stepper {
 #pragma unroll
       for (int j = 0; j < kGroup; ++j) {
         ax64[l0 + j] = y[j];
-        if (dinv[l0 + j] != Real(0)) {
+        if (unknown(k, j)) {
           r64[k][j] = b64[l0 + j] - y[j];
           rr = fma(r64[k][j], r64[k][j], rr);
         }
@@ -421,7 +420,7 @@ struct Stepper {
       if (l0 < 0) continue;
 #pragma unroll
       for (int j = 0; j < kGroup; ++j) {
-        if (dinv[l0 + j] != Real(0)) {
+        if (unknown(k, j)) {
           r64[k][j] = b64[l0 + j] - ax64[l0 + j];
           rr = fma(r64[k][j], r64[k][j], rr);
         }
@@ -490,8 +489,7 @@ struct Stepper {
       if (item0 < items) {
         const int ajl0 = item0 / naxp, ax0 = item0 - ajl0 * naxp;
         const int dst = sb.rank * ncp + (aj0 + ajl0) * naxp + ax0;
-        for (int q = lane & 15; q < sb.cs; q += 16)
-          *reinterpret_cast<float4*>(cluster.map_shared_rank(tl_slot + dst, (unsigned)q)) = chunk;
+        comm.publish_tl(tl_slot, dst, chunk, lane & 15, sb.cs);
       }
     }
   }
@@ -501,11 +499,15 @@ struct Stepper {
   // ec -= alpha Ac^-1 qc on the CTA's aggregate rows (8 lanes per row of Ac^-1, 16-byte loads).
   __device__ void coarse_gather(bool first, float alpha) {
     const int naxp = coarse_row_stride(P.nax), ncp = naxp * P.nay;
-    for (int L = threadIdx.x; L < ncp; L += blockDim.x) {
-      const int J = L / naxp;
-      float acc = 0.f;
-      for (int q = tl_cov[2 * J]; q <= tl_cov[2 * J + 1]; ++q) acc += tl_slot[q * ncp + L];
-      tl_qc[L] = acc;
+    const float* slots = comm.tl_slots(tl_slot);
+    for (int L4 = threadIdx.x; L4 < ncp / 4; L4 += blockDim.x) {
+      const int J = (4 * L4) / naxp;            // a 16-byte chunk lies in one aggregate row
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int q = tl_cov[2 * J]; q <= tl_cov[2 * J + 1]; ++q) {
+        const float4 u = comm.tl_load4(slots, q * ncp + 4 * L4);
+        acc.x += u.x; acc.y += u.y; acc.z += u.z; acc.w += u.w;
+      }
+      reinterpret_cast<float4*>(tl_qc)[L4] = acc;
     }
     __syncthreads();
     const int nrows = naj * naxp, n4 = ncp / 4;
@@ -547,7 +549,7 @@ struct Stepper {
 #pragma unroll
       for (int j = 0; j < kGroup; ++j) {
         const Real di = dinv[l0 + j];
-        const Real z = di != Real(0) ? fma(di, r[k][j], e) : Real(0);
+        const Real z = unknown(k, j) ? fma(di, r[k][j], e) : Real(0);
         zbuf[l0 + j] = z;
         rz = fma(r[k][j], z, rz);
       }
@@ -579,12 +581,12 @@ struct Stepper {
       }
       if (tl) {
         coarse_restrict_push(r);
-        cluster_sync_all();
+        comm.sync();
         coarse_gather(true, 0.f);
         v[0] = prolong_precondition(r);
       }
       __syncthreads();
-      push_halos(zbuf, sb, cluster);
+      comm.push_halos(zbuf, sb);
       allreduce<Real, 1>(v);
       rz = v[0];
     }
@@ -602,8 +604,7 @@ struct Stepper {
         apply_A(zbuf, l0, w);
 #pragma unroll
         for (int j = 0; j < kGroup; ++j) {
-          const Real di = dinv[l0 + j];
-          const Real wj = di != Real(0) ? w[j] : Real(0);
+          const Real wj = unknown(k, j) ? w[j] : Real(0);
           const Real z = zbuf[l0 + j];
           p[k][j] = fma(beta, p[k][j], z);
           q[k][j] = fma(beta, q[k][j], wj);
@@ -635,7 +636,7 @@ struct Stepper {
       }
       if (tl) v[0] = prolong_precondition(r);
       __syncthreads();
-      push_halos(zbuf, sb, cluster);
+      comm.push_halos(zbuf, sb);
       allreduce<Real, 2, 1>(v, [rz_c](Real* t) { t[2] = t[0] / rz_c; });
       ++it;
       if (!(v[1] > target2)) done = true;  // NaN keeps iterating until the limit
@@ -980,7 +981,7 @@ struct Stepper {
       // g_s = g_{s+1} - (1/Ntau) term(lambda_G) + F_g[s] - G_g[s]
       accumulate_g(Tk, Tkm, P.dtau, (double)P.Ntau, P.out_aux + (size_t)(s + 1) * P.Ne, P.out_aux + (size_t)s * P.Ne,
                    P.F_aux + (size_t)s * P.Ne, P.G_aux + (size_t)s * P.Ne);
-      cluster_sync_all();                       // every CTA is done reading lambda_G halos
+      comm.sync();                              // every CTA is done reading lambda_G halos
       apply_correction(P.F_field + (size_t)s * P.Nn, P.G_field + (size_t)s * P.Nn, P.out_field + (size_t)s * P.Nn,
                        nullptr);
       exchange_x64();
@@ -993,8 +994,8 @@ struct Stepper {
 // plan picks the block size), at most 128 registers per thread.
 constexpr int kStepMaxThreads = 512;
 
-template <class Real, int NG, int KIND>
-__device__ __forceinline__ void run_task(Stepper<Real, NG>& st, int task) {
+template <class Real, int NG, int KIND, class Comm>
+__device__ __forceinline__ void run_task(Stepper<Real, NG, Comm>& st, int task) {
   if constexpr (KIND == KIND_FINE_PRI) st.fine_primal(task);
   if constexpr (KIND == KIND_COARSE_PRI) st.coarse_primal(task);
   if constexpr (KIND == KIND_CORRECT_PRI) st.correct_primal();
@@ -1007,13 +1008,25 @@ template <class Real, int NG, int KIND>
 __global__ void __launch_bounds__(kStepMaxThreads, 1) stepper_kernel(const __grid_constant__ StepParams P) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   __shared__ RedSmem rs;
-  cg::cluster_group cluster = cg::this_cluster();
-  Stepper<Real, NG> st(P, cluster, rs, dyn_smem);
+  ClusterComm comm(rs);
+  Stepper<Real, NG, ClusterComm> st(P, comm, dyn_smem);
   // every CTA of the cluster has initialised its shared memory before any DSMEM traffic
   cluster_sync_all();
   run_task<Real, NG, KIND>(st, (int)(blockIdx.x / (unsigned)P.cs));
   // no CTA leaves while another may still read or write its shared memory
   cluster_sync_all();
+}
+
+// One system spread over the whole grid of a cooperative launch (P.cs = gridDim.x CTAs, one
+// slab each); halo rows, reduction partials and the two-level partials go through global
+// memory (GridComm).  For the single-task kinds whose CG runs in FP64.
+template <class Real, int NG, int KIND>
+__global__ void __launch_bounds__(kStepMaxThreads, 1) stepper_wide_kernel(const __grid_constant__ StepParams P) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  __shared__ RedSmem rs;
+  GridComm comm(P, rs);
+  Stepper<Real, NG, GridComm> st(P, comm, dyn_smem);
+  run_task<Real, NG, KIND>(st, 0);
 }
 
 // Persistent multi-design variant: `tasks` lists (design, task) pairs, largest designs first;
@@ -1028,21 +1041,21 @@ __global__ void __launch_bounds__(kStepMaxThreads, 1) stepper_batch_kernel(const
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   __shared__ RedSmem rs;
   __shared__ int s_task;
-  cg::cluster_group cluster = cg::this_cluster();
-  const unsigned rank = cluster.block_rank();
+  ClusterComm comm(rs);
+  const unsigned rank = comm.cl.block_rank();
   cluster_sync_all();                          // all CTAs running before any DSMEM store
   for (;;) {
     // rank 0 claims the next task and writes it into every CTA of the cluster; the barrier
     // publishes it (and orders it after the previous task's last shared-memory access)
     if (rank == 0 && threadIdx.x == 0) {
       const int t = atomicAdd(queue, 1);
-      for (unsigned r = 0; r < cluster.num_blocks(); ++r) *cluster.map_shared_rank(&s_task, r) = t;
+      for (unsigned r = 0; r < comm.cl.num_blocks(); ++r) *comm.cl.map_shared_rank(&s_task, r) = t;
     }
     cluster_sync_all();
     const int t = s_task;                      // identical in every CTA: the loop is uniform
     if (t >= ntasks) break;
     const int2 tk = tasks[t];
-    Stepper<Real, NG> st(table[tk.x], cluster, rs, dyn_smem);
+    Stepper<Real, NG, ClusterComm> st(table[tk.x], comm, dyn_smem);
     cluster_sync_all();
     run_task<Real, NG, KIND>(st, tk.y);
     cluster_sync_all();

@@ -19,9 +19,21 @@
 
 namespace ptg {
 
+// The grid-wide variant exists for the FP64 kernels of the kinds that run as one task (the
+// correction sweeps and chained sequential runs), for up to 3 groups per thread.
+constexpr bool kWideKind = std::is_same<PTG_REAL, double>::value &&
+                           (PTG_KIND == KIND_FINE_PRI || PTG_KIND == KIND_CORRECT_PRI ||
+                            PTG_KIND == KIND_FINE_ADJ || PTG_KIND == KIND_CORRECT_ADJ);
+template <int NG>
+StepKernel wide_kernel() {
+  if constexpr (kWideKind && NG <= 3) return &stepper_wide_kernel<PTG_REAL, NG, PTG_KIND>;
+  else return nullptr;
+}
+
 StepKernels PTG_SELECT_NAME(PTG_TAG, PTG_KIND)(int ng) {
-#define PTG_PAIR(NG_) \
-  StepKernels{&stepper_kernel<PTG_REAL, NG_, PTG_KIND>, &stepper_batch_kernel<PTG_REAL, NG_, PTG_KIND>}
+#define PTG_PAIR(NG_)                                                                                   \
+  StepKernels{&stepper_kernel<PTG_REAL, NG_, PTG_KIND>, &stepper_batch_kernel<PTG_REAL, NG_, PTG_KIND>, \
+              wide_kernel<NG_>()}
   switch (ng) {
     case 1: return PTG_PAIR(1);
     case 2: return PTG_PAIR(2);
@@ -29,7 +41,7 @@ StepKernels PTG_SELECT_NAME(PTG_TAG, PTG_KIND)(int ng) {
     case 4: return PTG_PAIR(4);
     case 5: return PTG_PAIR(5);
     case 6: return PTG_PAIR(6);
-    default: return StepKernels{nullptr, nullptr};
+    default: return StepKernels{nullptr, nullptr, nullptr};
   }
 #undef PTG_PAIR
 }

@@ -9,6 +9,7 @@ using BatchKernel = void (*)(const StepParams*, const int2*, int, int*);
 struct StepKernels {
   StepKernel single;
   BatchKernel batch;
+  StepKernel wide;      // grid-wide variant (FP64, single-task kinds, NG <= 3), else null
 };
 
 // Groups of 4 nodes per thread (NG) supported by the build; a CTA has up to 512 threads, so
@@ -34,7 +35,7 @@ inline StepKernels stepper_kernels_for(int precision, int kind, int ng) {
     case 3: return f32 ? stepper_select_f32_3(ng) : stepper_select_f64_3(ng);
     case 4: return f32 ? stepper_select_f32_4(ng) : stepper_select_f64_4(ng);
     case 5: return f32 ? stepper_select_f32_5(ng) : stepper_select_f64_5(ng);
-    default: return StepKernels{nullptr, nullptr};
+    default: return StepKernels{nullptr, nullptr, nullptr};
   }
 }
 inline StepKernel stepper_kernel_for(int precision, int kind, int ng) { return stepper_kernels_for(precision, kind, ng).single; }
