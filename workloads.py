@@ -25,6 +25,9 @@ variants used for measurement):
 * ``loop512``   512x512, Nt=4096 in 128 slices, rho = 0.4 uniform.
 * ``paper100``  100x100, Nt=480, Table 1 materials, bottom-edge sink,
   q(t) = (1 - t)(1 + cos 50 t)/2 (Eq. 5.1), p = 20.
+* ``batch48``   48 designs of uneven size for the batching pattern: design i has side
+  (64, 96, 128, 192, 256)[i mod 5], (Nt, Ntau) = ((512, 16), (1024, 32), (2048, 64))[i mod 3]
+  (M = 32), dt = 1/Nt, rho ~ U(0.2, 0.8) seed 100 + i (see ``batch48``).
 """
 from __future__ import annotations
 
@@ -33,7 +36,7 @@ import numpy as np
 __all__ = [
     "WORKLOADS", "workload", "rho_plain", "rho_uniform", "rho_warm_perturb",
     "dirichlet_left_centre", "dirichlet_bottom_centre", "dirichlet_none",
-    "q_time_paper", "fd_elements", "rho_mirror_y",
+    "q_time_paper", "fd_elements", "rho_mirror_y", "batch48",
 ]
 
 # Material sets.  "simp_k" is conductivity-only SIMP k = 1e-3 + (1 - 1e-3) rho^3
@@ -127,3 +130,17 @@ def fd_elements(Ne: int, count: int = 32, seed: int = 1) -> np.ndarray:
     """Element indices for finite-difference gradient checks (drawn without replacement)."""
     rng = np.random.default_rng(seed)
     return np.sort(rng.choice(Ne, size=count, replace=False))
+
+
+def batch48() -> list[dict]:
+    """The 48 designs of the batching workload: sides cycle through 64, 96, 128, 192, 256
+    (10, 10, 10, 9, 9 designs), time grids through (512, 16), (1024, 32), (2048, 64);
+    conductivity SIMP, left-centre sink, p = 8, rho ~ U(0.2, 0.8) with seed 100 + index."""
+    out = []
+    for i in range(48):
+        n = (64, 96, 128, 192, 256)[i % 5]
+        Nt, Ntau = ((512, 16), (1024, 32), (2048, 64))[i % 3]
+        out.append(dict(index=i, n=n, Nt=Nt, Ntau=Ntau, dt=1.0 / Nt, p=8.0, material="simp_k", sink="left",
+                        seed=100 + i, rho=rho_uniform(n, n, 100 + i, 0.2, 0.8)))
+    return out
+
