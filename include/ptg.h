@@ -102,10 +102,12 @@ typedef struct {
                           D^-1 + P Ac^-1 P^T: P piecewise constant on aggregates of m x m nodes
                           (m the smallest multiple of 4 giving <= 16 aggregates per direction),
                           Ac = P^T A P, its inverse applied in FP32.  0: Jacobi everywhere. */
-    int grid_wide;     /* a single FP64 system (correction sweeps, chained sequential runs) may run
-                          over a cooperative grid of up to one CTA per SM, communicating through
-                          global memory, instead of one 16-CTA cluster: 0 never; 1 when the grid
-                          has >= 40000 nodes or no cluster plan fits; 2 always. */
+    int grid_wide;     /* systems may run on groups of CTAs of one cooperative launch, talking
+                          through global memory, instead of one 16-CTA cluster each: a single
+                          FP64 system (correction sweeps, chained runs) over every SM, other
+                          kinds in groups of the fewest CTAs whose slabs fit.  0 never; 1 for a
+                          single FP64 system on >= 40000 nodes and whenever no cluster plan fits
+                          (grids beyond about 300 x 300); 2 always. */
 } ptg_solve;
 
 typedef struct {

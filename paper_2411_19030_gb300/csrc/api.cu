@@ -197,15 +197,21 @@ int choose_plan(ptg_op* op, int precision, int kind, int ntasks, Plan* out) {
   // launch spreads the FP64 work over every SM, but each of its reductions costs a few
   // microseconds of global-memory round trips against about one for a cluster.  Measured on
   // GB300 the cluster wins at 128 x 128; the grid wins once the per-iteration FP64 work of 16
-  // SMs dominates (kWideMinNodes) or when no cluster plan fits (large grids in FP64).
-  // grid_wide: 0 never, 1 by that rule, 2 always.
+  // SMs dominates (kWideMinNodes).  Grids whose slabs do not fit 16 CTAs (512 x 512) run in
+  // groups of CTAs of one cooperative launch.  grid_wide: 0 never, 1 by these rules, 2 always.
   Plan jac, two;
   const long wj = best_plan(op, precision, kind, ntasks, false, &jac);
-  const bool want_wide = op->sv.grid_wide == 2 || (op->sv.grid_wide == 1 && (wj < 0 || op->Nn >= kWideMinNodes));
-  if (ntasks == 1 && precision == PTG_FP64 && want_wide) {
+  const long wt = twolevel_rows(op, precision, kind, 1) > 0 ? best_plan(op, precision, kind, ntasks, true, &two) : -1;
+  const bool spread = ntasks == 1 && precision == PTG_FP64;
+  const bool no_cluster = wj < 0 && wt < 0;
+  const bool want_wide = op->sv.grid_wide == 2 ||
+                         (op->sv.grid_wide == 1 && (no_cluster || (spread && op->Nn >= kWideMinNodes)));
+  if (want_wide) {
+    // one FP64 system over every SM (spread), or groups of the fewest CTAs whose slabs fit
     Plan w;
     WideCtx ctx{op, precision, kind};
-    if (query_wide_plan(op->g.nx, op->g.ny, precision, kind, wide_twolevel_bytes, &ctx, &w) == cudaSuccess) {
+    if (query_wide_plan(op->g.nx, op->g.ny, precision, kind, ntasks, spread, wide_twolevel_bytes, &ctx, &w) ==
+        cudaSuccess) {
       w.twolevel = twolevel_rows(op, precision, kind, w.cs) > 0;
       op->plans[key] = w;
       *out = w;
@@ -213,9 +219,8 @@ int choose_plan(ptg_op* op, int precision, int kind, int ntasks, Plan* out) {
     }
     cudaGetLastError();
   }
-  const long wt = twolevel_rows(op, precision, kind, 1) > 0 ? best_plan(op, precision, kind, ntasks, true, &two) : -1;
-  if (wj < 0 && wt < 0) {
-    std::snprintf(g_last_error, sizeof(g_last_error), "no cluster plan fits a %dx%d grid", op->g.nx, op->g.ny);
+  if (no_cluster) {
+    std::snprintf(g_last_error, sizeof(g_last_error), "no launch plan fits a %dx%d grid", op->g.nx, op->g.ny);
     return PTG_EINVAL;
   }
   // FP64 CG on GB300 is bound by the FP64 pipe, so the cut in iterations outweighs extra
@@ -282,6 +287,7 @@ int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream) {
   P.rmax = plan.rmax;
   if (plan.wide) {
     P.wide = 1;
+    P.wide_tasks = ntasks;
     P.g_red = op->g_red;
     P.g_bar = op->g_bar;
     P.g_halo = op->g_halo;
@@ -392,7 +398,7 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
   }
   A(&op->scratch, 2 * sizeof(double));
   A(&op->g_red, 2 * kMaxGrid * 4 * sizeof(double));
-  A(&op->g_bar, 64);
+  A(&op->g_bar, 4 * kMaxGrid * sizeof(unsigned));
   A(&op->g_halo, (size_t)kMaxGrid * 2 * op->W * sizeof(double));
   A(&op->stats, sizeof(DevStats));
   if (e != cudaSuccess) {

@@ -8,10 +8,11 @@
 //   ClusterComm  one thread-block cluster (up to 16 CTAs): distributed shared memory stores
 //                and the hardware cluster barrier.  Used wherever several independent
 //                systems run side by side (one cluster each).
-//   GridComm     one cooperative launch of G CTAs (up to kMaxGrid, one per SM): global memory
-//                and a counting grid barrier.  Used for a single system whose solves are
-//                bound by the FP64 pipe (1/58 of the FP32 rate on this chip): spreading it
-//                over every SM instead of one cluster multiplies the FP64 throughput.
+//   GridComm     groups of G CTAs of one cooperative launch (up to kMaxGrid CTAs in all, one
+//                per SM), each group running one system at a time: global memory and a
+//                counting barrier per group.  Used for a single system whose solves are bound
+//                by the FP64 pipe (1/58 of the FP32 rate on this chip), spread over every SM
+//                instead of one cluster, and for grids whose slabs do not fit 16 CTAs.
 //
 // Both produce bitwise identical reductions in every CTA (fixed summation orders).
 #pragma once
@@ -61,17 +62,25 @@ __device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// The CTAs of a cooperative launch form groups of G = P.cs consecutive CTAs; each group runs
+// one system at a time.  Reduction partials, halo rows and two-level partials are indexed by
+// the global block index (every group owns its range); the barrier has one set of counters per
+// group.
 struct GridComm {
   const StepParams& P;
   RedSmem& rs;
   int phase = 0;
+  const int G;                   // CTAs of the group
+  const int gid;                 // group index
+  const int base;                // first block of the group
   // halo rows published by push_halos and pulled in after the next barrier
   unsigned char* pending = nullptr;
   int pending_bytes = 0;         // bytes of one row
   int R = 0, W = 0;
 
-  __device__ GridComm(const StepParams& P_, RedSmem& rs_) : P(P_), rs(rs_) {}
-  __device__ int rank() const { return (int)blockIdx.x; }
+  __device__ GridComm(const StepParams& P_, RedSmem& rs_)
+      : P(P_), rs(rs_), G(P_.cs), gid((int)blockIdx.x / P_.cs), base(((int)blockIdx.x / P_.cs) * P_.cs) {}
+  __device__ int rank() const { return (int)blockIdx.x - base; }
 
   // Counting barrier over all CTAs of the launch (co-resident: cooperative launch).  Thread 0
   // of each CTA makes the CTA's global writes visible, arrives, and waits for the generation
@@ -82,13 +91,13 @@ struct GridComm {
   __device__ void barrier() {
     __syncthreads();
     if (threadIdx.x == 0) {
-      unsigned* count = P.g_bar;
-      unsigned* gen = P.g_bar + 1;
-      unsigned* broken = P.g_bar + 2;
+      unsigned* count = P.g_bar + 4 * gid;
+      unsigned* gen = count + 1;
+      unsigned* broken = count + 2;
       const unsigned g0 = ld_acquire_gpu(gen);
       __threadfence();
       const unsigned arrived = atomicAdd(count, 1u);
-      if (arrived == gridDim.x - 1) {
+      if (arrived == (unsigned)G - 1u) {
         atomicExch(count, 0u);
         __threadfence();
         st_release_gpu(gen, g0 + 1u);
@@ -111,7 +120,7 @@ struct GridComm {
   __device__ void sync() { barrier(); }
 
   template <class T, int NV, int NX, class Post>
-  __device__ void allreduce(T (&v)[NV + NX], int G, Post post) {
+  __device__ void allreduce(T (&v)[NV + NX], int /*cs*/, Post post) {
     RedBank<T>& rb = bank<T>(rs);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
 #pragma unroll
@@ -130,7 +139,7 @@ struct GridComm {
       for (int i = 0; i < NV; ++i) {
         T s = rb.warp[0][i];
         for (int w = 1; w < nwarps; ++w) s += rb.warp[w][i];
-        slots[rank() * 4 + i] = (double)s;          // exact for T = float too
+        slots[(int)blockIdx.x * 4 + i] = (double)s;  // exact for T = float too
       }
     }
     barrier();
@@ -139,7 +148,7 @@ struct GridComm {
 #pragma unroll
       for (int i = 0; i < NV; ++i) {
         T t = T(0);
-        for (int r = lane; r < G; r += 32) t += (T)__ldcg(slots + r * 4 + i);
+        for (int r = lane; r < G; r += 32) t += (T)__ldcg(slots + (base + r) * 4 + i);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         v[i] = t;
@@ -153,7 +162,7 @@ struct GridComm {
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
           T a = T(0);
-          for (int r = lane; r < G; r += 32) a += (T)__ldcg(slots + r * 4 + i);
+          for (int r = lane; r < G; r += 32) a += (T)__ldcg(slots + (base + r) * 4 + i);
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
           t[i] = a;
@@ -178,7 +187,7 @@ struct GridComm {
   template <class T>
   __device__ void push_halos(T* buf, const Slab& sb) {
     const int nb = sb.W * (int)sizeof(T);           // bytes per row, a multiple of 16
-    unsigned char* out = reinterpret_cast<unsigned char*>(P.g_halo) + (size_t)rank() * 2 * P.g_halo_row_bytes;
+    unsigned char* out = reinterpret_cast<unsigned char*>(P.g_halo) + (size_t)blockIdx.x * 2 * P.g_halo_row_bytes;
     const uint4* s0 = reinterpret_cast<const uint4*>(buf + 1 * sb.W);
     const uint4* s1 = reinterpret_cast<const uint4*>(buf + sb.R * sb.W);
     uint4* d0 = reinterpret_cast<uint4*>(out);
@@ -196,32 +205,34 @@ struct GridComm {
   // After a barrier: the neighbours' last / first rows into the local halo rows -1 and R.
   __device__ void pull_halos() {
     if (!pending) return;
-    const unsigned char* base = reinterpret_cast<const unsigned char*>(P.g_halo);
+    const unsigned char* hb = reinterpret_cast<const unsigned char*>(P.g_halo);
     const size_t rb = P.g_halo_row_bytes;
     const int n16 = pending_bytes / 16;
     uint4* lo = reinterpret_cast<uint4*>(pending);                                    // row -1
     uint4* hi = reinterpret_cast<uint4*>(pending + (size_t)(R + 1) * pending_bytes);  // row R
-    const int r = rank();
+    const int r = rank(), b = (int)blockIdx.x;
     if (r > 0) {
-      const uint4* src = reinterpret_cast<const uint4*>(base + (size_t)(r - 1) * 2 * rb + rb);
+      const uint4* src = reinterpret_cast<const uint4*>(hb + (size_t)(b - 1) * 2 * rb + rb);
       for (int i = threadIdx.x; i < n16; i += blockDim.x) lo[i] = __ldcg(src + i);
     }
-    if (r < (int)gridDim.x - 1) {
-      const uint4* src = reinterpret_cast<const uint4*>(base + (size_t)(r + 1) * 2 * rb);
+    if (r < G - 1) {
+      const uint4* src = reinterpret_cast<const uint4*>(hb + (size_t)(b + 1) * 2 * rb);
       for (int i = threadIdx.x; i < n16; i += blockDim.x) hi[i] = __ldcg(src + i);
     }
     pending = nullptr;
     __syncthreads();
   }
 
-  // the partials live in one global array read by every CTA after the barrier
+  // the partials live in one global array read by every CTA of the group after the barrier
+  // (dst is rank-relative; the group's range starts at its first block)
   __device__ void publish_tl(float* /*slot*/, int dst, const float4& chunk, int sub, int /*cs*/) {
     if (sub == 0) {
-      *reinterpret_cast<float4*>(P.g_tl + dst) = chunk;
+      *reinterpret_cast<float4*>(P.g_tl + (size_t)base * tl_ncp() + dst) = chunk;
       __threadfence();
     }
   }
-  __device__ const float* tl_slots(const float* /*local*/) const { return P.g_tl; }
+  __device__ int tl_ncp() const { return coarse_row_stride(P.nax) * P.nay; }
+  __device__ const float* tl_slots(const float* /*local*/) const { return P.g_tl + (size_t)base * tl_ncp(); }
   __device__ float4 tl_load4(const float* slots, int idx) const {
     return __ldcg(reinterpret_cast<const float4*>(slots + idx));
   }

@@ -54,14 +54,15 @@ cudaError_t launch_stepper(const StepParams& P, const Plan& plan, int precision,
     // one system over a cooperative grid: every CTA must be resident (the grid barrier waits
     // for all of them); the barrier's count and generation start at zero
     StepKernel k = stepper_kernels_for(precision, P.kind, plan.ng).wide;
-    if (!k || ntasks != 1) return cudaErrorInvalidConfiguration;
+    const int ngroups = plan.max_active_clusters < ntasks ? plan.max_active_clusters : ntasks;
+    if (!k || ngroups < 1 || ngroups * plan.cs > kMaxGrid || P.wide_tasks != ntasks) return cudaErrorInvalidConfiguration;
     cudaError_t e = configure_kernel((const void*)k, plan.smem, false);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(P.g_bar, 0, 3 * sizeof(unsigned), stream);
+    e = cudaMemsetAsync(P.g_bar, 0, 4 * sizeof(unsigned) * ngroups, stream);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
-    cfg.gridDim = dim3((unsigned)plan.cs, 1, 1);
+    cfg.gridDim = dim3((unsigned)(ngroups * plan.cs), 1, 1);
     cfg.blockDim = dim3((unsigned)plan.nthreads, 1, 1);
     cfg.dynamicSmemBytes = plan.smem;
     cfg.stream = stream;
@@ -121,40 +122,56 @@ cudaError_t query_stepper_plan(int nx, int ny, int precision, int kind, int cs, 
   return e;
 }
 
-cudaError_t query_wide_plan(int nx, int ny, int precision, int kind, size_t (*extra_smem)(const void*, int),
-                            const void* ctx, Plan* plan) {
+cudaError_t query_wide_plan(int nx, int ny, int precision, int kind, int ntasks, bool spread,
+                            size_t (*extra_smem)(const void*, int), const void* ctx, Plan* plan) {
   int dev = 0, nsm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   const int rows = ny + 1;
-  int G = nsm < kMaxGrid ? nsm : kMaxGrid;
-  if (G > rows / 2) G = rows / 2;                  // at least 2 rows per CTA
-  if (G < 2) return cudaErrorInvalidConfiguration;
-  const int rmax = (rows + G - 1) / G;
-  const int groups = rmax * (padded_width(nx) / kGroup);
-  for (int ng = 1; ng <= 3; ++ng) {
-    StepKernel k = stepper_kernels_for(precision, kind, ng).wide;
-    if (!k) return cudaErrorInvalidConfiguration;
-    const int nthreads = ((groups + ng - 1) / ng + 31) / 32 * 32;
-    if (nthreads > kStepMaxThreadsHost) continue;
-    const size_t smem = stepper_smem_bytes(nx, rmax, precision == PTG_FP32_REFINE ? 4 : 8) + extra_smem(ctx, G);
-    if (smem > 227 * 1024) continue;
-    e = configure_kernel((const void*)k, smem, false);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nthreads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1 || G > per_sm * nsm) continue;
-    plan->cs = G;
-    plan->nthreads = nthreads;
-    plan->ng = ng;
-    plan->rmax = rmax;
-    plan->smem = smem;
-    plan->max_active_clusters = 1;
-    plan->wide = true;
-    return cudaSuccess;
+  const int cap = nsm < kMaxGrid ? nsm : kMaxGrid;
+  const int gw = padded_width(nx) / kGroup;
+  // candidate CTA counts per group: spread -> as many as possible; else the fewest that fit
+  int gfirst, glast, gstep;
+  if (spread) {
+    gfirst = cap < rows / 2 ? cap : rows / 2;
+    glast = 2;
+    gstep = -1;
+  } else {
+    gfirst = 2;
+    glast = cap;
+    gstep = 1;
+  }
+  for (int G = gfirst; spread ? G >= glast : G <= glast; G += gstep) {
+    const int rmax = (rows + G - 1) / G;
+    if (rmax < 2) continue;
+    const int groups = rmax * gw;
+    for (int ng = 1; ng <= 3; ++ng) {
+      StepKernel k = stepper_kernels_for(precision, kind, ng).wide;
+      if (!k) return cudaErrorInvalidConfiguration;
+      const int nthreads = ((groups + ng - 1) / ng + 31) / 32 * 32;
+      if (nthreads > kStepMaxThreadsHost) continue;
+      const size_t smem = stepper_smem_bytes(nx, rmax, precision == PTG_FP32_REFINE ? 4 : 8) + extra_smem(ctx, G);
+      if (smem > 227 * 1024) continue;
+      e = configure_kernel((const void*)k, smem, false);
+      if (e != cudaSuccess) return e;
+      int per_sm = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nthreads, smem);
+      if (e != cudaSuccess) return e;
+      const int resident = per_sm * nsm < kMaxGrid ? per_sm * nsm : kMaxGrid;
+      if (per_sm < 1 || G > resident) continue;
+      int ngroups = resident / G;
+      if (ngroups > ntasks) ngroups = ntasks;
+      plan->cs = G;
+      plan->nthreads = nthreads;
+      plan->ng = ng;
+      plan->rmax = rmax;
+      plan->smem = smem;
+      plan->max_active_clusters = ngroups;
+      plan->wide = true;
+      return cudaSuccess;
+    }
   }
   return cudaErrorInvalidConfiguration;
 }

@@ -101,9 +101,10 @@ struct StepParams {
   int cm, nax, nay;          // aggregate size m and aggregate counts per direction
   int tl_naj;                // aggregate rows reserved per CTA (0: two-level disabled for this launch)
   // one system over a whole cooperative grid (GridComm): global scratch of the op
-  int wide;                  // 1: launched as stepper_wide_kernel, cs = gridDim.x
+  int wide;                  // 1: launched as stepper_wide_kernel, groups of cs CTAs
+  int wide_tasks;            // tasks of a grid-wide launch (group g runs g, g + groups, ...)
   double* g_red;             // [2][kMaxGrid][4] reduction partials
-  unsigned* g_bar;           // [3] grid barrier: arrival count, generation, broken flag (zeroed per launch)
+  unsigned* g_bar;           // [4 per group] barrier: arrival count, generation, broken flag (zeroed per launch)
   void* g_halo;              // [kMaxGrid][2] rows of g_halo_row_bytes: first / last owned row
   int g_halo_row_bytes;      // W * 8 (a row of doubles; float rows use the first half)
   float* g_tl;               // [kMaxGrid][ncp] restricted partials of the two-level preconditioner
@@ -193,11 +194,12 @@ cudaError_t launch_coarse_setup(int nx, int ny, int W, int m, const NodeWeights&
 cudaError_t configure_kernel(const void* k, size_t smem, bool cluster);
 cudaError_t query_stepper_plan(int nx, int ny, int precision, int kind, int cs, int ng, int nthreads, size_t extra_smem,
                                Plan* plan);
-// Plan of the grid-wide variant for one task: G CTAs (one per SM at most) of rmax >= 2 rows;
-// extra_smem(G) gives the two-level bytes for G.  cudaErrorInvalidConfiguration if the kernel
-// does not exist for (precision, kind) or nothing fits.
-cudaError_t query_wide_plan(int nx, int ny, int precision, int kind, size_t (*extra_smem)(const void*, int),
-                            const void* ctx, Plan* plan);
+// Plan of the grid-wide variant.  spread: one system over as many CTAs as there are SMs (rmax
+// >= 2 rows each); otherwise the fewest CTAs per group whose slabs fit, and as many groups as
+// fit the chip (plan.max_active_clusters = groups, at most ntasks).  extra_smem(G) gives the
+// two-level bytes for G CTAs.  cudaErrorInvalidConfiguration if nothing fits.
+cudaError_t query_wide_plan(int nx, int ny, int precision, int kind, int ntasks, bool spread,
+                            size_t (*extra_smem)(const void*, int), const void* ctx, Plan* plan);
 
 // Device arrays written by the assembly (see ptg_op in api.cu for their shapes).
 struct AssembleOut {

@@ -1017,16 +1017,22 @@ __global__ void __launch_bounds__(kStepMaxThreads, 1) stepper_kernel(const __gri
   cluster_sync_all();
 }
 
-// One system spread over the whole grid of a cooperative launch (P.cs = gridDim.x CTAs, one
-// slab each); halo rows, reduction partials and the two-level partials go through global
-// memory (GridComm).  For the single-task kinds whose CG runs in FP64.
+// Systems spread over groups of CTAs of a cooperative launch: the grid holds gridDim.x / P.cs
+// groups of P.cs CTAs (one slab each); group g runs tasks g, g + groups, ... < P.wide_tasks one
+// after the other.  Halo rows, reduction partials and the two-level partials go through global
+// memory (GridComm).  Used for one FP64 system over every SM, and for grids whose slabs do not
+// fit the 16 CTAs of a cluster.
 template <class Real, int NG, int KIND>
 __global__ void __launch_bounds__(kStepMaxThreads, 1) stepper_wide_kernel(const __grid_constant__ StepParams P) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   __shared__ RedSmem rs;
   GridComm comm(P, rs);
-  Stepper<Real, NG, GridComm> st(P, comm, dyn_smem);
-  run_task<Real, NG, KIND>(st, 0);
+  const int ngroups = (int)gridDim.x / P.cs;
+  for (int task = comm.gid; task < P.wide_tasks; task += ngroups) {
+    Stepper<Real, NG, GridComm> st(P, comm, dyn_smem);
+    run_task<Real, NG, KIND>(st, task);
+    comm.sync();                               // the group's halo slots are free again
+  }
 }
 
 // Persistent multi-design variant: `tasks` lists (design, task) pairs, largest designs first;

@@ -19,14 +19,11 @@
 
 namespace ptg {
 
-// The grid-wide variant exists for the FP64 kernels of the kinds that run as one task (the
-// correction sweeps and chained sequential runs), for up to 3 groups per thread.
-constexpr bool kWideKind = std::is_same<PTG_REAL, double>::value &&
-                           (PTG_KIND == KIND_FINE_PRI || PTG_KIND == KIND_CORRECT_PRI ||
-                            PTG_KIND == KIND_FINE_ADJ || PTG_KIND == KIND_CORRECT_ADJ);
+// The grid-wide (grouped) variant exists for every kind and precision, for up to 3 groups
+// per thread.
 template <int NG>
 StepKernel wide_kernel() {
-  if constexpr (kWideKind && NG <= 3) return &stepper_wide_kernel<PTG_REAL, NG, PTG_KIND>;
+  if constexpr (NG <= 3) return &stepper_wide_kernel<PTG_REAL, NG, PTG_KIND>;
   else return nullptr;
 }
 
