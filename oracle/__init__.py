@@ -19,6 +19,9 @@ Modules
                k-iteration scheme, the one-shot pass and the PLT variant (Sec. 7).
 ``allatonce``  Eq. 2.8-2.9 and 4.3: dense brute-force space-time solves, used only on
                tiny grids as an independent check of the time-stepping recursions.
+``design``     Sec. 2.1 and 3: the density filter, the threshold projection, the area
+               constraint, their chain rule, and the Method of Moving Asymptotes (Svanberg's
+               1987 method, one constraint) of the design update in Alg. 3.
 
 Pins (``tests/test_oracle_*.py``, run with ``-m "not gpu"``): the separable-eigenmode
 closed form, the discrete energy balance, the dense all-at-once solve, central
@@ -27,7 +30,10 @@ the M = 1 and N_tau = 1 degenerate cases, the one-shot fixed point, mirror symme
 the constant-field objective identity and the homogeneity of Theta in q; for the
 modified objective of Sec. 7.1, Theta~ = Theta^p and the gradient identity
 grad Theta = Theta^(1-p)/p grad Theta~; for PLT (G = 0, Sec. 7), its fixed point and its
-exactness after N_tau iterations.
+exactness after N_tau iterations; for the design update, the filter's averaging and its
+reproduction of affine fields, the projection's fixed points and derivative, central
+differences through filter, projection and objective, and MMA on problems with closed-form
+optima.
 The one-shot estimate for a design that differs from the warm-start design has
 no closed form: beyond the fixed point it is "parity unpinned" (it is the literal
 algorithm, checked only for consistency with the pinned pieces it is made of).
