@@ -342,6 +342,42 @@ int ptg_batch_run_phase(ptg_batch* b, int phase, cudaStream_t stream);
 int ptg_batch_set_plan(ptg_batch* b, int phase, int cs, int ng, int nthreads);
 int ptg_batch_get_plan(ptg_batch* b, int phase, int* cs, int* ng, int* nthreads, int* nclusters);
 
+/*
+ * Design parametrisation (Sec. 2.1) and area constraint (Sec. 3), on the device, FP64.
+ *   chi_fil = H chi: weighted average over the elements whose centres lie within r_fil of the
+ *             element's centre, cone weights r_fil - distance, each row normalised;
+ *   rho     = P(chi_fil) = (tanh(beta (chi_fil - eta)) + tanh(beta eta)) /
+ *                          (tanh(beta (1 - eta)) + tanh(beta eta)),  dproj = P'(chi_fil).
+ * ptg_design_forward: chi [Ne] -> rho [Ne], dproj [Ne].
+ * ptg_design_backward: df_dchi = H^T (dproj * df_drho) [Ne] (the chain rule of a function of
+ *             rho); df_drho == NULL stands for the constant 1/Ne (the area-fraction gradient).
+ * ptg_design_volume: *vol_d = mean(rho) (the area fraction on the uniform grid).
+ * Element arrays are row-major (ey, ex), caller-owned device memory; calls are asynchronous.
+ * r_fil must be positive and at most 64 h; 0 < eta < 1; beta > 0.
+ */
+typedef struct ptg_design ptg_design;
+int ptg_design_create(int nx, int ny, double h, double r_fil, double beta, double eta, int device,
+                      ptg_design** out);
+void ptg_design_destroy(ptg_design* d);
+int ptg_design_forward(ptg_design* d, const double* chi_d, double* rho_d, double* dproj_d, cudaStream_t stream);
+int ptg_design_backward(ptg_design* d, const double* dproj_d, const double* df_drho_d, double* df_dchi_d,
+                        cudaStream_t stream);
+int ptg_design_volume(ptg_design* d, const double* rho_d, double* vol_d, cudaStream_t stream);
+
+/*
+ * The design update of Alg. 3 on the host: the Method of Moving Asymptotes (Svanberg 1987) for
+ * min f0(x) s.t. f1(x) <= 0 and x_min <= x <= x_max (the paper's large-beta variant is not
+ * given; this is the plain method).  Moving asymptotes (shrink 0.7 on oscillation, expand 1.2
+ * on monotone progress), move limit `move`, convex separable models, and the single-multiplier
+ * dual solved by bisection.  ptg_mma_update takes host arrays of length n (x, df0, df1) and
+ * writes the next iterate to x_new (host); it keeps the last two iterates and asymptotes.
+ */
+typedef struct ptg_mma ptg_mma;
+int ptg_mma_create(int n, double x_min, double x_max, double move, ptg_mma** out);
+void ptg_mma_destroy(ptg_mma* m);
+int ptg_mma_update(ptg_mma* m, const double* x, double f0, const double* df0, double f1, const double* df1,
+                   double* x_new);
+
 /* Copy the device status and counters into *out (synchronises the op's last stream). */
 int ptg_get_stats(ptg_op* op, ptg_stats* out);
 

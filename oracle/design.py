@@ -159,3 +159,40 @@ class MMA:
         self.L, self.U = L, U
         self.k += 1
         return x_new
+
+
+def design_loop(prob, r_fil: float, beta: float, eta: float, a_max: float, chi0, iterations: int,
+                move: float = 0.2) -> dict:
+    """Alg. 3 for one problem: iteration 1 by sequential time stepping, later iterations by one
+    one-shot Parareal pass warm-started from the previous iteration's coarse states; the
+    design rho = P(H chi); MMA on (Theta / Theta_1, area fraction - a_max).  Returns the
+    objective, area fraction and chi of every iteration."""
+    from .parareal import coarse_states_from_sequential, oneshot_pass
+    from .stepping import Operator
+
+    des = Design(prob.nx, prob.ny, prob.h, r_fil, beta, eta)
+    mma = MMA(prob.nx * prob.ny, 0.0, 1.0, move)
+    chi = np.asarray(chi0, dtype=np.float64).copy()
+    U = V = None
+    theta1 = None
+    hist = dict(Theta=[], volume=[], chi=[])
+    for k in range(iterations):
+        rho, dproj = des.forward(chi)
+        op = Operator(prob, rho)
+        if k == 0:
+            U, V, seq = coarse_states_from_sequential(op)
+            Theta, grad = seq["Theta"], seq["grad"]
+        else:
+            out = oneshot_pass(op, U, V)
+            Theta, grad = out["Theta"], out["grad"]
+            U, V = out["U"], out["V"]
+        if theta1 is None:
+            theta1 = Theta
+        vol = float(np.mean(rho))
+        chi = mma.update(chi, Theta / theta1, des.backward(dproj, grad) / theta1, vol - a_max,
+                         des.volume_gradient(dproj))
+        hist["Theta"].append(Theta)
+        hist["volume"].append(vol)
+        hist["chi"].append(chi.copy())
+    return hist
+

@@ -80,6 +80,14 @@ SIGNATURES = {
     "ptg_batch_run_phase": (c_int, [_P, c_int, _P]),
     "ptg_batch_set_plan": (c_int, [_P, c_int, c_int, c_int, c_int]),
     "ptg_batch_get_plan": (c_int, [_P, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+    "ptg_design_create": (c_int, [c_int, c_int, c_double, c_double, c_double, c_double, c_int, POINTER(c_void_p)]),
+    "ptg_design_destroy": (None, [_P]),
+    "ptg_design_forward": (c_int, [_P, _P, _P, _P, _P]),
+    "ptg_design_backward": (c_int, [_P, _P, _P, _P, _P]),
+    "ptg_design_volume": (c_int, [_P, _P, _P, _P]),
+    "ptg_mma_create": (c_int, [c_int, c_double, c_double, c_double, POINTER(c_void_p)]),
+    "ptg_mma_destroy": (None, [_P]),
+    "ptg_mma_update": (c_int, [_P, _P, c_double, _P, c_double, _P, _P]),
     "ptg_get_stats": (c_int, [_P, POINTER(ptg_stats)]),
     "ptg_reset_stats": (c_int, [_P, _P]),
 }
