@@ -419,6 +419,64 @@ def roofline(kind_ms: dict, stats: dict, w: dict, N_free: int, args) -> dict:
                     "(ncu: barrier, membar and shared-memory stalls), not HBM"}
 
 
+# ---------------------------------------------------------------------------- full design loop
+
+def run_loop(args):
+    """Alg. 3 at 512 x 512, Nt = 4096 in 128 slices (M = 32): rho(0) = a_max = 0.4 uniform, the
+    paper's filter and projection (r_fil = 0.03, beta = 32, eta = 0.5, no continuation), host MMA
+    (move 0.2); design iteration 1 sequential, the rest one-shot.  Reports the time of every
+    design iteration and the objective history; the true objective of the final design by a
+    sequential FP64 pass, outside the timed loop."""
+    import torch
+
+    from paper_2411_19030_gb300 import Operator, SolveConfig
+    from paper_2411_19030_gb300.build import build_library
+    from paper_2411_19030_gb300.design import DesignMap, OneShotLoop
+
+    build_library()
+    n = args.loop_n
+    w = W.workload("loop512")
+    Nt, Ntau = (w["Nt"], w["Ntau"]) if n == 512 else (8 * n, n // 4)
+    h = 1.0 / n
+    dt = 1.0 / Nt
+    sink = W.dirichlet_left_centre(n, n, h)
+    a_max, r_fil, beta, eta = 0.4, 0.03, 32.0, 0.5
+    op = Operator(n, n, h, w["material"], Nt, Ntau, dt, w["p"], sink,
+                  solve=SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=4000, refine_max=8,
+                                    twolevel=args.twolevel))
+    true_op = Operator(n, n, h, w["material"], Nt, Ntau, dt, w["p"], sink,
+                       solve=SolveConfig("fp64", rtol=1e-12, cg_iters_max=8000, refine_max=8))
+    design = DesignMap(n, n, h, r_fil, beta, eta)
+    loop = OneShotLoop(op, design, a_max, move=0.2, true_op=true_op)
+    # uniform chi with P(chi) = a_max (the filter keeps a uniform field)
+    den = np.tanh(beta * (1 - eta)) + np.tanh(beta * eta)
+    chi0 = np.full(n * n, eta + np.arctanh(a_max * den - np.tanh(beta * eta)) / beta)
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        hist = loop.run(chi0, args.loop, true_every=0)
+        wall = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    true_final = loop.true_objective()
+    ms = hist["ms"]
+    oneshot = ms[1:] if len(ms) > 1 else ms
+    N_free = (n + 1) ** 2 - int(sink.sum())
+    line = {
+        "metric": "ms per one-shot design iteration (full design loop, host MMA)", "value": float(np.mean(oneshot)),
+        "unit": "ms", "higher_is_better": False, "n_gpus": 1, "steps": len(ms), "warmup": 0,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+        "config": {"workload": f"loop{n}: {n}x{n} grid, Nt={Nt}, Ntau={Ntau}, p=8, SIMP k, a_max={a_max}, "
+                               f"r_fil={r_fil}, beta={beta}, eta={eta}, MMA move 0.2",
+                   "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel},
+        "first_iteration_sequential_ms": ms[0],
+        "fine_dof_steps_per_s": 2.0 * N_free * Nt / (np.mean(oneshot) * 1e-3),
+        "history": {"Theta_estimate": hist["Theta"], "area_fraction": hist["volume"], "ms": ms},
+        "final": {"Theta_estimate": hist["Theta"][-1], "Theta_true_fp64_sequential": true_final,
+                  "area_fraction": hist["volume"][-1]},
+        "wall_s": wall, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------------------- CPU oracle arms
 
 ORACLE_SNIPPET = r"""
@@ -510,9 +568,15 @@ def main():
                     help="time the passes only: no end-to-end run, comparator, accuracy checks or G = 0 probe "
                          "(for profiling the launch sequence of the timed steps)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--loop", type=int, default=0, metavar="ITERATIONS",
+                    help="instead of the pass benchmark: the full design loop (512x512, Nt=4096, 128 slices, "
+                         "host MMA) for this many design iterations")
+    ap.add_argument("--loop-n", type=int, default=512, help="grid side of --loop")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.loop:
+        run_loop(args)
     else:
         run_gpu(args)
 
