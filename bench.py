@@ -477,6 +477,64 @@ def run_loop(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------- Parareal sweep
+
+def run_sweep(args):
+    """Sec. 5.2 on the GPU: k-iteration Parareal of the paper's test case for N_tau in divisors
+    of 480 and k = 1..8, FP64, against sequential FP64 time stepping of the same design with the
+    same solver: relative errors of Theta and of the gradient (2-norm) as defined in Sec. 5.2,
+    and the speedup of the Parareal run over the sequential run (CUDA events, one warm-up run
+    each).  Designs: rho = 0.3 uniform, and a near-binary branched stand-in for an optimised
+    design (high contrast)."""
+    import torch
+
+    from paper_2411_19030_gb300 import Operator, PassBuffers, SolveConfig, parareal_pass, sequential_pass
+    from paper_2411_19030_gb300.build import build_library
+
+    build_library()
+    n, Nt = 100, 480
+    w = W.workload("paper100")
+    h, dt = 1.0 / n, 1.0 / Nt
+    sink = W.dirichlet_bottom_centre(n, n, h)
+    qt = W.q_time_paper(Nt, dt)
+    solve = SolveConfig("fp64", rtol=1e-12, cg_iters_max=8000, refine_max=8)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b), out
+
+    rows = []
+    for dname, rho_np in (("uniform0.3", np.full(n * n, 0.3)), ("branches", W.rho_branches(n, n))):
+        rho = torch.tensor(rho_np, dtype=torch.float64, device="cuda")
+        for Ntau in (5, 10, 16, 20, 30, 32, 48, 60, 80, 96, 120, 160, 240):
+            op = Operator(n, n, h, w["material"], Nt, Ntau, dt, w["p"], sink, q_time=qt, solve=solve)
+            op.assemble(rho)
+            buf = PassBuffers(op)
+            if Ntau == 5:
+                t_seq, (Th_s, g_s) = timed(lambda: sequential_pass(op, buf))
+                Th_s, g_s = float(Th_s.item()), g_s.clone()
+            for k in range(1, 9):
+                if k > Ntau:
+                    break
+                t, (Th, g) = timed(lambda: parareal_pass(op, buf, k))
+                rows.append(dict(design=dname, Ntau=Ntau, k=k, ms=t, sequential_ms=t_seq, speedup=t_seq / t,
+                                 e_Theta=abs(float(Th.item()) - Th_s) / abs(Th_s),
+                                 e_grad=float(torch.linalg.norm(g - g_s) / torch.linalg.norm(g_s))))
+            del buf, op
+    print(json.dumps({"metric": "k-iteration Parareal vs sequential FP64 GPU time stepping (paper test case)",
+                      "config": {"workload": "paper100: 100x100, Nt=480, Table 1, q(t) of Eq. 5.1, bottom sink, p=20",
+                                 "precision": "fp64", "rtol": 1e-12},
+                      "paper_context": "MATLAB, CPU threads: Parareal speedup up to 5x at 16 threads with one iteration",
+                      "rows": rows}), flush=True)
+
+
 # ---------------------------------------------------------------------------- CPU oracle arms
 
 ORACLE_SNIPPET = r"""
@@ -572,11 +630,16 @@ def main():
                     help="instead of the pass benchmark: the full design loop (512x512, Nt=4096, 128 slices, "
                          "host MMA) for this many design iterations")
     ap.add_argument("--loop-n", type=int, default=512, help="grid side of --loop")
+    ap.add_argument("--sweep", action="store_true",
+                    help="instead of the pass benchmark: k-iteration Parareal error / speedup sweep of the paper's "
+                         "test case (100x100, Nt=480, Table 1, Eq. 5.1 load, bottom sink, p=20)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.loop:
         run_loop(args)
+    elif args.sweep:
+        run_sweep(args)
     else:
         run_gpu(args)
 

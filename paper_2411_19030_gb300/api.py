@@ -285,3 +285,47 @@ def oneshot_pass(op: Operator, buf: PassBuffers, stream=None, plt: bool = False)
     op.parareal_correct(PTG_ADJOINT, buf.F_l, buf.F_g, None if plt else buf.G_l, None if plt else buf.G_g,
                         buf.V_l_new, buf.V_g_new, T_hist=buf.T_hist, Theta=Theta, stream=stream)
     return Theta, buf.V_g_new[0]
+
+
+def parareal_pass(op: Operator, buf: PassBuffers, k: int, T0: torch.Tensor | None = None, stream=None):
+    """The k-iteration Parareal of the preliminary tests (Sec. 5.2): the coarse initial guess
+    u_{s+1}^0 = G_pri(u_s^0), k modified forward Parareal iterations, then the coarse adjoint
+    initial guess v_s^0 = G_adj(v_{s+1}^0) on the final history and k reverse iterations.
+    Returns (Theta, grad) views; buf.U_* / buf.V_* hold the final coarse states and buf.T_hist
+    the final modified-Parareal history.  The initial guesses are correction sweeps with
+    F = G_old = 0, so every step runs in the library's kernels."""
+    if k < 1:
+        raise ValueError("k must be >= 1")
+    Ntau = op.Ntau
+    for t in (buf.F_T, buf.F_th, buf.G_T, buf.G_th, buf.F_l, buf.F_g, buf.G_l, buf.G_g):
+        t.zero_()
+    if T0 is None:
+        buf.U_T[0].zero_()
+    else:
+        buf.U_T[0].copy_(T0)
+    buf.U_th[0].zero_()
+    op.parareal_correct(PTG_PRIMAL, buf.F_T, buf.F_th, buf.G_T, buf.G_th, buf.U_T, buf.U_th, stream=stream)
+    for _ in range(k):
+        op.fine_propagate_slices(buf.U_T, buf.U_th, buf.F_T, buf.F_th, T_hist=buf.T_hist, stream=stream)
+        op.coarse_sweep(PTG_PRIMAL, buf.U_T, buf.U_th, buf.G_T, buf.G_th, stream=stream)
+        buf.U_T_new[0].copy_(buf.U_T[0])
+        buf.U_th_new[0].copy_(buf.U_th[0])
+        op.parareal_correct(PTG_PRIMAL, buf.F_T, buf.F_th, buf.G_T, buf.G_th, buf.U_T_new, buf.U_th_new,
+                            T_hist=buf.T_hist, stream=stream)
+        buf.U_T, buf.U_T_new = buf.U_T_new, buf.U_T
+        buf.U_th, buf.U_th_new = buf.U_th_new, buf.U_th
+    Theta = buf.U_th[Ntau:Ntau + 1]
+    zl, zg = buf.F_l.zero_(), buf.F_g.zero_()
+    buf.G_l.zero_()
+    buf.G_g.zero_()
+    op.parareal_correct(PTG_ADJOINT, zl, zg, buf.G_l, buf.G_g, buf.V_l, buf.V_g, T_hist=buf.T_hist, Theta=Theta,
+                        stream=stream)
+    for _ in range(k):
+        op.adjoint_sweep(buf.T_hist, Theta, buf.V_l, buf.V_g, buf.F_l, buf.F_g, stream=stream)
+        op.coarse_sweep(PTG_ADJOINT, buf.V_l, buf.V_g, buf.G_l, buf.G_g, T_hist=buf.T_hist, Theta=Theta,
+                        stream=stream)
+        op.parareal_correct(PTG_ADJOINT, buf.F_l, buf.F_g, buf.G_l, buf.G_g, buf.V_l_new, buf.V_g_new,
+                            T_hist=buf.T_hist, Theta=Theta, stream=stream)
+        buf.V_l, buf.V_l_new = buf.V_l_new, buf.V_l
+        buf.V_g, buf.V_g_new = buf.V_g_new, buf.V_g
+    return Theta, buf.V_g[0]

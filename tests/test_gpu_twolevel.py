@@ -90,3 +90,27 @@ def test_twolevel_reduces_coarse_iterations(case, precision):
     for name in ("fine_primal", "fine_adjoint"):      # fine solves keep Jacobi (the adjoint
         assert k_on[name]["solves"] == k_off[name]["solves"]  # source moves with Theta's rounding)
         assert abs(k_on[name]["cg_iters"] - k_off[name]["cg_iters"]) <= 0.01 * k_off[name]["cg_iters"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine_all"])
+@pytest.mark.parametrize("design", ["branches_table1_bottom", "uniform_simp_left"])
+def test_twolevel_helps_on_high_contrast_designs(design, precision):
+    """The preconditioner must pay on a near-binary design too (an iteration-count check: the
+    parity tests pass even with a useless preconditioner, because CG still converges)."""
+    from paper_2411_19030_gb300 import parareal_pass
+    n, Nt = 64, 256
+    if design == "branches_table1_bottom":
+        prob, rho = make_problem(n, Nt=Nt, Ntau=16, dt=1 / Nt, material="table1", sink="bottom"), W.rho_branches(n, n)
+    else:
+        prob, rho = make_problem(n, Nt=Nt, Ntau=16, dt=1 / Nt), W.rho_uniform(n, n, 1, 0.2, 0.8)
+    its = {}
+    for tl in (True, False):
+        op = gpu_operator(prob, precision, rtol=1e-10, twolevel=tl)
+        buf = PassBuffers(op)
+        op.assemble(dev(rho))
+        parareal_pass(op, buf, 1)
+        torch.cuda.synchronize()
+        assert op.stats()["status"] == 0
+        st = op.stats()["by_kind"]["coarse_primal"]
+        its[tl] = st["cg_iters"] / st["solves"]
+    assert its[True] < 0.6 * its[False], its

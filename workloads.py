@@ -36,7 +36,7 @@ import numpy as np
 __all__ = [
     "WORKLOADS", "workload", "rho_plain", "rho_uniform", "rho_warm_perturb",
     "dirichlet_left_centre", "dirichlet_bottom_centre", "dirichlet_none",
-    "q_time_paper", "fd_elements", "rho_mirror_y", "batch48",
+    "q_time_paper", "fd_elements", "rho_mirror_y", "batch48", "rho_branches",
 ]
 
 # Material sets.  "simp_k" is conductivity-only SIMP k = 1e-3 + (1 - 1e-3) rho^3
@@ -143,4 +143,18 @@ def batch48() -> list[dict]:
         out.append(dict(index=i, n=n, Nt=Nt, Ntau=Ntau, dt=1.0 / Nt, p=8.0, material="simp_k", sink="left",
                         seed=100 + i, rho=rho_uniform(n, n, 100 + i, 0.2, 0.8)))
     return out
+
+
+def rho_branches(nx: int, ny: int, lo: float = 0.01, hi: float = 0.99) -> np.ndarray:
+    """A near-binary design (stand-in for an optimised topology, which is not published): a
+    vertical conducting trunk of half-width 0.04 L at x = L/2 over the full height, rising from
+    the bottom-edge sink, with three horizontal branches of half-width 0.02 L at y = 0.3, 0.6,
+    0.85 L spanning x in [0.1, 0.9] L; rho = hi there and lo elsewhere (element centres)."""
+    ey, ex = np.divmod(np.arange(nx * ny), nx)
+    x = (ex + 0.5) / nx
+    y = (ey + 0.5) / ny
+    on = np.abs(x - 0.5) < 0.04
+    for yb in (0.3, 0.6, 0.85):
+        on |= (np.abs(y - yb) < 0.02) & (x > 0.1) & (x < 0.9)
+    return np.where(on, hi, lo).astype(np.float64)
 
