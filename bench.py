@@ -375,22 +375,39 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-# DRAM bytes per launch (read + write) from the committed ncu capture of the 128x128 pass
-# (profiles/stepper_fine_and_correct_oneshot128.md); a kernel changed since has no entry.
-NCU_TRAFFIC_BYTES = {"fine_primal": 7.166720e6 + 80.248320e6, "correct_primal": 10.990080e6 + 0.0,
-                     "correct_adjoint": 23.498496e6 + 0.007424e6}
+# DRAM bytes per launch (read + write) from the committed ncu captures of the 128x128 pass in
+# the default precision (profiles/); a kernel changed since has no entry.
+NCU_TRAFFIC_BYTES = {"fine_primal": 6.586112e6 + 80.368640e6, "coarse_primal": 6.463488e6 + 3.840e3,
+                     "correct_primal": 10.891264e6 + 0.0, "fine_adjoint": 146.939136e6 + 0.134400e6,
+                     "coarse_adjoint": 14.757888e6 + 1.536e3, "correct_adjoint": 23.534848e6 + 0.0}
+
+# FP64 peak of the chip (nominal, the GB300 table of the profiling notes: 1.25 TFLOP/s) and the
+# FLOPs of one FP64 CG iteration per unknown: the 9-point stencil (9 FMA), the p, q, d, r
+# updates (4 FMA), three dot products (3 FMA) and the preconditioned residual (1 FMA) = 17 FMA;
+# one FP64 residual evaluation per refinement sweep and per solve: stencil + subtraction + dot.
+FP64_PEAK_TFLOPS = 1.25
+FLOPS_PER_CG_ITER = 34.0
+FLOPS_PER_RESIDUAL = 21.0
+KIND_PRECISION = {"fp64": {k: "f64" for k in ("fine_primal", "coarse_primal", "correct_primal", "fine_adjoint",
+                                              "coarse_adjoint", "correct_adjoint")},
+                  "fp32_refine_all": {k: "f32" for k in ("fine_primal", "coarse_primal", "correct_primal",
+                                                         "fine_adjoint", "coarse_adjoint", "correct_adjoint")},
+                  "fp32_refine": {"fine_primal": "f32", "fine_adjoint": "f32", "coarse_primal": "f64",
+                                  "correct_primal": "f64", "coarse_adjoint": "f64", "correct_adjoint": "f64"}}
 
 
 def roofline(kind_ms: dict, stats: dict, w: dict, N_free: int, args) -> dict:
     """Roofline entry of the dominant kernel (largest share of the step).
 
     The stepper keeps every CG vector of a slice on chip (registers and shared memory of one
-    thread-block cluster), so its algorithmic HBM traffic per launch is the compulsory state
-    traffic only: for a correction sweep, the F and G slice results read and the corrected
-    states (and history rows) written, 8 B per node each, N_tau times; for a fine propagator,
-    the FP64 history (8 B per node per fine step written by the primal, T_j and T_{j-1} read by
-    the adjoint) plus the slice start/end states.  The kernel is limited by the latency of its
-    cluster reductions, so the fraction of the HBM roofline is small by construction.
+    thread-block cluster), so its compulsory HBM traffic per launch is the state traffic only:
+    for a correction sweep, the F and G slice results read and the corrected states (and
+    history rows) written, 8 B per node each, N_tau times; for a fine propagator, the FP64
+    history (8 B per node per fine step, written by the primal, read once by the adjoint) plus
+    the slice start and end states.  A kernel whose CG runs in FP64 is bound by
+    the FP64 pipe of its SMs (1/58 of the FP32 rate on this chip): it is reported as "alu"
+    against the chip's FP64 peak with its algorithmic FLOPs (CG iterations and FP64 residuals
+    from the solver counters); an FP32-CG kernel is reported against HBM.
     """
     peaks = {}
     try:
@@ -404,14 +421,27 @@ def roofline(kind_ms: dict, stats: dict, w: dict, N_free: int, args) -> dict:
     nn = (w["n"] + 1) ** 2
     bytes_per_launch = {
         "fine_primal": 8.0 * nn * Nt + 16.0 * nn * Ntau,
-        "fine_adjoint": 16.0 * nn * Nt + 16.0 * nn * Ntau,
+        "fine_adjoint": 8.0 * nn * Nt + 16.0 * nn * Ntau,      # each T_j read once (T_{j-1} reused)
         "coarse_primal": 16.0 * nn * Ntau,
         "coarse_adjoint": 32.0 * nn * Ntau,
         "correct_primal": 32.0 * nn * Ntau,     # F, G read; X, history row written
         "correct_adjoint": 40.0 * nn * Ntau,    # F, G read; X written; T_k, T_{k-M} read
     }[dom]
-    achieved = bytes_per_launch / (kind_ms[dom] * 1e-3) / 1e9
     traffic = NCU_TRAFFIC_BYTES.get(dom)
+    sec = kind_ms[dom] * 1e-3
+    if KIND_PRECISION[args.precision][dom] == "f64":
+        st = stats["by_kind"][dom]
+        flops = N_free * (FLOPS_PER_CG_ITER * st["cg_iters"] + FLOPS_PER_RESIDUAL * (st["refinements"] + st["solves"]))
+        flops /= max(1, args.steps)               # counters cover the timed steps
+        achieved = flops / sec / 1e12
+        return {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "peak_source": "nominal FP64 peak of the chip (no measured FP64 peak in MEASURED_PEAKS.json)",
+                "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": bytes_per_launch,
+                "note": "FP64 CG of one sequential sweep on one 16-CTA cluster (16 of 152 SMs); ncu shows its "
+                        "FP64 pipe about half busy: the fraction of the whole chip's FP64 peak is small by "
+                        "construction of a sequential sweep"}
+    achieved = bytes_per_launch / sec / 1e9
     return {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": traffic, "peak_source": source,
             "algorithmic_bytes_per_launch": bytes_per_launch,
