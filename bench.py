@@ -362,7 +362,7 @@ def run_gpu(args):
         "e2e": None if e2e is None else {"value": world * dof_steps / (e2e * 1e-3), "unit": UNIT, "ms": e2e,
                                          "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": (1 + n * n) * 8},
         # per pass: assembly 3 kernels (+ 4 for the two-level coarse set-up) + 6 stepper launches
-        "gpu_launches": (9 + (4 if args.precision == "fp32_refine" and args.twolevel else 0)) * args.steps,
+        "gpu_launches": (9 + (4 if args.twolevel != "none" else 0)) * args.steps,
         "roofline": roof,
         "clocks": clk.summary(),
     }
@@ -649,8 +649,11 @@ def main():
                     help="fp32_refine: fine-step CG in FP32 with FP64 refinement, coarse-step solves FP64; "
                          "fp32_refine_all: every CG in FP32 with FP64 refinement")
     ap.add_argument("--rtol", type=float, default=1e-10)
-    ap.add_argument("--no-twolevel", dest="twolevel", action="store_false",
-                    help="Jacobi only on the coarse-step solves (default: two-level preconditioner)")
+    ap.add_argument("--twolevel", default="vcycle", choices=["none", "additive", "vcycle"],
+                    help="preconditioner of the coarse-step solves: Jacobi, additive two-level, or the "
+                         "two-grid V(1,1) cycle")
+    ap.add_argument("--no-twolevel", dest="twolevel", action="store_const", const="none",
+                    help="same as --twolevel none")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="time the passes only: no end-to-end run, comparator, accuracy checks or G = 0 probe "

@@ -92,16 +92,28 @@ typedef struct {
                           passes then refers to that objective */
 } ptg_time;
 
+#define PTG_TWOLEVEL_NONE 0
+#define PTG_TWOLEVEL_ADDITIVE 1
+#define PTG_TWOLEVEL_VCYCLE 2
+
 typedef struct {
     int precision;     /* PTG_FP64, PTG_FP32_REFINE or PTG_FP32_REFINE_ALL */
     double rtol;       /* stop when ||b - A x||_2 <= rtol ||b||_2 (FP64 residual) */
     double inner_rtol; /* relative residual reduction of each FP32 CG (FP32 solves only) */
     int cg_iters_max;  /* iteration limit of one CG */
     int refine_max;    /* limit of refinement sweeps of one solve */
-    int twolevel;      /* precondition the CG of the coarse-step solves (C/dtau + K) with
-                          D^-1 + P Ac^-1 P^T: P piecewise constant on aggregates of m x m nodes
-                          (m the smallest multiple of 4 giving <= 16 aggregates per direction),
-                          Ac = P^T A P, its inverse applied in FP32.  0: Jacobi everywhere. */
+    int twolevel;      /* preconditioner of the CG of the coarse-step solves (C/dtau + K), with
+                          P piecewise constant on aggregates of m x m nodes (m the smallest
+                          multiple of 4 giving <= 16 aggregates per direction), Ac = P^T A P
+                          and its inverse applied in FP32:
+                          PTG_TWOLEVEL_NONE      Jacobi everywhere;
+                          PTG_TWOLEVEL_ADDITIVE  D^-1 + P Ac^-1 P^T;
+                          PTG_TWOLEVEL_VCYCLE    a symmetric two-grid cycle: one damped-Jacobi
+                                                 step (S = 0.8 D^-1), the coarse correction of
+                                                 the residual, one more Jacobi step, i.e.
+                                                 I - M^-1 A = (I - S A)(I - P Ac^-1 P^T A)(I - S A),
+                                                 applied in FP32.
+                          Other values: PTG_EINVAL. */
     int grid_wide;     /* systems may run on groups of CTAs of one cooperative launch, talking
                           through global memory, instead of one 16-CTA cluster each: a single
                           FP64 system (correction sweeps, chained runs) over every SM, other

@@ -14,6 +14,7 @@ PTG_SLICES_PARALLEL, PTG_SLICES_CHAINED = 0, 1
 PTG_PRIMAL, PTG_ADJOINT = 1, -1
 PTG_OBJ_POWER_MEAN, PTG_OBJ_MODIFIED = 0, 1
 PTG_PARAREAL, PTG_PLT = 0, 1
+PTG_TWOLEVEL_NONE, PTG_TWOLEVEL_ADDITIVE, PTG_TWOLEVEL_VCYCLE = 0, 1, 2
 
 ERROR_NAMES = {0: "PTG_OK", -1: "PTG_EINVAL", -2: "PTG_ENOCONV", -3: "PTG_ENONFINITE",
                -4: "PTG_ETIMEOUT", -5: "PTG_ECUDA", -6: "PTG_ENOMEM"}

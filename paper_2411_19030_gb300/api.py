@@ -46,6 +46,14 @@ def _ptr(t: torch.Tensor | None, device: torch.device | None = None) -> int | No
     return t.data_ptr()
 
 
+def twolevel_code(v) -> int:
+    """The ptg_solve.twolevel value of SolveConfig.twolevel."""
+    if isinstance(v, str):
+        return {"none": _ffi.PTG_TWOLEVEL_NONE, "additive": _ffi.PTG_TWOLEVEL_ADDITIVE,
+                "vcycle": _ffi.PTG_TWOLEVEL_VCYCLE}[v]
+    return int(v)
+
+
 @dataclass
 class SolveConfig:
     precision: str = "fp64"          # "fp64"; "fp32_refine": fine-step CG in FP32 with FP64 refinement,
@@ -54,7 +62,9 @@ class SolveConfig:
     inner_rtol: float = 1e-4
     cg_iters_max: int = 2000
     refine_max: int = 8
-    twolevel: bool = True            # two-level preconditioner of the coarse-step solves
+    twolevel: bool | int | str = "vcycle"  # preconditioner of the coarse-step solves: "vcycle"
+    #                                  (symmetric two-grid cycle with damped-Jacobi smoothing),
+    #                                  True / "additive" (D^-1 + P Ac^-1 P^T), False / "none" (Jacobi)
     grid_wide: int = 1               # single FP64 systems over every SM (cooperative grid):
     #                                  0 never, 1 for large grids or when no cluster fits, 2 always
 
@@ -94,7 +104,7 @@ class Operator:
         prec = {"fp64": PTG_FP64, "fp32_refine": PTG_FP32_REFINE,
                 "fp32_refine_all": PTG_FP32_REFINE_ALL}[solve.precision]
         s = _ffi.ptg_solve(prec, solve.rtol, solve.inner_rtol, solve.cg_iters_max, solve.refine_max,
-                           int(solve.twolevel), int(solve.grid_wide))
+                           twolevel_code(solve.twolevel), int(solve.grid_wide))
         self._dir = np.ascontiguousarray(dirichlet, dtype=np.uint8).reshape(-1)
         if self._dir.size != self.Nn:
             raise ValueError("dirichlet mask must have (nx+1)(ny+1) entries")

@@ -23,6 +23,7 @@ struct ptg_op {
   int W = 0;               // padded row width
   // two-level preconditioner of the coarse-step solves (FP32 CG); tl_m == 0: disabled
   int tl_m = 0, tl_nax = 0, tl_nay = 0;
+  int tl_vc = 0;   // 1: the V(1,1) two-grid cycle instead of the additive form
   double* tl_Ac = nullptr;
   float *tl_band = nullptr, *tl_X = nullptr, *tl_Ainv = nullptr;
   // device workspace
@@ -89,8 +90,9 @@ int kind_precision(int solve_precision, int kind) {
   return coarse_kind(kind) ? PTG_FP64 : PTG_FP32_REFINE;
 }
 
-// Aggregate rows reserved per CTA for cluster size cs (the largest over the ranks), 0 if the
-// two-level preconditioner is off for this op, kind or plan.
+// Aggregate rows reserved per CTA for cluster size cs (the largest over the ranks; with the
+// V-cycle the rows its halo rows touch too), 0 if the two-level preconditioner is off for this
+// op, kind or plan.
 int twolevel_rows(const ptg_op* op, int precision, int kind, int cs, bool use = true) {
   (void)precision;
   if (!use || op->tl_m == 0 || !coarse_kind(kind)) return 0;
@@ -100,18 +102,28 @@ int twolevel_rows(const ptg_op* op, int precision, int kind, int cs, bool use = 
     const int rows = op->g.ny + 1, base = rows / cs, rem = rows % cs;
     r0 = q * base + (q < rem ? q : rem);
     R = base + (q < rem ? 1 : 0);
-    coarse_rows_of_slab(r0, R, op->tl_m, op->tl_nay, lo, hi);
+    if (op->tl_vc)
+      coarse_rows_of_halo_slab(r0, R, op->g.ny, op->tl_m, op->tl_nay, lo, hi);
+    else
+      coarse_rows_of_slab(r0, R, op->tl_m, op->tl_nay, lo, hi);
     best = std::max(best, hi - lo + 1);
   }
   return best;
 }
 
+// precision: the kernel's (PTG_FP64 or PTG_FP32_REFINE)
 size_t twolevel_bytes(const ptg_op* op, int precision, int kind, int cs, bool use = true, bool slots = true) {
   const int ncj = twolevel_rows(op, precision, kind, cs, use);
   if (ncj == 0) return 0;
   const int rmax = (op->g.ny + 1 + cs - 1) / cs;
-  return twolevel_smem_bytes(op->W, rmax, cs, op->tl_nax, op->tl_nay, ncj, slots);
+  return twolevel_smem_bytes(op->W, rmax, cs, op->tl_nax, op->tl_nay, ncj, slots, op->tl_vc != 0,
+                             precision == PTG_FP64 ? 8 : 4);
 }
+
+// Damping of the V-cycle's Jacobi smoother: the largest eigenvalue of D^-1 A lies between 1.5
+// (conduction-dominated) and 2.25 (capacity-dominated: the consistent Q1 mass matrix), so
+// omega lambda_max stays below 1.8 < 2 for every step size.
+constexpr float kVcycleOmega = 0.8f;
 
 // Node count from which a single FP64 system runs grid-wide (see choose_plan).
 constexpr int kWideMinNodes = 40000;
@@ -137,6 +149,8 @@ constexpr double kTwoLevelInnerFp64 = 1e-4;
 
 void twolevel_params(const ptg_op* op, int precision, StepParams& P, bool use) {
   P.tl_naj = twolevel_rows(op, precision, P.kind, P.cs, use);
+  P.tl_vc = P.tl_naj > 0 ? op->tl_vc : 0;
+  P.tl_omega = kVcycleOmega;
   // FP32 CG: the op's inner tolerance; FP64 CG: to the final tolerance in one go, or in
   // kTwoLevelInnerFp64 steps with the two-level preconditioner
   if (precision == PTG_FP64) P.inner_rtol = P.tl_naj > 0 ? std::max(kTwoLevelInnerFp64, op->sv.inner_rtol) : 0.0;
@@ -341,6 +355,7 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
   if (time->objective != PTG_OBJ_POWER_MEAN && time->objective != PTG_OBJ_MODIFIED) return PTG_EINVAL;
   if (solve->precision != PTG_FP64 && solve->precision != PTG_FP32_REFINE && solve->precision != PTG_FP32_REFINE_ALL)
     return PTG_EINVAL;
+  if (solve->twolevel < PTG_TWOLEVEL_NONE || solve->twolevel > PTG_TWOLEVEL_VCYCLE) return PTG_EINVAL;
   if (!(solve->rtol > 0.0) || solve->cg_iters_max < 1 || solve->refine_max < 1 || !(solve->inner_rtol >= 0.0))
     return PTG_EINVAL;
   if (!(mat->k0 > 0.0) || !(mat->kmin > 0.0) || !(mat->c0 > 0.0) || !(mat->cmin > 0.0)) return PTG_EINVAL;
@@ -390,6 +405,7 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
     int m = 4;
     while ((grid->nx + 1) / m > kCoarseMaxAgg || (grid->ny + 1) / m > kCoarseMaxAgg) m += 4;
     op->tl_m = m;
+    op->tl_vc = solve->twolevel == PTG_TWOLEVEL_VCYCLE;
     op->tl_nax = coarse_aggregates(grid->nx, m);
     op->tl_nay = coarse_aggregates(grid->ny, m);
     const size_t nc = (size_t)op->tl_nax * op->tl_nay;
@@ -403,7 +419,7 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
   A(&op->scratch, 2 * sizeof(double));
   A(&op->g_red, 2 * kMaxGrid * 4 * sizeof(double));
   A(&op->g_bar, 4 * kMaxGrid * sizeof(unsigned));
-  A(&op->g_halo, (size_t)kMaxGrid * 2 * op->W * sizeof(double));
+  A(&op->g_halo, (size_t)2 * kMaxGrid * 2 * op->W * sizeof(double));
   A(&op->stats, sizeof(DevStats));
   if (e != cudaSuccess) {
     cudaGetLastError();

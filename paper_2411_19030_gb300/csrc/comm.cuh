@@ -73,10 +73,13 @@ struct GridComm {
   const int G;                   // CTAs of the group
   const int gid;                 // group index
   const int base;                // first block of the group
-  // halo rows published by push_halos and pulled in after the next barrier
+  // halo rows published by push_halos and pulled in after the next barrier; pushes alternate
+  // between two slot sets, so a CTA that has passed a barrier never overwrites slots that a
+  // slower CTA of the group may still be pulling from the push before it
   unsigned char* pending = nullptr;
   int pending_bytes = 0;         // bytes of one row
   int R = 0, W = 0;
+  int hset = 0;                  // slot set of the latest push
 
   __device__ GridComm(const StepParams& P_, RedSmem& rs_)
       : P(P_), rs(rs_), G(P_.cs), gid((int)blockIdx.x / P_.cs), base(((int)blockIdx.x / P_.cs) * P_.cs) {}
@@ -182,12 +185,17 @@ struct GridComm {
     phase ^= 1;
   }
 
+  __device__ size_t halo_slot(int set, int block) const {
+    return ((size_t)set * kMaxGrid + (size_t)block) * 2 * (size_t)P.g_halo_row_bytes;
+  }
   // Publish the own first and last rows (local rows 0 and R-1 of buf, which points at row -1)
-  // to this CTA's two global halo slots; the neighbours pull them after the next barrier.
+  // to this CTA's two global halo slots of the next set; the neighbours pull them after the
+  // next barrier.
   template <class T>
   __device__ void push_halos(T* buf, const Slab& sb) {
     const int nb = sb.W * (int)sizeof(T);           // bytes per row, a multiple of 16
-    unsigned char* out = reinterpret_cast<unsigned char*>(P.g_halo) + (size_t)blockIdx.x * 2 * P.g_halo_row_bytes;
+    hset ^= 1;
+    unsigned char* out = reinterpret_cast<unsigned char*>(P.g_halo) + halo_slot(hset, (int)blockIdx.x);
     const uint4* s0 = reinterpret_cast<const uint4*>(buf + 1 * sb.W);
     const uint4* s1 = reinterpret_cast<const uint4*>(buf + sb.R * sb.W);
     uint4* d0 = reinterpret_cast<uint4*>(out);
@@ -212,11 +220,11 @@ struct GridComm {
     uint4* hi = reinterpret_cast<uint4*>(pending + (size_t)(R + 1) * pending_bytes);  // row R
     const int r = rank(), b = (int)blockIdx.x;
     if (r > 0) {
-      const uint4* src = reinterpret_cast<const uint4*>(hb + (size_t)(b - 1) * 2 * rb + rb);
+      const uint4* src = reinterpret_cast<const uint4*>(hb + halo_slot(hset, b - 1) + rb);
       for (int i = threadIdx.x; i < n16; i += blockDim.x) lo[i] = __ldcg(src + i);
     }
     if (r < G - 1) {
-      const uint4* src = reinterpret_cast<const uint4*>(hb + (size_t)(b + 1) * 2 * rb);
+      const uint4* src = reinterpret_cast<const uint4*>(hb + halo_slot(hset, b + 1));
       for (int i = threadIdx.x; i < n16; i += blockDim.x) hi[i] = __ldcg(src + i);
     }
     pending = nullptr;

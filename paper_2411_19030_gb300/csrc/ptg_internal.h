@@ -100,12 +100,14 @@ struct StepParams {
   const float* Ainv;         // [ncp][ncp] inverse of the Galerkin coarse matrix (padded layout)
   int cm, nax, nay;          // aggregate size m and aggregate counts per direction
   int tl_naj;                // aggregate rows reserved per CTA (0: two-level disabled for this launch)
+  int tl_vc;                 // 1: V(1,1) two-grid cycle with damped-Jacobi smoothing; 0: additive D^-1 + P Ac^-1 P^T
+  float tl_omega;            // damping of the V-cycle's Jacobi smoother
   // one system over a whole cooperative grid (GridComm): global scratch of the op
   int wide;                  // 1: launched as stepper_wide_kernel, groups of cs CTAs
   int wide_tasks;            // tasks of a grid-wide launch (group g runs g, g + groups, ...)
   double* g_red;             // [2][kMaxGrid][4] reduction partials
   unsigned* g_bar;           // [4 per group] barrier: arrival count, generation, broken flag (zeroed per launch)
-  void* g_halo;              // [kMaxGrid][2] rows of g_halo_row_bytes: first / last owned row
+  void* g_halo;              // [2 sets][kMaxGrid][2] rows of g_halo_row_bytes: first / last owned row
   int g_halo_row_bytes;      // W * 8 (a row of doubles; float rows use the first half)
   float* g_tl;               // [kMaxGrid][ncp] restricted partials of the two-level preconditioner
 };
@@ -133,6 +135,12 @@ inline __host__ __device__ void coarse_rows_of_slab(int r0, int R, int m, int na
   jlo = coarse_agg_y(r0, m, nay);
   jhi = coarse_agg_y(r0 + R - 1, m, nay);
 }
+// aggregate rows touched by the slab and its two halo rows (node rows r0-1 .. r0+R inside
+// 0 .. ny): the V-cycle prolongs the coarse correction onto the halo rows as well
+inline __host__ __device__ void coarse_rows_of_halo_slab(int r0, int R, int ny, int m, int nay, int& jlo, int& jhi) {
+  jlo = coarse_agg_y(r0 > 0 ? r0 - 1 : 0, m, nay);
+  jhi = coarse_agg_y(r0 + R <= ny ? r0 + R : ny, m, nay);
+}
 // Coarse vectors index aggregate (ay, ax) as L = ay * naxp + ax with naxp = nax rounded up to
 // a multiple of 4 (16-byte chunks never straddle two aggregate rows); ncp = nay * naxp is the
 // padded length of a coarse vector and of a row of the dense inverse (zero in the padding).
@@ -140,17 +148,29 @@ inline __host__ __device__ int coarse_row_stride(int nax) { return (nax + 3) / 4
 
 // Shared-memory bytes of the two-level preconditioner for one CTA (naj aggregate rows); the
 // partials of every rank sit in shared memory for a cluster (slots = true), in global memory
-// for a grid-wide launch.
-inline size_t twolevel_smem_bytes(int W, int rmax, int cs, int nax, int nay, int naj, bool slots = true) {
+// for a grid-wide launch.  The V-cycle (vc) adds its smoother buffers over the slab and its
+// halo rows, the halo rows of q and r in the CG precision (real_bytes), and FP32 element
+// weights where the CG runs in FP64 (the FP32 CG has them already).
+inline size_t twolevel_smem_bytes(int W, int rmax, int cs, int nax, int nay, int naj, bool slots = true,
+                                  bool vc = false, int real_bytes = 4) {
   const size_t naxp = (size_t)coarse_row_stride(nax), ncp = naxp * nay;
-  const size_t groups = (size_t)rmax * (W / kGroup);
+  const size_t G = (size_t)(W / kGroup);
+  const size_t groups = (size_t)rmax * G;
+  const size_t halo = (size_t)(rmax + 2) * W + 2 * kSlack;   // a buffer over rows -1..R
+  const size_t elems = (size_t)(rmax + 1) * W + 2 * kSlack;  // element rows -1..R-1
   size_t b = 0;
   b += (size_t)naj * naxp * ncp * 4;        // rows of Ainv for the CTA's aggregates
   if (slots) b += (size_t)cs * ncp * 4;     // restricted partials of every rank
   b += ncp * 4;                             // their sum over the covering ranks
   b += (size_t)naj * naxp * 4;              // coarse correction of the CTA's aggregates
+  if (vc) {
+    b += halo * real_bytes;                 // q's owned edge rows out, the neighbours' in
+    b += 2 * (size_t)W * real_bytes;        // r on the two halo rows
+    b += 3 * halo * 4;                      // smoother iterates y, u and w D^-1
+    if (real_bytes == 8) b += 3 * elems * 4;  // FP32 (D, S, T) element weights
+  }
   b += groups * 4;                          // group sums of the restricted vector
-  b += groups * 4;                          // local aggregate of every group
+  b += (vc ? groups + 2 * G : groups) * 4;  // aggregate of every group (V-cycle: halo rows too)
   b += (size_t)nay * 2 * 4;                 // covering rank range per aggregate row
   return (b + 15) & ~size_t(15);
 }

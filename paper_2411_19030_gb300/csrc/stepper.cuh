@@ -144,9 +144,9 @@ struct Stepper {
   double* b64;      // FP64 right-hand side, rows 0..R-1
   Real* zbuf;       // CG stencil operand, rows -1..R
   Real* dinv;       // Jacobi inverse diagonal, rows 0..R-1 (0 on Dirichlet and pad nodes)
-  float* wd;        // FP32 element weights (D, S, T), element rows r0-1..r0+R-1 (FP32 CG only)
-  float* ws;
-  float* wt;
+  float* wd = nullptr;  // FP32 element weights (D, S, T), element rows r0-1..r0+R-1 (FP32 CG, V-cycle)
+  float* ws = nullptr;
+  float* wt = nullptr;
   // per-thread groups: loc0[k] = offset of the group's first node in the halo buffers, -1 if none
   int loc0[NG];
   unsigned fmask = 0;   // bit 4k+j: node j of group k is an unknown (free, not a pad)
@@ -167,6 +167,14 @@ struct Stepper {
   float* tl_gs = nullptr;    // group sums of the vector being restricted, [R * G]
   int* tl_gagg = nullptr;    // local aggregate (row-major in [naj][nax]) of every group, [R * G]
   int* tl_cov = nullptr;     // first / last rank covering each aggregate row, [nay][2]
+  // V(1,1) two-grid cycle (P.tl_vc), see vcycle; aj0 / naj then cover the halo rows too
+  bool vc = false;
+  int ajo0 = 0, najo = 0;    // aggregate rows of the owned rows (the restriction's partials)
+  Real* vq = nullptr;        // rows -1..R: q's first / last owned rows out, the neighbours' in
+  Real* vrh = nullptr;       // r on the halo rows -1 and R, [2][W]
+  float* vy = nullptr;       // y = S r, rows -1..R
+  float* vu = nullptr;       // u = y + P ec, rows -1..R
+  float* vsd = nullptr;      // S = omega D^-1, rows -1..R (0 off the unknowns)
 
   __device__ Stepper(const StepParams& P_, Comm& comm_, unsigned char* dyn) : P(P_), comm(comm_) {
     sb.nx = P.nx;
@@ -211,17 +219,47 @@ struct Stepper {
         tl_slot = t;  t += P.wide ? 0 : P.cs * ncp;   // grid-wide: the partials are in global memory
         tl_qc = t;    t += ncp;
         tl_ec = t;    t += P.tl_naj * naxp;
-        tl_gs = t;    t += groups;
-        tl_gagg = reinterpret_cast<int*>(t);  t += groups;
-        tl_cov = reinterpret_cast<int*>(t);
-        int ajhi;
-        coarse_rows_of_slab(sb.r0, sb.R, P.cm, P.nay, aj0, ajhi);
-        naj = ajhi - aj0 + 1;
-        for (int gi = threadIdx.x; gi < sb.ngroups; gi += blockDim.x) {
-          const int lr = gi / sb.G, g = gi - lr * sb.G;
-          tl_gagg[gi] = (coarse_agg_y(sb.r0 + lr, P.cm, P.nay) - aj0) * coarse_row_stride(P.nax) +
-                        coarse_agg_x(g, P.cm, P.nax);
+        if (P.tl_vc) {
+          // every array a multiple of 4 words, so each starts 16-byte aligned
+          constexpr int rw = (int)(sizeof(Real) / 4);
+          float* v0 = t;
+          vq = reinterpret_cast<Real*>(t) + kSlack;  t += halo * rw;
+          vrh = reinterpret_cast<Real*>(t);          t += 2 * W * rw;
+          vy = t + kSlack;   t += halo;
+          vu = t + kSlack;   t += halo;
+          vsd = t + kSlack;  t += halo;
+          if constexpr (!kMixed) {
+            wd = t + kSlack;
+            ws = t + elems + kSlack;
+            wt = t + 2 * elems + kSlack;
+            t += 3 * elems;
+          }
+          for (float* z = v0 + threadIdx.x; z < t; z += blockDim.x) *z = 0.f;
         }
+        tl_gs = t;    t += groups;
+        tl_gagg = reinterpret_cast<int*>(t);  t += P.tl_vc ? groups + 2 * (W / kGroup) : groups;
+        tl_cov = reinterpret_cast<int*>(t);
+        int ajhi, ajo1;
+        coarse_rows_of_slab(sb.r0, sb.R, P.cm, P.nay, ajo0, ajo1);
+        najo = ajo1 - ajo0 + 1;
+        if (P.tl_vc) {
+          coarse_rows_of_halo_slab(sb.r0, sb.R, P.ny, P.cm, P.nay, aj0, ajhi);
+          // rows -1..R: group gi of row gi / G - 1 (no aggregate outside the grid)
+          for (int gi = threadIdx.x; gi < (sb.R + 2) * sb.G; gi += blockDim.x) {
+            const int lr = gi / sb.G - 1, g = gi - (lr + 1) * sb.G, row = sb.r0 + lr;
+            tl_gagg[gi] = (row < 0 || row > P.ny)
+                              ? -1
+                              : (coarse_agg_y(row, P.cm, P.nay) - aj0) * naxp + coarse_agg_x(g, P.cm, P.nax);
+          }
+        } else {
+          aj0 = ajo0;
+          ajhi = ajo1;
+          for (int gi = threadIdx.x; gi < sb.ngroups; gi += blockDim.x) {
+            const int lr = gi / sb.G, g = gi - lr * sb.G;
+            tl_gagg[gi] = (coarse_agg_y(sb.r0 + lr, P.cm, P.nay) - aj0) * naxp + coarse_agg_x(g, P.cm, P.nax);
+          }
+        }
+        naj = ajhi - aj0 + 1;
         for (int J = threadIdx.x; J < P.nay; J += blockDim.x) {
           int lo = -1, hi = -1;
           for (int q = 0; q < P.cs; ++q) {
@@ -243,9 +281,11 @@ struct Stepper {
     ax64 = axb + kSlack - W;
     zbuf = zb + kSlack;
     dinv = db + kSlack - W;    // dinv[loc] likewise
-    wd = eb + kSlack;
-    ws = eb + elems + kSlack;
-    wt = eb + 2 * elems + kSlack;
+    if constexpr (kMixed) {
+      wd = eb + kSlack;
+      ws = eb + elems + kSlack;
+      wt = eb + 2 * elems + kSlack;
+    }
 #pragma unroll
     for (int k = 0; k < NG; ++k) {
       const int gi = threadIdx.x + k * blockDim.x;
@@ -279,6 +319,7 @@ struct Stepper {
     inv_dt = 1.0 / step_dt;
     ax_valid = false;
     tl = coarse && P.tl_naj > 0 && P.Ainv != nullptr;
+    vc = tl && P.tl_vc;
     if (tl && !tl_loaded) {        // rows of the aggregate rows aj0 .. aj0+naj-1 of Ainv, 16-byte copies
       const int naxp = coarse_row_stride(P.nax), ncp = naxp * P.nay;
       const int n4 = naj * naxp * ncp / 4;
@@ -289,7 +330,7 @@ struct Stepper {
     }
     const int W = sb.W;
     __syncthreads();
-    if constexpr (kMixed) {
+    if (kMixed || vc) {
       const double* wE = coarse ? P.wE_coarse : P.wE_fine;
       const int PE = (P.ny + 2) * W + 2 * kSlack;      // one element array incl. slack
       const int n = (sb.R + 1) * W;
@@ -314,6 +355,16 @@ struct Stepper {
           fmask |= 1u << (kGroup * k + j);
         }
         dinv[l0 + j] = v;
+      }
+    }
+    if (vc) {
+      // S = omega / diag on rows -1..R; 0 on Dirichlet, pad and out-of-grid nodes
+      for (int i = threadIdx.x; i < (sb.R + 2) * W; i += blockDim.x) {
+        const int lr = i / W - 1, ix = i - (lr + 1) * W - 1, row = sb.r0 + lr;
+        float v = 0.f;
+        if (row >= 0 && row <= P.ny && ix >= 0 && ix <= P.nx && P.dirichlet[row * (P.nx + 1) + ix] == 0)
+          v = (float)((double)P.tl_omega / A.C[i + gshift]);
+        vsd[i] = v;
       }
     }
     __syncthreads();
@@ -450,7 +501,8 @@ struct Stepper {
   // partials of the covering ranks in rank order and multiplies by the CTA's rows of Ac^-1.
   // In the CG loop the coarse correction follows r by the same recurrence as r,
   // ec -= alpha Ac^-1 P^T q, so restricting q needs no cluster barrier of its own.
-  __device__ void coarse_restrict_push(const Real (&v)[NG][4]) {
+  template <class T>
+  __device__ void coarse_restrict_push(const T (&v)[NG][4]) {
     const int G = sb.G, m4 = P.cm / 4, nax = P.nax, naxp = coarse_row_stride(nax), ncp = naxp * P.nay;
 #pragma unroll
     for (int k = 0; k < NG; ++k) {
@@ -460,13 +512,13 @@ struct Stepper {
     __syncthreads();
     // 4 lanes per local aggregate (16 lanes per chunk of 4 aggregates), each summing every
     // 4th node row; padding aggregates (ax >= nax) sum to 0
-    const int items = naj * naxp, padded = ((4 * items + 31) / 32) * 32;
+    const int items = najo * naxp, padded = ((4 * items + 31) / 32) * 32;
     const int rlast = sb.r0 + sb.R - 1;
     const int lane = threadIdx.x & 31;
     for (int t = threadIdx.x; t < padded; t += blockDim.x) {
       const int item = t >> 2, part = t & 3;
       const int ajl = item / naxp, ax = item - ajl * naxp;
-      const int ay = aj0 + ajl;
+      const int ay = ajo0 + ajl;
       float acc = 0.f;
       if (item < items && ax < nax) {
         const int y0 = max(ay * P.cm, sb.r0), y1 = min(ay == P.nay - 1 ? P.ny : ay * P.cm + P.cm - 1, rlast);
@@ -488,7 +540,7 @@ struct Stepper {
       const int item0 = (t & ~15) >> 2;              // first aggregate of the chunk
       if (item0 < items) {
         const int ajl0 = item0 / naxp, ax0 = item0 - ajl0 * naxp;
-        const int dst = sb.rank * ncp + (aj0 + ajl0) * naxp + ax0;
+        const int dst = sb.rank * ncp + (ajo0 + ajl0) * naxp + ax0;
         comm.publish_tl(tl_slot, dst, chunk, lane & 15, sb.cs);
       }
     }
@@ -557,6 +609,71 @@ struct Stepper {
     return rz;
   }
 
+  // offset in a rows -1..R buffer of entry i of the two halo rows ([0, W): row -1, [W, 2W): row R)
+  __device__ __forceinline__ int halo_offset(int i) const { return i < sb.W ? i : (sb.R + 1) * sb.W + (i - sb.W); }
+
+  // V(1,1) two-grid cycle z = M^-1 r in FP32 over the owned rows and the two halo rows:
+  //   y = S r,  ec = Ac^-1 P^T (r - A y),  u = y + P ec,  z = u + S (r - A u),
+  // with the damped-Jacobi smoother S = omega D^-1 and A applied with the FP32 element weights,
+  // so that I - M^-1 A = (I - S A)(I - P Ac^-1 P^T A)(I - S A) (symmetric).  The halo rows of r
+  // (vrh) follow the owners' CG recurrence bit for bit, and every CTA computes ec for the
+  // aggregate rows its halo rows touch from the same restricted vector, so y and u on a halo
+  // row equal the owner's values: M^-1 is one operator across the CTAs.  One cluster barrier
+  // (the restricted partials).  z goes to zbuf on the owned rows; returns the local (r, z).
+  __device__ Real vcycle(const Real (&r)[NG][4]) {
+    const int W = sb.W, G = sb.G;
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+      if (l0 < 0) continue;
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) vy[l0 + j] = vsd[l0 + j] * (float)r[k][j];
+    }
+    for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) {
+      const int l = halo_offset(i);
+      vy[l] = vsd[l] * (float)vrh[i];
+    }
+    __syncthreads();
+    float w[NG][4];
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) w[k][j] = 0.f;
+      if (l0 < 0) continue;
+      float t[4];
+      stencil_elem32(vy, wd, ws, wt, l0, W, t);
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) w[k][j] = unknown(k, j) ? (float)r[k][j] - t[j] : 0.f;
+    }
+    coarse_restrict_push(w);
+    comm.sync();
+    coarse_gather(true, 0.f);
+    for (int gi = threadIdx.x; gi < (sb.R + 2) * G; gi += blockDim.x) {
+      const int a = tl_gagg[gi];
+      const float e = a >= 0 ? tl_ec[a] : 0.f;
+      const int l = (gi / G) * W + kGroup * (gi % G);   // row gi / G - 1, group gi % G
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) vu[l + j] = vsd[l + j] != 0.f ? vy[l + j] + e : 0.f;
+    }
+    __syncthreads();
+    Real rz = Real(0);
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+      if (l0 < 0) continue;
+      float t[4];
+      stencil_elem32(vu, wd, ws, wt, l0, W, t);
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) {
+        const float z = unknown(k, j) ? fmaf(vsd[l0 + j], (float)r[k][j] - t[j], vu[l0 + j]) : 0.f;
+        zbuf[l0 + j] = (Real)z;
+        rz = fma(r[k][j], (Real)z, rz);
+      }
+    }
+    return rz;
+  }
+
   // Jacobi-preconditioned CG in precision Real on A d = r, where r (given per node) is the FP64
   // residual scaled to unit 2-norm; on return x64 += unscale * d.  Stops when ||r||^2 <= target2
   // (scaled units) or at the iteration limit; returns the iteration count.  All CG scalars and
@@ -579,7 +696,19 @@ struct Stepper {
           v[0] = fma(r[k][j], z, v[0]);
         }
       }
-      if (tl) {
+      if (vc) {
+        // r on the halo rows from the neighbours' owned edge rows
+#pragma unroll
+        for (int k = 0; k < NG; ++k) {
+          const int l0 = loc0[k];
+          if (l0 < 0) continue;
+#pragma unroll
+          for (int j = 0; j < kGroup; ++j) vq[l0 + j] = r[k][j];
+        }
+        exchange(vq);
+        for (int i = threadIdx.x; i < 2 * sb.W; i += blockDim.x) vrh[i] = vq[halo_offset(i)];
+        v[0] = vcycle(r);
+      } else if (tl) {
         coarse_restrict_push(r);
         comm.sync();
         coarse_gather(true, 0.f);
@@ -611,11 +740,27 @@ struct Stepper {
           pq[0] = fma(p[k][j], q[k][j], pq[0]);
         }
       }
-      if (tl) coarse_restrict_push(q);       // visible after the all-reduce's cluster barrier
+      if (vc) {
+        // q's owned edge rows to the neighbours, whose copies of r on their halo rows follow
+        // the same recurrence (visible after the all-reduce's barrier)
+#pragma unroll
+        for (int k = 0; k < NG; ++k) {
+          const int l0 = loc0[k];
+          if (l0 < 0) continue;
+          const int lr = l0 / sb.W - 1;
+          if (lr != 0 && lr != sb.R - 1) continue;
+#pragma unroll
+          for (int j = 0; j < kGroup; ++j) vq[l0 + j] = q[k][j];
+        }
+        __syncthreads();
+        comm.push_halos(vq, sb);
+      } else if (tl) {
+        coarse_restrict_push(q);             // visible after the all-reduce's cluster barrier
+      }
       const Real rz_c = rz;
       allreduce<Real, 1>(pq, [rz_c](Real* t) { t[0] = rz_c / t[0]; });
       const Real alpha = pq[0];
-      if (tl) coarse_gather(false, (float)alpha);
+      if (tl && !vc) coarse_gather(false, (float)alpha);
       // d += alpha p, r -= alpha q, z = D^-1 r; (r, z), (r, r) and beta = (r, z)_new / (r, z)
       Real v[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
@@ -634,7 +779,12 @@ struct Stepper {
           }
         }
       }
-      if (tl) v[0] = prolong_precondition(r);
+      if (vc) {
+        for (int i = threadIdx.x; i < 2 * sb.W; i += blockDim.x) vrh[i] = fma(-alpha, vq[halo_offset(i)], vrh[i]);
+        v[0] = vcycle(r);
+      } else if (tl) {
+        v[0] = prolong_precondition(r);
+      }
       __syncthreads();
       comm.push_halos(zbuf, sb);
       allreduce<Real, 2, 1>(v, [rz_c](Real* t) { t[2] = t[0] / rz_c; });

@@ -1,7 +1,9 @@
-"""Two-level preconditioner of the coarse-step solves (FP32 CG, aggregation coarse space):
-the one-shot pass with it matches the oracle for every cluster size (the restricted residual
-is summed across the CTAs of a cluster whose slabs split aggregate rows differently), and it
-needs fewer CG iterations than Jacobi alone on the coarse and correction solves."""
+"""Two-level preconditioners of the coarse-step solves (aggregation coarse space), additive
+(D^-1 + P Ac^-1 P^T) and the symmetric V(1,1) two-grid cycle with damped-Jacobi smoothing: the
+one-shot pass with either matches the oracle for every cluster size (the restricted residual is
+summed across the CTAs of a cluster whose slabs split aggregate rows differently; the V-cycle
+also smooths across slab edges), and they need fewer CG iterations than Jacobi alone on the
+coarse and correction solves, the V-cycle fewer than the additive form."""
 from __future__ import annotations
 
 import pytest
@@ -63,24 +65,30 @@ def check(case, op, buf, Theta, grad, tol_t=MIXED_T_TOL, tol_g=MIXED_G_TOL):
     assert op.stats()["status"] == 0
 
 
+MODES = ["additive", "vcycle"]
+
+
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("precision", ["fp32_refine", "fp32_refine_all"])
 @pytest.mark.parametrize("cs", [2, 4, 8, 16])
-def test_twolevel_pass_matches_oracle_for_every_cluster_size(case, cs, precision):
-    op, buf, Theta, grad = run_pass(case, True, cs, precision)
+def test_twolevel_pass_matches_oracle_for_every_cluster_size(case, cs, precision, mode):
+    op, buf, Theta, grad = run_pass(case, mode, cs, precision)
     assert op.plan(1, 1)["cs"] == cs
     check(case, op, buf, Theta, grad)
 
 
-def test_twolevel_fp64_path_keeps_the_fp64_tolerance(case):
+@pytest.mark.parametrize("mode", MODES)
+def test_twolevel_fp64_path_keeps_the_fp64_tolerance(case, mode):
     """FP64 CG with the two-level coarse correction (applied in FP32, refined in FP64)."""
-    op, buf, Theta, grad = run_pass(case, True, 0, "fp64")
+    op, buf, Theta, grad = run_pass(case, mode, 0, "fp64")
     check(case, op, buf, Theta, grad, FP64_TOL, FP64_TOL)
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("precision", ["fp32_refine", "fp32_refine_all"])
-def test_twolevel_reduces_coarse_iterations(case, precision):
-    on = run_pass(case, True, 0, precision)
-    off = run_pass(case, False, 0, precision)
+def test_twolevel_reduces_coarse_iterations(case, precision, mode):
+    on = run_pass(case, mode, 0, precision)
+    off = run_pass(case, "none", 0, precision)
     check(case, *on)
     check(case, *off)
     k_on, k_off = on[0].stats()["by_kind"], off[0].stats()["by_kind"]
@@ -92,9 +100,26 @@ def test_twolevel_reduces_coarse_iterations(case, precision):
         assert abs(k_on[name]["cg_iters"] - k_off[name]["cg_iters"]) <= 0.01 * k_off[name]["cg_iters"]
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine", "fp32_refine_all"])
+def test_vcycle_needs_fewer_iterations_than_additive(case, precision):
+    """Coarse-step solves: the two-grid cycle's smoothing removes the high-frequency error
+    that the additive form leaves to CG (an iteration-count check, as above)."""
+    runs = {m: run_pass(case, m, 0, precision) for m in MODES}
+    tol = FP64_TOL if precision == "fp64" else None
+    for m in MODES:
+        if tol:
+            check(case, *runs[m], tol, tol)
+        else:
+            check(case, *runs[m])
+    k = {m: runs[m][0].stats()["by_kind"] for m in MODES}
+    for name in ("coarse_primal", "correct_primal", "coarse_adjoint", "correct_adjoint"):
+        assert k["vcycle"][name]["cg_iters"] < 0.75 * k["additive"][name]["cg_iters"], (name, k)
+
+
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refine_all"])
 @pytest.mark.parametrize("design", ["branches_table1_bottom", "uniform_simp_left"])
-def test_twolevel_helps_on_high_contrast_designs(design, precision):
+def test_twolevel_helps_on_high_contrast_designs(design, precision, mode):
     """The preconditioner must pay on a near-binary design too (an iteration-count check: the
     parity tests pass even with a useless preconditioner, because CG still converges)."""
     from paper_2411_19030_gb300 import parareal_pass
@@ -104,7 +129,7 @@ def test_twolevel_helps_on_high_contrast_designs(design, precision):
     else:
         prob, rho = make_problem(n, Nt=Nt, Ntau=16, dt=1 / Nt), W.rho_uniform(n, n, 1, 0.2, 0.8)
     its = {}
-    for tl in (True, False):
+    for tl in (mode, "none"):
         op = gpu_operator(prob, precision, rtol=1e-10, twolevel=tl)
         buf = PassBuffers(op)
         op.assemble(dev(rho))
@@ -113,4 +138,4 @@ def test_twolevel_helps_on_high_contrast_designs(design, precision):
         assert op.stats()["status"] == 0
         st = op.stats()["by_kind"]["coarse_primal"]
         its[tl] = st["cg_iters"] / st["solves"]
-    assert its[True] < 0.6 * its[False], its
+    assert its[mode] < 0.6 * its["none"], its
