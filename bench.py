@@ -144,7 +144,7 @@ def run_gpu(args):
     n, Nt, Ntau, dt, p = w["n"], w["Nt"], w["Ntau"], w["dt"], w["p"]
     N_free = (n + 1) ** 2 - int(sink.sum())
     solve = SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=2000, refine_max=8,
-                        twolevel=args.twolevel)
+                        twolevel=args.twolevel, smooth_steps=args.smooth)
     op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink, solve=solve, device=local)
     seq_op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink,
                       solve=SolveConfig("fp64", rtol=1e-13, cg_iters_max=4000, refine_max=8), device=local)
@@ -288,7 +288,7 @@ def run_gpu(args):
             vname = "fp32_refine_all" if args.precision == "fp32_refine" else "fp32_refine"
             v_op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink,
                             solve=SolveConfig(vname, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=2000,
-                                              refine_max=8, twolevel=args.twolevel), device=local)
+                                              refine_max=8, twolevel=args.twolevel, smooth_steps=args.smooth), device=local)
             v_buf = PassBuffers(v_op)
             for a_, b_ in ((v_buf.U_T, buf.U_T), (v_buf.U_th, buf.U_th), (v_buf.V_l, buf.V_l),
                            (v_buf.V_g, buf.V_g)):
@@ -341,7 +341,7 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": f"{WORKLOAD}: 128x128 grid, Nt=1024, Ntau=32 (M=32), p=8, SIMP k, warm start from "
                                "the sequential coarse states of a design 1% away",
-                   "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel, "l2": "flushed between steps (256 MB write)",
+                   "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel, "smooth_steps": args.smooth, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "wall_s": wall},
         "per_kernel_ms": kind_ms,
@@ -473,7 +473,7 @@ def run_loop(args):
     a_max, r_fil, beta, eta = 0.4, 0.03, 32.0, 0.5
     op = Operator(n, n, h, w["material"], Nt, Ntau, dt, w["p"], sink,
                   solve=SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=4000, refine_max=8,
-                                    twolevel=args.twolevel))
+                                    twolevel=args.twolevel, smooth_steps=args.smooth))
     true_op = Operator(n, n, h, w["material"], Nt, Ntau, dt, w["p"], sink,
                        solve=SolveConfig("fp64", rtol=1e-12, cg_iters_max=8000, refine_max=8))
     design = DesignMap(n, n, h, r_fil, beta, eta)
@@ -496,7 +496,7 @@ def run_loop(args):
         "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
         "config": {"workload": f"loop{n}: {n}x{n} grid, Nt={Nt}, Ntau={Ntau}, p=8, SIMP k, a_max={a_max}, "
                                f"r_fil={r_fil}, beta={beta}, eta={eta}, MMA move 0.2",
-                   "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel},
+                   "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel, "smooth_steps": args.smooth},
         "first_iteration_sequential_ms": ms[0],
         "fine_dof_steps_per_s": 2.0 * N_free * Nt / (np.mean(oneshot) * 1e-3),
         "history": {"Theta_estimate": hist["Theta"], "area_fraction": hist["volume"], "ms": ms},
@@ -652,6 +652,9 @@ def main():
     ap.add_argument("--twolevel", default="vcycle", choices=["none", "additive", "vcycle"],
                     help="preconditioner of the coarse-step solves: Jacobi, additive two-level, or the "
                          "two-grid V(1,1) cycle")
+    ap.add_argument("--smooth", type=int, default=0,
+                    help="V-cycle smoothing steps (1: one global Jacobi step; k >= 2: k slab-local steps; "
+                         "0: the library default)")
     ap.add_argument("--no-twolevel", dest="twolevel", action="store_const", const="none",
                     help="same as --twolevel none")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

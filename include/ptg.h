@@ -108,9 +108,9 @@ typedef struct {
                           and its inverse applied in FP32:
                           PTG_TWOLEVEL_NONE      Jacobi everywhere;
                           PTG_TWOLEVEL_ADDITIVE  D^-1 + P Ac^-1 P^T;
-                          PTG_TWOLEVEL_VCYCLE    a symmetric two-grid cycle: one damped-Jacobi
-                                                 step (S = 0.8 D^-1), the coarse correction of
-                                                 the residual, one more Jacobi step, i.e.
+                          PTG_TWOLEVEL_VCYCLE    a symmetric two-grid cycle: damped-Jacobi
+                                                 smoothing S (omega = 0.8, smooth_steps), the
+                                                 coarse correction of the residual, S again, i.e.
                                                  I - M^-1 A = (I - S A)(I - P Ac^-1 P^T A)(I - S A),
                                                  applied in FP32.
                           Other values: PTG_EINVAL. */
@@ -120,6 +120,10 @@ typedef struct {
                           kinds in groups of the fewest CTAs whose slabs fit.  0 never; 1 for a
                           single FP64 system on >= 40000 nodes and whenever no cluster plan fits
                           (grids beyond about 300 x 300); 2 always. */
+    int smooth_steps;  /* PTG_TWOLEVEL_VCYCLE smoothing, before and after the coarse correction:
+                          1: one damped-Jacobi step on the whole grid; k in 2..16: k damped-Jacobi
+                          steps on each CTA's slab alone (the slab's diagonal block of A, no
+                          communication).  0: the library's default.  Other values: PTG_EINVAL. */
 } ptg_solve;
 
 typedef struct {

@@ -67,6 +67,8 @@ class SolveConfig:
     #                                  True / "additive" (D^-1 + P Ac^-1 P^T), False / "none" (Jacobi)
     grid_wide: int = 1               # single FP64 systems over every SM (cooperative grid):
     #                                  0 never, 1 for large grids or when no cluster fits, 2 always
+    smooth_steps: int = 0            # V-cycle smoothing: 1 global Jacobi step, k >= 2 slab-local
+    #                                  steps, 0 the library default
 
 
 class Operator:
@@ -104,7 +106,7 @@ class Operator:
         prec = {"fp64": PTG_FP64, "fp32_refine": PTG_FP32_REFINE,
                 "fp32_refine_all": PTG_FP32_REFINE_ALL}[solve.precision]
         s = _ffi.ptg_solve(prec, solve.rtol, solve.inner_rtol, solve.cg_iters_max, solve.refine_max,
-                           twolevel_code(solve.twolevel), int(solve.grid_wide))
+                           twolevel_code(solve.twolevel), int(solve.grid_wide), int(solve.smooth_steps))
         self._dir = np.ascontiguousarray(dirichlet, dtype=np.uint8).reshape(-1)
         if self._dir.size != self.Nn:
             raise ValueError("dirichlet mask must have (nx+1)(ny+1) entries")

@@ -23,7 +23,8 @@ struct ptg_op {
   int W = 0;               // padded row width
   // two-level preconditioner of the coarse-step solves (FP32 CG); tl_m == 0: disabled
   int tl_m = 0, tl_nax = 0, tl_nay = 0;
-  int tl_vc = 0;   // 1: the V(1,1) two-grid cycle instead of the additive form
+  int tl_vc = 0;   // 1: the two-grid cycle instead of the additive form
+  int tl_nu = 1;   // its smoothing steps (see StepParams::tl_nu)
   double* tl_Ac = nullptr;
   float *tl_band = nullptr, *tl_X = nullptr, *tl_Ainv = nullptr;
   // device workspace
@@ -90,19 +91,27 @@ int kind_precision(int solve_precision, int kind) {
   return coarse_kind(kind) ? PTG_FP64 : PTG_FP32_REFINE;
 }
 
+// Two-level forms a plan may use, strongest last: tl_mode caps the op's choice (an op set up
+// for the V-cycle runs the additive form under a plan capped at TL_ADDITIVE, e.g. when the
+// V-cycle's buffers do not fit).
+enum TlMode : int { TL_NONE = 0, TL_ADDITIVE = 1, TL_VCYCLE = 2 };
+bool uses_vcycle(const ptg_op* op, int tl_mode) { return tl_mode >= TL_VCYCLE && op->tl_vc; }
+int strongest_mode(const ptg_op* op) { return op->tl_m == 0 ? TL_NONE : (op->tl_vc ? TL_VCYCLE : TL_ADDITIVE); }
+
 // Aggregate rows reserved per CTA for cluster size cs (the largest over the ranks; with the
 // V-cycle the rows its halo rows touch too), 0 if the two-level preconditioner is off for this
 // op, kind or plan.
-int twolevel_rows(const ptg_op* op, int precision, int kind, int cs, bool use = true) {
+int twolevel_rows(const ptg_op* op, int precision, int kind, int cs, int tl_mode = TL_VCYCLE) {
   (void)precision;
-  if (!use || op->tl_m == 0 || !coarse_kind(kind)) return 0;
+  if (tl_mode == TL_NONE || op->tl_m == 0 || !coarse_kind(kind)) return 0;
+  const bool vc = uses_vcycle(op, tl_mode);
   int best = 0;
   for (int q = 0; q < cs; ++q) {
     int r0, R, lo, hi;
     const int rows = op->g.ny + 1, base = rows / cs, rem = rows % cs;
     r0 = q * base + (q < rem ? q : rem);
     R = base + (q < rem ? 1 : 0);
-    if (op->tl_vc)
+    if (vc)
       coarse_rows_of_halo_slab(r0, R, op->g.ny, op->tl_m, op->tl_nay, lo, hi);
     else
       coarse_rows_of_slab(r0, R, op->tl_m, op->tl_nay, lo, hi);
@@ -112,18 +121,23 @@ int twolevel_rows(const ptg_op* op, int precision, int kind, int cs, bool use = 
 }
 
 // precision: the kernel's (PTG_FP64 or PTG_FP32_REFINE)
-size_t twolevel_bytes(const ptg_op* op, int precision, int kind, int cs, bool use = true, bool slots = true) {
-  const int ncj = twolevel_rows(op, precision, kind, cs, use);
+size_t twolevel_bytes(const ptg_op* op, int precision, int kind, int cs, int tl_mode, bool slots = true) {
+  const int ncj = twolevel_rows(op, precision, kind, cs, tl_mode);
   if (ncj == 0) return 0;
   const int rmax = (op->g.ny + 1 + cs - 1) / cs;
-  return twolevel_smem_bytes(op->W, rmax, cs, op->tl_nax, op->tl_nay, ncj, slots, op->tl_vc != 0,
-                             precision == PTG_FP64 ? 8 : 4);
+  return twolevel_smem_bytes(op->W, rmax, cs, op->tl_nax, op->tl_nay, ncj, slots, uses_vcycle(op, tl_mode),
+                             precision == PTG_FP64 ? 8 : 4, op->tl_nu);
 }
 
 // Damping of the V-cycle's Jacobi smoother: the largest eigenvalue of D^-1 A lies between 1.5
 // (conduction-dominated) and 2.25 (capacity-dominated: the consistent Q1 mass matrix), so
 // omega lambda_max stays below 1.8 < 2 for every step size.
 constexpr float kVcycleOmega = 0.8f;
+// Default smoothing steps of the V-cycle (ptg_solve.smooth_steps = 0): four slab-local Jacobi
+// steps before and after the coarse correction.  Measured on the 128 x 128 one-shot pass
+// (FP64 coarse-step CG): 1 global step 66.1 ms; 2, 3, 4, 6 local steps 59.2, 56.5, 55.9,
+// 56.8 ms, the CG iterations per correction solve falling from 34 to 26, 23, 21, 19.
+constexpr int kVcycleSmoothSteps = 4;
 
 // Node count from which a single FP64 system runs grid-wide (see choose_plan).
 constexpr int kWideMinNodes = 40000;
@@ -131,11 +145,11 @@ constexpr int kWideMinNodes = 40000;
 // two-level bytes of a grid-wide launch of G CTAs (the partials live in global memory)
 struct WideCtx {
   const ptg_op* op;
-  int precision, kind;
+  int precision, kind, tl_mode;
 };
 size_t wide_twolevel_bytes(const void* ctx, int G) {
   const WideCtx* c = static_cast<const WideCtx*>(ctx);
-  return twolevel_bytes(c->op, c->precision, c->kind, G, true, false);
+  return twolevel_bytes(c->op, c->precision, c->kind, G, c->tl_mode, false);
 }
 
 // Inner tolerance of an FP64 CG with the two-level preconditioner.  The coarse correction is
@@ -147,10 +161,11 @@ size_t wide_twolevel_bytes(const void* ctx, int G) {
 // loop restarts it from the exact residual.
 constexpr double kTwoLevelInnerFp64 = 1e-4;
 
-void twolevel_params(const ptg_op* op, int precision, StepParams& P, bool use) {
-  P.tl_naj = twolevel_rows(op, precision, P.kind, P.cs, use);
-  P.tl_vc = P.tl_naj > 0 ? op->tl_vc : 0;
+void twolevel_params(const ptg_op* op, int precision, StepParams& P, int tl_mode) {
+  P.tl_naj = twolevel_rows(op, precision, P.kind, P.cs, tl_mode);
+  P.tl_vc = P.tl_naj > 0 && uses_vcycle(op, tl_mode);
   P.tl_omega = kVcycleOmega;
+  P.tl_nu = op->tl_nu;
   // FP32 CG: the op's inner tolerance; FP64 CG: to the final tolerance in one go, or in
   // kTwoLevelInnerFp64 steps with the two-level preconditioner
   if (precision == PTG_FP64) P.inner_rtol = P.tl_naj > 0 ? std::max(kTwoLevelInnerFp64, op->sv.inner_rtol) : 0.0;
@@ -164,7 +179,7 @@ void twolevel_params(const ptg_op* op, int precision, StepParams& P, bool use) {
 // Best plan for `ntasks` concurrent clusters with or without the two-level preconditioner:
 // fewest waves, then the shortest per-thread work (ng), then the largest cluster.  Returns
 // the number of waves, or -1 if nothing fits.
-long best_plan(ptg_op* op, int precision, int kind, int ntasks, bool tl, Plan* out) {
+long best_plan(ptg_op* op, int precision, int kind, int ntasks, int tl_mode, Plan* out) {
   const int nx = op->g.nx, ny = op->g.ny;
   const int G = op->W / kGroup;
   long best_waves = -1;
@@ -177,7 +192,7 @@ long best_plan(ptg_op* op, int precision, int kind, int ntasks, bool tl, Plan* o
       if (nthreads > kStepMaxThreadsHost) continue;
       Plan p;
       cudaError_t e = query_stepper_plan(nx, ny, precision, kind, cs, ng, nthreads,
-                                         twolevel_bytes(op, precision, kind, cs, tl), &p);
+                                         twolevel_bytes(op, precision, kind, cs, tl_mode), &p);
       if (e != cudaSuccess) {
         cudaGetLastError();
         continue;
@@ -185,7 +200,8 @@ long best_plan(ptg_op* op, int precision, int kind, int ntasks, bool tl, Plan* o
       if (p.max_active_clusters <= 0) continue;
       const long waves = (ntasks + p.max_active_clusters - 1) / p.max_active_clusters;
       if (best_waves < 0 || waves < best_waves || (waves == best_waves && ng < out->ng)) {
-        p.twolevel = tl && twolevel_rows(op, precision, kind, cs) > 0;
+        p.twolevel = twolevel_rows(op, precision, kind, cs, tl_mode) > 0;
+        p.vc = p.twolevel && uses_vcycle(op, tl_mode);
         *out = p;
         best_waves = waves;
       }
@@ -217,34 +233,49 @@ int choose_plan(ptg_op* op, int precision, int kind, int ntasks, Plan* out) {
   // GB300 the cluster wins at 128 x 128; the grid wins once the per-iteration FP64 work of 16
   // SMs dominates (kWideMinNodes).  Grids whose slabs do not fit 16 CTAs (512 x 512) run in
   // groups of CTAs of one cooperative launch.  grid_wide: 0 never, 1 by these rules, 2 always.
+  // The strongest two-level form whose plan fits (and, for FP32 CG, adds no wave over
+  // Jacobi's: FP64 CG on GB300 is bound by the FP64 pipe, so the cut in iterations outweighs
+  // extra waves; FP32 CG is bound by latency).
   Plan jac, two;
-  const long wj = best_plan(op, precision, kind, ntasks, false, &jac);
-  const long wt = twolevel_rows(op, precision, kind, 1) > 0 ? best_plan(op, precision, kind, ntasks, true, &two) : -1;
+  const long wj = best_plan(op, precision, kind, ntasks, TL_NONE, &jac);
+  long wt = -1;
+  if (twolevel_rows(op, precision, kind, 1) > 0) {
+    for (int mode = strongest_mode(op); mode > TL_NONE; --mode) {
+      Plan c;
+      const long w = best_plan(op, precision, kind, ntasks, mode, &c);
+      if (w >= 0 && (wj < 0 || w <= wj || precision == PTG_FP64)) {
+        two = c;
+        wt = w;
+        break;
+      }
+    }
+  }
   const bool spread = ntasks == 1 && precision == PTG_FP64;
   const bool no_cluster = wj < 0 && wt < 0;
   const bool want_wide = op->sv.grid_wide == 2 ||
                          (op->sv.grid_wide == 1 && (no_cluster || (spread && op->Nn >= kWideMinNodes)));
   if (want_wide) {
-    // one FP64 system over every SM (spread), or groups of the fewest CTAs whose slabs fit
-    Plan w;
-    WideCtx ctx{op, precision, kind};
-    if (query_wide_plan(op->g.nx, op->g.ny, precision, kind, ntasks, spread, wide_twolevel_bytes, &ctx, &w) ==
-        cudaSuccess) {
-      w.twolevel = twolevel_rows(op, precision, kind, w.cs) > 0;
-      op->plans[key] = w;
-      *out = w;
-      return PTG_OK;
+    // one FP64 system over every SM (spread), or groups of the fewest CTAs whose slabs fit,
+    // with the strongest two-level form that fits
+    for (int mode = strongest_mode(op); mode >= TL_NONE; --mode) {
+      Plan w;
+      WideCtx ctx{op, precision, kind, mode};
+      if (query_wide_plan(op->g.nx, op->g.ny, precision, kind, ntasks, spread, wide_twolevel_bytes, &ctx, &w) ==
+          cudaSuccess) {
+        w.twolevel = twolevel_rows(op, precision, kind, w.cs, mode) > 0;
+        w.vc = w.twolevel && uses_vcycle(op, mode);
+        op->plans[key] = w;
+        *out = w;
+        return PTG_OK;
+      }
+      cudaGetLastError();
     }
-    cudaGetLastError();
   }
   if (no_cluster) {
     std::snprintf(g_last_error, sizeof(g_last_error), "no launch plan fits a %dx%d grid", op->g.nx, op->g.ny);
     return PTG_EINVAL;
   }
-  // FP64 CG on GB300 is bound by the FP64 pipe, so the cut in iterations outweighs extra
-  // waves; FP32 CG is bound by latency, so two-level must not add waves
-  const bool prefer_two = wt >= 0 && (wj < 0 || wt <= wj || precision == PTG_FP64);
-  const Plan best = prefer_two ? two : jac;
+  const Plan best = wt >= 0 ? two : jac;
   op->plans[key] = best;
   *out = best;
   return PTG_OK;
@@ -312,7 +343,7 @@ int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream) {
     P.g_halo_row_bytes = op->W * (int)sizeof(double);
     P.g_tl = op->g_tl;
   }
-  twolevel_params(op, prec, P, plan.twolevel && !P.plt);
+  twolevel_params(op, prec, P, plan.twolevel && !P.plt ? (plan.vc ? TL_VCYCLE : TL_ADDITIVE) : TL_NONE);
   op->last_stream = stream;
   PTG_CUDA(launch_stepper(P, plan, prec, ntasks, stream));
   return PTG_OK;
@@ -356,6 +387,7 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
   if (solve->precision != PTG_FP64 && solve->precision != PTG_FP32_REFINE && solve->precision != PTG_FP32_REFINE_ALL)
     return PTG_EINVAL;
   if (solve->twolevel < PTG_TWOLEVEL_NONE || solve->twolevel > PTG_TWOLEVEL_VCYCLE) return PTG_EINVAL;
+  if (solve->smooth_steps < 0 || solve->smooth_steps > 16) return PTG_EINVAL;
   if (!(solve->rtol > 0.0) || solve->cg_iters_max < 1 || solve->refine_max < 1 || !(solve->inner_rtol >= 0.0))
     return PTG_EINVAL;
   if (!(mat->k0 > 0.0) || !(mat->kmin > 0.0) || !(mat->c0 > 0.0) || !(mat->cmin > 0.0)) return PTG_EINVAL;
@@ -406,6 +438,7 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
     while ((grid->nx + 1) / m > kCoarseMaxAgg || (grid->ny + 1) / m > kCoarseMaxAgg) m += 4;
     op->tl_m = m;
     op->tl_vc = solve->twolevel == PTG_TWOLEVEL_VCYCLE;
+    op->tl_nu = solve->smooth_steps > 0 ? solve->smooth_steps : kVcycleSmoothSteps;
     op->tl_nax = coarse_aggregates(grid->nx, m);
     op->tl_nay = coarse_aggregates(grid->ny, m);
     const size_t nc = (size_t)op->tl_nax * op->tl_nay;
@@ -496,19 +529,20 @@ int ptg_op_set_plan(ptg_op* op, int kind, int cs, int ng) {
   if (ng < 1 || ng > kStepNG[kNumStepNG - 1]) return PTG_EINVAL;
   const int nthreads = ((groups + ng - 1) / ng + 31) / 32 * 32;
   if (nthreads > kStepMaxThreadsHost) return PTG_EINVAL;
-  // with the two-level preconditioner where it applies and fits, else with Jacobi
-  for (bool tl : {true, false}) {
+  // with the strongest two-level form where it applies and fits, else with Jacobi
+  for (int mode = strongest_mode(op); mode >= TL_NONE; --mode) {
     const int prec = kind_precision(op->sv.precision, kind);
-    if (tl && twolevel_rows(op, prec, kind, cs) == 0) continue;
+    if (mode > TL_NONE && twolevel_rows(op, prec, kind, cs, mode) == 0) continue;
     Plan p;
     cudaError_t e = query_stepper_plan(op->g.nx, op->g.ny, prec, kind, cs, ng, nthreads,
-                                       twolevel_bytes(op, prec, kind, cs, tl), &p);
+                                       twolevel_bytes(op, prec, kind, cs, mode), &p);
     if (e != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
     if (p.max_active_clusters <= 0) continue;
-    p.twolevel = tl;
+    p.twolevel = mode > TL_NONE;
+    p.vc = uses_vcycle(op, mode);
     op->plan_override[kind] = p;
     return PTG_OK;
   }
@@ -773,7 +807,7 @@ void batch_free(ptg_batch* b) {
 }
 
 // Per-design parameters of one phase with cluster size cs.
-StepParams phase_params(const ptg_batch* b, int d, int ph, int cs, bool tl) {
+StepParams phase_params(const ptg_batch* b, int d, int ph, int cs, int tl_mode) {
   const ptg_op* op = b->ops[d];
   const BatchBuf& B = b->bufs[d];
   StepParams P;
@@ -786,7 +820,7 @@ StepParams phase_params(const ptg_batch* b, int d, int ph, int cs, bool tl) {
   P.hist = B.T_hist;
   P.hist_j0 = 0;
   P.hist_rows = op->tm.Nt + 1;
-  twolevel_params(op, kind_precision(b->precision, P.kind), P, tl);
+  twolevel_params(op, kind_precision(b->precision, P.kind), P, tl_mode);
   const int Ntau = op->tm.Ntau;
   switch (ph) {
     case 0:  P.in_field = B.U_T; P.in_aux = B.U_th; P.out_field = B.F_T; P.out_aux = B.F_th; break;
@@ -837,8 +871,9 @@ std::vector<int2> phase_tasks(const ptg_batch* b, int ph) {
 }
 
 // Install a plan for a phase: validate it for every design, upload the parameter table and
-// the task list, and size the persistent grid.  tl: two-level preconditioner where it applies.
-int batch_install(ptg_batch* b, int ph, int cs, int ng, int nthreads, bool tl) {
+// the task list, and size the persistent grid.  tl_mode: the strongest two-level form the
+// designs may use where it applies.
+int batch_install(ptg_batch* b, int ph, int cs, int ng, int nthreads, int tl_mode) {
   const int kind = phase_kind(ph);
   const int prec = kind_precision(b->precision, kind);
   size_t smem = 0;
@@ -848,7 +883,7 @@ int batch_install(ptg_batch* b, int ph, int cs, int ng, int nthreads, bool tl) {
     const int groups = rmax * (op->W / kGroup);
     if (groups > ng * nthreads) return PTG_EINVAL;
     smem = std::max(smem, stepper_smem_bytes(op->g.nx, rmax, prec == PTG_FP32_REFINE ? 4 : 8) +
-                              twolevel_bytes(op, prec, kind, cs, tl));
+                              twolevel_bytes(op, prec, kind, cs, tl_mode));
   }
   int nclusters = 0;
   if (query_batch_occupancy(prec, kind, cs, ng, nthreads, smem, &nclusters) != cudaSuccess || nclusters <= 0) {
@@ -856,7 +891,7 @@ int batch_install(ptg_batch* b, int ph, int cs, int ng, int nthreads, bool tl) {
     return PTG_EINVAL;
   }
   std::vector<StepParams> table;
-  for (int d = 0; d < (int)b->ops.size(); ++d) table.push_back(phase_params(b, d, ph, cs, tl));
+  for (int d = 0; d < (int)b->ops.size(); ++d) table.push_back(phase_params(b, d, ph, cs, tl_mode));
   std::vector<int2> tasks = phase_tasks(b, ph);
   PhasePlan& pp = b->ph[ph];
   if (!pp.table) PTG_CUDA(cudaMalloc(&pp.table, sizeof(StepParams) * table.size()));
@@ -868,7 +903,8 @@ int batch_install(ptg_batch* b, int ph, int cs, int ng, int nthreads, bool tl) {
   pp.plan.nthreads = nthreads;
   pp.plan.smem = smem;
   pp.plan.max_active_clusters = nclusters;
-  pp.plan.twolevel = tl;
+  pp.plan.twolevel = tl_mode > TL_NONE;
+  pp.plan.vc = tl_mode >= TL_VCYCLE;
   pp.ntasks = (int)tasks.size();
   pp.nclusters = std::min(nclusters, pp.ntasks);
   pp.ready = true;
@@ -878,7 +914,7 @@ int batch_install(ptg_batch* b, int ph, int cs, int ng, int nthreads, bool tl) {
 // Default plan of a phase: fewest waves, then the fewest groups per thread, then the largest
 // cluster; the two-level preconditioner unless it needs more waves (the autotuner may replace
 // the plan).
-long batch_best(ptg_batch* b, int ph, bool tl, int ntasks, int* best_cs, int* best_ng, int* best_nt) {
+long batch_best(ptg_batch* b, int ph, int tl_mode, int ntasks, int* best_cs, int* best_ng, int* best_nt) {
   long best_waves = -1;
   const int prec = kind_precision(b->precision, phase_kind(ph));
   for (int cs : {16, 8, 4, 2}) {
@@ -892,7 +928,7 @@ long batch_best(ptg_batch* b, int ph, bool tl, int ntasks, int* best_cs, int* be
         const int groups = rmax * (op->W / kGroup);
         nt = std::max(nt, ((groups + ng - 1) / ng + 31) / 32 * 32);
         smem = std::max(smem, stepper_smem_bytes(op->g.nx, rmax, prec == PTG_FP32_REFINE ? 4 : 8) +
-                                  twolevel_bytes(op, prec, phase_kind(ph), cs, tl));
+                                  twolevel_bytes(op, prec, phase_kind(ph), cs, tl_mode));
       }
       if (!ok || nt > kStepMaxThreadsHost) continue;
       int ncl = 0;
@@ -912,22 +948,27 @@ long batch_best(ptg_batch* b, int ph, bool tl, int ntasks, int* best_cs, int* be
   return best_waves;
 }
 
-bool batch_has_twolevel(const ptg_batch* b, int ph) {
-  if (ph >= 8) return false;   // the PLT corrections solve nothing
+// The strongest two-level form of any design of the batch for a phase (TL_NONE: none applies).
+int batch_twolevel_mode(const ptg_batch* b, int ph) {
+  if (ph >= 8) return TL_NONE;   // the PLT corrections solve nothing
+  int mode = TL_NONE;
   for (const ptg_op* op : b->ops)
-    if (twolevel_rows(op, b->precision, phase_kind(ph), 1) > 0) return true;
-  return false;
+    if (twolevel_rows(op, b->precision, phase_kind(ph), 1) > 0) mode = std::max(mode, strongest_mode(op));
+  return mode;
 }
 
 int batch_default(ptg_batch* b, int ph) {
   const int ntasks = (int)phase_tasks(b, ph).size();
-  int jc = 0, jg = 0, jt = 0, tc = 0, tg = 0, tt = 0;
-  const long wj = batch_best(b, ph, false, ntasks, &jc, &jg, &jt);
-  const long wt = batch_has_twolevel(b, ph) ? batch_best(b, ph, true, ntasks, &tc, &tg, &tt) : -1;
-  if (wj < 0 && wt < 0) return PTG_EINVAL;
+  int jc = 0, jg = 0, jt = 0;
+  const long wj = batch_best(b, ph, TL_NONE, ntasks, &jc, &jg, &jt);
   const bool fp64 = kind_precision(b->precision, phase_kind(ph)) == PTG_FP64;
-  if (wt >= 0 && (wj < 0 || wt <= wj || fp64)) return batch_install(b, ph, tc, tg, tt, true);
-  return batch_install(b, ph, jc, jg, jt, false);
+  for (int mode = batch_twolevel_mode(b, ph); mode > TL_NONE; --mode) {
+    int tc = 0, tg = 0, tt = 0;
+    const long wt = batch_best(b, ph, mode, ntasks, &tc, &tg, &tt);
+    if (wt >= 0 && (wj < 0 || wt <= wj || fp64)) return batch_install(b, ph, tc, tg, tt, mode);
+  }
+  if (wj < 0) return PTG_EINVAL;
+  return batch_install(b, ph, jc, jg, jt, TL_NONE);
 }
 
 int batch_run(ptg_batch* b, int ph, cudaStream_t stream) {
@@ -1076,9 +1117,10 @@ int ptg_batch_set_plan(ptg_batch* b, int phase, int cs, int ng, int nthreads) {
     return PTG_EINVAL;
   DeviceGuard dg(b->device);
   std::lock_guard<std::mutex> lk(b->mu);
-  // with the two-level preconditioner where it applies and fits, else with Jacobi
-  if (batch_has_twolevel(b, phase) && batch_install(b, phase, cs, ng, nthreads, true) == PTG_OK) return PTG_OK;
-  return batch_install(b, phase, cs, ng, nthreads, false);
+  // with the strongest two-level form where it applies and fits, else with Jacobi
+  for (int mode = batch_twolevel_mode(b, phase); mode > TL_NONE; --mode)
+    if (batch_install(b, phase, cs, ng, nthreads, mode) == PTG_OK) return PTG_OK;
+  return batch_install(b, phase, cs, ng, nthreads, TL_NONE);
 }
 
 int ptg_batch_get_plan(ptg_batch* b, int phase, int* cs, int* ng, int* nthreads, int* nclusters) {

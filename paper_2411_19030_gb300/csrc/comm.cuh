@@ -41,6 +41,25 @@ struct ClusterComm {
   __device__ void push_halos(T* buf, const Slab& sb) {
     ptg::push_halos(buf, sb, cl);
   }
+  // Edge rows sent straight from registers: the thread holding columns [col, col+4) of the
+  // owned row lr (0 or R-1) stores them into the neighbour's two-row buffer `edge` ([0]: the
+  // row below that CTA's slab, [1]: the row above); visible after the next barrier.
+  __device__ void begin_edges() {}
+  template <class T>
+  __device__ void put_edge(T* edge, int lr, int col, const T (&v)[4], const Slab& sb) {
+    if (lr == 0 && sb.rank > 0) {
+      T* d = cl.map_shared_rank(edge, (unsigned)(sb.rank - 1)) + sb.W + col;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) d[j] = v[j];
+    }
+    if (lr == sb.R - 1 && sb.rank < sb.cs - 1) {
+      T* d = cl.map_shared_rank(edge, (unsigned)(sb.rank + 1)) + col;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) d[j] = v[j];
+    }
+  }
+  template <class T>
+  __device__ void end_edges(T*, const Slab&) {}
   // a 16-byte chunk of restricted partials, written at offset dst of every rank's slot array;
   // the 16 lanes `sub` = 0..15 of a half-warp share the destinations
   __device__ void publish_tl(float* slot, int dst, const float4& chunk, int sub, int cs) {
@@ -76,9 +95,9 @@ struct GridComm {
   // halo rows published by push_halos and pulled in after the next barrier; pushes alternate
   // between two slot sets, so a CTA that has passed a barrier never overwrites slots that a
   // slower CTA of the group may still be pulling from the push before it
-  unsigned char* pending = nullptr;
+  unsigned char* pending_lo = nullptr;   // where the row below the slab goes (null: nothing pending)
+  unsigned char* pending_hi = nullptr;   // where the row above goes
   int pending_bytes = 0;         // bytes of one row
-  int R = 0, W = 0;
   int hset = 0;                  // slot set of the latest push
 
   __device__ GridComm(const StepParams& P_, RedSmem& rs_)
@@ -205,19 +224,41 @@ struct GridComm {
       d1[i] = s1[i];
     }
     __threadfence();                                // each writer orders its own stores
-    pending = reinterpret_cast<unsigned char*>(buf);
+    pending_lo = reinterpret_cast<unsigned char*>(buf);
+    pending_hi = reinterpret_cast<unsigned char*>(buf + (sb.R + 1) * sb.W);
     pending_bytes = nb;
-    R = sb.R;
-    W = sb.W;
+  }
+  // Edge rows from registers (see ClusterComm::put_edge): into this CTA's slots of the next set.
+  __device__ void begin_edges() { hset ^= 1; }
+  template <class T>
+  __device__ void put_edge(T*, int lr, int col, const T (&v)[4], const Slab& sb) {
+    unsigned char* out = reinterpret_cast<unsigned char*>(P.g_halo) + halo_slot(hset, (int)blockIdx.x);
+    if (lr == 0) {
+      T* d = reinterpret_cast<T*>(out) + col;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) d[j] = v[j];
+    }
+    if (lr == sb.R - 1) {
+      T* d = reinterpret_cast<T*>(out + P.g_halo_row_bytes) + col;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) d[j] = v[j];
+    }
+    __threadfence();                                // each writer orders its own stores
+  }
+  template <class T>
+  __device__ void end_edges(T* edge, const Slab& sb) {
+    pending_lo = reinterpret_cast<unsigned char*>(edge);
+    pending_hi = reinterpret_cast<unsigned char*>(edge + sb.W);
+    pending_bytes = sb.W * (int)sizeof(T);
   }
   // After a barrier: the neighbours' last / first rows into the local halo rows -1 and R.
   __device__ void pull_halos() {
-    if (!pending) return;
+    if (!pending_lo) return;
     const unsigned char* hb = reinterpret_cast<const unsigned char*>(P.g_halo);
     const size_t rb = P.g_halo_row_bytes;
     const int n16 = pending_bytes / 16;
-    uint4* lo = reinterpret_cast<uint4*>(pending);                                    // row -1
-    uint4* hi = reinterpret_cast<uint4*>(pending + (size_t)(R + 1) * pending_bytes);  // row R
+    uint4* lo = reinterpret_cast<uint4*>(pending_lo);   // row -1
+    uint4* hi = reinterpret_cast<uint4*>(pending_hi);   // row R
     const int r = rank(), b = (int)blockIdx.x;
     if (r > 0) {
       const uint4* src = reinterpret_cast<const uint4*>(hb + halo_slot(hset, b - 1) + rb);
@@ -227,7 +268,7 @@ struct GridComm {
       const uint4* src = reinterpret_cast<const uint4*>(hb + halo_slot(hset, b + 1));
       for (int i = threadIdx.x; i < n16; i += blockDim.x) hi[i] = __ldcg(src + i);
     }
-    pending = nullptr;
+    pending_lo = pending_hi = nullptr;
     __syncthreads();
   }
 

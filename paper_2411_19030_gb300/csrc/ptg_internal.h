@@ -102,6 +102,8 @@ struct StepParams {
   int tl_naj;                // aggregate rows reserved per CTA (0: two-level disabled for this launch)
   int tl_vc;                 // 1: V(1,1) two-grid cycle with damped-Jacobi smoothing; 0: additive D^-1 + P Ac^-1 P^T
   float tl_omega;            // damping of the V-cycle's Jacobi smoother
+  int tl_nu;                 // V-cycle smoothing: <= 1 one global Jacobi step before and after; k >= 2 k
+                             // slab-local steps before and after
   // one system over a whole cooperative grid (GridComm): global scratch of the op
   int wide;                  // 1: launched as stepper_wide_kernel, groups of cs CTAs
   int wide_tasks;            // tasks of a grid-wide launch (group g runs g, g + groups, ...)
@@ -152,7 +154,7 @@ inline __host__ __device__ int coarse_row_stride(int nax) { return (nax + 3) / 4
 // halo rows, the halo rows of q and r in the CG precision (real_bytes), and FP32 element
 // weights where the CG runs in FP64 (the FP32 CG has them already).
 inline size_t twolevel_smem_bytes(int W, int rmax, int cs, int nax, int nay, int naj, bool slots = true,
-                                  bool vc = false, int real_bytes = 4) {
+                                  bool vc = false, int real_bytes = 4, int nu = 1) {
   const size_t naxp = (size_t)coarse_row_stride(nax), ncp = naxp * nay;
   const size_t G = (size_t)(W / kGroup);
   const size_t groups = (size_t)rmax * G;
@@ -164,10 +166,10 @@ inline size_t twolevel_smem_bytes(int W, int rmax, int cs, int nax, int nay, int
   b += ncp * 4;                             // their sum over the covering ranks
   b += (size_t)naj * naxp * 4;              // coarse correction of the CTA's aggregates
   if (vc) {
-    b += halo * real_bytes;                 // q's owned edge rows out, the neighbours' in
-    b += 2 * (size_t)W * real_bytes;        // r on the two halo rows
-    b += 3 * halo * 4;                      // smoother iterates y, u and w D^-1
+    b += 4 * (size_t)W * real_bytes;        // q and r on the two halo rows
+    b += 2 * halo * 4;                      // the smoother iterate (y, then u) and omega D^-1
     if (real_bytes == 8) b += 3 * elems * 4;  // FP32 (D, S, T) element weights
+    if (nu >= 2) b += 2 * halo * 4;         // the slab-local smoother's two iterates
   }
   b += groups * 4;                          // group sums of the restricted vector
   b += (vc ? groups + 2 * G : groups) * 4;  // aggregate of every group (V-cycle: halo rows too)
@@ -197,6 +199,7 @@ struct Plan {
   size_t smem = 0;
   int max_active_clusters = 0;
   bool twolevel = false;     // coarse kinds: two-level preconditioner (its shared memory is in smem)
+  bool vc = false;           // ... in the V(1,1) cycle form (else additive)
   bool wide = false;         // one task over a cooperative grid of cs CTAs (GridComm), no clusters
 };
 

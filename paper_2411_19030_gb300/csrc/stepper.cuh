@@ -170,11 +170,12 @@ struct Stepper {
   // V(1,1) two-grid cycle (P.tl_vc), see vcycle; aj0 / naj then cover the halo rows too
   bool vc = false;
   int ajo0 = 0, najo = 0;    // aggregate rows of the owned rows (the restriction's partials)
-  Real* vq = nullptr;        // rows -1..R: q's first / last owned rows out, the neighbours' in
+  Real* vqh = nullptr;       // q on the halo rows -1 and R (the neighbours' edge rows), [2][W]
   Real* vrh = nullptr;       // r on the halo rows -1 and R, [2][W]
-  float* vy = nullptr;       // y = S r, rows -1..R
-  float* vu = nullptr;       // u = y + P ec, rows -1..R
+  float* vy = nullptr;       // y = S r, then u = y + P ec, rows -1..R
   float* vsd = nullptr;      // S = omega D^-1, rows -1..R (0 off the unknowns)
+  float* ve0 = nullptr;      // slab-local smoothing (P.tl_nu >= 2): ping-pong iterates, rows -1..R,
+  float* ve1 = nullptr;      // halo rows kept at zero
 
   __device__ Stepper(const StepParams& P_, Comm& comm_, unsigned char* dyn) : P(P_), comm(comm_) {
     sb.nx = P.nx;
@@ -223,11 +224,14 @@ struct Stepper {
           // every array a multiple of 4 words, so each starts 16-byte aligned
           constexpr int rw = (int)(sizeof(Real) / 4);
           float* v0 = t;
-          vq = reinterpret_cast<Real*>(t) + kSlack;  t += halo * rw;
-          vrh = reinterpret_cast<Real*>(t);          t += 2 * W * rw;
+          vqh = reinterpret_cast<Real*>(t);  t += 2 * W * rw;
+          vrh = reinterpret_cast<Real*>(t);  t += 2 * W * rw;
           vy = t + kSlack;   t += halo;
-          vu = t + kSlack;   t += halo;
           vsd = t + kSlack;  t += halo;
+          if (P.tl_nu >= 2) {
+            ve0 = t + kSlack;  t += halo;
+            ve1 = t + kSlack;  t += halo;
+          }
           if constexpr (!kMixed) {
             wd = t + kSlack;
             ws = t + elems + kSlack;
@@ -609,11 +613,26 @@ struct Stepper {
     return rz;
   }
 
+  // The owned edge rows (0 and R-1) of a per-thread vector into the neighbours' two-row buffer
+  // `edge` ([0]: the row below the slab, [1]: the row above), straight from registers;
+  // visible after the next barrier.
+  __device__ void put_edges(Real* edge, const Real (&v)[NG][4]) {
+    comm.begin_edges();
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+      if (l0 < 0) continue;
+      const int lr = l0 / sb.W - 1;
+      if (lr == 0 || lr == sb.R - 1) comm.put_edge(edge, lr, l0 - (lr + 1) * sb.W, v[k], sb);
+    }
+    comm.end_edges(edge, sb);
+  }
+
   // offset in a rows -1..R buffer of entry i of the two halo rows ([0, W): row -1, [W, 2W): row R)
   __device__ __forceinline__ int halo_offset(int i) const { return i < sb.W ? i : (sb.R + 1) * sb.W + (i - sb.W); }
 
   // V(1,1) two-grid cycle z = M^-1 r in FP32 over the owned rows and the two halo rows:
-  //   y = S r,  ec = Ac^-1 P^T (r - A y),  u = y + P ec,  z = u + S (r - A u),
+  //   y = S r,  ec = Ac^-1 P^T (r - A y),  u = y + P ec (in place of y),  z = u + S (r - A u),
   // with the damped-Jacobi smoother S = omega D^-1 and A applied with the FP32 element weights,
   // so that I - M^-1 A = (I - S A)(I - P Ac^-1 P^T A)(I - S A) (symmetric).  The halo rows of r
   // (vrh) follow the owners' CG recurrence bit for bit, and every CTA computes ec for the
@@ -622,12 +641,15 @@ struct Stepper {
   // (the restricted partials).  z goes to zbuf on the owned rows; returns the local (r, z).
   __device__ Real vcycle(const Real (&r)[NG][4]) {
     const int W = sb.W, G = sb.G;
+    float rf[NG][4];   // r in FP32, converted once (FP64 conversions run on the FP64 pipe)
 #pragma unroll
     for (int k = 0; k < NG; ++k) {
       const int l0 = loc0[k];
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) rf[k][j] = (float)r[k][j];
       if (l0 < 0) continue;
 #pragma unroll
-      for (int j = 0; j < kGroup; ++j) vy[l0 + j] = vsd[l0 + j] * (float)r[k][j];
+      for (int j = 0; j < kGroup; ++j) vy[l0 + j] = vsd[l0 + j] * rf[k][j];
     }
     for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) {
       const int l = halo_offset(i);
@@ -644,7 +666,7 @@ struct Stepper {
       float t[4];
       stencil_elem32(vy, wd, ws, wt, l0, W, t);
 #pragma unroll
-      for (int j = 0; j < kGroup; ++j) w[k][j] = unknown(k, j) ? (float)r[k][j] - t[j] : 0.f;
+      for (int j = 0; j < kGroup; ++j) w[k][j] = unknown(k, j) ? rf[k][j] - t[j] : 0.f;
     }
     coarse_restrict_push(w);
     comm.sync();
@@ -654,7 +676,7 @@ struct Stepper {
       const float e = a >= 0 ? tl_ec[a] : 0.f;
       const int l = (gi / G) * W + kGroup * (gi % G);   // row gi / G - 1, group gi % G
 #pragma unroll
-      for (int j = 0; j < kGroup; ++j) vu[l + j] = vsd[l + j] != 0.f ? vy[l + j] + e : 0.f;
+      for (int j = 0; j < kGroup; ++j) vy[l + j] = vsd[l + j] != 0.f ? vy[l + j] + e : 0.f;
     }
     __syncthreads();
     Real rz = Real(0);
@@ -663,10 +685,113 @@ struct Stepper {
       const int l0 = loc0[k];
       if (l0 < 0) continue;
       float t[4];
-      stencil_elem32(vu, wd, ws, wt, l0, W, t);
+      stencil_elem32(vy, wd, ws, wt, l0, W, t);
 #pragma unroll
       for (int j = 0; j < kGroup; ++j) {
-        const float z = unknown(k, j) ? fmaf(vsd[l0 + j], (float)r[k][j] - t[j], vu[l0 + j]) : 0.f;
+        const float z = unknown(k, j) ? fmaf(vsd[l0 + j], rf[k][j] - t[j], vy[l0 + j]) : 0.f;
+        zbuf[l0 + j] = (Real)z;
+        rz = fma(r[k][j], (Real)z, rz);
+      }
+    }
+    return rz;
+  }
+
+  // Slab-local damped-Jacobi smoothing of A e = s: P.tl_nu steps from e = 0 over the owned rows
+  // with the halo rows held at zero (the slab's diagonal block A_s of A), in FP32, the iterate
+  // ping-ponging between two buffers; e returned in registers.  The result is a fixed polynomial
+  // in D^-1 A_s times D^-1, a symmetric operator, so the cycle that uses it stays symmetric; it
+  // needs no communication.
+  __device__ void smooth_local(const float (&s)[NG][4], float (&e)[NG][4]) {
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) e[k][j] = l0 >= 0 ? vsd[l0 + j] * s[k][j] : 0.f;
+    }
+    for (int it = 1; it < P.tl_nu; ++it) {
+      float* buf = (it & 1) ? ve0 : ve1;
+#pragma unroll
+      for (int k = 0; k < NG; ++k) {
+        const int l0 = loc0[k];
+        if (l0 < 0) continue;
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j) buf[l0 + j] = e[k][j];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < NG; ++k) {
+        const int l0 = loc0[k];
+        if (l0 < 0) continue;
+        float t[4];
+        stencil_elem32(buf, wd, ws, wt, l0, sb.W, t);
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j) e[k][j] = fmaf(vsd[l0 + j], s[k][j] - t[j], e[k][j]);
+      }
+    }
+  }
+
+  // Two-grid cycle with the slab-local smoother S_s of smooth_local before and after the coarse
+  // correction: e1 = S_s r;  ec = Ac^-1 P^T (r - A e1);  u = e1 + P ec;  z = u + S_s (r - A u),
+  // so that I - M^-1 A = (I - S_s A)(I - P Ac^-1 P^T A)(I - S_s A).  e1's edge rows are
+  // exchanged (a cluster barrier) before the residual; u on the halo rows is then the owner's
+  // value (e1 from the owner, ec computed from the same restricted vector).  Two cluster
+  // barriers.  z goes to zbuf on the owned rows; returns the local (r, z).
+  __device__ Real vcycle_local(const Real (&r)[NG][4]) {
+    const int W = sb.W, G = sb.G;
+    float rf[NG][4], e[NG][4], w[NG][4];
+#pragma unroll
+    for (int k = 0; k < NG; ++k)
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) rf[k][j] = (float)r[k][j];
+    smooth_local(rf, e);
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+      if (l0 < 0) continue;
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) vy[l0 + j] = e[k][j];
+    }
+    exchange(vy);
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) w[k][j] = 0.f;
+      if (l0 < 0) continue;
+      float t[4];
+      stencil_elem32(vy, wd, ws, wt, l0, W, t);
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) w[k][j] = unknown(k, j) ? rf[k][j] - t[j] : 0.f;
+    }
+    coarse_restrict_push(w);
+    comm.sync();
+    coarse_gather(true, 0.f);
+    for (int gi = threadIdx.x; gi < (sb.R + 2) * G; gi += blockDim.x) {
+      const int a = tl_gagg[gi];
+      const float ea = a >= 0 ? tl_ec[a] : 0.f;
+      const int l = (gi / G) * W + kGroup * (gi % G);   // row gi / G - 1, group gi % G
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) vy[l + j] = vsd[l + j] != 0.f ? vy[l + j] + ea : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+      if (l0 < 0) continue;
+      float t[4];
+      stencil_elem32(vy, wd, ws, wt, l0, W, t);
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) w[k][j] = unknown(k, j) ? rf[k][j] - t[j] : 0.f;
+    }
+    smooth_local(w, e);
+    Real rz = Real(0);
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+      if (l0 < 0) continue;
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) {
+        const float z = vy[l0 + j] + e[k][j];
         zbuf[l0 + j] = (Real)z;
         rz = fma(r[k][j], (Real)z, rz);
       }
@@ -696,17 +821,12 @@ struct Stepper {
           v[0] = fma(r[k][j], z, v[0]);
         }
       }
-      if (vc) {
+      if (vc && P.tl_nu >= 2) {
+        v[0] = vcycle_local(r);
+      } else if (vc) {
         // r on the halo rows from the neighbours' owned edge rows
-#pragma unroll
-        for (int k = 0; k < NG; ++k) {
-          const int l0 = loc0[k];
-          if (l0 < 0) continue;
-#pragma unroll
-          for (int j = 0; j < kGroup; ++j) vq[l0 + j] = r[k][j];
-        }
-        exchange(vq);
-        for (int i = threadIdx.x; i < 2 * sb.W; i += blockDim.x) vrh[i] = vq[halo_offset(i)];
+        put_edges(vrh, r);
+        comm.sync();
         v[0] = vcycle(r);
       } else if (tl) {
         coarse_restrict_push(r);
@@ -740,21 +860,11 @@ struct Stepper {
           pq[0] = fma(p[k][j], q[k][j], pq[0]);
         }
       }
-      if (vc) {
+      if (vc && P.tl_nu < 2) {
         // q's owned edge rows to the neighbours, whose copies of r on their halo rows follow
         // the same recurrence (visible after the all-reduce's barrier)
-#pragma unroll
-        for (int k = 0; k < NG; ++k) {
-          const int l0 = loc0[k];
-          if (l0 < 0) continue;
-          const int lr = l0 / sb.W - 1;
-          if (lr != 0 && lr != sb.R - 1) continue;
-#pragma unroll
-          for (int j = 0; j < kGroup; ++j) vq[l0 + j] = q[k][j];
-        }
-        __syncthreads();
-        comm.push_halos(vq, sb);
-      } else if (tl) {
+        put_edges(vqh, q);
+      } else if (tl && !vc) {
         coarse_restrict_push(q);             // visible after the all-reduce's cluster barrier
       }
       const Real rz_c = rz;
@@ -779,8 +889,10 @@ struct Stepper {
           }
         }
       }
-      if (vc) {
-        for (int i = threadIdx.x; i < 2 * sb.W; i += blockDim.x) vrh[i] = fma(-alpha, vq[halo_offset(i)], vrh[i]);
+      if (vc && P.tl_nu >= 2) {
+        v[0] = vcycle_local(r);
+      } else if (vc) {
+        for (int i = threadIdx.x; i < 2 * sb.W; i += blockDim.x) vrh[i] = fma(-alpha, vqh[i], vrh[i]);
         v[0] = vcycle(r);
       } else if (tl) {
         v[0] = prolong_precondition(r);

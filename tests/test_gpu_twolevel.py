@@ -39,8 +39,11 @@ def case():
 
 
 def run_pass(case, twolevel, cs=0, precision="fp32_refine"):
+    """twolevel: "none", "additive", "vcycle" or "vcycle<k>" (k smoothing steps)."""
     prob, rho, U_old, V_old, _ = case
-    op = gpu_operator(prob, precision, rtol=1e-13 if precision == "fp64" else 1e-10, twolevel=twolevel)
+    smooth = int(twolevel[6:]) if twolevel.startswith("vcycle") and len(twolevel) > 6 else 0
+    op = gpu_operator(prob, precision, rtol=1e-13 if precision == "fp64" else 1e-10,
+                      twolevel=twolevel[:6] if smooth else twolevel, smooth_steps=smooth)
     if cs:
         for kind in COARSE_KINDS:
             op.set_plan(kind, cs, 1 if cs >= 8 else 2)
@@ -65,7 +68,7 @@ def check(case, op, buf, Theta, grad, tol_t=MIXED_T_TOL, tol_g=MIXED_G_TOL):
     assert op.stats()["status"] == 0
 
 
-MODES = ["additive", "vcycle"]
+MODES = ["additive", "vcycle1", "vcycle3"]
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -113,7 +116,8 @@ def test_vcycle_needs_fewer_iterations_than_additive(case, precision):
             check(case, *runs[m])
     k = {m: runs[m][0].stats()["by_kind"] for m in MODES}
     for name in ("coarse_primal", "correct_primal", "coarse_adjoint", "correct_adjoint"):
-        assert k["vcycle"][name]["cg_iters"] < 0.75 * k["additive"][name]["cg_iters"], (name, k)
+        assert k["vcycle1"][name]["cg_iters"] < 0.75 * k["additive"][name]["cg_iters"], (name, k)
+        assert k["vcycle3"][name]["cg_iters"] < 0.9 * k["vcycle1"][name]["cg_iters"], (name, k)
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -129,8 +133,10 @@ def test_twolevel_helps_on_high_contrast_designs(design, precision, mode):
     else:
         prob, rho = make_problem(n, Nt=Nt, Ntau=16, dt=1 / Nt), W.rho_uniform(n, n, 1, 0.2, 0.8)
     its = {}
+    smooth = int(mode[6:]) if mode.startswith("vcycle") else 0
     for tl in (mode, "none"):
-        op = gpu_operator(prob, precision, rtol=1e-10, twolevel=tl)
+        op = gpu_operator(prob, precision, rtol=1e-10, twolevel=tl[:6] if tl.startswith("vcycle") else tl,
+                          smooth_steps=smooth if tl == mode else 0)
         buf = PassBuffers(op)
         op.assemble(dev(rho))
         parareal_pass(op, buf, 1)

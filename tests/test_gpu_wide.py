@@ -53,7 +53,7 @@ def test_wide_sequential_pass_matches_oracle_and_cluster_path(name):
     assert_close("wide vs cluster", out[True], out[False], 1e-11)
 
 
-@pytest.mark.parametrize("mode", ["additive", "vcycle"])
+@pytest.mark.parametrize("mode", ["additive", "vcycle1", "vcycle3"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
 @pytest.mark.parametrize("name", ["square64", "tall"])
 def test_wide_correction_sweeps_match_oracle(name, precision, mode):
@@ -62,7 +62,9 @@ def test_wide_correction_sweeps_match_oracle(name, precision, mode):
     U_old, V_old, _ = coarse_states_from_sequential(OracleOp(prob, rho_old))
     ref = o_oneshot(OracleOp(prob, rho), U_old, V_old)
     tol_t, tol_g = (FP64_TOL, FP64_TOL) if precision == "fp64" else (MIXED_T_TOL, MIXED_G_TOL)
-    op = gpu_operator(prob, precision, rtol=1e-13 if precision == "fp64" else 1e-10, grid_wide=2, twolevel=mode)
+    op = gpu_operator(prob, precision, rtol=1e-13 if precision == "fp64" else 1e-10, grid_wide=2,
+                      twolevel=mode[:6] if mode.startswith("vcycle") else mode,
+                      smooth_steps=int(mode[6:]) if mode.startswith("vcycle") else 0)
     assert op.plan(2, 1)["cs"] > 16
     buf = PassBuffers(op)
     buf.U_T.copy_(dev(U_old[0])); buf.U_th.copy_(dev(U_old[1]))
@@ -91,7 +93,7 @@ def test_wide_path_is_deterministic():
     assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
 
 
-@pytest.mark.parametrize("mode", ["additive", "vcycle"])
+@pytest.mark.parametrize("mode", ["additive", "vcycle1", "vcycle3"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
 @pytest.mark.parametrize("name", ["square64", "ragged_table1", "tall"])
 def test_grouped_launches_for_every_kind_match_oracle(name, precision, mode):
@@ -102,7 +104,9 @@ def test_grouped_launches_for_every_kind_match_oracle(name, precision, mode):
     U_old, V_old, _ = coarse_states_from_sequential(OracleOp(prob, rho_old))
     ref = o_oneshot(OracleOp(prob, rho), U_old, V_old)
     tol_t, tol_g = (FP64_TOL, FP64_TOL) if precision == "fp64" else (MIXED_T_TOL, MIXED_G_TOL)
-    op = gpu_operator(prob, precision, rtol=1e-13 if precision == "fp64" else 1e-10, grid_wide=2, twolevel=mode)
+    op = gpu_operator(prob, precision, rtol=1e-13 if precision == "fp64" else 1e-10, grid_wide=2,
+                      twolevel=mode[:6] if mode.startswith("vcycle") else mode,
+                      smooth_steps=int(mode[6:]) if mode.startswith("vcycle") else 0)
     buf = PassBuffers(op)
     buf.U_T.copy_(dev(U_old[0])); buf.U_th.copy_(dev(U_old[1]))
     buf.V_l.copy_(dev(V_old[0])); buf.V_g.copy_(dev(V_old[1]))
