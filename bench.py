@@ -377,9 +377,9 @@ def run_gpu(args):
 
 # DRAM bytes per launch (read + write) from the committed ncu captures of the 128x128 pass in
 # the default precision (profiles/); a kernel changed since has no entry.
-NCU_TRAFFIC_BYTES = {"fine_primal": 6.586112e6 + 80.368640e6, "coarse_primal": 6.463488e6 + 3.840e3,
-                     "correct_primal": 10.891264e6 + 0.0, "fine_adjoint": 146.939136e6 + 0.134400e6,
-                     "coarse_adjoint": 14.757888e6 + 1.536e3, "correct_adjoint": 23.534848e6 + 0.0}
+NCU_TRAFFIC_BYTES = {"fine_primal": 6.485248e6 + 80.445696e6, "coarse_primal": 6.699264e6 + 0.0,
+                     "correct_primal": 11.467776e6 + 0.0, "fine_adjoint": 147.761920e6 + 0.055296e6,
+                     "coarse_adjoint": 15.199744e6 + 0.0, "correct_adjoint": 23.892736e6 + 0.0}
 
 # FP64 peak of the chip (nominal, the GB300 table of the profiling notes: 1.25 TFLOP/s) and the
 # FLOPs of one FP64 CG iteration per unknown: the 9-point stencil (9 FMA), the p, q, d, r
