@@ -22,6 +22,8 @@ Modules
 ``design``     Sec. 2.1 and 3: the density filter, the threshold projection, the area
                constraint, their chain rule, and the Method of Moving Asymptotes (Svanberg's
                1987 method, one constraint) of the design update in Alg. 3.
+``coarse_mesh`` Sec. 7.3 (future work): coarse propagators on the mesh of spacing 2h
+               (averaged design, injection and bilinear interpolation between the meshes).
 
 Pins (``tests/test_oracle_*.py``, run with ``-m "not gpu"``): the separable-eigenmode
 closed form, the discrete energy balance, the dense all-at-once solve, central
@@ -33,7 +35,10 @@ grad Theta = Theta^(1-p)/p grad Theta~; for PLT (G = 0, Sec. 7), its fixed point
 exactness after N_tau iterations; for the design update, the filter's averaging and its
 reproduction of affine fields, the projection's fixed points and derivative, central
 differences through filter, projection and objective, and MMA on problems with closed-form
-optima.
+optima; for the coarse-mesh propagators, bilinear reproduction by the interpolation,
+the restricted load and the Galerkin products against the operators assembled on 2h,
+Galerkin orthogonality of a coarse step, the one-shot fixed point, exactness after N_tau
+iterations, and second-order agreement with the fine-mesh coarse step.
 The one-shot estimate for a design that differs from the warm-start design has
 no closed form: beyond the fixed point it is "parity unpinned" (it is the literal
 algorithm, checked only for consistency with the pinned pieces it is made of).

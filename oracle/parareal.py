@@ -100,10 +100,19 @@ def coarse_states_from_sequential(op: Operator, seq: dict | None = None):
 
 # ------------------------------------------------------------------ Parareal iterations
 
-def primal_iteration(op: Operator, U_old, plt: bool = False):
+def _coarse_fns(op: Operator, coarse):
+    """The coarse propagators: the fine-mesh G of Sec. 4.4, or those of a coarse-mesh object
+    (``oracle.coarse_mesh.CoarseMesh``, Sec. 7.3 future work)."""
+    if coarse is None:
+        return (lambda s, T, th: G_pri(op, s, T, th)), (lambda s, l, g, Th, Tt: G_adj(op, s, l, g, Th, Tt))
+    return coarse.G_pri, coarse.G_adj
+
+
+def primal_iteration(op: Operator, U_old, plt: bool = False, coarse=None):
     """One modified forward Parareal iteration (Eq. 4.9 with the history of Sec. 4.3)
     from the guess U_old = (T[Ntau+1, Nn], theta[Ntau+1]).  With plt=True the coarse
-    propagator is identically zero (Eq. 7.1-7.2)."""
+    propagator is identically zero (Eq. 7.1-7.2); ``coarse`` replaces G (coarse mesh)."""
+    Gp, _ = _coarse_fns(op, coarse)
     prob = op.prob
     M, Ntau = prob.M, prob.Ntau
     U_T_old, U_th_old = U_old
@@ -114,7 +123,7 @@ def primal_iteration(op: Operator, U_old, plt: bool = False):
         F_T[s], F_th[s], inter = F_pri(op, s, U_T_old[s], U_th_old[s])
         T_hist[M * s + 1: M * (s + 1) + 1] = inter
         if not plt:
-            G_T[s], G_th[s] = G_pri(op, s, U_T_old[s], U_th_old[s])
+            G_T[s], G_th[s] = Gp(s, U_T_old[s], U_th_old[s])
     U_T = np.zeros_like(U_T_old); U_th = np.zeros_like(U_th_old)
     U_T[0], U_th[0] = U_T_old[0], U_th_old[0]             # u_0^k = u_0
     T_hist[0] = U_T[0]
@@ -122,7 +131,7 @@ def primal_iteration(op: Operator, U_old, plt: bool = False):
         if plt:
             gT, gth = np.zeros(prob.Nn), 0.0
         else:
-            gT, gth = G_pri(op, s, U_T[s], U_th[s])
+            gT, gth = Gp(s, U_T[s], U_th[s])
         U_T[s + 1] = gT + F_T[s] - G_T[s]
         U_th[s + 1] = gth + F_th[s] - G_th[s]
         T_hist[M * (s + 1)] = U_T[s + 1]
@@ -130,9 +139,10 @@ def primal_iteration(op: Operator, U_old, plt: bool = False):
                 F=(F_T, F_th), G_old=(G_T, G_th))
 
 
-def adjoint_iteration(op: Operator, V_old, T_hist: np.ndarray, Theta: float, plt: bool = False):
+def adjoint_iteration(op: Operator, V_old, T_hist: np.ndarray, Theta: float, plt: bool = False, coarse=None):
     """One reverse vanilla Parareal iteration (Eq. 4.10) from the guess V_old =
     (lam[Ntau+1, Nn], g[Ntau+1, Ne]); v_Ntau = 0 always."""
+    _, Ga = _coarse_fns(op, coarse)
     prob = op.prob
     Ntau = prob.Ntau
     V_lam_old, V_g_old = V_old
@@ -141,24 +151,25 @@ def adjoint_iteration(op: Operator, V_old, T_hist: np.ndarray, Theta: float, plt
     for s in range(Ntau):                                  # parallel part
         F_l[s], F_g[s] = F_adj(op, s, V_lam_old[s + 1], V_g_old[s + 1], T_hist, Theta)
         if not plt:
-            G_l[s], G_g[s] = G_adj(op, s, V_lam_old[s + 1], V_g_old[s + 1], T_hist, Theta)
+            G_l[s], G_g[s] = Ga(s, V_lam_old[s + 1], V_g_old[s + 1], T_hist, Theta)
     V_lam = np.zeros_like(V_lam_old); V_g = np.zeros_like(V_g_old)
     for s in range(Ntau - 1, -1, -1):                      # sequential correction, reversed
         if plt:
             gl, gg = np.zeros(prob.Nn), np.zeros(prob.Ne)
         else:
-            gl, gg = G_adj(op, s, V_lam[s + 1], V_g[s + 1], T_hist, Theta)
+            gl, gg = Ga(s, V_lam[s + 1], V_g[s + 1], T_hist, Theta)
         V_lam[s] = gl + F_l[s] - G_l[s]
         V_g[s] = gg + F_g[s] - G_g[s]
     return dict(V=(V_lam, V_g), grad=V_g[0].copy(), F=(F_l, F_g), G_old=(G_l, G_g))
 
 
-def oneshot_pass(op: Operator, U_old, V_old, plt: bool = False) -> dict:
+def oneshot_pass(op: Operator, U_old, V_old, plt: bool = False, coarse=None) -> dict:
     """The iteration body of Alg. 3: one modified forward Parareal iteration and one reverse
     vanilla Parareal iteration, each warm-started from the previous design iteration's
-    coarse states; Theta = theta_Nt and grad = g_1 (Sec. 4.4, four-step procedure)."""
-    pri = primal_iteration(op, U_old, plt=plt)
-    adj = adjoint_iteration(op, V_old, pri["T_hist"], pri["Theta"], plt=plt)
+    coarse states; Theta = theta_Nt and grad = g_1 (Sec. 4.4, four-step procedure).
+    ``coarse``: coarse propagators on a coarsened mesh (``oracle.coarse_mesh.CoarseMesh``)."""
+    pri = primal_iteration(op, U_old, plt=plt, coarse=coarse)
+    adj = adjoint_iteration(op, V_old, pri["T_hist"], pri["Theta"], plt=plt, coarse=coarse)
     out = dict(pri)
     out.update(V=adj["V"], grad=adj["grad"], F_adj=adj["F"], G_adj_old=adj["G_old"])
     out["F_pri"] = pri["F"]
@@ -166,40 +177,42 @@ def oneshot_pass(op: Operator, U_old, V_old, plt: bool = False) -> dict:
     return out
 
 
-def initial_guess_primal(op: Operator):
+def initial_guess_primal(op: Operator, coarse=None):
     """u_{n+1}^0 = G_pri(u_n^0) from u_0 (Sec. 5.2)."""
+    Gp, _ = _coarse_fns(op, coarse)
     prob = op.prob
     U_T = np.zeros((prob.Ntau + 1, prob.Nn)); U_th = np.zeros(prob.Ntau + 1)
     if prob.T0 is not None:
         U_T[0] = prob.T0
     for s in range(prob.Ntau):
-        U_T[s + 1], U_th[s + 1] = G_pri(op, s, U_T[s], U_th[s])
+        U_T[s + 1], U_th[s + 1] = Gp(s, U_T[s], U_th[s])
     return U_T, U_th
 
 
-def initial_guess_adjoint(op: Operator, T_hist: np.ndarray, Theta: float):
+def initial_guess_adjoint(op: Operator, T_hist: np.ndarray, Theta: float, coarse=None):
     """v_{n-1}^0 = G_adj(v_n^0) from v_Ntau = 0 (Sec. 5.2)."""
+    _, Ga = _coarse_fns(op, coarse)
     prob = op.prob
     V_lam = np.zeros((prob.Ntau + 1, prob.Nn)); V_g = np.zeros((prob.Ntau + 1, prob.Ne))
     for s in range(prob.Ntau - 1, -1, -1):
-        V_lam[s], V_g[s] = G_adj(op, s, V_lam[s + 1], V_g[s + 1], T_hist, Theta)
+        V_lam[s], V_g[s] = Ga(s, V_lam[s + 1], V_g[s + 1], T_hist, Theta)
     return V_lam, V_g
 
 
-def parareal(op: Operator, k: int, plt: bool = False) -> dict:
+def parareal(op: Operator, k: int, plt: bool = False, coarse=None) -> dict:
     """k-iteration Parareal of the preliminary tests (Sec. 5.2): coarse initial guess,
     k modified forward iterations, then a coarse adjoint initial guess from the final
     history and k reverse iterations."""
-    U = initial_guess_primal(op)
+    U = initial_guess_primal(op, coarse=coarse)
     pri = None
     for _ in range(k):
-        pri = primal_iteration(op, U, plt=plt)
+        pri = primal_iteration(op, U, plt=plt, coarse=coarse)
         U = pri["U"]
     if pri is None:
         raise ValueError("k must be >= 1")
-    V = initial_guess_adjoint(op, pri["T_hist"], pri["Theta"])
+    V = initial_guess_adjoint(op, pri["T_hist"], pri["Theta"], coarse=coarse)
     adj = None
     for _ in range(k):
-        adj = adjoint_iteration(op, V, pri["T_hist"], pri["Theta"], plt=plt)
+        adj = adjoint_iteration(op, V, pri["T_hist"], pri["Theta"], plt=plt, coarse=coarse)
         V = adj["V"]
     return dict(U=U, T_hist=pri["T_hist"], Theta=pri["Theta"], V=V, grad=adj["grad"])
