@@ -310,6 +310,38 @@ def run_gpu(args):
                        "T_hist_rel_max": relmax(v_buf.T_hist, f64_T), "grad_rel_max": relmax(gv, g64)}
             del v_buf, f64_buf
 
+        # Sec. 7.3 future work: the same pass with the coarse propagators on the 2h mesh, timed
+        # like the main steps, with the error of its one-shot estimate against the sequential result
+        c_op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink,
+                        solve=SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=2000,
+                                          refine_max=8, twolevel=args.twolevel, smooth_steps=args.smooth,
+                                          coarse_mesh=True), device=local)
+        c_buf = PassBuffers(c_op)
+        for a_, b_ in ((c_buf.U_T, buf.U_T), (c_buf.U_th, buf.U_th), (c_buf.V_l, buf.V_l), (c_buf.V_g, buf.V_g)):
+            a_.copy_(b_)
+        c_ms = []
+        for i in range(args.warmup + args.steps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            c_op.assemble(rho)
+            Thc, gc = oneshot_pass(c_op, c_buf)
+            b.record(stream)
+            b.synchronize()
+            if i >= args.warmup:
+                c_ms.append(a.elapsed_time(b))
+        cm_ms = slowest_rank_ms(float(np.mean(c_ms)), device)
+        cst = c_op.stats()
+        coarse_mesh = {"what": "Sec. 7.3 future work: G_pri and G_adj on the 2h mesh (64x64 elements)",
+                       "ms_per_step": cm_ms, "value": job_throughput(dof_steps, world, cm_ms), "unit": UNIT,
+                       "speedup_vs_sequential_fp64": seq_ms / cm_ms, "status": cst["status"],
+                       "Theta_rel_vs_sequential": abs(float(Thc.item()) - float(Theta_seq.item()))
+                       / abs(float(Theta_seq.item())),
+                       "grad_rel_l2_vs_sequential": float(torch.linalg.norm(gc - grad_seq) / torch.linalg.norm(grad_seq)),
+                       "cg_per_solve": {k: round(v["cg_iters"] / max(1, v["solves"]), 2)
+                                        for k, v in cst["by_kind"].items() if v["solves"]}}
+        del c_buf, c_op
+
         # Sec. 7.3 bottleneck probe: the same pass with the coarse propagators identically zero
         # (G_pri = G_adj = 0, the corrections copy F), timed like the main steps
         g0_ms = []
@@ -330,7 +362,7 @@ def run_gpu(args):
                  "paper_context": "MATLAB on 32 CPU threads: 3.81x (one-shot) vs 10.8x (G = 0) over its sequential run"}
     else:
         e2e = seq_ms = None
-        seq_stats, prec, probe, variant = {}, {}, None, None
+        seq_stats, prec, probe, variant, coarse_mesh = {}, {}, None, None, None
         err_theta = err_grad = None
 
     roof = roofline(kind_ms, stats, w, N_free, args)
@@ -358,6 +390,7 @@ def run_gpu(args):
                                                 "sequential result of the current design"},
         "accuracy_mixed_vs_fp64_oneshot": prec,
         "bottleneck_probe": probe,
+        "coarse_mesh_variant": coarse_mesh,
         "precision_variant": variant,
         "e2e": None if e2e is None else {"value": world * dof_steps / (e2e * 1e-3), "unit": UNIT, "ms": e2e,
                                          "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": (1 + n * n) * 8},

@@ -124,6 +124,16 @@ typedef struct {
                           1: one damped-Jacobi step on the whole grid; k in 2..16: k damped-Jacobi
                           steps on each CTA's slab alone (the slab's diagonal block of A, no
                           communication).  0: the library's default.  Other values: PTG_EINVAL. */
+    int coarse_mesh;   /* 1: the coarse propagators G_pri and G_adj take their step of dtau on the
+                          mesh of spacing 2h (the remedy for the sequential coarse sweep proposed
+                          as future work in Sec. 7.3): nx/2 x ny/2 elements whose density is the
+                          mean of their four children, states restricted by injection and
+                          prolongated by bilinear interpolation, the adjoint source restricted by
+                          the transpose of the interpolation; theta and g increments of G from the
+                          prolongated state on the fine mesh.  F, the corrections, the history and
+                          every output stay on the fine mesh.  Needs even nx, ny >= 4 (else
+                          PTG_EINVAL); the batch entry points reject such ops.  0: G on the fine
+                          mesh (Sec. 4.4). */
 } ptg_solve;
 
 typedef struct {

@@ -69,6 +69,7 @@ class SolveConfig:
     #                                  0 never, 1 for large grids or when no cluster fits, 2 always
     smooth_steps: int = 0            # V-cycle smoothing: 1 global Jacobi step, k >= 2 slab-local
     #                                  steps, 0 the library default
+    coarse_mesh: bool = False        # coarse propagators on the 2h mesh (Sec. 7.3 future work)
 
 
 class Operator:
@@ -106,7 +107,8 @@ class Operator:
         prec = {"fp64": PTG_FP64, "fp32_refine": PTG_FP32_REFINE,
                 "fp32_refine_all": PTG_FP32_REFINE_ALL}[solve.precision]
         s = _ffi.ptg_solve(prec, solve.rtol, solve.inner_rtol, solve.cg_iters_max, solve.refine_max,
-                           twolevel_code(solve.twolevel), int(solve.grid_wide), int(solve.smooth_steps))
+                           twolevel_code(solve.twolevel), int(solve.grid_wide), int(solve.smooth_steps),
+                           int(solve.coarse_mesh))
         self._dir = np.ascontiguousarray(dirichlet, dtype=np.uint8).reshape(-1)
         if self._dir.size != self.Nn:
             raise ValueError("dirichlet mask must have (nx+1)(ny+1) entries")

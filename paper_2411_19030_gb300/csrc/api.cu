@@ -7,6 +7,7 @@
 #include <new>
 #include <tuple>
 #include <vector>
+#include "mesh.h"
 #include "ptg_internal.h"
 #include "stepper_launch.cuh"
 
@@ -44,6 +45,20 @@ struct ptg_op {
   float* g_tl = nullptr;
   int sens_chunks = 0;
   DevStats* stats = nullptr;
+  // coarse propagators on the mesh of spacing 2h (ptg_solve.coarse_mesh): the op of that mesh
+  // (its coarse kinds run the coarse steps) and the transfer workspace
+  ptg_op* mesh = nullptr;
+  double* mesh_rho = nullptr;    // [NeH] coarse design
+  double* mesh_XH = nullptr;     // [Ntau+1][NnH] coarse states of a correction sweep
+  double* mesh_FH = nullptr;     // [Ntau][NnH] injected F (or the states a coarse sweep starts from)
+  double* mesh_GH = nullptr;     // [Ntau][NnH] injected G_old
+  double* mesh_SH = nullptr;     // [Ntau][NnH] restricted adjoint sources
+  double* mesh_YH = nullptr;     // [Ntau][NnH] results of independent coarse steps
+  double* mesh_zero = nullptr;   // [Ntau+1] zeros (theta and F/G theta slots of the coarse op)
+  double* mesh_aux = nullptr;    // [Ntau+1] theta outputs of the coarse op (not used)
+  double* mesh_pn = nullptr;     // [Ntau][blocks] p-norm partials of the prolongated states
+  double* mesh_lam = nullptr;    // [Ntau][Nn] prolongated adjoint states of G
+  double* mesh_dg = nullptr;     // [Ntau][Ne] g increments of G
   cudaStream_t last_stream = nullptr;
   std::mutex mu;
   std::map<std::tuple<int, int, int>, Plan> plans;   // (precision, kind, ntasks) -> plan
@@ -331,7 +346,8 @@ void base_params(const ptg_op* op, StepParams& P) {
   P.hist_rows = 0;
 }
 
-int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream) {
+int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream, int stats_kind = -1) {
+  P.stats_kind = stats_kind >= 0 ? stats_kind : P.kind;
   Plan plan;
   const int prec = kind_precision(op->sv.precision, P.kind);
   int rc = choose_plan(op, prec, P.kind, ntasks, &plan);
@@ -355,13 +371,185 @@ int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream) {
 
 bool window_covers(int j0, int rows, int lo, int hi) { return lo >= j0 && hi < j0 + rows; }
 
+void ptg_op_free(ptg_op* op);
+
 void free_all(ptg_op* op) {
   void* ptrs[] = {op->k, op->c, op->dk, op->dc, op->wE, op->nodew, op->fload,
                   op->q_elem, op->q_time, op->dirichlet, op->sens_partial, op->scratch, op->stats,
                   op->g_red, op->g_bar, op->g_halo, op->g_tl,
-                  op->tl_Ac, op->tl_band, op->tl_X, op->tl_Ainv};
+                  op->tl_Ac, op->tl_band, op->tl_X, op->tl_Ainv,
+                  op->mesh_rho, op->mesh_XH, op->mesh_FH, op->mesh_GH, op->mesh_SH, op->mesh_YH,
+                  op->mesh_zero, op->mesh_aux, op->mesh_pn, op->mesh_lam, op->mesh_dg};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (op->mesh) ptg_op_free(op->mesh);
+  op->mesh = nullptr;
+}
+
+void ptg_op_free(ptg_op* op) {
+  free_all(op);
+  delete op;
+}
+
+// Launch coarse-kind tasks of the 2h-mesh op on behalf of the fine op: the solver counters
+// and errors go to the fine op's status word under the fine kind they stand for.
+int mesh_run(ptg_op* op, StepParams& P, int ntasks, int stats_kind, cudaStream_t st) {
+  P.stats = op->stats;
+  op->mesh->last_stream = st;
+  return run(op->mesh, P, ntasks, st, stats_kind);
+}
+
+// G_pri / G_adj of every slice on the 2h mesh (Sec. 7.3 future work; the readings are those of
+// the oracle's coarse_mesh module): R the states, one coarse step each on the 2h-mesh op, P
+// the results; theta from the fine-mesh p-norm of P x, g from the fine-mesh sensitivity term of
+// P z (Eq. 4.7).
+int mesh_coarse_sweep(ptg_op* op, int direction, const double* X_field, const double* X_aux, const double* T_hist,
+                      const double* Theta_d, double* G_field, double* G_aux, cudaStream_t st) {
+  ptg_op* H = op->mesh;
+  const int nx = op->g.nx, ny = op->g.ny, Ne = op->Ne, Ntau = op->tm.Ntau, M = op->M;
+  const uint8_t *dirF = op->dirichlet, *dirH = H->dirichlet;
+  const MeshRows none = mrows(nullptr);
+  const MeshRowsW nonew = mrowsw(nullptr);
+  StepParams P;
+  base_params(H, P);
+  P.kind = KIND_COARSE_PRI;
+  P.s0 = 0;
+  P.ns = Ntau;
+  P.in_field = op->mesh_FH;
+  P.in_aux = op->mesh_zero;
+  P.out_field = op->mesh_YH;
+  P.out_aux = op->mesh_aux;
+  if (direction == PTG_PRIMAL) {
+    PTG_CUDA(mesh_inject(nx, ny, mrows(X_field), mrowsw(op->mesh_FH), Ntau, dirH, st));
+    int rc = mesh_run(op, P, Ntau, KIND_COARSE_PRI, st);
+    if (rc != PTG_OK) return rc;
+    PTG_CUDA(mesh_prolong(nx, ny, mrows(op->mesh_YH), none, none, none, none, mrowsw(G_field), nonew, nonew, Ntau,
+                          dirF, dirH, op->p_int, op->mesh_pn, st));
+    PTG_CUDA(mesh_theta_old(Ntau, mesh_blocks(op->Nn), op->mesh_pn, X_aux, G_aux, 1.0 / ((double)Ntau * Ne), op->tm.p,
+                            op->p_int, op->tm.objective, st));
+  } else {
+    // lambda_{s+1}^old and the source of step k = M s + 1
+    PTG_CUDA(mesh_inject(nx, ny, mrows(X_field, 1), mrowsw(op->mesh_FH), Ntau, dirH, st));
+    PTG_CUDA(mesh_source(nx, ny, mrows(T_hist, 1, M), mrowsw(op->mesh_SH), Ntau, Theta_d, op->tm.p, op->p_int,
+                         op->tm.objective, dirF, dirH, st));
+    P.src_field = op->mesh_SH;
+    int rc = mesh_run(op, P, Ntau, KIND_COARSE_ADJ, st);
+    if (rc != PTG_OK) return rc;
+    PTG_CUDA(mesh_prolong(nx, ny, mrows(op->mesh_YH), none, none, none, none, mrowsw(G_field), nonew, nonew, Ntau,
+                          dirF, dirH, op->p_int, op->mesh_pn, st));
+    PTG_CUDA(mesh_dg(nx, ny, op->g.h, op->dtau, op->has_dc, op->dk, op->dc, mrows(G_field), T_hist, M, 0, 1, Ntau,
+                     1.0 / Ntau, op->mesh_dg, st));
+    PTG_CUDA(mesh_g_old(Ne, Ntau, X_aux, op->mesh_dg, G_aux, st));
+  }
+  return PTG_OK;
+}
+
+// The 2h-mesh op of a fine op (ptg_solve.coarse_mesh): nx/2 x ny/2 elements of side 2h, the
+// fine op's materials, precision and solver settings, one step of dtau per slice (Nt = Ntau,
+// M = 1, the load at t_{M(s+1)}), sink nodes where the fine node is a sink, element sources
+// averaged over the four children; and the transfer workspace.
+int create_mesh(ptg_op* op, const uint8_t* dirichlet_h, const double* q_elem_h, const double* q_time_h) {
+  const int nx = op->g.nx, ny = op->g.ny, nxH = nx / 2, nyH = ny / 2, Ntau = op->tm.Ntau, M = op->M;
+  const int NnH = (nxH + 1) * (nyH + 1), NeH = nxH * nyH;
+  ptg_grid gH{nxH, nyH, 2.0 * op->g.h};
+  ptg_time tH = op->tm;
+  tH.Nt = Ntau;
+  tH.Ntau = Ntau;
+  tH.dt = op->dtau;
+  ptg_solve sH = op->sv;
+  sH.coarse_mesh = 0;
+  std::vector<uint8_t> dH(NnH);
+  for (int J = 0; J <= nyH; ++J)
+    for (int I = 0; I <= nxH; ++I) dH[J * (nxH + 1) + I] = dirichlet_h[2 * J * (nx + 1) + 2 * I];
+  std::vector<double> qH(NeH), qtH(Ntau + 1);
+  for (int EY = 0; EY < nyH; ++EY)
+    for (int EX = 0; EX < nxH; ++EX) {
+      auto q = [&](int ey, int ex) { return q_elem_h ? q_elem_h[ey * nx + ex] : 1.0; };
+      qH[EY * nxH + EX] = 0.25 * ((q(2 * EY, 2 * EX) + q(2 * EY, 2 * EX + 1)) +
+                                  (q(2 * EY + 1, 2 * EX) + q(2 * EY + 1, 2 * EX + 1)));
+    }
+  for (int j = 0; j <= Ntau; ++j) qtH[j] = q_time_h ? q_time_h[(size_t)M * j] : 1.0;
+  int rc = ptg_op_create(&gH, &op->mat, &tH, &sH, dH.data(), qH.data(), qtH.data(), op->device, &op->mesh);
+  if (rc != PTG_OK) return rc;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](auto** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+  };
+  const size_t nb = (size_t)mesh_blocks(op->Nn);
+  A(&op->mesh_rho, (size_t)NeH * sizeof(double));
+  A(&op->mesh_XH, (size_t)(Ntau + 1) * NnH * sizeof(double));
+  A(&op->mesh_FH, (size_t)Ntau * NnH * sizeof(double));
+  A(&op->mesh_GH, (size_t)Ntau * NnH * sizeof(double));
+  A(&op->mesh_SH, (size_t)Ntau * NnH * sizeof(double));
+  A(&op->mesh_YH, (size_t)Ntau * NnH * sizeof(double));
+  A(&op->mesh_zero, (size_t)(Ntau + 1) * sizeof(double));
+  A(&op->mesh_aux, (size_t)(Ntau + 1) * sizeof(double));
+  A(&op->mesh_pn, (size_t)Ntau * nb * sizeof(double));
+  A(&op->mesh_lam, (size_t)Ntau * op->Nn * sizeof(double));
+  A(&op->mesh_dg, (size_t)Ntau * op->Ne * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(op->mesh_zero, 0, (size_t)(Ntau + 1) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(op->mesh_aux, 0, (size_t)(Ntau + 1) * sizeof(double));
+  if (e != cudaSuccess) return cuda_fail(e, "coarse mesh workspace");
+  return PTG_OK;
+}
+
+// The correction sweeps with the 2h-mesh G.  With w_s = F_s - G_s (fine) the corrected state
+// is u_{s+1} = P x_{s+1} + w_s, where x_{s+1} is the coarse step from R u_s; and R u_{s+1} =
+// x_{s+1} + R w_s, so the 2h-mesh op's own correction sweep on R F and R G_old (same
+// recurrence, on the coarse mesh) yields R u_{s+1}, hence x_{s+1} = R u_{s+1} - R F_s + R G_s.
+// Only the coarse solves are sequential; prolongation, history rows, theta and g follow in
+// parallel over the slices (the theta and g recurrences are scalar / per element).
+int mesh_correct(ptg_op* op, int direction, const double* F_field, const double* F_aux, const double* G_field,
+                 const double* G_aux, double* X_field, double* X_aux, double* T_hist, const double* Theta_d,
+                 cudaStream_t st) {
+  ptg_op* H = op->mesh;
+  const int nx = op->g.nx, ny = op->g.ny, Nn = op->Nn, NnH = H->Nn, Ne = op->Ne, Ntau = op->tm.Ntau, M = op->M;
+  const uint8_t *dirF = op->dirichlet, *dirH = H->dirichlet;
+  const MeshRows none = mrows(nullptr);
+  const MeshRowsW nonew = mrowsw(nullptr);
+  StepParams P;
+  base_params(H, P);
+  P.kind = KIND_CORRECT_PRI;
+  P.s0 = 0;
+  P.ns = Ntau;
+  P.in_field = nullptr;                   // x_0 given in row 0 of the coarse states
+  P.out_field = op->mesh_XH;
+  P.out_aux = op->mesh_aux;
+  P.F_field = op->mesh_FH;
+  P.F_aux = op->mesh_zero;
+  P.G_field = op->mesh_GH;
+  P.G_aux = op->mesh_zero;
+  if (direction == PTG_PRIMAL) {
+    PTG_CUDA(mesh_inject(nx, ny, mrows(F_field), mrowsw(op->mesh_FH), Ntau, dirH, st));
+    PTG_CUDA(mesh_inject(nx, ny, mrows(G_field), mrowsw(op->mesh_GH), Ntau, dirH, st));
+    PTG_CUDA(mesh_inject(nx, ny, mrows(X_field), mrowsw(op->mesh_XH), 1, dirH, st));
+    int rc = mesh_run(op, P, 1, KIND_CORRECT_PRI, st);
+    if (rc != PTG_OK) return rc;
+    if (T_hist) PTG_CUDA(cudaMemcpyAsync(T_hist, X_field, (size_t)Nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    PTG_CUDA(mesh_prolong(nx, ny, mrows(op->mesh_XH, 1), mrows(op->mesh_FH), mrows(op->mesh_GH), mrows(F_field),
+                          mrows(G_field), mrowsw(X_field, 1), nonew, T_hist ? mrowsw(T_hist, M, M) : nonew, Ntau,
+                          dirF, dirH, op->p_int, op->mesh_pn, st));
+    PTG_CUDA(mesh_theta_chain(Ntau, mesh_blocks(Nn), op->mesh_pn, F_aux, G_aux, X_aux, 1.0 / ((double)Ntau * Ne),
+                              op->tm.p, op->p_int, op->tm.objective, st));
+  } else {
+    // time-reversed on the coarse mesh: coarse row r stands for slice s = Ntau - 1 - r
+    PTG_CUDA(cudaMemsetAsync(X_field + (size_t)Ntau * Nn, 0, (size_t)Nn * sizeof(double), st));
+    PTG_CUDA(cudaMemsetAsync(op->mesh_XH, 0, (size_t)NnH * sizeof(double), st));
+    PTG_CUDA(mesh_inject(nx, ny, mrows(F_field, Ntau - 1, -1), mrowsw(op->mesh_FH), Ntau, dirH, st));
+    PTG_CUDA(mesh_inject(nx, ny, mrows(G_field, Ntau - 1, -1), mrowsw(op->mesh_GH), Ntau, dirH, st));
+    PTG_CUDA(mesh_source(nx, ny, mrows(T_hist, (long long)M * (Ntau - 1) + 1, -M), mrowsw(op->mesh_SH), Ntau, Theta_d,
+                         op->tm.p, op->p_int, op->tm.objective, dirF, dirH, st));
+    P.src_field = op->mesh_SH;
+    int rc = mesh_run(op, P, 1, KIND_CORRECT_ADJ, st);
+    if (rc != PTG_OK) return rc;
+    PTG_CUDA(mesh_prolong(nx, ny, mrows(op->mesh_XH, 1), mrows(op->mesh_FH), mrows(op->mesh_GH),
+                          mrows(F_field, Ntau - 1, -1), mrows(G_field, Ntau - 1, -1), mrowsw(X_field, Ntau - 1, -1),
+                          mrowsw(op->mesh_lam), nonew, Ntau, dirF, dirH, op->p_int, op->mesh_pn, st));
+    PTG_CUDA(mesh_dg(nx, ny, op->g.h, op->dtau, op->has_dc, op->dk, op->dc, mrows(op->mesh_lam), T_hist, M, Ntau - 1,
+                     -1, Ntau, 1.0 / Ntau, op->mesh_dg, st));
+    PTG_CUDA(mesh_g_chain(Ne, Ntau, op->mesh_dg, F_aux, G_aux, X_aux, st));
+  }
+  return PTG_OK;
 }
 
 }  // namespace
@@ -392,6 +580,8 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
     return PTG_EINVAL;
   if (solve->twolevel < PTG_TWOLEVEL_NONE || solve->twolevel > PTG_TWOLEVEL_VCYCLE) return PTG_EINVAL;
   if (solve->smooth_steps < 0 || solve->smooth_steps > 16) return PTG_EINVAL;
+  if (solve->coarse_mesh != 0 && solve->coarse_mesh != 1) return PTG_EINVAL;
+  if (solve->coarse_mesh && (grid->nx % 2 || grid->ny % 2 || grid->nx < 4 || grid->ny < 4)) return PTG_EINVAL;
   if (!(solve->rtol > 0.0) || solve->cg_iters_max < 1 || solve->refine_max < 1 || !(solve->inner_rtol >= 0.0))
     return PTG_EINVAL;
   if (!(mat->k0 > 0.0) || !(mat->kmin > 0.0) || !(mat->c0 > 0.0) || !(mat->cmin > 0.0)) return PTG_EINVAL;
@@ -496,6 +686,14 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
       return rc;
     }
   }
+  if (solve->coarse_mesh) {
+    int rc = create_mesh(op, dirichlet_h, q_elem_h, q_time_h);
+    if (rc != PTG_OK) {
+      free_all(op);
+      delete op;
+      return rc;
+    }
+  }
   *out = op;
   return PTG_OK;
 }
@@ -504,8 +702,7 @@ void ptg_op_destroy(ptg_op* op) {
   if (!op) return;
   DeviceGuard dg(op->device);
   cudaDeviceSynchronize();
-  free_all(op);
-  delete op;
+  ptg_op_free(op);
 }
 
 int ptg_op_sizes(const ptg_op* op, int* Nn, int* Ne, int* Nt, int* Ntau, int* M) {
@@ -593,6 +790,10 @@ int ptg_fe_assemble_operator(ptg_op* op, const double* rho_d, cudaStream_t strea
     PTG_CUDA(launch_coarse_setup(op->g.nx, op->g.ny, op->W, op->tl_m, Ac, op->dirichlet, op->tl_Ac, op->tl_band,
                                  op->tl_X, op->tl_Ainv, stream));
   }
+  if (op->mesh) {                // the 2h-mesh op on the averaged design
+    PTG_CUDA(mesh_design(op->g.nx, op->g.ny, rho_d, op->mesh_rho, stream));
+    return ptg_fe_assemble_operator(op->mesh, op->mesh_rho, stream);
+  }
   return PTG_OK;
 }
 
@@ -626,6 +827,10 @@ int ptg_coarse_sweep(ptg_op* op, int direction, const double* X_field, const dou
   if (direction != PTG_PRIMAL && direction != PTG_ADJOINT) return PTG_EINVAL;
   if (direction == PTG_ADJOINT && (!T_hist || !Theta_d)) return PTG_EINVAL;
   DeviceGuard dg(op->device);
+  if (op->mesh) {
+    op->last_stream = stream;
+    return mesh_coarse_sweep(op, direction, X_field, X_aux, T_hist, Theta_d, G_field, G_aux, stream);
+  }
   StepParams P;
   base_params(op, P);
   P.kind = direction == PTG_PRIMAL ? KIND_COARSE_PRI : KIND_COARSE_ADJ;
@@ -650,6 +855,10 @@ int ptg_parareal_correct(ptg_op* op, int direction, const double* F_field, const
   if (direction != PTG_PRIMAL && direction != PTG_ADJOINT) return PTG_EINVAL;
   if (direction == PTG_ADJOINT && (!T_hist || !Theta_d)) return PTG_EINVAL;
   DeviceGuard dg(op->device);
+  if (op->mesh && G_field) {
+    op->last_stream = stream;
+    return mesh_correct(op, direction, F_field, F_aux, G_field, G_aux, X_field, X_aux, T_hist, Theta_d, stream);
+  }
   StepParams P;
   base_params(op, P);
   P.kind = direction == PTG_PRIMAL ? KIND_CORRECT_PRI : KIND_CORRECT_ADJ;
@@ -819,6 +1028,7 @@ StepParams phase_params(const ptg_batch* b, int d, int ph, int cs, int tl_mode) 
   P.cs = cs;
   P.rmax = (op->g.ny + 1 + cs - 1) / cs;
   P.kind = phase_kind(ph);
+  P.stats_kind = P.kind;
   P.s0 = 0;
   P.ns = op->tm.Ntau;
   P.hist = B.T_hist;
@@ -1000,6 +1210,7 @@ int ptg_batch_create(ptg_op* const* ops, int nops, ptg_batch** out) {
   for (int d = 0; d < nops; ++d) {
     if (!ops[d]) return PTG_EINVAL;
     if (ops[d]->device != ops[0]->device || ops[d]->sv.precision != ops[0]->sv.precision) return PTG_EINVAL;
+    if (ops[d]->mesh) return PTG_EINVAL;   // the persistent batch kernels run fine-mesh G only
   }
   DeviceGuard dg(ops[0]->device);
   ptg_batch* b = new (std::nothrow) ptg_batch();

@@ -128,7 +128,7 @@ struct GridComm {
         while (ld_acquire_gpu(gen) == g0) {
           if ((++spins & 255) == 0 && ld_acquire_gpu(broken) != 0u) break;
           if (spins > kGridSpinLimit) {
-            record_error(P.stats, PTG_ETIMEOUT, P.kind, -1);
+            record_error(P.stats, PTG_ETIMEOUT, P.stats_kind, -1);
             atomicExch(broken, 1u);
             break;
           }

@@ -94,6 +94,8 @@ struct StepParams {
   int hist_j0, hist_rows;
   const double* Theta;       // device scalar (adjoint kinds)
   DevStats* stats;
+  int stats_kind;            // task kind under which the solver counters and errors are recorded
+  const double* src_field;   // coarse kinds: [Ntau][Nn] right-hand-side source per slice instead of q_j f
   int objective;             // PTG_OBJ_POWER_MEAN or PTG_OBJ_MODIFIED
   int plt;                   // correction kinds: coarse propagators identically zero (copy F)
   // two-level preconditioner of the coarse-step solves (Ainv == null: Jacobi)

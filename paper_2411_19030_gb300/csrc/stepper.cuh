@@ -957,13 +957,13 @@ struct Stepper {
       atomicAdd(&P.stats->cg_iters, (unsigned long long)its);
       atomicAdd(&P.stats->refinements, (unsigned long long)sweeps);
       atomicMax(&P.stats->max_cg_iters, (unsigned long long)its);
-      atomicAdd(&P.stats->kind_solves[P.kind], 1ull);
-      atomicAdd(&P.stats->kind_cg_iters[P.kind], (unsigned long long)its);
-      atomicAdd(&P.stats->kind_refinements[P.kind], (unsigned long long)sweeps);
+      atomicAdd(&P.stats->kind_solves[P.stats_kind], 1ull);
+      atomicAdd(&P.stats->kind_cg_iters[P.stats_kind], (unsigned long long)its);
+      atomicAdd(&P.stats->kind_refinements[P.stats_kind], (unsigned long long)sweeps);
       if (!(rr == rr) || !(bb == bb) || isinf(rr)) {
-        record_error(P.stats, PTG_ENONFINITE, P.kind, step);
+        record_error(P.stats, PTG_ENONFINITE, P.stats_kind, step);
       } else if (rr > tol2) {
-        record_error(P.stats, PTG_ENOCONV, P.kind, step);
+        record_error(P.stats, PTG_ENOCONV, P.stats_kind, step);
       }
     }
   }
@@ -1110,8 +1110,13 @@ struct Stepper {
     load_x64(P.in_field + (size_t)s * P.Nn);
     const double theta0 = P.in_aux[s];
     const int j = P.M * (s + 1);
-    const double qj = P.q_time[j];
-    build_rhs([&](int g) { return qj * P.fload[g]; });
+    if (P.src_field) {                          // a given source per slice (coarse-mesh G)
+      const double* src = P.src_field + (size_t)s * P.Nn;
+      build_rhs([&](int g) { return src[g]; });
+    } else {
+      const double qj = P.q_time[j];
+      build_rhs([&](int g) { return qj * P.fload[g]; });
+    }
     solve(j);
     const double sp = pnorm_p();
     store_x64(P.out_field + (size_t)s * P.Nn);
@@ -1140,8 +1145,13 @@ struct Stepper {
     }
     for (int s = 0; s < P.Ntau; ++s) {
       const int j = P.M * (s + 1);
-      const double qj = P.q_time[j];
-      build_rhs([&](int g) { return qj * P.fload[g]; });
+      if (P.src_field) {                        // a given source per slice (coarse-mesh G)
+        const double* src = P.src_field + (size_t)s * P.Nn;
+        build_rhs([&](int g) { return src[g]; });
+      } else {
+        const double qj = P.q_time[j];
+        build_rhs([&](int g) { return qj * P.fload[g]; });
+      }
       load_x64(P.G_field + (size_t)s * P.Nn);   // initial guess G(u_s^old)
       solve(j);
       const double sp = pnorm_p();
@@ -1171,7 +1181,7 @@ struct Stepper {
         const double* Tj = hist_row(j);
         const double* Tjm = hist_row(j - 1);
         if (Tj == nullptr || Tjm == nullptr) {   // host validation makes this unreachable
-          if (threadIdx.x == 0 && sb.rank == 0) record_error(P.stats, PTG_EINVAL, P.kind, j);
+          if (threadIdx.x == 0 && sb.rank == 0) record_error(P.stats, PTG_EINVAL, P.stats_kind, j);
           return;
         }
         build_rhs([&](int g) { return scale * ipow(Tj[g], P.p_int - 1); });
