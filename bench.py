@@ -507,7 +507,7 @@ def run_loop(args):
     a_max, r_fil, beta, eta = 0.4, 0.03, 32.0, 0.5
     op = Operator(n, n, h, w["material"], Nt, Ntau, dt, w["p"], sink,
                   solve=SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=4000, refine_max=8,
-                                    twolevel=args.twolevel, smooth_steps=args.smooth))
+                                    twolevel=args.twolevel, smooth_steps=args.smooth, coarse_mesh=args.coarse_mesh))
     true_op = Operator(n, n, h, w["material"], Nt, Ntau, dt, w["p"], sink,
                        solve=SolveConfig("fp64", rtol=1e-12, cg_iters_max=8000, refine_max=8))
     design = DesignMap(n, n, h, r_fil, beta, eta)
@@ -541,7 +541,8 @@ def run_loop(args):
         "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
         "config": {"workload": f"loop{n}: {n}x{n} grid, Nt={Nt}, Ntau={Ntau}, p=8, SIMP k, a_max={a_max}, "
                                f"r_fil={r_fil}, beta={beta}, eta={eta}, MMA move 0.2",
-                   "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel, "smooth_steps": args.smooth},
+                   "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel, "smooth_steps": args.smooth,
+                   "coarse_propagator": "2h mesh (Sec. 7.3 future work)" if args.coarse_mesh else "h mesh"},
         "first_iteration_sequential_ms": ms[0],
         "fine_dof_steps_per_s": 2.0 * N_free * Nt / (np.mean(oneshot) * 1e-3),
         "history": {"Theta_estimate": hist["Theta"], "area_fraction": hist["volume"], "ms": ms},
@@ -574,7 +575,8 @@ def run_sweep(args):
     h, dt = 1.0 / n, 1.0 / Nt
     sink = W.dirichlet_bottom_centre(n, n, h)
     qt = W.q_time_paper(Nt, dt)
-    solve = SolveConfig("fp64", rtol=1e-12, cg_iters_max=8000, refine_max=8)
+    solve = SolveConfig("fp64", rtol=1e-12, cg_iters_max=8000, refine_max=8, coarse_mesh=args.coarse_mesh)
+    seq_solve = SolveConfig("fp64", rtol=1e-12, cg_iters_max=8000, refine_max=8)
     stream = torch.cuda.current_stream()
 
     def timed(fn):
@@ -590,14 +592,18 @@ def run_sweep(args):
     rows = []
     for dname, rho_np in (("uniform0.3", np.full(n * n, 0.3)), ("branches", W.rho_branches(n, n))):
         rho = torch.tensor(rho_np, dtype=torch.float64, device="cuda")
-        for Ntau in (5, 10, 16, 20, 30, 32, 48, 60, 80, 96, 120, 160, 240):
+        ntaus = [int(v) for v in args.sweep_ntau.split(",")]
+        seq_op = Operator(n, n, h, w["material"], Nt, ntaus[0], dt, w["p"], sink, q_time=qt, solve=seq_solve)
+        seq_op.assemble(rho)
+        seq_buf = PassBuffers(seq_op)
+        t_seq, (Th_s, g_s) = timed(lambda: sequential_pass(seq_op, seq_buf))
+        Th_s, g_s = float(Th_s.item()), g_s.clone()
+        del seq_buf, seq_op
+        for Ntau in ntaus:
             op = Operator(n, n, h, w["material"], Nt, Ntau, dt, w["p"], sink, q_time=qt, solve=solve)
             op.assemble(rho)
             buf = PassBuffers(op)
-            if Ntau == 5:
-                t_seq, (Th_s, g_s) = timed(lambda: sequential_pass(op, buf))
-                Th_s, g_s = float(Th_s.item()), g_s.clone()
-            for k in range(1, 9):
+            for k in range(1, args.sweep_kmax + 1):
                 if k > Ntau:
                     break
                 t, (Th, g) = timed(lambda: parareal_pass(op, buf, k))
@@ -607,7 +613,8 @@ def run_sweep(args):
             del buf, op
     print(json.dumps({"metric": "k-iteration Parareal vs sequential FP64 GPU time stepping (paper test case)",
                       "config": {"workload": "paper100: 100x100, Nt=480, Table 1, q(t) of Eq. 5.1, bottom sink, p=20",
-                                 "precision": "fp64", "rtol": 1e-12},
+                                 "precision": "fp64", "rtol": 1e-12,
+                                 "coarse_propagator": "2h mesh (Sec. 7.3 future work)" if args.coarse_mesh else "h mesh"},
                       "paper_context": "MATLAB, CPU threads: Parareal speedup up to 5x at 16 threads with one iteration",
                       "rows": rows}), flush=True)
 
@@ -702,6 +709,11 @@ def main():
     ap.add_argument("--smooth", type=int, default=0,
                     help="V-cycle smoothing steps (1: one global Jacobi step; k >= 2: k slab-local steps; "
                          "0: the library default)")
+    ap.add_argument("--coarse-mesh", action="store_true",
+                    help="--sweep / --loop: coarse propagators on the 2h mesh (Sec. 7.3 future work)")
+    ap.add_argument("--sweep-ntau", default="5,10,16,20,30,32,48,60,80,96,120,160,240",
+                    help="--sweep: slice counts (divisors of 480)")
+    ap.add_argument("--sweep-kmax", type=int, default=8, help="--sweep: largest iteration count")
     ap.add_argument("--no-twolevel", dest="twolevel", action="store_const", const="none",
                     help="same as --twolevel none")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
