@@ -144,7 +144,7 @@ def run_gpu(args):
     n, Nt, Ntau, dt, p = w["n"], w["Nt"], w["Ntau"], w["dt"], w["p"]
     N_free = (n + 1) ** 2 - int(sink.sum())
     solve = SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=2000, refine_max=8,
-                        twolevel=args.twolevel, smooth_steps=args.smooth)
+                        twolevel=args.twolevel, smooth_steps=args.smooth, local_steps=args.local)
     op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink, solve=solve, device=local)
     seq_op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink,
                       solve=SolveConfig("fp64", rtol=1e-13, cg_iters_max=4000, refine_max=8), device=local)
@@ -288,7 +288,7 @@ def run_gpu(args):
             vname = "fp32_refine_all" if args.precision == "fp32_refine" else "fp32_refine"
             v_op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink,
                             solve=SolveConfig(vname, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=2000,
-                                              refine_max=8, twolevel=args.twolevel, smooth_steps=args.smooth), device=local)
+                                              refine_max=8, twolevel=args.twolevel, smooth_steps=args.smooth, local_steps=args.local), device=local)
             v_buf = PassBuffers(v_op)
             for a_, b_ in ((v_buf.U_T, buf.U_T), (v_buf.U_th, buf.U_th), (v_buf.V_l, buf.V_l),
                            (v_buf.V_g, buf.V_g)):
@@ -314,7 +314,7 @@ def run_gpu(args):
         # like the main steps, with the error of its one-shot estimate against the sequential result
         c_op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink,
                         solve=SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=2000,
-                                          refine_max=8, twolevel=args.twolevel, smooth_steps=args.smooth,
+                                          refine_max=8, twolevel=args.twolevel, smooth_steps=args.smooth, local_steps=args.local,
                                           coarse_mesh=True), device=local)
         c_buf = PassBuffers(c_op)
         for a_, b_ in ((c_buf.U_T, buf.U_T), (c_buf.U_th, buf.U_th), (c_buf.V_l, buf.V_l), (c_buf.V_g, buf.V_g)):
@@ -373,7 +373,7 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": f"{WORKLOAD}: 128x128 grid, Nt=1024, Ntau=32 (M=32), p=8, SIMP k, warm start from "
                                "the sequential coarse states of a design 1% away",
-                   "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel, "smooth_steps": args.smooth, "l2": "flushed between steps (256 MB write)",
+                   "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel, "smooth_steps": args.smooth, "local_steps": args.local, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "wall_s": wall},
         "per_kernel_ms": kind_ms,
@@ -507,7 +507,7 @@ def run_loop(args):
     a_max, r_fil, beta, eta = 0.4, 0.03, 32.0, 0.5
     op = Operator(n, n, h, w["material"], Nt, Ntau, dt, w["p"], sink,
                   solve=SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=4000, refine_max=8,
-                                    twolevel=args.twolevel, smooth_steps=args.smooth, coarse_mesh=args.coarse_mesh))
+                                    twolevel=args.twolevel, smooth_steps=args.smooth, local_steps=args.local, coarse_mesh=args.coarse_mesh))
     true_op = Operator(n, n, h, w["material"], Nt, Ntau, dt, w["p"], sink,
                        solve=SolveConfig("fp64", rtol=1e-12, cg_iters_max=8000, refine_max=8))
     design = DesignMap(n, n, h, r_fil, beta, eta)
@@ -541,7 +541,7 @@ def run_loop(args):
         "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
         "config": {"workload": f"loop{n}: {n}x{n} grid, Nt={Nt}, Ntau={Ntau}, p=8, SIMP k, a_max={a_max}, "
                                f"r_fil={r_fil}, beta={beta}, eta={eta}, MMA move 0.2",
-                   "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel, "smooth_steps": args.smooth,
+                   "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel, "smooth_steps": args.smooth, "local_steps": args.local,
                    "coarse_propagator": "2h mesh (Sec. 7.3 future work)" if args.coarse_mesh else "h mesh"},
         "first_iteration_sequential_ms": ms[0],
         "fine_dof_steps_per_s": 2.0 * N_free * Nt / (np.mean(oneshot) * 1e-3),
@@ -709,6 +709,8 @@ def main():
     ap.add_argument("--smooth", type=int, default=0,
                     help="V-cycle smoothing steps (1: one global Jacobi step; k >= 2: k slab-local steps; "
                          "0: the library default)")
+    ap.add_argument("--local", type=int, default=0,
+                    help="FP32 CG without two-level: 1 Jacobi, 2 two slab-local Jacobi steps, 0 the library default")
     ap.add_argument("--coarse-mesh", action="store_true",
                     help="--sweep / --loop: coarse propagators on the 2h mesh (Sec. 7.3 future work)")
     ap.add_argument("--sweep-ntau", default="5,10,16,20,30,32,48,60,80,96,120,160,240",

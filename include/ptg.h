@@ -134,6 +134,11 @@ typedef struct {
                           every output stay on the fine mesh.  Needs even nx, ny >= 4 (else
                           PTG_EINVAL); the batch entry points reject such ops.  0: G on the fine
                           mesh (Sec. 4.4). */
+    int local_steps;   /* preconditioner of the FP32 CG solves that use no two-level form (the fine
+                          steps): 1 Jacobi; 2 two damped-Jacobi steps (omega = 0.8) on each CTA's
+                          slab alone, z = (2S - S A_s S) r with S = omega D^-1 and A_s the slab's
+                          diagonal block of A (symmetric, no communication); 0 the library's
+                          default.  Other values: PTG_EINVAL. */
 } ptg_solve;
 
 typedef struct {

@@ -70,6 +70,8 @@ class SolveConfig:
     smooth_steps: int = 0            # V-cycle smoothing: 1 global Jacobi step, k >= 2 slab-local
     #                                  steps, 0 the library default
     coarse_mesh: bool = False        # coarse propagators on the 2h mesh (Sec. 7.3 future work)
+    local_steps: int = 0             # FP32 CG without two-level: 1 Jacobi, 2 two slab-local Jacobi
+    #                                  steps, 0 the library default
 
 
 class Operator:
@@ -108,7 +110,7 @@ class Operator:
                 "fp32_refine_all": PTG_FP32_REFINE_ALL}[solve.precision]
         s = _ffi.ptg_solve(prec, solve.rtol, solve.inner_rtol, solve.cg_iters_max, solve.refine_max,
                            twolevel_code(solve.twolevel), int(solve.grid_wide), int(solve.smooth_steps),
-                           int(solve.coarse_mesh))
+                           int(solve.coarse_mesh), int(solve.local_steps))
         self._dir = np.ascontiguousarray(dirichlet, dtype=np.uint8).reshape(-1)
         if self._dir.size != self.Nn:
             raise ValueError("dirichlet mask must have (nx+1)(ny+1) entries")

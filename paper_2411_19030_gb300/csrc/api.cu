@@ -148,6 +148,12 @@ size_t twolevel_bytes(const ptg_op* op, int precision, int kind, int cs, int tl_
 // (conduction-dominated) and 2.25 (capacity-dominated: the consistent Q1 mass matrix), so
 // omega lambda_max stays below 1.8 < 2 for every step size.
 constexpr float kVcycleOmega = 0.8f;
+// Default preconditioner of FP32 CG solves without a two-level form (ptg_solve.local_steps = 0):
+// Jacobi.  The two slab-local steps cut the fine-step CG iterations (128 x 128 pass: 34 -> 27
+// primal, 31 -> 24.5 adjoint) but cost more than they save there (fine kernels 7.6 + 8.5 ->
+// 8.6 + 9.4 ms); on high-contrast 512 x 512 designs they pay (one-shot design iteration 13.2 ->
+// 11.5 s).
+constexpr int kLocalSteps = 1;
 // Default smoothing steps of the V-cycle (ptg_solve.smooth_steps = 0): four slab-local Jacobi
 // steps before and after the coarse correction.  Measured on the 128 x 128 one-shot pass
 // (FP64 coarse-step CG): 1 global step 66.1 ms; 2, 3, 4, 6 local steps 59.2, 56.5, 55.9,
@@ -184,6 +190,7 @@ void twolevel_params(const ptg_op* op, int precision, StepParams& P, int tl_mode
   P.tl_vc = P.tl_naj > 0 && uses_vcycle(op, tl_mode);
   P.tl_omega = kVcycleOmega;
   P.tl_nu = op->tl_nu;
+  P.local_steps = op->sv.local_steps > 0 ? op->sv.local_steps : kLocalSteps;
   // FP32 CG: the op's inner tolerance; FP64 CG: to the final tolerance in one go, or in
   // kTwoLevelInnerFp64 steps with the additive two-level preconditioner
   if (precision == PTG_FP64)
@@ -581,6 +588,7 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
   if (solve->twolevel < PTG_TWOLEVEL_NONE || solve->twolevel > PTG_TWOLEVEL_VCYCLE) return PTG_EINVAL;
   if (solve->smooth_steps < 0 || solve->smooth_steps > 16) return PTG_EINVAL;
   if (solve->coarse_mesh != 0 && solve->coarse_mesh != 1) return PTG_EINVAL;
+  if (solve->local_steps < 0 || solve->local_steps > 2) return PTG_EINVAL;
   if (solve->coarse_mesh && (grid->nx % 2 || grid->ny % 2 || grid->nx < 4 || grid->ny < 4)) return PTG_EINVAL;
   if (!(solve->rtol > 0.0) || solve->cg_iters_max < 1 || solve->refine_max < 1 || !(solve->inner_rtol >= 0.0))
     return PTG_EINVAL;

@@ -104,6 +104,7 @@ struct StepParams {
   int tl_naj;                // aggregate rows reserved per CTA (0: two-level disabled for this launch)
   int tl_vc;                 // 1: V(1,1) two-grid cycle with damped-Jacobi smoothing; 0: additive D^-1 + P Ac^-1 P^T
   float tl_omega;            // damping of the V-cycle's Jacobi smoother
+  int local_steps;           // FP32 CG without two-level: 1 Jacobi, 2 two slab-local damped-Jacobi steps
   int tl_nu;                 // V-cycle smoothing: <= 1 one global Jacobi step before and after; k >= 2 k
                              // slab-local steps before and after
   // one system over a whole cooperative grid (GridComm): global scratch of the op

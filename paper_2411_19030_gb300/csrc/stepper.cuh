@@ -100,13 +100,25 @@ __device__ __forceinline__ void stencil_node64(const T* __restrict__ x, int loc0
 // y = A z for the 4 nodes of a group, FP32 element weights (D, S, T) in shared memory.
 // For the node at window position c = j+1: elements a, b below-left / below-right and c, d
 // above-left / above-right, i.e. element windows lower[j], lower[j+1], upper[j], upper[j+1].
+// no_lo / no_hi: the node row below / above is left out (taken as zero), which applies the
+// slab's diagonal block of the operator on its first / last row.
 __device__ __forceinline__ void stencil_elem32(const float* __restrict__ z, const float* __restrict__ wd,
                                                const float* __restrict__ ws, const float* __restrict__ wt, int loc0,
-                                               int W, float (&y)[4]) {
+                                               int W, float (&y)[4], bool no_lo = false, bool no_hi = false) {
   float zl[6], zm[6], zh[6];
-  load_window(z, loc0 - W, zl);
+  if (no_lo) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) zl[i] = 0.f;
+  } else {
+    load_window(z, loc0 - W, zl);
+  }
   load_window(z, loc0, zm);
-  load_window(z, loc0 + W, zh);
+  if (no_hi) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) zh[i] = 0.f;
+  } else {
+    load_window(z, loc0 + W, zh);
+  }
   float dl[5], sl[5], tl[5], du[5], su[5], tu[5];
   const int el = loc0 - W, eu = loc0;   // element windows share the node buffers' row offsets
   load_ewindow(wd, el, dl);
@@ -799,11 +811,67 @@ struct Stepper {
     return rz;
   }
 
+  // Two damped-Jacobi steps on the slab's diagonal block A_s (the rows of the other slabs left
+  // out): z = S r + S (r - A_s S r) = (2S - S A_s S) r, S = omega D^-1, a symmetric operator,
+  // positive definite while omega lambda_max(D^-1 A_s) < 2 (at most 0.8 * 2.25).  FP32 CG only
+  // (the FP32 element weights); the first step's iterate goes through zbuf, whose halo rows are
+  // not read, so the neighbours may already be writing their new edge rows into them.  No
+  // communication; two block barriers.  z goes to zbuf; returns the local (r, z).
+  __device__ Real precond_local2(const Real (&r)[NG][4]) {
+    if constexpr (!kMixed) {
+      return Real(0);   // not used: FP64 CG has no FP32 element weights
+    } else {
+    const float om = P.tl_omega;
+    float e[NG][4];
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) e[k][j] = 0.f;
+      if (l0 < 0) continue;
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) {
+        e[k][j] = om * (float)dinv[l0 + j] * (float)r[k][j];
+        zbuf[l0 + j] = (Real)e[k][j];
+      }
+    }
+    __syncthreads();
+    float z[NG][4];
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) z[k][j] = 0.f;
+      if (l0 < 0) continue;
+      const int lr = l0 / sb.W - 1;
+      float t[4];
+      stencil_elem32(zbuf, wd, ws, wt, l0, sb.W, t, lr == 0, lr == sb.R - 1);
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) z[k][j] = fmaf(om * (float)dinv[l0 + j], (float)r[k][j] - t[j], e[k][j]);
+    }
+    __syncthreads();
+    Real rz = Real(0);
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+      if (l0 < 0) continue;
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) {
+        zbuf[l0 + j] = (Real)z[k][j];
+        rz = fma(r[k][j], (Real)z[k][j], rz);
+      }
+    }
+    return rz;
+    }
+  }
+
   // Jacobi-preconditioned CG in precision Real on A d = r, where r (given per node) is the FP64
   // residual scaled to unit 2-norm; on return x64 += unscale * d.  Stops when ||r||^2 <= target2
   // (scaled units) or at the iteration limit; returns the iteration count.  All CG scalars and
   // dot products are in precision Real.
   __device__ int cg_correct(Real (&r)[NG][4], Real target2, double unscale) {
+    // FP32 CG without a two-level form: the slab-local two-step preconditioner if asked for
+    const bool local2 = kMixed && !tl && P.local_steps >= 2;
     Real d[NG][4], p[NG][4], q[NG][4];
     Real rz;
     {
@@ -813,7 +881,7 @@ struct Stepper {
         const int l0 = loc0[k];
 #pragma unroll
         for (int j = 0; j < kGroup; ++j) { d[k][j] = Real(0); p[k][j] = Real(0); q[k][j] = Real(0); }
-        if (l0 < 0 || tl) continue;
+        if (l0 < 0 || tl || local2) continue;
 #pragma unroll
         for (int j = 0; j < kGroup; ++j) {
           const Real z = dinv[l0 + j] * r[k][j];
@@ -821,7 +889,9 @@ struct Stepper {
           v[0] = fma(r[k][j], z, v[0]);
         }
       }
-      if (vc && P.tl_nu >= 2) {
+      if (local2) {
+        v[0] = precond_local2(r);
+      } else if (vc && P.tl_nu >= 2) {
         v[0] = vcycle_local(r);
       } else if (vc) {
         // r on the halo rows from the neighbours' owned edge rows
@@ -882,14 +952,16 @@ struct Stepper {
           d[k][j] = fma(alpha, p[k][j], d[k][j]);
           r[k][j] = fma(-alpha, q[k][j], r[k][j]);
           v[1] = fma(r[k][j], r[k][j], v[1]);
-          if (!tl) {
+          if (!tl && !local2) {
             const Real z = dinv[l0 + j] * r[k][j];
             zbuf[l0 + j] = z;
             v[0] = fma(r[k][j], z, v[0]);
           }
         }
       }
-      if (vc && P.tl_nu >= 2) {
+      if (local2) {
+        v[0] = precond_local2(r);
+      } else if (vc && P.tl_nu >= 2) {
         v[0] = vcycle_local(r);
       } else if (vc) {
         for (int i = threadIdx.x; i < 2 * sb.W; i += blockDim.x) vrh[i] = fma(-alpha, vqh[i], vrh[i]);

@@ -145,3 +145,23 @@ def test_twolevel_helps_on_high_contrast_designs(design, precision, mode):
         st = op.stats()["by_kind"]["coarse_primal"]
         its[tl] = st["cg_iters"] / st["solves"]
     assert its[mode] < 0.6 * its["none"], its
+
+
+@pytest.mark.parametrize("precision", ["fp32_refine", "fp32_refine_all"])
+def test_slab_local_two_step_preconditioner_of_the_fine_solves(case, precision):
+    """local_steps = 2: the FP32 fine-step CG preconditioned by two damped-Jacobi steps on each
+    CTA's slab; the pass still matches the oracle, with fewer fine CG iterations than Jacobi."""
+    prob, rho, U_old, V_old, _ = case
+    out = {}
+    for steps in (1, 2):
+        op = gpu_operator(prob, precision, rtol=1e-10, local_steps=steps)
+        buf = PassBuffers(op)
+        buf.U_T.copy_(dev(U_old[0])); buf.U_th.copy_(dev(U_old[1]))
+        buf.V_l.copy_(dev(V_old[0])); buf.V_g.copy_(dev(V_old[1]))
+        op.assemble(dev(rho))
+        Theta, grad = oneshot_pass(op, buf)
+        torch.cuda.synchronize()
+        check(case, op, buf, Theta, grad)
+        out[steps] = op.stats()["by_kind"]
+    for name in ("fine_primal", "fine_adjoint"):
+        assert out[2][name]["cg_iters"] < 0.9 * out[1][name]["cg_iters"], (name, out)
