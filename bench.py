@@ -555,6 +555,92 @@ def run_loop(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------- batching
+
+def run_batch48(args):
+    """The batching workload: 48 designs of uneven size (64^2 .. 256^2, Nt 512 .. 2048, 16 .. 64
+    slices), warm-started from the sequential coarse states of designs 1% away, advanced
+    together: each phase of the one-shot pass is one persistent launch over every design and
+    slice, assembly plus pass captured in one CUDA graph and replayed.  Reports the aggregate
+    fine DOF*steps/s of the batched pass, and the time of the same 48 passes run design by
+    design (each with its own plans), both with CUDA events and the L2 flushed before each."""
+    import torch
+
+    from paper_2411_19030_gb300 import Operator, PassBuffers, SolveConfig, oneshot_pass, sequential_pass
+    from paper_2411_19030_gb300.batch import Batch, autotune
+    from paper_2411_19030_gb300.build import build_library
+
+    build_library()
+    device = torch.device("cuda", 0)
+    designs = W.batch48()
+    solve = SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=2000, refine_max=8,
+                        twolevel=args.twolevel, smooth_steps=args.smooth)
+    mats = W.MATERIALS["simp_k"]
+    ops, dof = [], 0.0
+    for d in designs:
+        n, h = d["n"], 1.0 / d["n"]
+        sink = W.dirichlet_left_centre(n, n, h)
+        ops.append(Operator(n, n, h, mats, d["Nt"], d["Ntau"], d["dt"], d["p"], sink, solve=solve))
+        dof += 2.0 * ((n + 1) ** 2 - int(sink.sum())) * d["Nt"]
+    batch = Batch(ops)
+    dv = lambda a: torch.tensor(a, dtype=torch.float64, device=device)
+    for i, d in enumerate(designs):
+        batch.buffers(i)["rho"].copy_(dv(W.rho_warm_perturb(d["rho"], seed=1000 + d["index"], amp=0.01)))
+    batch.assemble()
+    batch.sequential_pass()
+    for i, d in enumerate(designs):
+        batch.buffers(i)["rho"].copy_(dv(d["rho"]))
+    batch.assemble()
+    tuned = autotune(batch) if args.autotune else None
+    batch.oneshot_pass()
+    batch.capture()
+    flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device=device)
+    stream = torch.cuda.current_stream(device)
+    steps = max(1, min(args.steps, 5))
+    for _ in range(max(1, args.warmup)):
+        batch.replay()
+    torch.cuda.synchronize()
+    times = []
+    with ClockSampler(0) as clk:
+        for _ in range(steps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            batch.replay()
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+    ms = float(np.mean(times))
+    status = max(op.stats()["status"] != 0 for op in ops)
+    # the same 48 passes design by design (warm start copied from the batch's buffers)
+    single = 0.0
+    for i, op in enumerate(ops):
+        bi = batch.buffers(i)
+        buf = PassBuffers(op)
+        for a_, k in ((buf.U_T, "U_T"), (buf.U_th, "U_theta"), (buf.V_l, "V_lam"), (buf.V_g, "V_g")):
+            a_.copy_(bi[k])
+        rho = bi["rho"].clone()
+        for rep in range(2):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            op.assemble(rho)
+            oneshot_pass(op, buf)
+            b.record(stream)
+            b.synchronize()
+        single += a.elapsed_time(b)
+        del buf
+    print(json.dumps({"metric": "fine DOF*steps/s of the batched one-shot pass (48 designs of uneven size)",
+                      "value": dof / (ms * 1e-3), "unit": UNIT, "ms_per_batched_pass": ms, "steps": steps,
+                      "design_by_design_ms": single, "batching_speedup": single / ms, "status": int(status),
+                      "autotuned": tuned is not None, "dtype": "f32+f64" if args.precision != "fp64" else "f64",
+                      "config": {"workload": "batch48: 48 designs, sides 64/96/128/192/256, (Nt, Ntau) in "
+                                             "(512,16)/(1024,32)/(2048,64), rho ~ U(0.2,0.8)",
+                                 "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel,
+                                 "l2": "flushed between steps (256 MB write)"},
+                      "clocks": clk.summary()}), flush=True)
+
+
 # ---------------------------------------------------------------------------- Parareal sweep
 
 def run_sweep(args):
@@ -730,9 +816,15 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="instead of the pass benchmark: k-iteration Parareal error / speedup sweep of the paper's "
                          "test case (100x100, Nt=480, Table 1, Eq. 5.1 load, bottom sink, p=20)")
+    ap.add_argument("--batch48", action="store_true",
+                    help="instead of the pass benchmark: the 48-design batching workload (persistent launches, "
+                         "CUDA graph) against the same passes design by design")
+    ap.add_argument("--autotune", action="store_true", help="--batch48: autotune every phase's plan first")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.batch48:
+        run_batch48(args)
     elif args.loop:
         run_loop(args)
     elif args.sweep:
