@@ -205,7 +205,7 @@ void twolevel_params(const ptg_op* op, int precision, StepParams& P, int tl_mode
 // Best plan for `ntasks` concurrent clusters with or without the two-level preconditioner:
 // fewest waves, then the shortest per-thread work (ng), then the largest cluster.  Returns
 // the number of waves, or -1 if nothing fits.
-long best_plan(ptg_op* op, int precision, int kind, int ntasks, int tl_mode, Plan* out) {
+long best_plan(ptg_op* op, int precision, int kind, int ntasks, int tl_mode, Plan* out, bool keep_ax = true) {
   const int nx = op->g.nx, ny = op->g.ny;
   const int G = op->W / kGroup;
   long best_waves = -1;
@@ -218,7 +218,7 @@ long best_plan(ptg_op* op, int precision, int kind, int ntasks, int tl_mode, Pla
       if (nthreads > kStepMaxThreadsHost) continue;
       Plan p;
       cudaError_t e = query_stepper_plan(nx, ny, precision, kind, cs, ng, nthreads,
-                                         twolevel_bytes(op, precision, kind, cs, tl_mode), &p);
+                                         twolevel_bytes(op, precision, kind, cs, tl_mode), &p, keep_ax);
       if (e != cudaSuccess) {
         cudaGetLastError();
         continue;
@@ -262,17 +262,22 @@ int choose_plan(ptg_op* op, int precision, int kind, int ntasks, Plan* out) {
   // The strongest two-level form whose plan fits (and, for FP32 CG, adds no wave over
   // Jacobi's: FP64 CG on GB300 is bound by the FP64 pipe, so the cut in iterations outweighs
   // extra waves; FP32 CG is bound by latency).
+  // A plan may leave out the saved A x of the last residual (one more FP64 stencil per step) when
+  // that lets a two-level form, or any plan at all, fit.
   Plan jac, two;
-  const long wj = best_plan(op, precision, kind, ntasks, TL_NONE, &jac);
+  long wj = best_plan(op, precision, kind, ntasks, TL_NONE, &jac);
+  if (wj < 0) wj = best_plan(op, precision, kind, ntasks, TL_NONE, &jac, false);
   long wt = -1;
   if (twolevel_rows(op, precision, kind, 1) > 0) {
-    for (int mode = strongest_mode(op); mode > TL_NONE; --mode) {
-      Plan c;
-      const long w = best_plan(op, precision, kind, ntasks, mode, &c);
-      if (w >= 0 && (wj < 0 || w <= wj || precision == PTG_FP64)) {
-        two = c;
-        wt = w;
-        break;
+    for (int mode = strongest_mode(op); mode > TL_NONE && wt < 0; --mode) {
+      for (bool keep_ax : {true, false}) {
+        Plan c;
+        const long w = best_plan(op, precision, kind, ntasks, mode, &c, keep_ax);
+        if (w >= 0 && (wj < 0 || w <= wj || precision == PTG_FP64)) {
+          two = c;
+          wt = w;
+          break;
+        }
       }
     }
   }
@@ -282,19 +287,22 @@ int choose_plan(ptg_op* op, int precision, int kind, int ntasks, Plan* out) {
                          (op->sv.grid_wide == 1 && (no_cluster || (spread && op->Nn >= kWideMinNodes)));
   if (want_wide) {
     // one FP64 system over every SM (spread), or groups of the fewest CTAs whose slabs fit,
-    // with the strongest two-level form that fits
+    // with the strongest two-level form that fits.  Groups leave out the saved A x: smaller
+    // slabs per CTA mean fewer CTAs per group and more systems at a time.
     for (int mode = strongest_mode(op); mode >= TL_NONE; --mode) {
-      Plan w;
-      WideCtx ctx{op, precision, kind, mode};
-      if (query_wide_plan(op->g.nx, op->g.ny, precision, kind, ntasks, spread, wide_twolevel_bytes, &ctx, &w) ==
-          cudaSuccess) {
-        w.twolevel = twolevel_rows(op, precision, kind, w.cs, mode) > 0;
-        w.vc = w.twolevel && uses_vcycle(op, mode);
-        op->plans[key] = w;
-        *out = w;
-        return PTG_OK;
+      for (bool keep_ax : {spread, !spread}) {
+        Plan w;
+        WideCtx ctx{op, precision, kind, mode};
+        if (query_wide_plan(op->g.nx, op->g.ny, precision, kind, ntasks, spread, wide_twolevel_bytes, &ctx, &w,
+                            keep_ax) == cudaSuccess) {
+          w.twolevel = twolevel_rows(op, precision, kind, w.cs, mode) > 0;
+          w.vc = w.twolevel && uses_vcycle(op, mode);
+          op->plans[key] = w;
+          *out = w;
+          return PTG_OK;
+        }
+        cudaGetLastError();
       }
-      cudaGetLastError();
     }
   }
   if (no_cluster) {
@@ -351,6 +359,7 @@ void base_params(const ptg_op* op, StepParams& P) {
   P.stats = op->stats;
   P.objective = op->tm.objective;
   P.hist_rows = 0;
+  P.keep_ax = 1;
 }
 
 int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream, int stats_kind = -1) {
@@ -371,6 +380,7 @@ int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream, int stats_ki
     P.g_tl = op->g_tl;
   }
   twolevel_params(op, prec, P, plan.twolevel && !P.plt ? (plan.vc ? TL_VCYCLE : TL_ADDITIVE) : TL_NONE);
+  P.keep_ax = plan.keep_ax ? 1 : 0;
   op->last_stream = stream;
   PTG_CUDA(launch_stepper(P, plan, prec, ntasks, stream));
   return PTG_OK;
@@ -742,18 +752,20 @@ int ptg_op_set_plan(ptg_op* op, int kind, int cs, int ng) {
   for (int mode = strongest_mode(op); mode >= TL_NONE; --mode) {
     const int prec = kind_precision(op->sv.precision, kind);
     if (mode > TL_NONE && twolevel_rows(op, prec, kind, cs, mode) == 0) continue;
-    Plan p;
-    cudaError_t e = query_stepper_plan(op->g.nx, op->g.ny, prec, kind, cs, ng, nthreads,
-                                       twolevel_bytes(op, prec, kind, cs, mode), &p);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      continue;
+    for (bool keep_ax : {true, false}) {
+      Plan p;
+      cudaError_t e = query_stepper_plan(op->g.nx, op->g.ny, prec, kind, cs, ng, nthreads,
+                                         twolevel_bytes(op, prec, kind, cs, mode), &p, keep_ax);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      if (p.max_active_clusters <= 0) continue;
+      p.twolevel = mode > TL_NONE;
+      p.vc = uses_vcycle(op, mode);
+      op->plan_override[kind] = p;
+      return PTG_OK;
     }
-    if (p.max_active_clusters <= 0) continue;
-    p.twolevel = mode > TL_NONE;
-    p.vc = uses_vcycle(op, mode);
-    op->plan_override[kind] = p;
-    return PTG_OK;
   }
   return PTG_EINVAL;
 }
@@ -1028,7 +1040,7 @@ void batch_free(ptg_batch* b) {
 }
 
 // Per-design parameters of one phase with cluster size cs.
-StepParams phase_params(const ptg_batch* b, int d, int ph, int cs, int tl_mode) {
+StepParams phase_params(const ptg_batch* b, int d, int ph, int cs, int tl_mode, bool keep_ax) {
   const ptg_op* op = b->ops[d];
   const BatchBuf& B = b->bufs[d];
   StepParams P;
@@ -1037,6 +1049,7 @@ StepParams phase_params(const ptg_batch* b, int d, int ph, int cs, int tl_mode) 
   P.rmax = (op->g.ny + 1 + cs - 1) / cs;
   P.kind = phase_kind(ph);
   P.stats_kind = P.kind;
+  P.keep_ax = keep_ax ? 1 : 0;
   P.s0 = 0;
   P.ns = op->tm.Ntau;
   P.hist = B.T_hist;
@@ -1095,7 +1108,7 @@ std::vector<int2> phase_tasks(const ptg_batch* b, int ph) {
 // Install a plan for a phase: validate it for every design, upload the parameter table and
 // the task list, and size the persistent grid.  tl_mode: the strongest two-level form the
 // designs may use where it applies.
-int batch_install(ptg_batch* b, int ph, int cs, int ng, int nthreads, int tl_mode) {
+int batch_install(ptg_batch* b, int ph, int cs, int ng, int nthreads, int tl_mode, bool keep_ax = true) {
   const int kind = phase_kind(ph);
   const int prec = kind_precision(b->precision, kind);
   size_t smem = 0;
@@ -1104,7 +1117,7 @@ int batch_install(ptg_batch* b, int ph, int cs, int ng, int nthreads, int tl_mod
     if (rmax < 2) return PTG_EINVAL;
     const int groups = rmax * (op->W / kGroup);
     if (groups > ng * nthreads) return PTG_EINVAL;
-    smem = std::max(smem, stepper_smem_bytes(op->g.nx, rmax, prec == PTG_FP32_REFINE ? 4 : 8) +
+    smem = std::max(smem, stepper_smem_bytes(op->g.nx, rmax, prec == PTG_FP32_REFINE ? 4 : 8, keep_ax) +
                               twolevel_bytes(op, prec, kind, cs, tl_mode));
   }
   int nclusters = 0;
@@ -1113,7 +1126,7 @@ int batch_install(ptg_batch* b, int ph, int cs, int ng, int nthreads, int tl_mod
     return PTG_EINVAL;
   }
   std::vector<StepParams> table;
-  for (int d = 0; d < (int)b->ops.size(); ++d) table.push_back(phase_params(b, d, ph, cs, tl_mode));
+  for (int d = 0; d < (int)b->ops.size(); ++d) table.push_back(phase_params(b, d, ph, cs, tl_mode, keep_ax));
   std::vector<int2> tasks = phase_tasks(b, ph);
   PhasePlan& pp = b->ph[ph];
   if (!pp.table) PTG_CUDA(cudaMalloc(&pp.table, sizeof(StepParams) * table.size()));
@@ -1127,6 +1140,7 @@ int batch_install(ptg_batch* b, int ph, int cs, int ng, int nthreads, int tl_mod
   pp.plan.max_active_clusters = nclusters;
   pp.plan.twolevel = tl_mode > TL_NONE;
   pp.plan.vc = tl_mode >= TL_VCYCLE;
+  pp.plan.keep_ax = keep_ax;
   pp.ntasks = (int)tasks.size();
   pp.nclusters = std::min(nclusters, pp.ntasks);
   pp.ready = true;
@@ -1136,7 +1150,8 @@ int batch_install(ptg_batch* b, int ph, int cs, int ng, int nthreads, int tl_mod
 // Default plan of a phase: fewest waves, then the fewest groups per thread, then the largest
 // cluster; the two-level preconditioner unless it needs more waves (the autotuner may replace
 // the plan).
-long batch_best(ptg_batch* b, int ph, int tl_mode, int ntasks, int* best_cs, int* best_ng, int* best_nt) {
+long batch_best(ptg_batch* b, int ph, int tl_mode, int ntasks, int* best_cs, int* best_ng, int* best_nt,
+                bool keep_ax = true) {
   long best_waves = -1;
   const int prec = kind_precision(b->precision, phase_kind(ph));
   for (int cs : {16, 8, 4, 2}) {
@@ -1149,7 +1164,7 @@ long batch_best(ptg_batch* b, int ph, int tl_mode, int ntasks, int* best_cs, int
         if (rmax < 2) { ok = false; break; }
         const int groups = rmax * (op->W / kGroup);
         nt = std::max(nt, ((groups + ng - 1) / ng + 31) / 32 * 32);
-        smem = std::max(smem, stepper_smem_bytes(op->g.nx, rmax, prec == PTG_FP32_REFINE ? 4 : 8) +
+        smem = std::max(smem, stepper_smem_bytes(op->g.nx, rmax, prec == PTG_FP32_REFINE ? 4 : 8, keep_ax) +
                                   twolevel_bytes(op, prec, phase_kind(ph), cs, tl_mode));
       }
       if (!ok || nt > kStepMaxThreadsHost) continue;
@@ -1182,15 +1197,23 @@ int batch_twolevel_mode(const ptg_batch* b, int ph) {
 int batch_default(ptg_batch* b, int ph) {
   const int ntasks = (int)phase_tasks(b, ph).size();
   int jc = 0, jg = 0, jt = 0;
-  const long wj = batch_best(b, ph, TL_NONE, ntasks, &jc, &jg, &jt);
+  bool jkeep = true;
+  long wj = batch_best(b, ph, TL_NONE, ntasks, &jc, &jg, &jt);
+  if (wj < 0) {
+    jkeep = false;
+    wj = batch_best(b, ph, TL_NONE, ntasks, &jc, &jg, &jt, false);
+  }
   const bool fp64 = kind_precision(b->precision, phase_kind(ph)) == PTG_FP64;
+  // the strongest two-level form that fits, leaving out the saved A x if that makes it fit
   for (int mode = batch_twolevel_mode(b, ph); mode > TL_NONE; --mode) {
-    int tc = 0, tg = 0, tt = 0;
-    const long wt = batch_best(b, ph, mode, ntasks, &tc, &tg, &tt);
-    if (wt >= 0 && (wj < 0 || wt <= wj || fp64)) return batch_install(b, ph, tc, tg, tt, mode);
+    for (bool keep_ax : {true, false}) {
+      int tc = 0, tg = 0, tt = 0;
+      const long wt = batch_best(b, ph, mode, ntasks, &tc, &tg, &tt, keep_ax);
+      if (wt >= 0 && (wj < 0 || wt <= wj || fp64)) return batch_install(b, ph, tc, tg, tt, mode, keep_ax);
+    }
   }
   if (wj < 0) return PTG_EINVAL;
-  return batch_install(b, ph, jc, jg, jt, TL_NONE);
+  return batch_install(b, ph, jc, jg, jt, TL_NONE, jkeep);
 }
 
 int batch_run(ptg_batch* b, int ph, cudaStream_t stream) {
@@ -1342,8 +1365,10 @@ int ptg_batch_set_plan(ptg_batch* b, int phase, int cs, int ng, int nthreads) {
   std::lock_guard<std::mutex> lk(b->mu);
   // with the strongest two-level form where it applies and fits, else with Jacobi
   for (int mode = batch_twolevel_mode(b, phase); mode > TL_NONE; --mode)
-    if (batch_install(b, phase, cs, ng, nthreads, mode) == PTG_OK) return PTG_OK;
-  return batch_install(b, phase, cs, ng, nthreads, TL_NONE);
+    for (bool keep_ax : {true, false})
+      if (batch_install(b, phase, cs, ng, nthreads, mode, keep_ax) == PTG_OK) return PTG_OK;
+  if (batch_install(b, phase, cs, ng, nthreads, TL_NONE) == PTG_OK) return PTG_OK;
+  return batch_install(b, phase, cs, ng, nthreads, TL_NONE, false);
 }
 
 int ptg_batch_get_plan(ptg_batch* b, int phase, int* cs, int* ng, int* nthreads, int* nclusters) {

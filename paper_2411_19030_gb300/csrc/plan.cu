@@ -106,14 +106,15 @@ static cudaError_t occupancy(const void* k, int cs, int nthreads, size_t smem, i
 }
 
 cudaError_t query_stepper_plan(int nx, int ny, int precision, int kind, int cs, int ng, int nthreads, size_t extra_smem,
-                               Plan* plan) {
+                               Plan* plan, bool keep_ax) {
   StepKernel k = stepper_kernel_for(precision, kind, ng);
   if (!k || nthreads < 32 || nthreads > kStepMaxThreadsHost || nthreads % 32) return cudaErrorInvalidConfiguration;
   plan->cs = cs;
   plan->nthreads = nthreads;
   plan->ng = ng;
   plan->rmax = (ny + 1 + cs - 1) / cs;
-  plan->smem = stepper_smem_bytes(nx, plan->rmax, precision == PTG_FP32_REFINE ? 4 : 8) + extra_smem;
+  plan->smem = stepper_smem_bytes(nx, plan->rmax, precision == PTG_FP32_REFINE ? 4 : 8, keep_ax) + extra_smem;
+  plan->keep_ax = keep_ax;
   plan->max_active_clusters = 0;
   if (plan->smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   int n = 0;
@@ -123,7 +124,7 @@ cudaError_t query_stepper_plan(int nx, int ny, int precision, int kind, int cs, 
 }
 
 cudaError_t query_wide_plan(int nx, int ny, int precision, int kind, int ntasks, bool spread,
-                            size_t (*extra_smem)(const void*, int), const void* ctx, Plan* plan) {
+                            size_t (*extra_smem)(const void*, int), const void* ctx, Plan* plan, bool keep_ax) {
   int dev = 0, nsm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -152,7 +153,7 @@ cudaError_t query_wide_plan(int nx, int ny, int precision, int kind, int ntasks,
       if (!k) return cudaErrorInvalidConfiguration;
       const int nthreads = ((groups + ng - 1) / ng + 31) / 32 * 32;
       if (nthreads > kStepMaxThreadsHost) continue;
-      const size_t smem = stepper_smem_bytes(nx, rmax, precision == PTG_FP32_REFINE ? 4 : 8) + extra_smem(ctx, G);
+      const size_t smem = stepper_smem_bytes(nx, rmax, precision == PTG_FP32_REFINE ? 4 : 8, keep_ax) + extra_smem(ctx, G);
       if (smem > 227 * 1024) continue;
       e = configure_kernel((const void*)k, smem, false);
       if (e != cudaSuccess) return e;
@@ -170,6 +171,7 @@ cudaError_t query_wide_plan(int nx, int ny, int precision, int kind, int ntasks,
       plan->smem = smem;
       plan->max_active_clusters = ngroups;
       plan->wide = true;
+      plan->keep_ax = keep_ax;
       return cudaSuccess;
     }
   }

@@ -105,6 +105,7 @@ struct StepParams {
   int tl_vc;                 // 1: V(1,1) two-grid cycle with damped-Jacobi smoothing; 0: additive D^-1 + P Ac^-1 P^T
   float tl_omega;            // damping of the V-cycle's Jacobi smoother
   int local_steps;           // FP32 CG without two-level: 1 Jacobi, 2 two slab-local damped-Jacobi steps
+  int keep_ax;               // 1: keep A x of the last residual (saves one FP64 stencil per step), 8 B per node
   int tl_nu;                 // V-cycle smoothing: <= 1 one global Jacobi step before and after; k >= 2 k
                              // slab-local steps before and after
   // one system over a whole cooperative grid (GridComm): global scratch of the op
@@ -181,7 +182,7 @@ inline size_t twolevel_smem_bytes(int W, int rmax, int cs, int nax, int nay, int
 }
 
 // Shared-memory footprint (bytes) of one CTA of the stepper.
-inline size_t stepper_smem_bytes(int nx, int rmax, int real_bytes) {
+inline size_t stepper_smem_bytes(int nx, int rmax, int real_bytes, bool keep_ax = true) {
   const size_t W = (size_t)padded_width(nx);
   const size_t halo = (size_t)(rmax + 2) * W + 2 * kSlack;   // rows -1..R
   const size_t own = (size_t)rmax * W + 2 * kSlack;          // rows 0..R-1
@@ -189,7 +190,7 @@ inline size_t stepper_smem_bytes(int nx, int rmax, int real_bytes) {
   size_t b = 0;
   b += halo * sizeof(double);                  // x64: FP64 state with halos
   b += own * sizeof(double);                   // b64: FP64 right-hand side
-  b += own * sizeof(double);                   // ax64: A x of the last residual evaluation
+  if (keep_ax) b += own * sizeof(double);      // ax64: A x of the last residual evaluation (optional)
   b += halo * real_bytes;                      // zbuf: CG stencil operand with halos
   b += own * real_bytes;                       // dinv: Jacobi inverse diagonal (0 off the unknowns)
   if (real_bytes == 4) b += 3 * elems * 4;     // (D, S, T) element weights for the FP32 CG
@@ -203,6 +204,7 @@ struct Plan {
   int max_active_clusters = 0;
   bool twolevel = false;     // coarse kinds: two-level preconditioner (its shared memory is in smem)
   bool vc = false;           // ... in the V(1,1) cycle form (else additive)
+  bool keep_ax = true;       // the saved A x of the last residual is in smem
   bool wide = false;         // one task over a cooperative grid of cs CTAs (GridComm), no clusters
 };
 
@@ -219,13 +221,13 @@ cudaError_t launch_coarse_setup(int nx, int ny, int W, int m, const NodeWeights&
 // device; later calls with no larger footprint make no attribute call.
 cudaError_t configure_kernel(const void* k, size_t smem, bool cluster);
 cudaError_t query_stepper_plan(int nx, int ny, int precision, int kind, int cs, int ng, int nthreads, size_t extra_smem,
-                               Plan* plan);
+                               Plan* plan, bool keep_ax = true);
 // Plan of the grid-wide variant.  spread: one system over as many CTAs as there are SMs (rmax
 // >= 2 rows each); otherwise the fewest CTAs per group whose slabs fit, and as many groups as
 // fit the chip (plan.max_active_clusters = groups, at most ntasks).  extra_smem(G) gives the
 // two-level bytes for G CTAs.  cudaErrorInvalidConfiguration if nothing fits.
 cudaError_t query_wide_plan(int nx, int ny, int precision, int kind, int ntasks, bool spread,
-                            size_t (*extra_smem)(const void*, int), const void* ctx, Plan* plan);
+                            size_t (*extra_smem)(const void*, int), const void* ctx, Plan* plan, bool keep_ax = true);
 
 // Device arrays written by the assembly (see ptg_op in api.cu for their shapes).
 struct AssembleOut {

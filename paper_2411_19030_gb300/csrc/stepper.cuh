@@ -166,7 +166,8 @@ struct Stepper {
   double step_dt = 0.0;
   double inv_dt = 0.0;
   int gshift = 0;   // offset from a halo-buffer node to the same node of the global padded arrays
-  double* ax64;     // A x64 from the last residual evaluation, rows 0..R-1 (reused by the next step)
+  double* ax64;     // A x64 from the last residual evaluation, rows 0..R-1 (reused by the next step;
+                    // null when the plan leaves it out, P.keep_ax == 0)
   bool ax_valid = false;
   // two-level preconditioner of the coarse-step solves: see coarse_restrict_push
   bool tl = false;
@@ -205,7 +206,7 @@ struct Stepper {
     unsigned char* p = dyn;
     double* x64b = reinterpret_cast<double*>(p);  p += sizeof(double) * halo;
     double* b64b = reinterpret_cast<double*>(p);  p += sizeof(double) * own;
-    double* axb = reinterpret_cast<double*>(p);   p += sizeof(double) * own;
+    double* axb = reinterpret_cast<double*>(p);   p += P.keep_ax ? sizeof(double) * own : 0;
     Real* zb = reinterpret_cast<Real*>(p);        p += sizeof(Real) * halo;
     Real* db = reinterpret_cast<Real*>(p);        p += sizeof(Real) * own;
     float* eb = reinterpret_cast<float*>(p);
@@ -215,7 +216,7 @@ struct Stepper {
     }
     for (int i = threadIdx.x; i < own; i += blockDim.x) {
       b64b[i] = 0.0;
-      axb[i] = 0.0;
+      if (P.keep_ax) axb[i] = 0.0;
       db[i] = Real(0);
     }
     if constexpr (kMixed) {
@@ -294,7 +295,7 @@ struct Stepper {
     }
     x64 = x64b + kSlack;
     b64 = b64b + kSlack - W;   // b64[loc] for loc in own rows (loc >= W)
-    ax64 = axb + kSlack - W;
+    ax64 = P.keep_ax ? axb + kSlack - W : nullptr;
     zbuf = zb + kSlack;
     dinv = db + kSlack - W;    // dinv[loc] likewise
     if constexpr (kMixed) {
@@ -466,7 +467,7 @@ struct Stepper {
       stencil_node64<double>(x64, l0, A, l0 + gshift, sb.W, y);
 #pragma unroll
       for (int j = 0; j < kGroup; ++j) {
-        ax64[l0 + j] = y[j];
+        if (ax64) ax64[l0 + j] = y[j];
         if (unknown(k, j)) {
           r64[k][j] = b64[l0 + j] - y[j];
           rr = fma(r64[k][j], r64[k][j], rr);
@@ -994,7 +995,7 @@ struct Stepper {
   __device__ void solve(int step, bool reuse_ax = false) {
     double r64[NG][4];
     double bb_rr[2] = {0.0, 0.0};
-    bb_rr[1] = (reuse_ax && ax_valid) ? residual_saved(r64) : residual(r64);
+    bb_rr[1] = (reuse_ax && ax_valid && ax64) ? residual_saved(r64) : residual(r64);
 #pragma unroll
     for (int k = 0; k < NG; ++k) {
       const int l0 = loc0[k];
