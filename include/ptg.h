@@ -138,7 +138,8 @@ typedef struct {
                           steps): 1 Jacobi; 2 two damped-Jacobi steps (omega = 0.8) on each CTA's
                           slab alone, z = (2S - S A_s S) r with S = omega D^-1 and A_s the slab's
                           diagonal block of A (symmetric, no communication); 0 the library's
-                          default.  Other values: PTG_EINVAL. */
+                          default: 1 on cluster launches, 2 on cooperative-grid launches (whose
+                          reductions go through global memory).  Other values: PTG_EINVAL. */
 } ptg_solve;
 
 typedef struct {

@@ -149,7 +149,7 @@ size_t twolevel_bytes(const ptg_op* op, int precision, int kind, int cs, int tl_
 // omega lambda_max stays below 1.8 < 2 for every step size.
 constexpr float kVcycleOmega = 0.8f;
 // Default preconditioner of FP32 CG solves without a two-level form (ptg_solve.local_steps = 0):
-// Jacobi.  The two slab-local steps cut the fine-step CG iterations (128 x 128 pass: 34 -> 27
+// Jacobi on cluster launches, the two slab-local steps on cooperative-grid launches (run()).  The two slab-local steps cut the fine-step CG iterations (128 x 128 pass: 34 -> 27
 // primal, 31 -> 24.5 adjoint) but cost more than they save there (fine kernels 7.6 + 8.5 ->
 // 8.6 + 9.4 ms); on high-contrast 512 x 512 designs they pay (one-shot design iteration 13.2 ->
 // 11.5 s).
@@ -381,6 +381,9 @@ int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream, int stats_ki
   }
   twolevel_params(op, prec, P, plan.twolevel && !P.plt ? (plan.vc ? TL_VCYCLE : TL_ADDITIVE) : TL_NONE);
   P.keep_ax = plan.keep_ax ? 1 : 0;
+  // on cooperative-grid launches every reduction is a global-memory round trip of several
+  // microseconds, so the default trades two slab-local sweeps for fewer CG iterations there
+  if (op->sv.local_steps == 0 && plan.wide) P.local_steps = 2;
   op->last_stream = stream;
   PTG_CUDA(launch_stepper(P, plan, prec, ntasks, stream));
   return PTG_OK;
