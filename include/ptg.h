@@ -140,6 +140,18 @@ typedef struct {
                           diagonal block of A (symmetric, no communication); 0 the library's
                           default: 1 on cluster launches, 2 on cooperative-grid launches (whose
                           reductions go through global memory).  Other values: PTG_EINVAL. */
+    int initial_guess; /* where each CG of a time step starts (only iteration counts change):
+                          1 plain: a fine step from the state it steps from, a batched coarse step
+                          (ptg_coarse_sweep) from the state it propagates;
+                          n in 2..4 predicted: a fine step from the polynomial extrapolation
+                          through the last n states of its slice (n = 2: 2 x_{j-1} - x_{j-2};
+                          fewer in the first steps of every slice, chained runs included, so a
+                          slice recomputed alone repeats its solves bit for bit; the states are
+                          kept in a workspace of the op, n rows per slice), a
+                          batched coarse step from the guess state at the other end of its slice
+                          (u_{s+1} for G_pri, lambda_{Ms+1} for G_adj), which the previous
+                          one-shot iteration left close to the answer;
+                          0 the library's default (4).  Other values: PTG_EINVAL. */
 } ptg_solve;
 
 typedef struct {
@@ -239,6 +251,8 @@ int ptg_fine_propagate_slices(ptg_op* op, int schedule, int s0, int ns,
  *             T_{k-M} is read as T_0 for s = 0.  X_field = V_lam [Ntau+1][Nn],
  *             X_aux = V_g [Ntau+1][Ne] (rows s+1 are read); outputs G_field [Ntau][Nn],
  *             G_aux [Ntau][Ne].  T_hist is the full history [Nt+1][Nn]; Theta_d points to Theta.
+ *   Every row of X_field is read (the start of one step, the initial guess of another: see
+ *   ptg_solve.initial_guess), so G_field must not overlap X_field.
  */
 int ptg_coarse_sweep(ptg_op* op, int direction, const double* X_field, const double* X_aux,
                      const double* T_hist, const double* Theta_d,

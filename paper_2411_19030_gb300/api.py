@@ -72,6 +72,8 @@ class SolveConfig:
     coarse_mesh: bool = False        # coarse propagators on the 2h mesh (Sec. 7.3 future work)
     local_steps: int = 0             # FP32 CG without two-level: 1 Jacobi, 2 two slab-local Jacobi
     #                                  steps, 0 the library default
+    initial_guess: int = 0           # CG start of a step: 1 plain, 2 extrapolated / the neighbouring
+    #                                  guess state, 0 the library default (2)
 
 
 class Operator:
@@ -110,7 +112,7 @@ class Operator:
                 "fp32_refine_all": PTG_FP32_REFINE_ALL}[solve.precision]
         s = _ffi.ptg_solve(prec, solve.rtol, solve.inner_rtol, solve.cg_iters_max, solve.refine_max,
                            twolevel_code(solve.twolevel), int(solve.grid_wide), int(solve.smooth_steps),
-                           int(solve.coarse_mesh), int(solve.local_steps))
+                           int(solve.coarse_mesh), int(solve.local_steps), int(solve.initial_guess))
         self._dir = np.ascontiguousarray(dirichlet, dtype=np.uint8).reshape(-1)
         if self._dir.size != self.Nn:
             raise ValueError("dirichlet mask must have (nx+1)(ny+1) entries")

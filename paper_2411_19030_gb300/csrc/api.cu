@@ -36,6 +36,7 @@ struct ptg_op {
   double *q_elem = nullptr, *q_time = nullptr;
   uint8_t* dirichlet = nullptr;
   double* sens_partial = nullptr;
+  double* lam_prev = nullptr;  // [n Ntau][Nn] ring of the last n states of each fine task (primal or adjoint)
   double* scratch = nullptr;   // [2] small device scalars
   // grid-wide launches (one system over every SM): reduction partials, barrier, halo rows,
   // two-level partials
@@ -315,6 +316,12 @@ int choose_plan(ptg_op* op, int precision, int kind, int ntasks, Plan* out) {
   return PTG_OK;
 }
 
+// States the initial guess of a fine step is extrapolated through (ptg_solve.initial_guess).
+// Measured in FP64 Jacobi CG to 1e-10 on the 128 x 128 case (dt = 1/1024): 36 iterations per
+// step from the last state, 21 linear, 14 quadratic, 8 cubic.
+constexpr int kInitialGuessDefault = 4;
+int guess_states(const ptg_solve& sv) { return sv.initial_guess > 0 ? sv.initial_guess : kInitialGuessDefault; }
+
 void base_params(const ptg_op* op, StepParams& P) {
   std::memset(&P, 0, sizeof(P));
   P.nx = op->g.nx;
@@ -360,6 +367,9 @@ void base_params(const ptg_op* op, StepParams& P) {
   P.objective = op->tm.objective;
   P.hist_rows = 0;
   P.keep_ax = 1;
+  P.extrap = guess_states(op->sv);
+  P.guess_next = P.extrap > 1;
+  P.prev_field = op->lam_prev;
 }
 
 int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream, int stats_kind = -1) {
@@ -395,7 +405,7 @@ void ptg_op_free(ptg_op* op);
 
 void free_all(ptg_op* op) {
   void* ptrs[] = {op->k, op->c, op->dk, op->dc, op->wE, op->nodew, op->fload,
-                  op->q_elem, op->q_time, op->dirichlet, op->sens_partial, op->scratch, op->stats,
+                  op->q_elem, op->q_time, op->dirichlet, op->sens_partial, op->lam_prev, op->scratch, op->stats,
                   op->g_red, op->g_bar, op->g_halo, op->g_tl,
                   op->tl_Ac, op->tl_band, op->tl_X, op->tl_Ainv,
                   op->mesh_rho, op->mesh_XH, op->mesh_FH, op->mesh_GH, op->mesh_SH, op->mesh_YH,
@@ -437,6 +447,7 @@ int mesh_coarse_sweep(ptg_op* op, int direction, const double* X_field, const do
   P.ns = Ntau;
   P.in_field = op->mesh_FH;
   P.in_aux = op->mesh_zero;
+  P.guess_next = 0;                       // the injected states hold no u_{s+1}
   P.out_field = op->mesh_YH;
   P.out_aux = op->mesh_aux;
   if (direction == PTG_PRIMAL) {
@@ -478,6 +489,7 @@ int create_mesh(ptg_op* op, const uint8_t* dirichlet_h, const double* q_elem_h, 
   tH.dt = op->dtau;
   ptg_solve sH = op->sv;
   sH.coarse_mesh = 0;
+  sH.initial_guess = 1;   // it runs coarse kinds only, and from injected states that hold no u_{s+1}
   std::vector<uint8_t> dH(NnH);
   for (int J = 0; J <= nyH; ++J)
     for (int I = 0; I <= nxH; ++I) dH[J * (nxH + 1) + I] = dirichlet_h[2 * J * (nx + 1) + 2 * I];
@@ -602,6 +614,7 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
   if (solve->smooth_steps < 0 || solve->smooth_steps > 16) return PTG_EINVAL;
   if (solve->coarse_mesh != 0 && solve->coarse_mesh != 1) return PTG_EINVAL;
   if (solve->local_steps < 0 || solve->local_steps > 2) return PTG_EINVAL;
+  if (solve->initial_guess < 0 || solve->initial_guess > kMaxExtrap) return PTG_EINVAL;
   if (solve->coarse_mesh && (grid->nx % 2 || grid->ny % 2 || grid->nx < 4 || grid->ny < 4)) return PTG_EINVAL;
   if (!(solve->rtol > 0.0) || solve->cg_iters_max < 1 || solve->refine_max < 1 || !(solve->inner_rtol >= 0.0))
     return PTG_EINVAL;
@@ -646,6 +659,8 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
   A(&op->q_time, (time->Nt + 1) * sizeof(double));
   A(&op->dirichlet, op->Nn);
   A(&op->sens_partial, (size_t)op->sens_chunks * op->Ne * sizeof(double));
+  if (guess_states(*solve) > 1)
+    A(&op->lam_prev, (size_t)guess_states(*solve) * time->Ntau * op->Nn * sizeof(double));
   // two-level preconditioner: aggregates of m x m nodes, m the smallest multiple of 4 giving
   // at most kCoarseMaxAgg aggregates per direction
   if (solve->twolevel) {
@@ -994,6 +1009,7 @@ constexpr int kPhases = 10;
 struct BatchBuf {
   double *T_hist, *U_T, *U_th, *V_l, *V_g, *U_T_new, *U_th_new, *V_l_new, *V_g_new;
   double *F_T, *F_th, *G_T, *G_th, *F_l, *F_g, *G_l, *G_g, *rho;
+  double* lam_prev;   // [n Ntau][Nn] fine-step initial guesses (null when the op starts plainly)
 };
 
 struct PhasePlan {
@@ -1053,6 +1069,7 @@ StepParams phase_params(const ptg_batch* b, int d, int ph, int cs, int tl_mode, 
   P.kind = phase_kind(ph);
   P.stats_kind = P.kind;
   P.keep_ax = keep_ax ? 1 : 0;
+  P.prev_field = B.lam_prev;   // the batch's own workspace: an op may appear twice
   P.s0 = 0;
   P.ns = op->tm.Ntau;
   P.hist = B.T_hist;
@@ -1268,6 +1285,8 @@ int ptg_batch_create(ptg_op* const* ops, int nops, ptg_batch** out) {
     A(&B.F_T, T * Nn); A(&B.F_th, T); A(&B.G_T, T * Nn); A(&B.G_th, T);
     A(&B.F_l, T * Nn); A(&B.F_g, T * Ne); A(&B.G_l, T * Nn); A(&B.G_g, T * Ne);
     A(&B.rho, Ne);
+    B.lam_prev = nullptr;
+    if (guess_states(op->sv) > 1) A(&B.lam_prev, guess_states(op->sv) * T * Nn);
     b->bufs.push_back(B);
   }
   if (e == cudaSuccess) e = cudaMalloc(&b->queue, kPhases * sizeof(int));

@@ -38,6 +38,7 @@ struct DevStats {
 // (offsets -1 and +4) are always inside the allocation.
 constexpr int kGroup = 4;
 constexpr int kSlack = 4;
+constexpr int kMaxExtrap = 4;   // most states an extrapolated initial guess goes through
 inline __host__ __device__ int padded_width(int nx) { return ((nx + 3 + kGroup - 1) / kGroup) * kGroup; }
 
 // Per-node FP64 weights of a symmetric 9-point operator (padded node grid, rows iy = -1..ny+1):
@@ -106,6 +107,11 @@ struct StepParams {
   float tl_omega;            // damping of the V-cycle's Jacobi smoother
   int local_steps;           // FP32 CG without two-level: 1 Jacobi, 2 two slab-local damped-Jacobi steps
   int keep_ax;               // 1: keep A x of the last residual (saves one FP64 stencil per step), 8 B per node
+  int extrap;                // fine kinds: start each CG from the extrapolation through the slice's
+                             // last `extrap` states (1: the last state alone; up to kMaxExtrap)
+  int guess_next;            // coarse kinds: start each CG from the guess state at the slice's other end
+  double* prev_field;        // fine kinds with extrap > 1: [extrap tasks][Nn] ring of each task's last
+                             // states (or null: every step starts from the last state)
   int tl_nu;                 // V-cycle smoothing: <= 1 one global Jacobi step before and after; k >= 2 k
                              // slab-local steps before and after
   // one system over a whole cooperative grid (GridComm): global scratch of the op

@@ -414,6 +414,42 @@ struct Stepper {
     __syncthreads();
   }
 
+  // Polynomial extrapolation in time of the initial guess: with x64 = x_1 (the last state) and
+  // X[i-2] = x_i, i = 2..n, the states of the n previous equidistant steps (global node vectors),
+  // x64 becomes the value at the next step of the polynomial of degree n-1 through them,
+  //   n = 2: 2 x_1 - x_2;  n = 3: 3 x_1 - 3 x_2 + x_3;  n = 4: 4 x_1 - 6 x_2 + 4 x_3 - x_4,
+  // on the owned rows and both halo rows.  x64's halo rows hold the neighbours' x_1, so every
+  // CTA evaluates the same expression on the same operands and the halos stay exact: no
+  // exchange is needed.  If wr is given, x_1 is first saved there on the owned rows (the
+  // adjoint's ring of states; wr is none of the X).  Ends with __syncthreads.
+  __device__ void extrapolate_x64(int n, const double* const* X, double* __restrict__ wr) {
+    ax_valid = false;
+    __syncthreads();
+    const int nn = P.nx + 1;
+    const int rows = sb.R + 2;
+    for (int t = threadIdx.x; t < rows * nn; t += blockDim.x) {
+      const int row = t / nn, ix = t - row * nn;
+      const int g = sb.r0 - 1 + row;
+      if (g >= 0 && g <= P.ny) {
+        const int gi = g * nn + ix;
+        double& x = x64[row * sb.W + ix + 1];
+        const double x1 = x;
+        if (wr && row >= 1 && row <= sb.R) wr[gi] = x1;
+        if (n < 2) continue;
+        double v;
+        if (n == 2) {
+          v = fma(2.0, x1, -X[0][gi]);
+        } else if (n == 3) {
+          v = fma(3.0, x1 - X[0][gi], X[1][gi]);
+        } else {
+          v = fma(4.0, x1 + X[1][gi], -fma(6.0, X[0][gi], X[2][gi]));
+        }
+        x = P.dirichlet[gi] ? 0.0 : v;
+      }
+    }
+    __syncthreads();
+  }
+
   // Store the owned nodes of x64 to a global node vector.
   __device__ void store_x64(double* __restrict__ dst) const {
 #pragma unroll
@@ -1163,11 +1199,29 @@ struct Stepper {
     if (P.chained) {                              // a sequential run also records its start
       if (double* row = hist_row(M * sa)) store_x64(row);
     }
+    const int nring = P.extrap;
+    double* ring = nring > 1 && P.prev_field ? P.prev_field + (size_t)task * nring * P.Nn : nullptr;
+    int saved = 0;                                // states of this slice in the ring
     for (int s = sa; s < sb_end; ++s) {
       for (int j = M * s + 1; j <= M * (s + 1); ++j) {
         const double qj = P.q_time[j];
         build_rhs([&](int g) { return qj * P.fload[g]; });
-        solve(j, true);
+        // initial guess: the polynomial extrapolation through T_{j-1} (in x64) .. T_{j-n}, kept in
+        // a ring of P.extrap rows per task (T_k in row k mod P.extrap; step j writes row
+        // (j-1) mod P.extrap and reads the others).  Each slice starts afresh, in a chained run
+        // too, so that a slice recomputed alone from its start state (checkpointed
+        // differentiation) repeats every solve bit for bit.
+        if (ring) {
+          if (j == M * s + 1) saved = 0;
+          const int n = min(saved + 1, nring);
+          const double* X[kMaxExtrap - 1];
+          for (int i = 2; i <= n; ++i) X[i - 2] = ring + (size_t)((j - i) % nring) * P.Nn;
+          extrapolate_x64(n, X, ring + (size_t)((j - 1) % nring) * P.Nn);
+          ++saved;
+          solve(j, false);
+        } else {
+          solve(j, true);
+        }
         const double sp = pnorm_p();
         if (threadIdx.x == 0) theta = accumulate_theta(theta, sp * inv_norm);  // used by thread 0 only
         if (double* row = hist_row(j)) store_x64(row);
@@ -1190,6 +1244,7 @@ struct Stepper {
       const double qj = P.q_time[j];
       build_rhs([&](int g) { return qj * P.fload[g]; });
     }
+    if (P.guess_next) load_x64(P.in_field + (size_t)(s + 1) * P.Nn);   // start from the guess u_{s+1}
     solve(j);
     const double sp = pnorm_p();
     store_x64(P.out_field + (size_t)s * P.Nn);
@@ -1248,8 +1303,16 @@ struct Stepper {
     set_operator(false);
     load_x64(P.in_field + (size_t)(s_hi + 1) * P.Nn);
     const double* gsrc = P.in_aux + (size_t)(s_hi + 1) * P.Ne;
+    // initial guess: the extrapolation through lambda_{j+1} (in x64) .. lambda_{j+n}, kept in a
+    // ring of P.extrap rows per task, lambda_k in row k mod P.extrap; step j writes row
+    // (j+1) mod P.extrap and reads the n-1 <= P.extrap-1 others, so no CTA writes a row that a
+    // neighbour reads in the same step
+    const int nring = P.extrap;
+    double* ring = nring > 1 && P.prev_field ? P.prev_field + (size_t)task * nring * P.Nn : nullptr;
+    int saved = 0;   // states of this slice in the ring
     for (int s = s_hi; s >= s_lo; --s) {
       double* gdst = P.out_aux + (size_t)s * P.Ne;
+      saved = 0;     // each slice starts afresh, as in the primal
       for (int j = M * (s + 1); j >= M * s + 1; --j) {
         const double* Tj = hist_row(j);
         const double* Tjm = hist_row(j - 1);
@@ -1258,7 +1321,16 @@ struct Stepper {
           return;
         }
         build_rhs([&](int g) { return scale * ipow(Tj[g], P.p_int - 1); });
-        solve(j, true);
+        if (ring) {
+          const int n = min(saved + 1, nring);
+          const double* X[kMaxExtrap - 1];
+          for (int i = 2; i <= n; ++i) X[i - 2] = ring + (size_t)((j + i) % nring) * P.Nn;
+          extrapolate_x64(n, X, ring + (size_t)((j + 1) % nring) * P.Nn);
+          ++saved;
+          solve(j, false);
+        } else {
+          solve(j, true);
+        }
         accumulate_g(Tj, Tjm, P.dt, (double)P.Nt, gsrc, gdst, nullptr, nullptr);
         gsrc = gdst;
         __syncthreads();
@@ -1278,6 +1350,7 @@ struct Stepper {
     set_operator(true);
     load_x64(P.in_field + (size_t)(s + 1) * P.Nn);
     build_rhs([&](int g) { return scale * ipow(Tk[g], P.p_int - 1); });
+    if (P.guess_next) load_x64(P.in_field + (size_t)s * P.Nn);   // start from the guess lambda_s
     solve(kidx);
     accumulate_g(Tk, Tkm, P.dtau, (double)P.Ntau, P.in_aux + (size_t)(s + 1) * P.Ne, P.out_aux + (size_t)s * P.Ne,
                  nullptr, nullptr);
