@@ -53,7 +53,8 @@ def _args(nx=4, ny=4, Nt=4, Ntau=2, p=8.0, prec=0):
     return g, m, t, s, d
 
 
-@pytest.mark.parametrize("bad", ["ntau", "p_odd", "p_frac", "nx", "precision", "objective"])
+@pytest.mark.parametrize("bad", ["ntau", "p_odd", "p_frac", "nx", "precision", "objective", "guess_high",
+                                 "guess_negative", "local_steps"])
 def test_invalid_problem_rejected_on_host(lib, bad):
     g, m, t, s, d = _args()
     if bad == "ntau":
@@ -68,6 +69,12 @@ def test_invalid_problem_rejected_on_host(lib, bad):
         s.precision = 7
     elif bad == "objective":
         t.objective = 2
+    elif bad == "guess_high":
+        s.initial_guess = 5
+    elif bad == "guess_negative":
+        s.initial_guess = -1
+    elif bad == "local_steps":
+        s.local_steps = 3
     h = ctypes.c_void_p()
     rc = lib.ptg_op_create(ctypes.byref(g), ctypes.byref(m), ctypes.byref(t), ctypes.byref(s), d.ctypes.data,
                            None, None, 0, ctypes.byref(h))
