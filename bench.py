@@ -432,9 +432,9 @@ def run_gpu(args):
 
 # DRAM bytes per launch (read + write) from the committed ncu captures of the 128x128 pass in
 # the default precision (profiles/); a kernel changed since has no entry.
-NCU_TRAFFIC_BYTES = {"fine_primal": 8.272896e6 + 107.914240e6, "coarse_primal": 6.861824e6 + 0.0,
-                     "correct_primal": 11.294208e6 + 0.0, "fine_adjoint": 148.258560e6 + 1.730560e6,
-                     "coarse_adjoint": 15.275264e6 + 0.0, "correct_adjoint": 24.137984e6 + 0.0}
+NCU_TRAFFIC_BYTES = {"fine_primal": 7.991040e6 + 107.795712e6, "coarse_primal": 6.969088e6 + 0.0,
+                     "correct_primal": 11.175168e6 + 0.0, "fine_adjoint": 148.516608e6 + 2.119936e6,
+                     "coarse_adjoint": 15.237376e6 + 0.0, "correct_adjoint": 24.019200e6 + 0.0}
 
 # FP64 peak of the chip (nominal, the GB300 table of the profiling notes: 1.25 TFLOP/s) and the
 # FLOPs of one FP64 CG iteration per unknown: the 9-point stencil (9 FMA), the p, q, d, r

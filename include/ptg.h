@@ -150,7 +150,10 @@ typedef struct {
                           kept in a workspace of the op, n rows per slice), a
                           batched coarse step from the guess state at the other end of its slice
                           (u_{s+1} for G_pri, lambda_{Ms+1} for G_adj), which the previous
-                          one-shot iteration left close to the answer;
+                          one-shot iteration left close to the answer, and a correction-sweep
+                          step (ptg_parareal_correct) from G_old[s] plus the previous step's
+                          increment G(x^new) - G(x^old), i.e. u_s - F[s-1] (primal) or
+                          v_{s+1} - F[s+1] (adjoint), instead of G_old[s] alone;
                           0 the library's default (4).  Other values: PTG_EINVAL. */
 } ptg_solve;
 

@@ -414,6 +414,27 @@ struct Stepper {
     __syncthreads();
   }
 
+  // Correction sweeps: x64 = G + (x64 - Fm) on the owned and both halo rows, with x64 holding
+  // the corrected state the step propagates and Fm the fine result of the step before it.
+  // Every CTA evaluates the same expression on the same operands (x64's halos are exact), so
+  // the halos stay exact.  Ends with __syncthreads.
+  __device__ void load_x64_increment(const double* __restrict__ G, const double* __restrict__ Fm) {
+    ax_valid = false;
+    __syncthreads();
+    const int nn = P.nx + 1;
+    const int rows = sb.R + 2;
+    for (int t = threadIdx.x; t < rows * nn; t += blockDim.x) {
+      const int row = t / nn, ix = t - row * nn;
+      const int g = sb.r0 - 1 + row;
+      if (g >= 0 && g <= P.ny) {
+        const int gi = g * nn + ix;
+        double& x = x64[row * sb.W + ix + 1];
+        x = P.dirichlet[gi] ? 0.0 : G[gi] + (x - Fm[gi]);
+      }
+    }
+    __syncthreads();
+  }
+
   // Polynomial extrapolation in time of the initial guess: with x64 = x_1 (the last state) and
   // X[i-2] = x_i, i = 2..n, the states of the n previous equidistant steps (global node vectors),
   // x64 becomes the value at the next step of the polynomial of degree n-1 through them,
@@ -1280,7 +1301,12 @@ struct Stepper {
         const double qj = P.q_time[j];
         build_rhs([&](int g) { return qj * P.fload[g]; });
       }
-      load_x64(P.G_field + (size_t)s * P.Nn);   // initial guess G(u_s^old)
+      // initial guess G(u_s^old) + (G(u_{s-1}^new) - G(u_{s-1}^old)): the previous step's
+      // increment, which is u_s^new - F[s-1] by the correction itself (plain: G(u_s^old))
+      if (P.extrap > 1 && s > 0)
+        load_x64_increment(P.G_field + (size_t)s * P.Nn, P.F_field + (size_t)(s - 1) * P.Nn);
+      else
+        load_x64(P.G_field + (size_t)s * P.Nn);
       solve(j);
       const double sp = pnorm_p();
       apply_correction(P.F_field + (size_t)s * P.Nn, P.G_field + (size_t)s * P.Nn,
@@ -1394,7 +1420,12 @@ struct Stepper {
       const double* Tk = P.hist + (size_t)kidx * P.Nn;
       const double* Tkm = P.hist + (size_t)kprev * P.Nn;
       build_rhs([&](int g) { return scale * ipow(Tk[g], P.p_int - 1); });
-      load_x64(P.G_field + (size_t)s * P.Nn);   // initial guess G(v_{s+1}^old)
+      // initial guess G(v_{s+1}^old) + (G(v_{s+2}^new) - G(v_{s+2}^old)) = G[s] + v_{s+1}^new - F[s+1]
+      // (plain: G(v_{s+1}^old))
+      if (P.extrap > 1 && s + 1 < P.Ntau)
+        load_x64_increment(P.G_field + (size_t)s * P.Nn, P.F_field + (size_t)(s + 1) * P.Nn);
+      else
+        load_x64(P.G_field + (size_t)s * P.Nn);
       solve(kidx);
       // g_s = g_{s+1} - (1/Ntau) term(lambda_G) + F_g[s] - G_g[s]
       accumulate_g(Tk, Tkm, P.dtau, (double)P.Ntau, P.out_aux + (size_t)(s + 1) * P.Ne, P.out_aux + (size_t)s * P.Ne,

@@ -21,7 +21,7 @@ from tests.problems import make_problem
 pytestmark = pytest.mark.gpu
 
 FINE = ("fine_primal", "fine_adjoint")
-COARSE = ("coarse_primal", "coarse_adjoint")
+COARSE = ("coarse_primal", "coarse_adjoint", "correct_primal", "correct_adjoint")
 
 
 @pytest.fixture(scope="module", autouse=True)
