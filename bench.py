@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -79,7 +80,8 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        # the raw samples (the JSON line carries their summary); PTG_CLOCKS_DIR picks the folder
+        self.path = os.path.join(os.environ.get("PTG_CLOCKS_DIR", tempfile.gettempdir()), f"clocks_gpu{gpu_index}.csv")
 
     def __enter__(self):
         try:
