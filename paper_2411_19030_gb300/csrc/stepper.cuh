@@ -442,7 +442,7 @@ struct Stepper {
   // on the owned rows and both halo rows.  x64's halo rows hold the neighbours' x_1, so every
   // CTA evaluates the same expression on the same operands and the halos stay exact: no
   // exchange is needed.  If wr is given, x_1 is first saved there on the owned rows (the
-  // adjoint's ring of states; wr is none of the X).  Ends with __syncthreads.
+  // slice's ring of states; wr is none of the X).  Ends with __syncthreads.
   __device__ void extrapolate_x64(int n, const double* const* X, double* __restrict__ wr) {
     ax_valid = false;
     __syncthreads();
