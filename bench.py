@@ -146,7 +146,7 @@ def run_gpu(args):
     n, Nt, Ntau, dt, p = w["n"], w["Nt"], w["Ntau"], w["dt"], w["p"]
     N_free = (n + 1) ** 2 - int(sink.sum())
     solve = SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=2000, refine_max=8,
-                        twolevel=args.twolevel, smooth_steps=args.smooth, local_steps=args.local)
+                        twolevel=args.twolevel, smooth_steps=args.smooth, local_steps=args.local, initial_guess=args.initial_guess)
     op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink, solve=solve, device=local)
     seq_op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink,
                       solve=SolveConfig("fp64", rtol=1e-13, cg_iters_max=4000, refine_max=8), device=local)
@@ -305,7 +305,7 @@ def run_gpu(args):
             vname = "fp32_refine_all" if args.precision == "fp32_refine" else "fp32_refine"
             v_op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink,
                             solve=SolveConfig(vname, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=2000,
-                                              refine_max=8, twolevel=args.twolevel, smooth_steps=args.smooth, local_steps=args.local), device=local)
+                                              refine_max=8, twolevel=args.twolevel, smooth_steps=args.smooth, local_steps=args.local, initial_guess=args.initial_guess), device=local)
             v_buf = PassBuffers(v_op)
             for a_, b_ in ((v_buf.U_T, buf.U_T), (v_buf.U_th, buf.U_th), (v_buf.V_l, buf.V_l),
                            (v_buf.V_g, buf.V_g)):
@@ -331,7 +331,7 @@ def run_gpu(args):
         # like the main steps, with the error of its one-shot estimate against the sequential result
         c_op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink,
                         solve=SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=2000,
-                                          refine_max=8, twolevel=args.twolevel, smooth_steps=args.smooth, local_steps=args.local,
+                                          refine_max=8, twolevel=args.twolevel, smooth_steps=args.smooth, local_steps=args.local, initial_guess=args.initial_guess,
                                           coarse_mesh=True), device=local)
         c_buf = PassBuffers(c_op)
         for a_, b_ in ((c_buf.U_T, buf.U_T), (c_buf.U_th, buf.U_th), (c_buf.V_l, buf.V_l), (c_buf.V_g, buf.V_g)):
@@ -390,7 +390,7 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": f"{WORKLOAD}: 128x128 grid, Nt=1024, Ntau=32 (M=32), p=8, SIMP k, warm start from "
                                "the sequential coarse states of a design 1% away",
-                   "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel, "smooth_steps": args.smooth, "local_steps": args.local, "l2": "flushed between steps (256 MB write)",
+                   "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel, "smooth_steps": args.smooth, "local_steps": args.local, "initial_guess": args.initial_guess, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "wall_s": wall},
         "per_kernel_ms": kind_ms,
@@ -531,9 +531,10 @@ def run_loop(args):
     a_max, r_fil, beta, eta = 0.4, 0.03, 32.0, 0.5
     op = Operator(n, n, h, w["material"], Nt, Ntau, dt, w["p"], sink,
                   solve=SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=4000, refine_max=8,
-                                    twolevel=args.twolevel, smooth_steps=args.smooth, local_steps=args.local, coarse_mesh=args.coarse_mesh))
+                                    twolevel=args.twolevel, smooth_steps=args.smooth, local_steps=args.local, initial_guess=args.initial_guess, coarse_mesh=args.coarse_mesh))
     true_op = Operator(n, n, h, w["material"], Nt, Ntau, dt, w["p"], sink,
-                       solve=SolveConfig("fp64", rtol=1e-12, cg_iters_max=8000, refine_max=8))
+                       solve=SolveConfig("fp64", rtol=1e-12, cg_iters_max=8000, refine_max=8,
+                                         initial_guess=args.initial_guess))
     design = DesignMap(n, n, h, r_fil, beta, eta)
     loop = OneShotLoop(op, design, a_max, move=0.2, true_op=true_op)
     # uniform chi with P(chi) = a_max (the filter keeps a uniform field)
@@ -565,7 +566,7 @@ def run_loop(args):
         "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
         "config": {"workload": f"loop{n}: {n}x{n} grid, Nt={Nt}, Ntau={Ntau}, p=8, SIMP k, a_max={a_max}, "
                                f"r_fil={r_fil}, beta={beta}, eta={eta}, MMA move 0.2",
-                   "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel, "smooth_steps": args.smooth, "local_steps": args.local,
+                   "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel, "smooth_steps": args.smooth, "local_steps": args.local, "initial_guess": args.initial_guess,
                    "coarse_propagator": "2h mesh (Sec. 7.3 future work)" if args.coarse_mesh else "h mesh"},
         "first_iteration_sequential_ms": ms[0],
         "fine_dof_steps_per_s": 2.0 * N_free * Nt / (np.mean(oneshot) * 1e-3),
@@ -598,7 +599,7 @@ def run_batch48(args):
     device = torch.device("cuda", 0)
     designs = W.batch48()
     solve = SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=2000, refine_max=8,
-                        twolevel=args.twolevel, smooth_steps=args.smooth)
+                        twolevel=args.twolevel, smooth_steps=args.smooth, initial_guess=args.initial_guess)
     mats = W.MATERIALS["simp_k"]
     ops, dof = [], 0.0
     for d in designs:
@@ -661,6 +662,7 @@ def run_batch48(args):
                       "config": {"workload": "batch48: 48 designs, sides 64/96/128/192/256, (Nt, Ntau) in "
                                              "(512,16)/(1024,32)/(2048,64), rho ~ U(0.2,0.8)",
                                  "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel,
+                                 "initial_guess": args.initial_guess,
                                  "l2": "flushed between steps (256 MB write)"},
                       "clocks": clk.summary()}), flush=True)
 
@@ -685,8 +687,9 @@ def run_sweep(args):
     h, dt = 1.0 / n, 1.0 / Nt
     sink = W.dirichlet_bottom_centre(n, n, h)
     qt = W.q_time_paper(Nt, dt)
-    solve = SolveConfig("fp64", rtol=1e-12, cg_iters_max=8000, refine_max=8, coarse_mesh=args.coarse_mesh)
-    seq_solve = SolveConfig("fp64", rtol=1e-12, cg_iters_max=8000, refine_max=8)
+    solve = SolveConfig("fp64", rtol=1e-12, cg_iters_max=8000, refine_max=8, coarse_mesh=args.coarse_mesh,
+                        initial_guess=args.initial_guess)
+    seq_solve = SolveConfig("fp64", rtol=1e-12, cg_iters_max=8000, refine_max=8, initial_guess=args.initial_guess)
     stream = torch.cuda.current_stream()
 
     def timed(fn):
@@ -723,7 +726,7 @@ def run_sweep(args):
             del buf, op
     print(json.dumps({"metric": "k-iteration Parareal vs sequential FP64 GPU time stepping (paper test case)",
                       "config": {"workload": "paper100: 100x100, Nt=480, Table 1, q(t) of Eq. 5.1, bottom sink, p=20",
-                                 "precision": "fp64", "rtol": 1e-12,
+                                 "precision": "fp64", "rtol": 1e-12, "initial_guess": args.initial_guess,
                                  "coarse_propagator": "2h mesh (Sec. 7.3 future work)" if args.coarse_mesh else "h mesh"},
                       "paper_context": "MATLAB, CPU threads: Parareal speedup up to 5x at 16 threads with one iteration",
                       "rows": rows}), flush=True)
@@ -821,6 +824,9 @@ def main():
                          "0: the library default)")
     ap.add_argument("--local", type=int, default=0,
                     help="FP32 CG without two-level: 1 Jacobi, 2 two slab-local Jacobi steps, 0 the library default")
+    ap.add_argument("--initial-guess", type=int, default=0,
+                    help="CG starts of the time steps (ptg_solve.initial_guess): 1 plain, 2-4 extrapolated "
+                         "through that many states, 0 the library default")
     ap.add_argument("--coarse-mesh", action="store_true",
                     help="--sweep / --loop: coarse propagators on the 2h mesh (Sec. 7.3 future work)")
     ap.add_argument("--sweep-ntau", default="5,10,16,20,30,32,48,60,80,96,120,160,240",
