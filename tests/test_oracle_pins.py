@@ -270,6 +270,36 @@ def test_adjoint_correction_independent_of_carried_g():
     assert rel(a["V"][1], b["V"][1]) < 1e-12
 
 
+@pytest.mark.parametrize("prop", ["F_adj", "G_adj"])
+def test_adjoint_propagators_are_affine_in_the_state_and_linear_in_the_source_scale(prop):
+    """lambda solves (C/dt + K) lambda_j = C/dt lambda_{j+1} + c T_j^(p-1) with c = Theta^(1-p)/Ne
+    (Eq. 4.6), and g accumulates a term linear in lambda (Eq. 4.7).  So F_adj and G_adj split
+    into a part driven by the state and a part proportional to c: their difference for two
+    objectives does not depend on the state, and the state-free part scales with c."""
+    from oracle.parareal import F_adj, G_adj
+    prob = make_problem(8, 6, Nt=12, Ntau=3, dt=1 / 12, material="table1", sink="left_wide")
+    op = Operator(prob, W.rho_uniform(8, 6, 5, 0.1, 0.9))
+    T_hist, _ = sequential_primal(op)
+    rng = np.random.default_rng(11)
+    lam = rng.standard_normal(prob.Nn)
+    lam[np.asarray(prob.dirichlet, bool)] = 0.0
+    g = rng.standard_normal(prob.Ne)
+    zl, zg = np.zeros(prob.Nn), np.zeros(prob.Ne)
+    fn = F_adj if prop == "F_adj" else G_adj
+    s = 1
+    Th1, Th2 = 0.7, 1.3
+    c1, c2 = Th1 ** (1 - prob.p), Th2 ** (1 - prob.p)
+    a1 = fn(op, s, lam, g, T_hist, Th1)
+    a2 = fn(op, s, lam, g, T_hist, Th2)
+    z1 = fn(op, s, zl, zg, T_hist, Th1)
+    z2 = fn(op, s, zl, zg, T_hist, Th2)
+    for i in range(2):
+        # the state-driven part cancels in the difference of two objectives
+        assert rel(a1[i] - a2[i], z1[i] - z2[i]) < 1e-10
+        # the state-free part is proportional to c
+        assert rel(z2[i], (c2 / c1) * z1[i]) < 1e-12
+
+
 # ------------------------------------------------------------------ symmetry, objective identities
 
 def test_mirror_symmetry_about_mid_height():
