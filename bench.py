@@ -394,6 +394,10 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "wall_s": wall},
         "per_kernel_ms": kind_ms,
+        # the metric per F phase: N_free * Nt fine DOF-steps in the fine primal and in the fine
+        # adjoint propagator alone, beside the whole pass (2 N_free Nt per pass)
+        "phase_dof_steps_per_s": {
+            k: N_free * Nt / (max(kind_ms.get(k, 0.0), 1e-9) * 1e-3) for k in ("fine_primal", "fine_adjoint")},
         "cg": {"solves": stats["solves"], "cg_iters": stats["cg_iters"], "refinements": stats["refinements"],
                "mean_cg_per_solve": stats["cg_iters"] / max(1, stats["solves"]),
                "by_kind": {k: {"cg_per_solve": v["cg_iters"] / max(1, v["solves"]),
