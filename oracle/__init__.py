@@ -29,7 +29,8 @@ Pins (``tests/test_oracle_*.py``, run with ``-m "not gpu"``): the separable-eige
 closed form, the discrete energy balance, the dense all-at-once solve, central
 finite differences of the gradient, Parareal's exactness after N_tau iterations,
 the M = 1 and N_tau = 1 degenerate cases, the one-shot fixed point, mirror symmetry,
-the constant-field objective identity and the homogeneity of Theta in q; for the
+the constant-field objective identity, the homogeneity of Theta in q, and the adjoint
+propagators' affinity in the state and linearity in the source scale (Eq. 4.6-4.7); for the
 modified objective of Sec. 7.1, Theta~ = Theta^p and the gradient identity
 grad Theta = Theta^(1-p)/p grad Theta~; for PLT (G = 0, Sec. 7), its fixed point and its
 exactness after N_tau iterations; for the design update, the filter's averaging and its
