@@ -131,3 +131,25 @@ def test_coarse_step_converges_to_the_fine_step_at_second_order():
         b, _ = CoarseMesh(op).G_pri(0, T, 0.0)
         errs.append(np.max(np.abs(a - b)))
     assert errs[0] / errs[1] > 3.0, errs
+
+
+@pytest.mark.parametrize("material", ["simp_k", "table1"])
+def test_galerkin_product_of_a_nonuniform_design_is_a_nine_point_stencil_on_2h(material):
+    """P^T A P couples each 2h node only to its eight 2h neighbours for any design (the bilinear
+    interpolation of a 2h element stays inside it), and it is symmetric positive definite on
+    the free 2h nodes: the coarse level of a multigrid cycle stays a 9-point operator."""
+    prob = make_problem(10, 8, Nt=4, Ntau=2, sink="left_wide", material=material)
+    op = Operator(prob, W.rho_uniform(10, 8, 41, 0.01, 1.0))
+    A = (op.C / prob.dtau + op.K).tocsr()
+    P = prolongation(prob)
+    G = (P.T @ A @ P).tocoo()
+    nxH = prob.nx // 2
+    iy, ix = np.divmod(G.row, nxH + 1)
+    jy, jx = np.divmod(G.col, nxH + 1)
+    nz = np.abs(G.data) > 0
+    assert np.all(np.abs(iy - jy)[nz] <= 1) and np.all(np.abs(ix - jx)[nz] <= 1)
+    Gd = G.toarray()
+    free = np.abs(np.diag(Gd)) > 0
+    Gf = Gd[np.ix_(free, free)]
+    assert np.allclose(Gf, Gf.T, rtol=0, atol=1e-14 * np.max(np.abs(Gf)))
+    assert np.min(np.linalg.eigvalsh(Gf)) > 0
