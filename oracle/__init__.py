@@ -28,7 +28,9 @@ Modules
 Pins (``tests/test_oracle_*.py``, run with ``-m "not gpu"``): the separable-eigenmode
 closed form, the discrete energy balance, the dense all-at-once solve, central
 finite differences of the gradient, Parareal's exactness after N_tau iterations,
-the M = 1 and N_tau = 1 degenerate cases, the one-shot fixed point, mirror symmetry,
+the M = 1 and N_tau = 1 degenerate cases, the coarse propagators G_pri and G_adj at M > 1
+chained over every slice against the sequential primal and adjoint passes of the coarsened
+problem (Ntau steps of dtau, loads at the coarse points), the one-shot fixed point, mirror symmetry,
 the constant-field objective identity, the homogeneity of Theta in q, and the adjoint
 propagators' affinity in the state and linearity in the source scale (Eq. 4.6-4.7); for the
 modified objective of Sec. 7.1, Theta~ = Theta^p and the gradient identity

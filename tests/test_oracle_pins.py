@@ -228,6 +228,79 @@ def test_fig1_indexing_Nt15_Ntau3():
     assert moved == [6, 7, 8, 9, 10, 15]
 
 
+def _coarsened(prob, q_time):
+    """The problem the coarse propagator steps when the substitution of Sec. 4.4 (dt -> dtau,
+    Nt -> Ntau, n -+ 1 -> n -+ M) is applied to Alg. 1-2: Ntau backward-Euler steps of size
+    dtau whose loads sit at the coarse points t_{Ms}."""
+    Ntau = prob.Ntau
+    return make_problem(prob.nx, prob.ny, Nt=Ntau, Ntau=Ntau, dt=prob.dtau, p=prob.p,
+                        material=prob.material, sink=np.asarray(prob.dirichlet), h=prob.h,
+                        q_time=np.asarray(q_time)[::prob.M].copy(), T0=prob.T0)
+
+
+@pytest.mark.parametrize("M,Ntau", [(3, 4), (5, 3)])
+def test_coarse_primal_propagator_chained_is_sequential_stepping_of_the_coarsened_problem(M, Ntau):
+    """G_pri (Sec. 4.4) chained from u_0 over every slice is backward Euler with step dtau = M dt
+    and the load at the new coarse point, and its theta accumulates with the divisor Ntau Ne.
+    That is the sequential primal pass (Alg. 1, Eq. 2.7, Eq. 2.11) of the problem with Ntau
+    steps of size dtau and the loads q(t_{Ms}), computed here by the plain sequential stepper.
+    The paper's time-varying load (Eq. 5.1) and capacity SIMP (Table 1) make a wrong load
+    index or a wrong divisor visible."""
+    from oracle.parareal import G_pri
+    Nt = M * Ntau
+    dt = 0.6 / Nt
+    qt = W.q_time_paper(Nt, dt)
+    prob = make_problem(7, 5, Nt=Nt, Ntau=Ntau, dt=dt, material="table1", sink="left_wide", q_time=qt)
+    op = Operator(prob, W.rho_uniform(7, 5, 21, 0.1, 0.9))
+    cprob = _coarsened(prob, qt)
+    Tc, thc = sequential_primal(Operator(cprob, op.rho))
+    T, th = np.zeros(prob.Nn), 0.0
+    for s in range(Ntau):
+        T, th = G_pri(op, s, T, th)
+        assert rel(T, Tc[s + 1]) < 1e-13
+        assert abs(th - thc[s + 1]) <= 1e-13 * thc[s + 1]
+    # the pin is not vacuous: the coarse chain differs from the fine run at the same times
+    T_fine, _ = sequential_primal(op)
+    assert rel(T_fine[Nt], Tc[Ntau]) > 1e-4
+
+
+@pytest.mark.parametrize("M,Ntau", [(3, 4), (5, 3)])
+def test_coarse_adjoint_propagator_chained_is_sequential_adjoint_of_the_coarsened_problem(M, Ntau):
+    """G_adj (Sec. 4.4) solves for lambda_k, k = Ms+1, from lambda_{k+M} with the source at T_k,
+    and adds to g the Eq. 4.7 bracket of (T_k - T_{k-M})/dtau with the divisor Ntau (T_{k-M}
+    read as T_0 for s = 0).  Given a history whose rows Ms+1 hold the coarsened problem's
+    temperatures T'_{s+1} and whose row 0 holds T_0, the chain from v_Ntau = 0 must be the
+    sequential discrete adjoint (Alg. 2) of the coarsened problem: lambda'_{s+1} and g'_{s+1}.
+    Every other history row holds noise, so reading a wrong row fails, and the capacity SIMP
+    of Table 1 makes the T_{k-M} term count."""
+    from oracle.parareal import G_adj
+    from oracle.stepping import sequential_adjoint
+    Nt = M * Ntau
+    dt = 0.6 / Nt
+    qt = W.q_time_paper(Nt, dt)
+    rng = np.random.default_rng(8)
+    T0 = rng.uniform(0.0, 0.3, (7 + 1) * (5 + 1))
+    prob = make_problem(7, 5, Nt=Nt, Ntau=Ntau, dt=dt, material="table1", sink="left_wide", q_time=qt, T0=T0)
+    prob.T0[np.asarray(prob.dirichlet, bool)] = 0.0
+    op = Operator(prob, W.rho_uniform(7, 5, 22, 0.1, 0.9))
+    cprob = _coarsened(prob, qt)
+    cop = Operator(cprob, op.rho)
+    Tc, thc = sequential_primal(cop)
+    Theta = thc[-1]
+    lam_c, g_c = sequential_adjoint(cop, Tc, Theta)
+    T_hist = rng.uniform(1.0, 2.0, (Nt + 1, prob.Nn))
+    T_hist[0] = Tc[0]
+    for s in range(Ntau):
+        T_hist[M * s + 1] = Tc[s + 1]
+    lam, g = np.zeros(prob.Nn), np.zeros(prob.Ne)
+    for s in range(Ntau - 1, -1, -1):
+        lam, g = G_adj(op, s, lam, g, T_hist, Theta)
+        assert rel(lam, lam_c[s + 1]) < 1e-12
+        assert rel(g, g_c[s + 1]) < 1e-11
+    # the dC/drho term is present: with unit capacity the gradient changes
+    assert np.max(np.abs(op.dc)) > 0
+
+
 def test_oneshot_fixed_point():
     """Alg. 3 warm start from the exact sequential coarse states of the same design returns the
     sequential history, objective and gradient (G(u^new) and G(u^old) cancel exactly)."""
