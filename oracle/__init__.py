@@ -12,8 +12,9 @@ Modules
                element matrices by Gauss quadrature, global K, C and load vectors.
 ``stepping``   Sec. 2.2 and 4.1: backward Euler (Eq. 2.7), the power-mean objective
                (Eq. 2.11), the discrete adjoint (Eq. 4.4-4.7) and the sequential pass.
-               Each linear solve is a banded Cholesky factorisation (factored once per
-               matrix) followed by two triangular solves.
+               Each linear solve is a direct factorisation (factored once per matrix) and
+               its triangular solves: banded Cholesky, or a sparse LU on grids whose band is
+               wider than 300 nodes.
 ``parareal``   Sec. 4.2-4.4, Algorithms 1-3: the propagators H, F, G, the modified
                (history-storing) forward Parareal, the reverse vanilla Parareal, the
                k-iteration scheme, the one-shot pass and the PLT variant (Sec. 7).

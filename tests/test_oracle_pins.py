@@ -410,3 +410,27 @@ def test_dirichlet_node_counts():
     """Centred 10% of the left edge, inclusive: 3 / 7 / 13 / 25 / 51 nodes for n = 32/64/128/256/512."""
     for n, cnt in ((32, 3), (64, 7), (128, 13), (256, 25), (512, 51)):
         assert int(W.dirichlet_left_centre(n, n, 1.0 / n).sum()) == cnt
+
+
+def test_sparse_lu_and_band_cholesky_give_the_same_passes():
+    """The oracle factors C/dt + K by banded Cholesky on narrow grids and by sparse LU on wide
+    ones (the band factor of a 512 x 512 grid takes minutes).  Both are direct solves of the
+    same systems, so the sequential pass and the one-shot pass agree to rounding."""
+    prob = make_problem(24, 18, Nt=12, Ntau=3, dt=0.4 / 12, material="table1", sink="left_wide",
+                        q_time=W.q_time_paper(12, 0.4 / 12))
+    rho = W.rho_uniform(24, 18, 41, 0.05, 0.95)
+    out = {}
+    for solver in ("band", "lu"):
+        op = Operator(prob, rho, solver=solver)
+        assert op._factor(prob.dt)[0] == solver
+        U, V, seq = coarse_states_from_sequential(Operator(prob, W.rho_warm_perturb(rho, seed=42, amp=0.05),
+                                                           solver=solver))
+        out[solver] = (sequential_pass(op), oneshot_pass(op, U, V))
+    (sb, ob), (sl, ol) = out["band"], out["lu"]
+    assert rel(sl["T_hist"], sb["T_hist"]) < 1e-13 and rel(sl["grad"], sb["grad"]) < 1e-12
+    assert rel(ol["T_hist"], ob["T_hist"]) < 1e-13 and rel(ol["grad"], ob["grad"]) < 1e-12
+    # the automatic choice switches at the band width
+    from oracle.stepping import BAND_MAX
+    wide = make_problem(BAND_MAX + 1, 4, Nt=2, dt=0.1)
+    assert Operator(wide, np.full(wide.Ne, 0.5))._factor(0.1)[0] == "lu"
+    assert Operator(prob, rho)._factor(prob.dt)[0] == "band"
