@@ -6,9 +6,14 @@
 // array for the lifetime of the process.  The host never dereferences the array's name:
 // in host code it is only a stand-in for the device symbol, so its device address is looked
 // up once per device with cudaGetSymbolAddress and passed to the kernel.
+//
+// The per-element accumulation (sens_element_sum) and the chunk reduction are the ones of
+// ptg_sensitivities; only the source of dk/drho and dc/drho differs (evaluated from rho here,
+// read from the op's workspace there).
 #include <algorithm>
 #include <cstdio>
 #include <mutex>
+#include "ptg_device.cuh"
 #include "ptg_internal.h"
 
 namespace {
@@ -23,9 +28,10 @@ std::mutex g_mu;
 double* g_scratch_ptr[kMaxDevices] = {};
 
 // Partial sums over a contiguous chunk of time steps of
-//   lambda_j,e^T ( dk_e Ke T_j,e + dc_e/dt Me (T_j - T_{j-1})_e ),
+//   lambda_j,e^T ( dk_e Ke T_j,e + dc_e/dt Me (T_j - T_{j-1})_e )   (sens_element_sum),
 // with dk_e and dc_e evaluated from rho (Eq. 2.5-2.6 differentiated) inside the kernel, so
-// the call needs no coefficient workspace.
+// the call needs no coefficient workspace.  A value of rho outside [0, 1] (or NaN) is taken
+// as 0, as the assembly does (which also records the error in its op's status word).
 __global__ void sens_noalloc_kernel(int nx, int ny, double h, double dt, ptg_material m, const double* __restrict__ rho,
                                     const double* __restrict__ lam, int j0, int j1, const double* __restrict__ T,
                                     int hist_j0, int steps_per_chunk, double* __restrict__ partial) {
@@ -36,53 +42,20 @@ __global__ void sens_noalloc_kernel(int nx, int ny, double h, double dt, ptg_mat
   const int ja = j0 + chunk * steps_per_chunk;
   const int jb = min(j1, ja + steps_per_chunk - 1);
   const int ey = e / nx, ex = e % nx;
-  const int g0 = ey * nn + ex;
-  const double r = rho[e];
+  double r = rho[e];
+  if (!(r >= 0.0 && r <= 1.0)) r = 0.0;
+  const bool has_dc = m.c0 != m.cmin;
   const double dke = (m.k0 == m.kmin) ? 0.0 : m.pk * (m.k0 - m.kmin) * pow(r, m.pk - 1.0);
-  const double dce = (m.c0 == m.cmin) ? 0.0 : m.pc * (m.c0 - m.cmin) * pow(r, m.pc - 1.0) / dt;
-  const double h2 = h * h / 36.0;
-  double acc = 0.0;
-  if (ja <= jb) {
-    const double* Tp = T + (size_t)(ja - 1 - hist_j0) * Nn;
-    double psw = Tp[g0], pse = Tp[g0 + 1], pne = Tp[g0 + nn + 1], pnw = Tp[g0 + nn];
-    for (int j = ja; j <= jb; ++j) {
-      const double* Tj = T + (size_t)(j - hist_j0) * Nn;
-      const double* Lj = lam + (size_t)(j - j0) * Nn;
-      const double tsw = Tj[g0], tse = Tj[g0 + 1], tne = Tj[g0 + nn + 1], tnw = Tj[g0 + nn];
-      const double lsw = Lj[g0], lse = Lj[g0 + 1], lne = Lj[g0 + nn + 1], lnw = Lj[g0 + nn];
-      // Ke = (1/6)[4 -1 -2 -1; -1 4 -1 -2; -2 -1 4 -1; -1 -2 -1 4], local order SW, SE, NE, NW
-      const double ksw = 4.0 * tsw - tse - 2.0 * tne - tnw;
-      const double kse = -tsw + 4.0 * tse - tne - 2.0 * tnw;
-      const double kne = -2.0 * tsw - tse + 4.0 * tne - tnw;
-      const double knw = -tsw - 2.0 * tse - tne + 4.0 * tnw;
-      double term = dke * (lsw * ksw + lse * kse + lne * kne + lnw * knw) / 6.0;
-      if (dce != 0.0) {
-        // Me = (h^2/36)[4 2 1 2; 2 4 2 1; 1 2 4 2; 2 1 2 4]
-        const double dsw = tsw - psw, dse = tse - pse, dne = tne - pne, dnw = tnw - pnw;
-        const double msw = 4.0 * dsw + 2.0 * dse + dne + 2.0 * dnw;
-        const double mse = 2.0 * dsw + 4.0 * dse + 2.0 * dne + dnw;
-        const double mne = dsw + 2.0 * dse + 4.0 * dne + 2.0 * dnw;
-        const double mnw = 2.0 * dsw + dse + 2.0 * dne + 4.0 * dnw;
-        term += dce * (lsw * msw + lse * mse + lne * mne + lnw * mnw) * h2;
-      }
-      acc += term;
-      psw = tsw; pse = tse; pne = tne; pnw = tnw;
-    }
-  }
+  const double dce = has_dc ? m.pc * (m.c0 - m.cmin) * pow(r, m.pc - 1.0) / dt : 0.0;
+  const double acc = ja <= jb ? ptg::sens_element_sum(ey * nn + ex, nn, Nn, h * h / 36.0, dke, dce, has_dc, lam, j0,
+                                                      T, hist_j0, ja, jb)
+                              : 0.0;
   partial[(size_t)chunk * Ne + e] = acc;
 }
 
-// grad_e += -(1/Nt) * (sum of the chunk partials in chunk order)
-__global__ void sens_noalloc_reduce_kernel(int Ne, int nchunks, double inv_nt, const double* __restrict__ partial,
-                                           double* __restrict__ grad) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= Ne) return;
-  double s = 0.0;
-  for (int c = 0; c < nchunks; ++c) s += partial[(size_t)c * Ne + e];
-  grad[e] -= inv_nt * s;
-}
-
-// Device address of the scratch array for the current device (looked up once per device).
+// Device address of the scratch array for the current device, looked up once per device and
+// kept for the life of the process (so the entry point must not be used after a
+// cudaDeviceReset of that device, which reloads the module).
 cudaError_t scratch_for_device(double** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -110,6 +83,11 @@ int ptg_sensitivities_noalloc(int nx, int ny, double h, int Nt, double dt, const
   if (nx < 1 || ny < 1 || Nt < 1 || !(h > 0.0) || !(dt > 0.0)) return PTG_EINVAL;
   if (j0 < 1 || j1 < j0 || j1 > Nt) return PTG_EINVAL;
   if (j0 - 1 < hist_j0 || j1 >= hist_j0 + hist_rows) return PTG_EINVAL;
+  // the material rules of ptg_op_create: positive conductivities and capacities
+  if (!(mat->k0 > 0.0) || !(mat->kmin > 0.0) || !(mat->c0 > 0.0) || !(mat->cmin > 0.0)) {
+    ptg::set_last_error("ptg_sensitivities_noalloc: k0, kmin, c0 and cmin must be positive");
+    return PTG_EINVAL;
+  }
   const long long Ne = (long long)nx * ny;
   if (Ne > kScratchDoubles) {
     char msg[200];
@@ -119,8 +97,9 @@ int ptg_sensitivities_noalloc(int nx, int ny, double h, int Nt, double dt, const
     return PTG_EINVAL;
   }
   double* scratch = nullptr;
-  if (scratch_for_device(&scratch) != cudaSuccess) {
-    ptg::set_last_error(cudaGetErrorString(cudaGetLastError()));
+  cudaError_t e = scratch_for_device(&scratch);
+  if (e != cudaSuccess) {
+    ptg::set_last_error(cudaGetErrorString(e));
     return PTG_ECUDA;
   }
   const int nsteps = j1 - j0 + 1;
@@ -131,10 +110,12 @@ int ptg_sensitivities_noalloc(int nx, int ny, double h, int Nt, double dt, const
   dim3 grid((unsigned)((Ne + 255) / 256), (unsigned)used);
   sens_noalloc_kernel<<<grid, 256, 0, stream>>>(nx, ny, h, dt, *mat, rho_d, lam_hist, j0, j1, T_hist, hist_j0, spc,
                                                 scratch);
-  if (cudaGetLastError() != cudaSuccess) return PTG_ECUDA;
-  sens_noalloc_reduce_kernel<<<(unsigned)((Ne + 255) / 256), 256, 0, stream>>>((int)Ne, used, 1.0 / Nt, scratch,
-                                                                              grad_d);
-  if (cudaGetLastError() != cudaSuccess) return PTG_ECUDA;
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = ptg::launch_sens_reduce((int)Ne, used, 1.0 / Nt, scratch, grad_d, stream);
+  if (e != cudaSuccess) {
+    ptg::set_last_error(cudaGetErrorString(e));
+    return PTG_ECUDA;
+  }
   return PTG_OK;
 }
 

@@ -180,4 +180,41 @@ __device__ __forceinline__ double ipow(double x, int e) {
   return r;
 }
 
+// Eq. 4.7, one element over the contiguous steps ja..jb (ja <= jb): the sum over j of
+//   lambda_j,e^T ( dke Ke T_j,e + dce Me (T_j - T_{j-1})_e ),
+// with dce already divided by the step size and Me = (h^2/36)[4 2 1 2; 2 4 2 1; 1 2 4 2; 2 1 2 4],
+// Ke = (1/6)[4 -1 -2 -1; -1 4 -1 -2; -2 -1 4 -1; -1 -2 -1 4] in the local order SW, SE, NE, NW.
+// g0 is the element's SW node, nn = nx + 1, Nn the node count; lambda_j is row j - j0 of lam and
+// T_j row j - hist_j0 of T.  T_{j-1} is carried in registers, so each step reads lambda_j and T_j
+// once.  The capacity term is evaluated only when has_dc is set.
+__device__ __forceinline__ double sens_element_sum(int g0, int nn, int Nn, double h2, double dke, double dce,
+                                                   bool has_dc, const double* __restrict__ lam, int j0,
+                                                   const double* __restrict__ T, int hist_j0, int ja, int jb) {
+  double acc = 0.0;
+  const double* Tp = T + (size_t)(ja - 1 - hist_j0) * Nn;
+  double psw = Tp[g0], pse = Tp[g0 + 1], pne = Tp[g0 + nn + 1], pnw = Tp[g0 + nn];
+  for (int j = ja; j <= jb; ++j) {
+    const double* Tj = T + (size_t)(j - hist_j0) * Nn;
+    const double* Lj = lam + (size_t)(j - j0) * Nn;
+    const double tsw = Tj[g0], tse = Tj[g0 + 1], tne = Tj[g0 + nn + 1], tnw = Tj[g0 + nn];
+    const double lsw = Lj[g0], lse = Lj[g0 + 1], lne = Lj[g0 + nn + 1], lnw = Lj[g0 + nn];
+    const double ksw = 4.0 * tsw - tse - 2.0 * tne - tnw;
+    const double kse = -tsw + 4.0 * tse - tne - 2.0 * tnw;
+    const double kne = -2.0 * tsw - tse + 4.0 * tne - tnw;
+    const double knw = -tsw - 2.0 * tse - tne + 4.0 * tnw;
+    double term = dke * (lsw * ksw + lse * kse + lne * kne + lnw * knw) / 6.0;
+    if (has_dc) {
+      const double dsw = tsw - psw, dse = tse - pse, dne = tne - pne, dnw = tnw - pnw;
+      const double msw = 4.0 * dsw + 2.0 * dse + dne + 2.0 * dnw;
+      const double mse = 2.0 * dsw + 4.0 * dse + 2.0 * dne + dnw;
+      const double mne = dsw + 2.0 * dse + 4.0 * dne + 2.0 * dnw;
+      const double mnw = 2.0 * dsw + dse + 2.0 * dne + 4.0 * dnw;
+      term += dce * (lsw * msw + lse * mse + lne * mne + lnw * mnw) * h2;
+    }
+    acc += term;
+    psw = tsw; pse = tse; pne = tne; pnw = tnw;
+  }
+  return acc;
+}
+
 }  // namespace ptg

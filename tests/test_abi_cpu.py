@@ -88,3 +88,15 @@ def test_null_op_rejected(lib):
     assert lib.ptg_objective_from_modified(None, None, None, None, None, None) == _ffi.PTG_EINVAL
     assert lib.ptg_parareal_correct(None, 1, None, None, None, None, None, None, None, None, None) == _ffi.PTG_EINVAL
     assert lib.ptg_batch_oneshot_pass(None, 0, None) == _ffi.PTG_EINVAL
+
+
+@pytest.mark.parametrize("field", ["k0", "kmin", "c0", "cmin"])
+def test_noalloc_rejects_non_positive_materials_on_host(lib, field):
+    """The entry point without allocation applies ptg_op_create's material rule before it touches
+    the device (the pointers here are never dereferenced)."""
+    m = _ffi.ptg_material(1.0, 1e-3, 3.0, 1.0, 0.5, 2.0)
+    setattr(m, field, 0.0)
+    fake = ctypes.c_void_p(16)
+    rc = lib.ptg_sensitivities_noalloc(4, 4, 0.25, 4, 0.1, ctypes.byref(m), fake, fake, 1, 4, fake, 0, 5, fake, None)
+    assert rc == _ffi.PTG_EINVAL
+    assert b"positive" in lib.ptg_last_error()
