@@ -164,33 +164,57 @@ def run_gpu(args):
     kinds = ["assemble", "fine_primal", "coarse_primal", "correct_primal", "fine_adjoint", "coarse_adjoint",
              "correct_adjoint"]
 
+    overlap = args.overlap and op.can_overlap_adjoint_coarse()
+    side, hi = op.side_stream(), op.sweep_stream()
+    split = buf.split_parts() if overlap else None
+
     def timed_step(ev):
-        """One one-shot design iteration with an event pair around every ABI call."""
+        """One one-shot design iteration with an event pair around every ABI call.  With the
+        overlap (the library default for this workload) the adjoint coarse propagators run as
+        their two Theta-free parts on a second stream beside the forward correction sweep, and
+        the main stream only combines them once Theta is known; ev[8], ev[9] bracket the parts."""
         from paper_2411_19030_gb300 import PTG_ADJOINT, PTG_PRIMAL
         e = ev
         e[0].record(stream)
         op.assemble(rho)
+        buf.U_T_new[0].copy_(buf.U_T[0])
+        buf.U_th_new[0].copy_(buf.U_th[0])
         e[1].record(stream)
         op.fine_propagate_slices(buf.U_T, buf.U_th, buf.F_T, buf.F_th, T_hist=buf.T_hist)
         e[2].record(stream)
         op.coarse_sweep(PTG_PRIMAL, buf.U_T, buf.U_th, buf.G_T, buf.G_th)
         e[3].record(stream)
-        buf.U_T_new[0].copy_(buf.U_T[0])
-        buf.U_th_new[0].copy_(buf.U_th[0])
-        op.parareal_correct(PTG_PRIMAL, buf.F_T, buf.F_th, buf.G_T, buf.G_th, buf.U_T_new, buf.U_th_new,
-                            T_hist=buf.T_hist)
-        e[4].record(stream)
         Theta = buf.U_th_new[Ntau:Ntau + 1]
-        op.adjoint_sweep(buf.T_hist, Theta, buf.V_l, buf.V_g, buf.F_l, buf.F_g)
-        e[5].record(stream)
-        op.coarse_sweep(PTG_ADJOINT, buf.V_l, buf.V_g, buf.G_l, buf.G_g, T_hist=buf.T_hist, Theta=Theta)
+        if overlap:
+            # as paper_2411_19030_gb300.api.oneshot_pass with the overlap: the forward sweep on a
+            # high-priority stream, the two parts of G_adj beside it
+            hi.wait_event(e[3])
+            op.parareal_correct(PTG_PRIMAL, buf.F_T, buf.F_th, buf.G_T, buf.G_th, buf.U_T_new, buf.U_th_new,
+                                T_hist=buf.T_hist, stream=hi)
+            e[4].record(hi)
+            side.wait_event(e[3])
+            e[8].record(side)
+            op.coarse_adjoint_split(buf.V_l, buf.V_g, buf.T_hist, *split, stream=side)
+            e[9].record(side)
+            stream.wait_event(e[4])
+            op.adjoint_sweep(buf.T_hist, Theta, buf.V_l, buf.V_g, buf.F_l, buf.F_g)
+            e[5].record(stream)
+            stream.wait_event(e[9])
+            op.coarse_adjoint_combine(Theta, *split, buf.G_l, buf.G_g)
+        else:
+            op.parareal_correct(PTG_PRIMAL, buf.F_T, buf.F_th, buf.G_T, buf.G_th, buf.U_T_new, buf.U_th_new,
+                                T_hist=buf.T_hist)
+            e[4].record(stream)
+            op.adjoint_sweep(buf.T_hist, Theta, buf.V_l, buf.V_g, buf.F_l, buf.F_g)
+            e[5].record(stream)
+            op.coarse_sweep(PTG_ADJOINT, buf.V_l, buf.V_g, buf.G_l, buf.G_g, T_hist=buf.T_hist, Theta=Theta)
         e[6].record(stream)
         op.parareal_correct(PTG_ADJOINT, buf.F_l, buf.F_g, buf.G_l, buf.G_g, buf.V_l_new, buf.V_g_new,
                             T_hist=buf.T_hist, Theta=Theta)
         e[7].record(stream)
 
     def new_events():
-        return [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+        return [torch.cuda.Event(enable_timing=True) for _ in range(10)]
 
     for _ in range(args.warmup):
         flush.fill_(1.0)
@@ -214,16 +238,24 @@ def run_gpu(args):
         dist.barrier()
     per_kind = np.zeros(len(kinds))
     step_ms = []
+    side_ms = []
     for ev in evs:
         d = [ev[i].elapsed_time(ev[i + 1]) for i in range(7)]
         per_kind += np.array(d)
         step_ms.append(ev[0].elapsed_time(ev[7]))
+        if overlap:
+            side_ms.append(ev[8].elapsed_time(ev[9]))
     ms = float(np.sum(step_ms)) / args.steps
     stats = op.stats()
     ms = slowest_rank_ms(ms, device)
     dof_steps = 2.0 * N_free * Nt
     value = job_throughput(dof_steps, world, ms)
     kind_ms = {k: float(v / args.steps) for k, v in zip(kinds, per_kind)}
+    if overlap:
+        # the adjoint coarse kind's solves ran on the side stream; the main stream only waited for
+        # them and combined the parts (the time it shows for that kind)
+        kind_ms["coarse_adjoint_combine_main"] = kind_ms.pop("coarse_adjoint")
+        kind_ms["coarse_adjoint"] = float(np.mean(side_ms))
 
     if args.extras:
         # end to end through the public API with host buffers: H2D of rho, D2H of Theta and grad
@@ -280,15 +312,35 @@ def run_gpu(args):
         # error of the precision pattern: the same one-shot pass in FP64 (CG and all sums FP64,
         # rtol 1e-13; this path matches the CPU oracle to 1e-10 in the parity tests), untimed
         prec = {}
+        fp64_arm = None
         if args.precision != "fp64":
             f64_op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink,
                               solve=SolveConfig("fp64", rtol=1e-13, cg_iters_max=8000, refine_max=8), device=local)
             f64_buf = PassBuffers(f64_op)
             for a_, b_ in ((f64_buf.U_T, buf.U_T), (f64_buf.U_th, buf.U_th), (f64_buf.V_l, buf.V_l), (f64_buf.V_g, buf.V_g)):
                 a_.copy_(b_)
-            f64_op.assemble(rho)
-            Th64, g64 = oneshot_pass(f64_op, f64_buf)
-            torch.cuda.synchronize()
+            # timed like the main steps: the FP64 half of the configuration (FP64 vs FP32 CG + FP64
+            # refinement); its comparator is sequential FP64 stepping at the same rtol 1e-13
+            f64_ms = []
+            for i in range(args.warmup + args.steps):
+                flush.fill_(1.0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                f64_op.assemble(rho)
+                Th64, g64 = oneshot_pass(f64_op, f64_buf)
+                b.record(stream)
+                b.synchronize()
+                if i >= args.warmup:
+                    f64_ms.append(a.elapsed_time(b))
+            f64_mean = slowest_rank_ms(float(np.mean(f64_ms)), device)
+            f64_st = f64_op.stats()
+            fp64_arm = {"what": "the same one-shot pass with every CG and sum in FP64 (rtol 1e-13), timed like the "
+                                "main steps", "ms_per_step": f64_mean, "value": job_throughput(dof_steps, world, f64_mean),
+                        "unit": UNIT, "sequential_fp64_rtol_1e-13_ms": tight_ms,
+                        "speedup_vs_sequential_fp64_same_rtol": tight_ms / f64_mean,
+                        "mixed_over_fp64_speedup": f64_mean / ms,
+                        "cg_per_solve": {k: round(v["cg_iters"] / max(1, v["solves"]), 2)
+                                         for k, v in f64_st["by_kind"].items() if v["solves"]}}
 
             def relmax(a, b):
                 return float((a - b).abs().max() / b.abs().max())
@@ -379,10 +431,11 @@ def run_gpu(args):
                  "paper_context": "MATLAB on 32 CPU threads: 3.81x (one-shot) vs 10.8x (G = 0) over its sequential run"}
     else:
         e2e = seq_ms = None
-        seq_stats, prec, probe, variant, coarse_mesh = {}, {}, None, None, None
+        seq_stats, prec, probe, variant, coarse_mesh, fp64_arm = {}, {}, None, None, None, None
         err_theta = err_grad = None
 
-    roof = roofline(kind_ms, stats, w, N_free, args)
+    roof = roofline(kind_ms, stats, N_free, args.steps, args.precision)
+    streaming = streaming_256(args, flush, stream, device) if (args.extras and args.c3) else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -390,6 +443,7 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": f"{WORKLOAD}: 128x128 grid, Nt=1024, Ntau=32 (M=32), p=8, SIMP k, warm start from "
                                "the sequential coarse states of a design 1% away",
+                   "overlap_adjoint_coarse": overlap,
                    "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel, "smooth_steps": args.smooth, "local_steps": args.local, "initial_guess": args.initial_guess, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "wall_s": wall},
@@ -420,6 +474,8 @@ def run_gpu(args):
         "bottleneck_probe": probe,
         "coarse_mesh_variant": coarse_mesh,
         "precision_variant": variant,
+        "fp64_oneshot": fp64_arm,
+        "streaming_256": streaming,
         "e2e": None if e2e is None else {"value": world * dof_steps / (e2e * 1e-3), "unit": UNIT, "ms": e2e,
                                          "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": (1 + n * n) * 8},
         # per pass: assembly 3 kernels (+ 4 for the two-level coarse set-up) + 6 stepper launches
@@ -436,13 +492,38 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-# DRAM bytes per launch (read + write) from the committed ncu captures of the 128x128 pass in
-# the default precision (profiles/); a kernel changed since has no entry.
-NCU_TRAFFIC_BYTES = {"fine_primal": 7.991040e6 + 107.795712e6, "coarse_primal": 6.969088e6 + 0.0,
-                     "correct_primal": 11.175168e6 + 0.0, "fine_adjoint": 148.516608e6 + 2.119936e6,
-                     "coarse_adjoint": 15.237376e6 + 0.0, "correct_adjoint": 24.019200e6 + 0.0}
+# DRAM bytes per launch (read + write) of the 128x128 pass in the default precision, from one
+# ncu capture (profiles/).  They hold only for the kernel source they were taken from: the hash
+# of the stepper sources at capture time is stored beside them, and a run whose sources hash
+# differently reports traffic as null.
+NCU_TRAFFIC = {
+    "captured": "2026-12-03",
+    "sources_sha16": None,
+    "bytes": {"fine_primal": 7.991040e6 + 107.795712e6, "coarse_primal": 6.969088e6 + 0.0,
+              "correct_primal": 11.175168e6 + 0.0, "fine_adjoint": 148.516608e6 + 2.119936e6,
+              "coarse_adjoint": 15.237376e6 + 0.0, "correct_adjoint": 24.019200e6 + 0.0},
+}
+STEPPER_SOURCES = ("stepper.cuh", "comm.cuh", "ptg_device.cuh", "stepper_inst.cu", "stepper_launch.cuh", "plan.cu")
 
-# FP64 peak of the chip (nominal, the GB300 table of the profiling notes: 1.25 TFLOP/s) and the
+
+def stepper_sources_sha16() -> str:
+    import hashlib
+    hsh = hashlib.sha256()
+    for name in STEPPER_SOURCES:
+        with open(os.path.join(ROOT, "paper_2411_19030_gb300", "csrc", name), "rb") as f:
+            hsh.update(f.read())
+    return hsh.hexdigest()[:16]
+
+
+def ncu_traffic(kind: str):
+    """(bytes per launch or None, provenance) of the stored ncu DRAM figure of a kernel."""
+    sha = stepper_sources_sha16()
+    if NCU_TRAFFIC["sources_sha16"] != sha or kind not in NCU_TRAFFIC["bytes"]:
+        return None, f"no ncu capture of the current stepper sources ({sha})"
+    return NCU_TRAFFIC["bytes"][kind], f"ncu capture of {NCU_TRAFFIC['captured']}, stepper sources {sha}"
+
+
+# FP64 peak of the chip (nominal, 1.25 TFLOP/s; MEASURED_PEAKS.json holds no FP64 figure) and the
 # FLOPs of one FP64 CG iteration per unknown: the 9-point stencil (9 FMA), the p, q, d, r
 # updates (4 FMA), three dot products (3 FMA) and the preconditioned residual (1 FMA) = 17 FMA;
 # one FP64 residual evaluation per refinement sweep and per solve: stencil + subtraction + dot.
@@ -455,59 +536,163 @@ KIND_PRECISION = {"fp64": {k: "f64" for k in ("fine_primal", "coarse_primal", "c
                                                          "fine_adjoint", "coarse_adjoint", "correct_adjoint")},
                   "fp32_refine": {"fine_primal": "f32", "fine_adjoint": "f32", "coarse_primal": "f64",
                                   "correct_primal": "f64", "coarse_adjoint": "f64", "correct_adjoint": "f64"}}
+ADJOINT_KINDS = ("fine_adjoint", "coarse_adjoint", "correct_adjoint")
 
 
-def roofline(kind_ms: dict, stats: dict, w: dict, N_free: int, args) -> dict:
-    """Roofline entry of the dominant kernel (largest share of the step).
-
-    The stepper keeps every CG vector of a slice on chip (registers and shared memory of one
-    thread-block cluster), so its compulsory HBM traffic per launch is the state traffic only:
-    for a correction sweep, the F and G slice results read and the corrected states (and
-    history rows) written, 8 B per node each, N_tau times; for a fine propagator, the FP64
-    history (8 B per node per fine step, written by the primal, read once by the adjoint) plus
-    the slice start and end states.  A kernel whose CG runs in FP64 is bound by
-    the FP64 pipe of its SMs (1/58 of the FP32 rate on this chip): it is reported as "alu"
-    against the chip's FP64 peak with its algorithmic FLOPs (CG iterations and FP64 residuals
-    from the solver counters); an FP32-CG kernel is reported against HBM.
-    """
+def hbm_peak():
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    source = "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback 6800 GB/s"
-    dom = max((k for k in kind_ms if k != "assemble"), key=lambda k: kind_ms[k])
-    Nt, Ntau = w["Nt"], w["Ntau"]
-    nn = (w["n"] + 1) ** 2
-    bytes_per_launch = {
-        "fine_primal": 8.0 * nn * Nt + 16.0 * nn * Ntau,
-        "fine_adjoint": 8.0 * nn * Nt + 16.0 * nn * Ntau,      # each T_j read once (T_{j-1} reused)
-        "coarse_primal": 16.0 * nn * Ntau,
-        "coarse_adjoint": 32.0 * nn * Ntau,
-        "correct_primal": 32.0 * nn * Ntau,     # F, G read; X, history row written
-        "correct_adjoint": 40.0 * nn * Ntau,    # F, G read; X written; T_k, T_{k-M} read
-    }[dom]
-    traffic = NCU_TRAFFIC_BYTES.get(dom)
-    sec = kind_ms[dom] * 1e-3
-    if KIND_PRECISION[args.precision][dom] == "f64":
+    if "hbm_gbs" in peaks:
+        return float(peaks["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, a STREAM-style copy)"
+    return 6800.0, "fallback 6800 GB/s (no MEASURED_PEAKS.json)"
+
+
+def algorithmic_bytes(kind: str, st: dict, N_free: int, launches: int) -> float:
+    """Algorithmic HBM bytes of one launch of a stepper kind, counted per free DOF and solve as
+    if every CG vector streamed from memory: 16 B per solve (the previous state read, the new
+    state written, FP64), 36 B per CG iteration (p, x, r, Ap and the coefficients read; Ap, x,
+    r, p written), 28 B per FP64 refinement sweep (T, b and the coefficients read; r written),
+    and 8 B more per adjoint solve (the T_j read shared by the source and the sensitivity
+    sum).  The solver counters give the iterations and sweeps; `launches` is the number of
+    launches they cover."""
+    per_dof = (16.0 + (8.0 if kind in ADJOINT_KINDS else 0.0)) * st["solves"] + 36.0 * st["cg_iters"] \
+        + 28.0 * st["refinements"]
+    return N_free * per_dof / max(1, launches)
+
+
+def roofline(kind_ms: dict, stats: dict, N_free: int, launches: int, precision: str) -> dict:
+    """Roofline entry of the dominant kernel (largest share of the step) against the measured
+    HBM copy bandwidth, with the algorithmic bytes of algorithmic_bytes(); beside it every
+    stepper kernel's figure, and for an FP64-CG kernel its algorithmic FP64 FLOP rate against
+    the nominal FP64 peak (context: the chip runs FP64 at 1/58 of its FP32 rate)."""
+    hbm, source = hbm_peak()
+    per = {}
+    for k, ms in kind_ms.items():
+        st = stats["by_kind"].get(k)
+        if not st or not st["solves"]:
+            continue
+        b = algorithmic_bytes(k, st, N_free, launches)
+        gbs = b / (ms * 1e-3) / 1e9
+        per[k] = {"ms": ms, "algorithmic_bytes": b, "achieved_gbs": gbs, "frac": gbs / hbm,
+                  "solves": st["solves"] / max(1, launches), "cg_per_solve": st["cg_iters"] / max(1, st["solves"]),
+                  "refine_per_solve": st["refinements"] / max(1, st["solves"])}
+    dom = max(per, key=lambda k: per[k]["ms"])
+    d = per[dom]
+    traffic, tsrc = ncu_traffic(dom)
+    out = {"kernel": dom, "bound": "hbm", "achieved": d["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+           "frac": d["frac"], "traffic": traffic, "traffic_source": tsrc, "peak_source": source,
+           "algorithmic_bytes_per_launch": d["algorithmic_bytes"],
+           "bytes_rule": "N_free x (16 B per solve (+8 adjoint) + 36 B per CG iteration + 28 B per FP64 refinement "
+                         "sweep), from the kernel's own solver counters",
+           "per_kernel": per}
+    if KIND_PRECISION[precision][dom] == "f64":
         st = stats["by_kind"][dom]
         flops = N_free * (FLOPS_PER_CG_ITER * st["cg_iters"] + FLOPS_PER_RESIDUAL * (st["refinements"] + st["solves"]))
-        flops /= max(1, args.steps)               # counters cover the timed steps
-        achieved = flops / sec / 1e12
-        return {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "peak_source": "nominal FP64 peak of the chip (no measured FP64 peak in MEASURED_PEAKS.json)",
-                "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": bytes_per_launch,
-                "note": "FP64 CG of one sequential sweep on one 16-CTA cluster (16 of 152 SMs); ncu shows its "
-                        "FP64 pipe about half busy: the fraction of the whole chip's FP64 peak is small by "
-                        "construction of a sequential sweep"}
-    achieved = bytes_per_launch / sec / 1e9
-    return {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": traffic, "peak_source": source,
-            "algorithmic_bytes_per_launch": bytes_per_launch,
-            "note": "CG vectors stay on chip; latency of the per-iteration cluster reductions bounds the kernel "
-                    "(ncu: barrier, membar and shared-memory stalls), not HBM"}
+        flops /= max(1, launches)
+        tf = flops / (kind_ms[dom] * 1e-3) / 1e12
+        out["fp64_alu"] = {"achieved_tflops": tf, "peak_tflops": FP64_PEAK_TFLOPS, "frac": tf / FP64_PEAK_TFLOPS,
+                           "peak_source": "nominal FP64 peak of the chip (no measured FP64 peak)"}
+    out["note"] = ("the CG vectors of a system stay on chip, so the bytes are what a streaming CG would move; the "
+                   "correction sweeps are sequential (one system on one 16-CTA cluster at a time) and bound by the "
+                   "latency of their cluster barriers and by the FP64 pipes of 16 SMs, not by HBM")
+    return out
+
+
+def streaming_256(args, flush, stream, device) -> dict:
+    """The one-shot pass on the 256x256 workload (Nt = 2048 in 64 slices, rho ~ U(0, 1) seed 1, the
+    timed design 1% away from the warm start's, seed 1000), the grid size at which the history
+    (1.08 GB) and a slice batch no longer fit in L2: per-kernel CUDA-event times and each stepper
+    kernel's algorithmic bandwidth against the measured HBM copy bandwidth.  Warm start from the
+    sequential FP64 coarse states of the nearby design (untimed)."""
+    import torch
+
+    from paper_2411_19030_gb300 import Operator, PassBuffers, SolveConfig, sequential_pass
+    from paper_2411_19030_gb300 import PTG_ADJOINT, PTG_PRIMAL
+
+    w = W.workload("diff256")
+    n, Nt, Ntau, dt, p = w["n"], w["Nt"], w["Ntau"], w["dt"], w["p"]
+    sink = W.dirichlet_left_centre(n, n, w["h"])
+    N_free = (n + 1) ** 2 - int(sink.sum())
+    rho_old_np = W.rho_uniform(n, n, 1, 0.0, 1.0)
+    rho_np = W.rho_warm_perturb(rho_old_np, seed=1000, amp=0.01)
+    solve = SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=4000, refine_max=8,
+                        twolevel=args.twolevel, smooth_steps=args.smooth, local_steps=args.local,
+                        initial_guess=args.initial_guess)
+    op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink, solve=solve, device=device.index)
+    wop = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink,
+                   solve=SolveConfig("fp64", rtol=1e-12, cg_iters_max=8000, refine_max=8), device=device.index)
+    buf = PassBuffers(op)
+    rho_old = torch.tensor(rho_old_np, dtype=torch.float64, device=device)
+    rho = torch.tensor(rho_np, dtype=torch.float64, device=device)
+    wop.assemble(rho_old)
+    sequential_pass(wop, buf)
+    torch.cuda.synchronize()
+    del wop
+    kinds = ["assemble", "fine_primal", "coarse_primal", "correct_primal", "fine_adjoint", "coarse_adjoint",
+             "correct_adjoint"]
+
+    def step(e):
+        e[0].record(stream)
+        op.assemble(rho)
+        e[1].record(stream)
+        op.fine_propagate_slices(buf.U_T, buf.U_th, buf.F_T, buf.F_th, T_hist=buf.T_hist)
+        e[2].record(stream)
+        op.coarse_sweep(PTG_PRIMAL, buf.U_T, buf.U_th, buf.G_T, buf.G_th)
+        e[3].record(stream)
+        buf.U_T_new[0].copy_(buf.U_T[0])
+        buf.U_th_new[0].copy_(buf.U_th[0])
+        op.parareal_correct(PTG_PRIMAL, buf.F_T, buf.F_th, buf.G_T, buf.G_th, buf.U_T_new, buf.U_th_new,
+                            T_hist=buf.T_hist)
+        e[4].record(stream)
+        Theta = buf.U_th_new[Ntau:Ntau + 1]
+        op.adjoint_sweep(buf.T_hist, Theta, buf.V_l, buf.V_g, buf.F_l, buf.F_g)
+        e[5].record(stream)
+        op.coarse_sweep(PTG_ADJOINT, buf.V_l, buf.V_g, buf.G_l, buf.G_g, T_hist=buf.T_hist, Theta=Theta)
+        e[6].record(stream)
+        op.parareal_correct(PTG_ADJOINT, buf.F_l, buf.F_g, buf.G_l, buf.G_g, buf.V_l_new, buf.V_g_new,
+                            T_hist=buf.T_hist, Theta=Theta)
+        e[7].record(stream)
+
+    flush.fill_(1.0)
+    step([torch.cuda.Event(enable_timing=True) for _ in range(8)])      # warm-up: plans, attributes
+    torch.cuda.synchronize()
+    op.reset_stats()
+    per = np.zeros(7)
+    tot = []
+    for _ in range(max(1, args.c3_steps)):
+        flush.fill_(1.0)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+        step(ev)
+        torch.cuda.synchronize()
+        per += np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(7)])
+        tot.append(ev[0].elapsed_time(ev[7]))
+    steps = max(1, args.c3_steps)
+    kind_ms = {k: float(v / steps) for k, v in zip(kinds, per)}
+    st = op.stats()
+    ms = float(np.mean(tot))
+    roof = roofline(kind_ms, st, N_free, steps, args.precision)
+    out = {"workload": f"diff256: {n}x{n} grid, Nt={Nt}, Ntau={Ntau} (M={Nt // Ntau}), p={p:g}, rho ~ U(0,1) seed 1, "
+                       "timed design 1% away (seed 1000), warm start from the sequential FP64 coarse states",
+           "precision": args.precision, "rtol": args.rtol, "steps": steps, "ms_per_step": ms,
+           "value": 2.0 * N_free * Nt / (ms * 1e-3), "unit": UNIT, "per_kernel_ms": kind_ms,
+           "status": st["status"], "roofline": roof}
+    del buf, op
+    torch.cuda.synchronize()
+    return out
+
+
+def run_c3_only(args):
+    import torch
+
+    from paper_2411_19030_gb300.build import build_library
+    build_library()
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device=device)
+    print(json.dumps(streaming_256(args, flush, torch.cuda.current_stream(device), device)), flush=True)
 
 
 # ---------------------------------------------------------------------------- full design loop
@@ -820,9 +1005,9 @@ def main():
                     help="fp32_refine: fine-step CG in FP32 with FP64 refinement, coarse-step solves FP64; "
                          "fp32_refine_all: every CG in FP32 with FP64 refinement")
     ap.add_argument("--rtol", type=float, default=1e-10)
-    ap.add_argument("--twolevel", default="vcycle", choices=["none", "additive", "vcycle"],
-                    help="preconditioner of the coarse-step solves: Jacobi, additive two-level, or the "
-                         "two-grid V(1,1) cycle")
+    ap.add_argument("--twolevel", default="threelevel", choices=["none", "additive", "vcycle", "threelevel"],
+                    help="preconditioner of the coarse-step solves: Jacobi, additive two-level, the "
+                         "two-grid V(1,1) cycle, or the three-level cycle (2h Galerkin level and its aggregates)")
     ap.add_argument("--smooth", type=int, default=0,
                     help="V-cycle smoothing steps (1: one global Jacobi step; k >= 2: k slab-local steps; "
                          "0: the library default)")
@@ -843,6 +1028,14 @@ def main():
                     help="time the passes only: no end-to-end run, comparator, accuracy checks or G = 0 probe "
                          "(for profiling the launch sequence of the timed steps)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-overlap", dest="overlap", action="store_false",
+                    help="run the adjoint coarse propagators after the forward correction sweep instead of as "
+                         "two Theta-free parts beside it on a second stream")
+    ap.add_argument("--no-c3", dest="c3", action="store_false",
+                    help="leave out the 256x256 pass (Nt=2048, 64 slices) with its per-kernel roofline")
+    ap.add_argument("--c3-steps", type=int, default=2, help="timed passes of the 256x256 line")
+    ap.add_argument("--c3-only", action="store_true",
+                    help="only the 256x256 line (its JSON object), e.g. to capture its kernels under a profiler")
     ap.add_argument("--loop", type=int, default=0, metavar="ITERATIONS",
                     help="instead of the pass benchmark: the full design loop (512x512, Nt=4096, 128 slices, "
                          "host MMA) for this many design iterations")
@@ -863,6 +1056,8 @@ def main():
         run_loop(args)
     elif args.sweep:
         run_sweep(args)
+    elif args.c3_only:
+        run_c3_only(args)
     else:
         run_gpu(args)
 

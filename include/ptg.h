@@ -95,6 +95,7 @@ typedef struct {
 #define PTG_TWOLEVEL_NONE 0
 #define PTG_TWOLEVEL_ADDITIVE 1
 #define PTG_TWOLEVEL_VCYCLE 2
+#define PTG_TWOLEVEL_THREELEVEL 3
 
 typedef struct {
     int precision;     /* PTG_FP64, PTG_FP32_REFINE or PTG_FP32_REFINE_ALL */
@@ -113,6 +114,17 @@ typedef struct {
                                                  coarse correction of the residual, S again, i.e.
                                                  I - M^-1 A = (I - S A)(I - P Ac^-1 P^T A)(I - S A),
                                                  applied in FP32.
+                          PTG_TWOLEVEL_THREELEVEL the same cycle with its coarse correction
+                                                 replaced by a two-grid cycle on the 2h level:
+                                                 P1 bilinear from the nodes (2I, 2J), A1 =
+                                                 P1^T A P1 (9-point), damped-Jacobi smoothing
+                                                 on the CTA's 2h rows (smooth_steps), and the
+                                                 aggregates of m x m 2h nodes (m giving <= 16
+                                                 per direction) with their dense inverse below
+                                                 it; symmetric, in FP32.  Needs even nx, ny and
+                                                 a one-cluster launch with >= 2 fine rows per
+                                                 CTA; elsewhere (odd grids, cooperative-grid
+                                                 launches, batches) the two-grid cycle.
                           Other values: PTG_EINVAL. */
     int grid_wide;     /* systems may run on groups of CTAs of one cooperative launch, talking
                           through global memory, instead of one 16-CTA cluster each: a single
@@ -155,6 +167,11 @@ typedef struct {
                           increment G(x^new) - G(x^old), i.e. u_s - F[s-1] (primal) or
                           v_{s+1} - F[s+1] (adjoint), instead of G_old[s] alone;
                           0 the library's default (4).  Other values: PTG_EINVAL. */
+    int fine_stream;   /* fine propagators of the parallel schedule (a2, a5): 2 with the Krylov vectors
+                          in global memory, one group of CTAs per slice and every slice at once
+                          (the FP32 operator stays in L2); 0 or 1 on chip (one thread-block
+                          cluster, or a cooperative group, per slice with its vectors on chip).
+                          Other values: PTG_EINVAL. */
 } ptg_solve;
 
 typedef struct {
@@ -262,6 +279,47 @@ int ptg_coarse_sweep(ptg_op* op, int direction, const double* X_field, const dou
                      double* G_field, double* G_aux, cudaStream_t stream);
 
 /*
+ * a3 on the slices s0 .. s0+ns-1 only (Sec. 4.2: the coarse propagators of different slices are
+ * independent), e.g. one process's share when the slices are split over several GPUs.  Arrays
+ * and their meaning as for ptg_coarse_sweep (full Ntau-row shapes); only rows s0 .. s0+ns-1 of
+ * G_field / G_aux are written, and only the rows of X_field, X_aux and T_hist that those slices
+ * read must be valid: X rows s and s+1, and for the adjoint T_hist rows M s + 1 and M(s-1) + 1
+ * (row 0 for s = 0).  0 <= s0, 1 <= ns, s0 + ns <= Ntau, else PTG_EINVAL; ops whose coarse
+ * propagators run on the 2h mesh accept only the whole range.
+ */
+int ptg_coarse_sweep_slices(ptg_op* op, int direction, int s0, int ns, const double* X_field, const double* X_aux,
+                            const double* T_hist, const double* Theta_d, double* G_field, double* G_aux,
+                            cudaStream_t stream);
+
+/*
+ * a3, adjoint direction, in two parts that need no Theta.  The adjoint source of Eq. 4.6 is
+ * c T_k^(p-1) with c = Theta^(1-p)/Ne (p/Ne for PTG_OBJ_MODIFIED), and the solve and the g update
+ * of G_adj are affine in c, so G_adj(s, v_{s+1}) = H[s] + c S[s] with
+ *   H[s] = G_adj(s, v_{s+1}) with the source left out (c = 0), started from lambda_{k+M},
+ *   S[s] = G_adj(s, 0) with c = 1 (lambda = 0 and g = 0 in), started from zero,
+ * each solved to the op's tolerance.  Slices s0 .. s0+ns-1; arrays as for ptg_coarse_sweep
+ * (H_lam, S_lam [Ntau][Nn]; H_g, S_g [Ntau][Ne]; only rows s0 .. s0+ns-1 written).  The parts read
+ * only the history rows M s + 1 and M(s-1) + 1 (row 0 for s = 0), which ptg_fine_propagate_slices
+ * writes and, for M > 1, the forward correction sweep does not, so they can run before Theta is
+ * known: beside ptg_parareal_correct(PTG_PRIMAL) of the same op on another stream, when M > 1 and
+ * neither call runs on a cooperative grid (ptg_op_overlap_ok).  That is
+ * the one exception to the rule that calls on one op do not overlap; the parts touch no op
+ * workspace but the counters.  Ops with the 2h-mesh coarse propagators: PTG_EINVAL.
+ * ptg_coarse_adjoint_combine then forms G_lam = H_lam + c S_lam and G_g = H_g + c S_g on the same
+ * rows, with c from the device scalar Theta_d.
+ */
+int ptg_coarse_adjoint_split(ptg_op* op, int s0, int ns, const double* V_lam, const double* V_g, const double* T_hist,
+                             double* H_lam, double* H_g, double* S_lam, double* S_g, cudaStream_t stream);
+int ptg_coarse_adjoint_combine(ptg_op* op, int s0, int ns, const double* Theta_d, const double* H_lam,
+                               const double* H_g, const double* S_lam, const double* S_g, double* G_lam, double* G_g,
+                               cudaStream_t stream);
+/* *ok = 1 when ptg_coarse_adjoint_split may run beside ptg_parareal_correct(PTG_PRIMAL) of this op:
+ * M > 1, coarse propagators on the fine mesh, and neither the forward sweep nor the batched
+ * coarse adjoint (Ntau tasks) planned as a cooperative-grid launch (those share the op's grid
+ * workspace); else *ok = 0. */
+int ptg_op_overlap_ok(ptg_op* op, int* ok);
+
+/*
  * a4 -- Eq. 4.9 / 4.14: the sequential correction sweep of one Parareal iteration.
  *   G_field == G_aux == NULL selects the PLT variant of Sec. 7 (coarse propagators identically
  *   zero, Eq. 7.1-7.2): u_{s+1} = F[s] and v_s = F[s], a copy with no solve.
@@ -335,7 +393,11 @@ int ptg_sensitivities(ptg_op* op, const double* lam_hist, int j0, int j1,
  *   clearing, but calls that overlap on the GPU (other streams, other threads) race on it
  *   and must be serialised by the caller.
  *   Set-up: the first call on a device (that device current) looks up the array's device
- *   address once; make that first call before any stream capture begins.
+ *   address once and keeps it; make that first call before any stream capture begins, and do
+ *   not call this entry point after a cudaDeviceReset of that device.
+ *   Materials: k0, kmin, c0, cmin must be positive (as for ptg_op_create; else PTG_EINVAL).
+ *   The design must lie in [0, 1]; a value outside (or NaN) is taken as 0, as
+ *   ptg_fe_assemble_operator does (which also reports it), and is not reported here.
  * Returns PTG_OK, PTG_EINVAL (arguments, size) or PTG_ECUDA.
  */
 #define PTG_NOALLOC_SCRATCH_DOUBLES (1 << 21)
@@ -426,9 +488,25 @@ int ptg_mma_create(int n, double x_min, double x_max, double move, ptg_mma** out
 void ptg_mma_destroy(ptg_mma* m);
 int ptg_mma_update(ptg_mma* m, const double* x, double f0, const double* df0, double f1, const double* df1,
                    double* x_new);
+/* The state MMA carries between updates (to save and resume a design loop): the update count k
+ * and, as host arrays of length n, the last two iterates x1 (newest) and x2 and the last
+ * asymptotes L, U.  set_state restores exactly what get_state returned. */
+int ptg_mma_get_state(const ptg_mma* m, long long* k, double* x1, double* x2, double* L, double* U);
+int ptg_mma_set_state(ptg_mma* m, long long k, const double* x1, const double* x2, const double* L, const double* U);
 
 /* Copy the device status and counters into *out (synchronises the op's last stream). */
 int ptg_get_stats(ptg_op* op, ptg_stats* out);
+
+/*
+ * Bound of the device-side waits of this op's cooperative-grid launches (ptg_solve.grid_wide):
+ * a CTA that has polled a grid barrier `polls` times without the release records PTG_ETIMEOUT
+ * in the status word and stops waiting, and so does every later wait of that launch, so the
+ * launch ends with the error and meaningless results instead of hanging.  0 restores the
+ * default (2^20 polls, never reached by a correct co-resident launch); a small value makes the
+ * waits give up early (failure-detection tests).  Negative: PTG_EINVAL.  Applies to launches
+ * made after the call.
+ */
+int ptg_op_set_wait_limit(ptg_op* op, long long polls);
 
 /* Clear the device status word and the counters (asynchronous on stream). */
 int ptg_reset_stats(ptg_op* op, cudaStream_t stream);

@@ -14,7 +14,7 @@ PTG_SLICES_PARALLEL, PTG_SLICES_CHAINED = 0, 1
 PTG_PRIMAL, PTG_ADJOINT = 1, -1
 PTG_OBJ_POWER_MEAN, PTG_OBJ_MODIFIED = 0, 1
 PTG_PARAREAL, PTG_PLT = 0, 1
-PTG_TWOLEVEL_NONE, PTG_TWOLEVEL_ADDITIVE, PTG_TWOLEVEL_VCYCLE = 0, 1, 2
+PTG_TWOLEVEL_NONE, PTG_TWOLEVEL_ADDITIVE, PTG_TWOLEVEL_VCYCLE, PTG_TWOLEVEL_THREELEVEL = 0, 1, 2, 3
 
 ERROR_NAMES = {0: "PTG_OK", -1: "PTG_EINVAL", -2: "PTG_ENOCONV", -3: "PTG_ENONFINITE",
                -4: "PTG_ETIMEOUT", -5: "PTG_ECUDA", -6: "PTG_ENOMEM"}
@@ -37,7 +37,7 @@ class ptg_solve(ctypes.Structure):
     _fields_ = [("precision", c_int), ("rtol", c_double), ("inner_rtol", c_double),
                 ("cg_iters_max", c_int), ("refine_max", c_int), ("twolevel", c_int), ("grid_wide", c_int),
                 ("smooth_steps", c_int), ("coarse_mesh", c_int),
-                ("local_steps", c_int), ("initial_guess", c_int)]
+                ("local_steps", c_int), ("initial_guess", c_int), ("fine_stream", c_int)]
 
 
 class ptg_stats(ctypes.Structure):
@@ -67,10 +67,15 @@ SIGNATURES = {
     "ptg_fe_assemble_operator": (c_int, [_P, _P, _P]),
     "ptg_fine_propagate_slices": (c_int, [_P, c_int, c_int, c_int, _P, _P, _P, c_int, c_int, _P, _P, _P]),
     "ptg_coarse_sweep": (c_int, [_P, c_int, _P, _P, _P, _P, _P, _P, _P]),
+    "ptg_coarse_sweep_slices": (c_int, [_P, c_int, c_int, c_int, _P, _P, _P, _P, _P, _P, _P]),
+    "ptg_op_overlap_ok": (c_int, [_P, POINTER(c_int)]),
+    "ptg_coarse_adjoint_split": (c_int, [_P, c_int, c_int, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "ptg_coarse_adjoint_combine": (c_int, [_P, c_int, c_int, _P, _P, _P, _P, _P, _P, _P, _P]),
     "ptg_parareal_correct": (c_int, [_P, c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "ptg_objective_from_modified": (c_int, [_P, _P, _P, _P, _P, _P]),
     "ptg_adjoint_sweep": (c_int, [_P, c_int, c_int, c_int, _P, c_int, c_int, _P, _P, _P, _P, _P, _P]),
     "ptg_sensitivities": (c_int, [_P, _P, c_int, c_int, _P, c_int, c_int, _P, _P]),
+    "ptg_op_set_wait_limit": (c_int, [_P, ctypes.c_longlong]),
     "ptg_sensitivities_noalloc": (c_int, [c_int, c_int, c_double, c_int, c_double, POINTER(ptg_material), _P, _P,
                                           c_int, c_int, _P, c_int, c_int, _P, _P]),
     "ptg_batch_create": (c_int, [POINTER(c_void_p), c_int, POINTER(c_void_p)]),
@@ -90,6 +95,8 @@ SIGNATURES = {
     "ptg_design_volume": (c_int, [_P, _P, _P, _P]),
     "ptg_mma_create": (c_int, [c_int, c_double, c_double, c_double, POINTER(c_void_p)]),
     "ptg_mma_destroy": (None, [_P]),
+    "ptg_mma_get_state": (c_int, [_P, POINTER(c_longlong), _P, _P, _P, _P]),
+    "ptg_mma_set_state": (c_int, [_P, c_longlong, _P, _P, _P, _P]),
     "ptg_mma_update": (c_int, [_P, _P, c_double, _P, c_double, _P, _P]),
     "ptg_get_stats": (c_int, [_P, POINTER(ptg_stats)]),
     "ptg_reset_stats": (c_int, [_P, _P]),

@@ -50,7 +50,7 @@ def twolevel_code(v) -> int:
     """The ptg_solve.twolevel value of SolveConfig.twolevel."""
     if isinstance(v, str):
         return {"none": _ffi.PTG_TWOLEVEL_NONE, "additive": _ffi.PTG_TWOLEVEL_ADDITIVE,
-                "vcycle": _ffi.PTG_TWOLEVEL_VCYCLE}[v]
+                "vcycle": _ffi.PTG_TWOLEVEL_VCYCLE, "threelevel": _ffi.PTG_TWOLEVEL_THREELEVEL}[v]
     return int(v)
 
 
@@ -62,7 +62,9 @@ class SolveConfig:
     inner_rtol: float = 1e-4
     cg_iters_max: int = 2000
     refine_max: int = 8
-    twolevel: bool | int | str = "vcycle"  # preconditioner of the coarse-step solves: "vcycle"
+    twolevel: bool | int | str = "threelevel"  # preconditioner of the coarse-step solves: "threelevel"
+    #                                  (the two-grid cycle whose coarse correction is a two-grid cycle
+    #                                  on the 2h level, over aggregates of 2h nodes), "vcycle"
     #                                  (symmetric two-grid cycle with damped-Jacobi smoothing),
     #                                  True / "additive" (D^-1 + P Ac^-1 P^T), False / "none" (Jacobi)
     grid_wide: int = 1               # single FP64 systems over every SM (cooperative grid):
@@ -74,6 +76,8 @@ class SolveConfig:
     #                                  steps, 0 the library default
     initial_guess: int = 0           # CG start of a step: 1 plain, 2 extrapolated / the neighbouring
     #                                  guess state, 0 the library default (2)
+    fine_stream: int = 0             # fine propagators with the CG vectors in global memory, every
+    #                                  slice at once: 2 always, 1 never, 0 the library's choice
 
 
 class Operator:
@@ -112,7 +116,8 @@ class Operator:
                 "fp32_refine_all": PTG_FP32_REFINE_ALL}[solve.precision]
         s = _ffi.ptg_solve(prec, solve.rtol, solve.inner_rtol, solve.cg_iters_max, solve.refine_max,
                            twolevel_code(solve.twolevel), int(solve.grid_wide), int(solve.smooth_steps),
-                           int(solve.coarse_mesh), int(solve.local_steps), int(solve.initial_guess))
+                           int(solve.coarse_mesh), int(solve.local_steps), int(solve.initial_guess),
+                           int(solve.fine_stream))
         self._dir = np.ascontiguousarray(dirichlet, dtype=np.uint8).reshape(-1)
         if self._dir.size != self.Nn:
             raise ValueError("dirichlet mask must have (nx+1)(ny+1) entries")
@@ -176,6 +181,51 @@ class Operator:
                                        _ptr(G_field, self.device), _ptr(G_aux, self.device), self._stream(stream)),
                "ptg_coarse_sweep")
 
+    def coarse_sweep_slices(self, direction, s0, ns, X_field, X_aux, G_field, G_aux, T_hist=None, Theta=None,
+                            stream=None):
+        """a3 on slices s0..s0+ns-1 only (full-size arrays; only those rows of G are written)."""
+        _check(_lib().ptg_coarse_sweep_slices(self._h, direction, s0, ns, _ptr(X_field, self.device),
+                                              _ptr(X_aux, self.device), _ptr(T_hist, self.device),
+                                              _ptr(Theta, self.device), _ptr(G_field, self.device),
+                                              _ptr(G_aux, self.device), self._stream(stream)),
+               "ptg_coarse_sweep_slices")
+
+    def coarse_adjoint_split(self, V_lam, V_g, T_hist, H_lam, H_g, S_lam, S_g, s0=0, ns=None, stream=None):
+        """a3 (adjoint) as its Theta-free part H and unit-source part S (see include/ptg.h)."""
+        ns = self.Ntau - s0 if ns is None else ns
+        d = self.device
+        _check(_lib().ptg_coarse_adjoint_split(self._h, s0, ns, _ptr(V_lam, d), _ptr(V_g, d), _ptr(T_hist, d),
+                                               _ptr(H_lam, d), _ptr(H_g, d), _ptr(S_lam, d), _ptr(S_g, d),
+                                               self._stream(stream)), "ptg_coarse_adjoint_split")
+
+    def coarse_adjoint_combine(self, Theta, H_lam, H_g, S_lam, S_g, G_lam, G_g, s0=0, ns=None, stream=None):
+        """G = H + c S with the adjoint source scale c of Theta."""
+        ns = self.Ntau - s0 if ns is None else ns
+        d = self.device
+        _check(_lib().ptg_coarse_adjoint_combine(self._h, s0, ns, _ptr(Theta, d), _ptr(H_lam, d), _ptr(H_g, d),
+                                                 _ptr(S_lam, d), _ptr(S_g, d), _ptr(G_lam, d), _ptr(G_g, d),
+                                                 self._stream(stream)), "ptg_coarse_adjoint_combine")
+
+    def can_overlap_adjoint_coarse(self) -> bool:
+        """Whether the split G_adj may run beside the forward correction sweep (ptg_op_overlap_ok):
+        M > 1, fine-mesh G, and neither kind on a cooperative grid."""
+        ok = ctypes.c_int()
+        _check(_lib().ptg_op_overlap_ok(self._h, ctypes.byref(ok)), "ptg_op_overlap_ok")
+        return bool(ok.value)
+
+    def side_stream(self):
+        """Stream of the work that runs beside the forward correction sweep (default priority)."""
+        if getattr(self, "_side", None) is None:
+            self._side = torch.cuda.Stream(self.device)
+        return self._side
+
+    def sweep_stream(self):
+        """High-priority stream of the forward correction sweep while work runs beside it: when
+        both become ready together, the sweep's thread-block cluster is placed first."""
+        if getattr(self, "_sweep", None) is None:
+            self._sweep = torch.cuda.Stream(self.device, priority=-100)   # mapped to the highest priority
+        return self._sweep
+
     def parareal_correct(self, direction, F_field, F_aux, G_field, G_aux, X_field, X_aux, T_hist=None, Theta=None,
                          stream=None):
         """a4: the sequential correction sweep (forward or reverse); G_field = G_aux = None is the
@@ -220,6 +270,10 @@ class Operator:
                                      refinements=out["kind_refinements"][i]) for i, name in enumerate(KIND_NAMES)}
         return out
 
+    def set_wait_limit(self, polls: int):
+        """Bound of the grid-barrier waits of cooperative-grid launches (0: the default)."""
+        _check(_lib().ptg_op_set_wait_limit(self._h, int(polls)), "ptg_op_set_wait_limit")
+
     def reset_stats(self, stream=None):
         _check(_lib().ptg_reset_stats(self._h, self._stream(stream)), "ptg_reset_stats")
 
@@ -251,6 +305,13 @@ class PassBuffers:
         self.U_T_new, self.U_th_new = z(Ntau + 1, Nn), z(Ntau + 1)
         self.V_l_new, self.V_g_new = z(Ntau + 1, Nn), z(Ntau + 1, Ne)
 
+    def split_parts(self):
+        """The two parts of the adjoint coarse propagator (allocated on first use)."""
+        if getattr(self, "H_l", None) is None:
+            z = torch.zeros_like
+            self.H_l, self.H_g, self.S_l, self.S_g = z(self.G_l), z(self.G_g), z(self.G_l), z(self.G_g)
+        return self.H_l, self.H_g, self.S_l, self.S_g
+
     def swap(self):
         """Make the pass result the warm start of the next pass."""
         self.U_T, self.U_T_new = self.U_T_new, self.U_T
@@ -279,12 +340,20 @@ def sequential_pass(op: Operator, buf: PassBuffers, T0: torch.Tensor | None = No
     return Theta, buf.V_g[0]
 
 
-def oneshot_pass(op: Operator, buf: PassBuffers, stream=None, plt: bool = False):
+def oneshot_pass(op: Operator, buf: PassBuffers, stream=None, plt: bool = False, overlap: bool | None = None):
     """Iteration body of Alg. 3: one modified forward Parareal iteration and one reverse vanilla
     Parareal iteration from the warm start (buf.U_*, buf.V_*).  The corrected states go to
     buf.U_*_new / buf.V_*_new, the history to buf.T_hist; returns (Theta, grad) views.
     plt=True: the coarse propagators are identically zero (Sec. 7): no coarse sweep, and the
-    corrections copy the fine results (buf.G_* are left untouched)."""
+    corrections copy the fine results (buf.G_* are left untouched).
+    overlap (default: whenever op.can_overlap_adjoint_coarse()): the adjoint coarse propagators
+    run as their Theta-free and unit-source parts on a second stream beside the forward
+    correction sweep, which occupies one thread-block cluster, and are combined once Theta is
+    known (G_adj is affine in the source scale of Eq. 4.6)."""
+    if overlap is None:
+        overlap = not plt and op.can_overlap_adjoint_coarse()
+    if overlap and not plt:
+        return _oneshot_pass_overlapped(op, buf, stream)
     Ntau = op.Ntau
     # primal: F and G of every slice on the guess, then the sequential correction
     op.fine_propagate_slices(buf.U_T, buf.U_th, buf.F_T, buf.F_th, T_hist=buf.T_hist, stream=stream)
@@ -302,6 +371,40 @@ def oneshot_pass(op: Operator, buf: PassBuffers, stream=None, plt: bool = False)
                         stream=stream)
     op.parareal_correct(PTG_ADJOINT, buf.F_l, buf.F_g, None if plt else buf.G_l, None if plt else buf.G_g,
                         buf.V_l_new, buf.V_g_new, T_hist=buf.T_hist, Theta=Theta, stream=stream)
+    return Theta, buf.V_g_new[0]
+
+
+def _oneshot_pass_overlapped(op: Operator, buf: PassBuffers, stream=None):
+    """oneshot_pass with the split adjoint coarse propagators beside the forward sweep.  The sweep
+    runs on a high-priority stream, so that when the fine and coarse primal launches end, its
+    single cluster is placed before the parts fill the rest of the GPU."""
+    Ntau = op.Ntau
+    main = stream if stream is not None else torch.cuda.current_stream(op.device)
+    side, hi = op.side_stream(), op.sweep_stream()
+    H_l, H_g, S_l, S_g = buf.split_parts()
+    with torch.cuda.stream(main):
+        buf.U_T_new[0].copy_(buf.U_T[0])
+        buf.U_th_new[0].copy_(buf.U_th[0])
+    op.fine_propagate_slices(buf.U_T, buf.U_th, buf.F_T, buf.F_th, T_hist=buf.T_hist, stream=main)
+    op.coarse_sweep(PTG_PRIMAL, buf.U_T, buf.U_th, buf.G_T, buf.G_th, stream=main)
+    primal_done = torch.cuda.Event()
+    primal_done.record(main)
+    hi.wait_event(primal_done)
+    op.parareal_correct(PTG_PRIMAL, buf.F_T, buf.F_th, buf.G_T, buf.G_th, buf.U_T_new, buf.U_th_new,
+                        T_hist=buf.T_hist, stream=hi)
+    sweep_done = torch.cuda.Event()
+    sweep_done.record(hi)
+    side.wait_event(primal_done)
+    op.coarse_adjoint_split(buf.V_l, buf.V_g, buf.T_hist, H_l, H_g, S_l, S_g, stream=side)
+    parts_done = torch.cuda.Event()
+    parts_done.record(side)
+    Theta = buf.U_th_new[Ntau:Ntau + 1]
+    main.wait_event(sweep_done)
+    op.adjoint_sweep(buf.T_hist, Theta, buf.V_l, buf.V_g, buf.F_l, buf.F_g, stream=main)
+    main.wait_event(parts_done)
+    op.coarse_adjoint_combine(Theta, H_l, H_g, S_l, S_g, buf.G_l, buf.G_g, stream=main)
+    op.parareal_correct(PTG_ADJOINT, buf.F_l, buf.F_g, buf.G_l, buf.G_g, buf.V_l_new, buf.V_g_new,
+                        T_hist=buf.T_hist, Theta=Theta, stream=main)
     return Theta, buf.V_g_new[0]
 
 

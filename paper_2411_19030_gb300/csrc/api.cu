@@ -26,8 +26,21 @@ struct ptg_op {
   int tl_m = 0, tl_nax = 0, tl_nay = 0;
   int tl_vc = 0;   // 1: the two-grid cycle instead of the additive form
   int tl_nu = 1;   // its smoothing steps (see StepParams::tl_nu)
+  int tl_nu3 = 1;  // the three-level cycle's smoothing steps on each smoothed level
   double* tl_Ac = nullptr;
   float *tl_band = nullptr, *tl_X = nullptr, *tl_Ainv = nullptr;
+  // three-level cycle (ptg_solve.twolevel = PTG_TWOLEVEL_THREELEVEL, even nx and ny): the 2h
+  // level and the aggregates of tl3_m x tl3_m of its nodes; tl3_m == 0: not set up
+  int tl3_m = 0, tl3_nax = 0, tl3_nay = 0;
+  double *tl3_A1 = nullptr, *tl3_Ac = nullptr;
+  float *tl3_band = nullptr, *tl3_X = nullptr, *tl3_Ainv = nullptr;
+  // streamed fine propagators (ptg_solve.fine_stream, stream.cuh): FP32 weights of C/dt + K and
+  // 1/C ([6][PN]), the FP64 1/C ([PN]), and the workspace of st_groups concurrent slices
+  float* w32 = nullptr;
+  double* w64_inv = nullptr;
+  double* st_w64 = nullptr;    // [st_groups][3][Nn]
+  void* st_wr = nullptr;       // [st_groups][4][Nn] in the fine CG precision
+  int st_groups = 0;           // 0: the op has no streaming workspace
   // device workspace
   double *k = nullptr, *c = nullptr, *dk = nullptr, *dc = nullptr;
   double* wE = nullptr;     // [2][3][PEe]: element (D, S, T) weights for dt and dtau (padded)
@@ -42,6 +55,7 @@ struct ptg_op {
   // two-level partials
   double* g_red = nullptr;
   unsigned* g_bar = nullptr;
+  long long wait_limit = 0;  // polls of a grid barrier before PTG_ETIMEOUT (0: the kernel's default)
   void* g_halo = nullptr;
   float* g_tl = nullptr;
   int sens_chunks = 0;
@@ -110,9 +124,36 @@ int kind_precision(int solve_precision, int kind) {
 // Two-level forms a plan may use, strongest last: tl_mode caps the op's choice (an op set up
 // for the V-cycle runs the additive form under a plan capped at TL_ADDITIVE, e.g. when the
 // V-cycle's buffers do not fit).
-enum TlMode : int { TL_NONE = 0, TL_ADDITIVE = 1, TL_VCYCLE = 2 };
+enum TlMode : int { TL_NONE = 0, TL_ADDITIVE = 1, TL_VCYCLE = 2, TL_VCYCLE3 = 3 };
 bool uses_vcycle(const ptg_op* op, int tl_mode) { return tl_mode >= TL_VCYCLE && op->tl_vc; }
-int strongest_mode(const ptg_op* op) { return op->tl_m == 0 ? TL_NONE : (op->tl_vc ? TL_VCYCLE : TL_ADDITIVE); }
+bool uses_three(const ptg_op* op, int tl_mode) { return tl_mode >= TL_VCYCLE3 && op->tl3_m > 0; }
+int strongest_mode(const ptg_op* op) {
+  if (op->tl_m == 0) return TL_NONE;
+  if (op->tl3_m > 0) return TL_VCYCLE3;
+  return op->tl_vc ? TL_VCYCLE : TL_ADDITIVE;
+}
+
+// Three-level cycle: the aggregate rows reserved per CTA for cluster size cs (those touched by
+// the CTA's 2h rows and its two 2h halo rows), 0 if a slab has fewer than two fine rows (then
+// some CTA would own no 2h row) or the mode does not apply; r1max the most 2h rows of a CTA.
+int threelevel_rows(const ptg_op* op, int kind, int cs, int tl_mode, int* r1max = nullptr) {
+  if (!uses_three(op, tl_mode) || !coarse_kind(kind)) return 0;
+  const int rows = op->g.ny + 1, base = rows / cs, rem = rows % cs;
+  const int ny1 = op->g.ny / 2;
+  int best = 0, rmx = 0;
+  for (int q = 0; q < cs; ++q) {
+    const int r0 = q * base + (q < rem ? q : rem), R = base + (q < rem ? 1 : 0);
+    if (R < 2) return 0;
+    int J0, R1;
+    l1_rows_of_slab(r0, R, J0, R1);
+    const int lo = l3_agg(J0 > 0 ? J0 - 1 : 0, op->tl3_m, op->tl3_nay);
+    const int hi = l3_agg(J0 + R1 <= ny1 ? J0 + R1 : ny1, op->tl3_m, op->tl3_nay);
+    best = std::max(best, hi - lo + 1);
+    rmx = std::max(rmx, R1);
+  }
+  if (r1max) *r1max = rmx;
+  return best;
+}
 
 // Aggregate rows reserved per CTA for cluster size cs (the largest over the ranks; with the
 // V-cycle the rows its halo rows touch too), 0 if the two-level preconditioner is off for this
@@ -120,6 +161,7 @@ int strongest_mode(const ptg_op* op) { return op->tl_m == 0 ? TL_NONE : (op->tl_
 int twolevel_rows(const ptg_op* op, int precision, int kind, int cs, int tl_mode = TL_VCYCLE) {
   (void)precision;
   if (tl_mode == TL_NONE || op->tl_m == 0 || !coarse_kind(kind)) return 0;
+  if (tl_mode >= TL_VCYCLE3) return threelevel_rows(op, kind, cs, tl_mode);
   const bool vc = uses_vcycle(op, tl_mode);
   int best = 0;
   for (int q = 0; q < cs; ++q) {
@@ -141,6 +183,12 @@ size_t twolevel_bytes(const ptg_op* op, int precision, int kind, int cs, int tl_
   const int ncj = twolevel_rows(op, precision, kind, cs, tl_mode);
   if (ncj == 0) return 0;
   const int rmax = (op->g.ny + 1 + cs - 1) / cs;
+  if (tl_mode >= TL_VCYCLE3) {
+    int r1max = 0;
+    threelevel_rows(op, kind, cs, tl_mode, &r1max);
+    return threelevel_smem_bytes(op->W, rmax, cs, padded_width(op->g.nx / 2), r1max, op->tl3_nax, op->tl3_nay, ncj,
+                                 slots, precision == PTG_FP64 ? 8 : 4, op->tl_nu3);
+  }
   return twolevel_smem_bytes(op->W, rmax, cs, op->tl_nax, op->tl_nay, ncj, slots, uses_vcycle(op, tl_mode),
                              precision == PTG_FP64 ? 8 : 4, op->tl_nu);
 }
@@ -160,6 +208,10 @@ constexpr int kLocalSteps = 1;
 // (FP64 coarse-step CG): 1 global step 66.1 ms; 2, 3, 4, 6 local steps 59.2, 56.5, 55.9,
 // 56.8 ms, the CG iterations per correction solve falling from 34 to 26, 23, 21, 19.
 constexpr int kVcycleSmoothSteps = 4;
+// Default smoothing steps of the three-level cycle on both its smoothed levels: a numpy model of
+// the 128 x 128 coarse-step operator (slab-local Jacobi on 16 slabs, aggregates of 4 x 4 2h nodes)
+// needs 13 PCG iterations with 3 or 4 steps, 14 with 2 on one level, 15 with 2 on both.
+constexpr int kThreeLevelSmoothSteps = 3;
 
 // Node count from which a single FP64 system runs grid-wide (see choose_plan).
 constexpr int kWideMinNodes = 40000;
@@ -197,6 +249,23 @@ void twolevel_params(const ptg_op* op, int precision, StepParams& P, int tl_mode
   if (precision == PTG_FP64)
     P.inner_rtol = P.tl_naj > 0 && !P.tl_vc ? std::max(kTwoLevelInnerFp64, op->sv.inner_rtol) : 0.0;
   if (P.tl_naj == 0) return;
+  if (tl_mode >= TL_VCYCLE3) {
+    // the V-cycle's fine buffers plus the 2h level; the aggregate level is on the 2h grid
+    P.tl_vc = 1;
+    P.tl_l3 = 1;
+    P.tl_nu = op->tl_nu3;
+    P.l3_nx1 = op->g.nx / 2;
+    P.l3_ny1 = op->g.ny / 2;
+    P.l3_W1 = padded_width(P.l3_nx1);
+    threelevel_rows(op, P.kind, P.cs, tl_mode, &P.l3_r1max);
+    P.A1 = op->tl3_A1;
+    P.Ainv = op->tl3_Ainv;
+    P.cm = op->tl3_m;
+    P.nax = op->tl3_nax;
+    P.nay = op->tl3_nay;
+    P.inner_rtol = precision == PTG_FP64 ? 0.0 : P.inner_rtol;
+    return;
+  }
   P.Ainv = op->tl_Ainv;
   P.cm = op->tl_m;
   P.nax = op->tl_nax;
@@ -229,6 +298,7 @@ long best_plan(ptg_op* op, int precision, int kind, int ntasks, int tl_mode, Pla
       if (best_waves < 0 || waves < best_waves || (waves == best_waves && ng < out->ng)) {
         p.twolevel = twolevel_rows(op, precision, kind, cs, tl_mode) > 0;
         p.vc = p.twolevel && uses_vcycle(op, tl_mode);
+        p.l3 = p.twolevel && uses_three(op, tl_mode);
         *out = p;
         best_waves = waves;
       }
@@ -253,6 +323,34 @@ int choose_plan(ptg_op* op, int precision, int kind, int ntasks, Plan* out) {
   if (it != op->plans.end()) {
     *out = it->second;
     return PTG_OK;
+  }
+  // Fine kinds of the parallel schedule (ntasks >= 2 slices at once) on the streamed propagator
+  // when ptg_solve.fine_stream = 2.  One CTA of 1024 threads per SM; G = SMs / slices CTAs per
+  // slice (at least 2 node rows each), all slices at once.
+  if ((kind == KIND_FINE_PRI || kind == KIND_FINE_ADJ) && op->st_groups > 0 && ntasks >= 2 &&
+      op->sv.fine_stream != 1) {
+    // fine_stream 0 keeps the on-chip path: measured at 256 x 256 (64 slices) the streamed
+    // propagators took 134 ms against 59 ms on chip
+    const bool want = op->sv.fine_stream == 2;
+    if (want) {
+      int dev = 0, nsm = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      nsm = std::min(nsm, kMaxGrid);
+      int G = std::max(1, nsm / ntasks);
+      G = std::min(G, std::max(1, (op->g.ny + 1) / 2));
+      Plan sp;
+      sp.cs = G;
+      sp.nthreads = 1024;
+      sp.ng = 1;
+      sp.rmax = (op->g.ny + 1 + G - 1) / G;
+      sp.smem = 0;
+      sp.max_active_clusters = std::max(1, std::min({ntasks, nsm / G, op->st_groups}));
+      sp.stream = true;
+      op->plans[key] = sp;
+      *out = sp;
+      return PTG_OK;
+    }
   }
   // One FP64 system: a cluster runs its CG on 16 SMs, bound by their FP64 pipes; a grid-wide
   // launch spreads the FP64 work over every SM, but each of its reductions costs a few
@@ -290,7 +388,7 @@ int choose_plan(ptg_op* op, int precision, int kind, int ntasks, Plan* out) {
     // one FP64 system over every SM (spread), or groups of the fewest CTAs whose slabs fit,
     // with the strongest two-level form that fits.  Groups leave out the saved A x: smaller
     // slabs per CTA mean fewer CTAs per group and more systems at a time.
-    for (int mode = strongest_mode(op); mode >= TL_NONE; --mode) {
+    for (int mode = std::min(strongest_mode(op), (int)TL_VCYCLE); mode >= TL_NONE; --mode) {   // no 3-level on grids
       for (bool keep_ax : {spread, !spread}) {
         Plan w;
         WideCtx ctx{op, precision, kind, mode};
@@ -358,6 +456,12 @@ void base_params(const ptg_op* op, StepParams& P) {
   P.A_fine = nw(0);
   P.A_coarse = nw(5);
   P.mass = nw(10);
+  if (op->w32) {
+    P.w32 = op->w32 + kSlack;
+    P.w32_inv = op->w32 + 5 * PN + kSlack;
+    P.w32_stride = (int)PN;
+    P.w64_inv = op->w64_inv + kSlack;
+  }
   P.dk = op->dk;
   P.dc = op->dc;
   P.fload = op->fload;
@@ -380,16 +484,32 @@ int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream, int stats_ki
   if (rc != PTG_OK) return rc;
   P.cs = plan.cs;
   P.rmax = plan.rmax;
+  if (plan.stream) {
+    if (P.chained) return PTG_EINVAL;            // a chained run is one task: never planned so
+    P.wide = 1;
+    P.wide_tasks = ntasks;
+    P.g_red = op->g_red;
+    P.g_bar = op->g_bar;
+    P.wait_limit = op->wait_limit;
+    P.st_w64 = op->st_w64;
+    P.st_wr = op->st_wr;
+    twolevel_params(op, prec, P, TL_NONE);
+    op->last_stream = stream;
+    PTG_CUDA(launch_stream(P, prec, plan.max_active_clusters, plan.nthreads, stream));
+    return PTG_OK;
+  }
   if (plan.wide) {
     P.wide = 1;
     P.wide_tasks = ntasks;
     P.g_red = op->g_red;
     P.g_bar = op->g_bar;
+    P.wait_limit = op->wait_limit;
     P.g_halo = op->g_halo;
     P.g_halo_row_bytes = op->W * (int)sizeof(double);
     P.g_tl = op->g_tl;
   }
-  twolevel_params(op, prec, P, plan.twolevel && !P.plt ? (plan.vc ? TL_VCYCLE : TL_ADDITIVE) : TL_NONE);
+  twolevel_params(op, prec, P,
+                  plan.twolevel && !P.plt ? (plan.l3 ? TL_VCYCLE3 : (plan.vc ? TL_VCYCLE : TL_ADDITIVE)) : TL_NONE);
   P.keep_ax = plan.keep_ax ? 1 : 0;
   // on cooperative-grid launches every reduction is a global-memory round trip of several
   // microseconds, so the default trades two slab-local sweeps for fewer CG iterations there
@@ -408,6 +528,8 @@ void free_all(ptg_op* op) {
                   op->q_elem, op->q_time, op->dirichlet, op->sens_partial, op->lam_prev, op->scratch, op->stats,
                   op->g_red, op->g_bar, op->g_halo, op->g_tl,
                   op->tl_Ac, op->tl_band, op->tl_X, op->tl_Ainv,
+                  op->tl3_A1, op->tl3_Ac, op->tl3_band, op->tl3_X, op->tl3_Ainv,
+                  op->w32, op->w64_inv, op->st_w64, op->st_wr,
                   op->mesh_rho, op->mesh_XH, op->mesh_FH, op->mesh_GH, op->mesh_SH, op->mesh_YH,
                   op->mesh_zero, op->mesh_aux, op->mesh_pn, op->mesh_lam, op->mesh_dg};
   for (void* p : ptrs)
@@ -610,7 +732,8 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
   if (time->objective != PTG_OBJ_POWER_MEAN && time->objective != PTG_OBJ_MODIFIED) return PTG_EINVAL;
   if (solve->precision != PTG_FP64 && solve->precision != PTG_FP32_REFINE && solve->precision != PTG_FP32_REFINE_ALL)
     return PTG_EINVAL;
-  if (solve->twolevel < PTG_TWOLEVEL_NONE || solve->twolevel > PTG_TWOLEVEL_VCYCLE) return PTG_EINVAL;
+  if (solve->twolevel < PTG_TWOLEVEL_NONE || solve->twolevel > PTG_TWOLEVEL_THREELEVEL) return PTG_EINVAL;
+  if (solve->fine_stream < 0 || solve->fine_stream > 2) return PTG_EINVAL;
   if (solve->smooth_steps < 0 || solve->smooth_steps > 16) return PTG_EINVAL;
   if (solve->coarse_mesh != 0 && solve->coarse_mesh != 1) return PTG_EINVAL;
   if (solve->local_steps < 0 || solve->local_steps > 2) return PTG_EINVAL;
@@ -667,8 +790,9 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
     int m = 4;
     while ((grid->nx + 1) / m > kCoarseMaxAgg || (grid->ny + 1) / m > kCoarseMaxAgg) m += 4;
     op->tl_m = m;
-    op->tl_vc = solve->twolevel == PTG_TWOLEVEL_VCYCLE;
+    op->tl_vc = solve->twolevel == PTG_TWOLEVEL_VCYCLE || solve->twolevel == PTG_TWOLEVEL_THREELEVEL;
     op->tl_nu = solve->smooth_steps > 0 ? solve->smooth_steps : kVcycleSmoothSteps;
+    op->tl_nu3 = solve->smooth_steps > 0 ? solve->smooth_steps : kThreeLevelSmoothSteps;
     op->tl_nax = coarse_aggregates(grid->nx, m);
     op->tl_nay = coarse_aggregates(grid->ny, m);
     const size_t nc = (size_t)op->tl_nax * op->tl_nay;
@@ -678,6 +802,36 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
     A(&op->tl_X, nc * nc * sizeof(float));
     A(&op->tl_Ainv, ncp * ncp * sizeof(float));
     A(&op->g_tl, (size_t)kMaxGrid * ncp * sizeof(float));
+    // the three-level cycle needs the 2h grid (even nx, ny) with at least 4 x 4 of its nodes;
+    // aggregates of m x m 2h nodes, m the smallest size giving at most kCoarseMaxAgg per direction
+    if (solve->twolevel == PTG_TWOLEVEL_THREELEVEL && grid->nx % 2 == 0 && grid->ny % 2 == 0 && grid->nx >= 6 &&
+        grid->ny >= 6) {
+      const int nx1 = grid->nx / 2, ny1 = grid->ny / 2;
+      int m3 = 2;
+      while ((nx1 + 1) / m3 > kCoarseMaxAgg || (ny1 + 1) / m3 > kCoarseMaxAgg) ++m3;
+      op->tl3_m = m3;
+      op->tl3_nax = coarse_aggregates(nx1, m3);
+      op->tl3_nay = coarse_aggregates(ny1, m3);
+      const size_t nc3 = (size_t)op->tl3_nax * op->tl3_nay;
+      const size_t ncp3 = (size_t)coarse_row_stride(op->tl3_nax) * op->tl3_nay;
+      A(&op->tl3_A1, (size_t)9 * (nx1 + 1) * (ny1 + 1) * sizeof(double));
+      A(&op->tl3_Ac, nc3 * nc3 * sizeof(double));
+      A(&op->tl3_band, nc3 * (op->tl3_nax + 2) * sizeof(float));
+      A(&op->tl3_X, nc3 * nc3 * sizeof(float));
+      A(&op->tl3_Ainv, ncp3 * ncp3 * sizeof(float));
+    }
+  }
+  // streamed fine propagators (fine_stream = 2)
+  if (solve->fine_stream == 2) {
+    int dev_sm = 0;
+    cudaDeviceGetAttribute(&dev_sm, cudaDevAttrMultiProcessorCount, device);
+    op->st_groups = std::max(1, std::min(time->Ntau, std::min(dev_sm, kMaxGrid)));
+    const size_t PNs = (size_t)(grid->ny + 3) * op->W + 2 * kSlack;
+    const size_t rb = kind_precision(solve->precision, KIND_FINE_PRI) == PTG_FP64 ? 8 : 4;
+    A(&op->w32, 6 * PNs * sizeof(float));
+    A(&op->w64_inv, PNs * sizeof(double));
+    A(&op->st_w64, (size_t)op->st_groups * 3 * op->Nn * sizeof(double));
+    A(&op->st_wr, (size_t)op->st_groups * 4 * op->Nn * rb);
   }
   A(&op->scratch, 2 * sizeof(double));
   A(&op->g_red, 2 * kMaxGrid * 4 * sizeof(double));
@@ -781,6 +935,7 @@ int ptg_op_set_plan(ptg_op* op, int kind, int cs, int ng) {
       if (p.max_active_clusters <= 0) continue;
       p.twolevel = mode > TL_NONE;
       p.vc = uses_vcycle(op, mode);
+      p.l3 = uses_three(op, mode);
       op->plan_override[kind] = p;
       return PTG_OK;
     }
@@ -818,6 +973,16 @@ int ptg_fe_assemble_operator(ptg_op* op, const double* rho_d, cudaStream_t strea
   out.fload = op->fload;
   PTG_CUDA(launch_assemble(op->g.nx, op->g.ny, op->g.h, op->mat, op->tm.dt, op->dtau, rho_d, op->q_elem,
                            op->dirichlet, out, op->stats, stream));
+  if (op->w32) {
+    NodeWeights Af;
+    Af.C = out.node[0];
+    Af.E = out.node[1];
+    Af.N = out.node[2];
+    Af.NE = out.node[3];
+    Af.NW = out.node[4];
+    PTG_CUDA(launch_stream_weights((int)PN, Af, op->dirichlet, op->g.nx, op->g.ny, op->W, op->w32 + kSlack,
+                                   op->w64_inv + kSlack, stream));
+  }
   if (op->tl_m) {
     NodeWeights Ac;
     Ac.C = out.node[5];
@@ -827,6 +992,9 @@ int ptg_fe_assemble_operator(ptg_op* op, const double* rho_d, cudaStream_t strea
     Ac.NW = out.node[9];
     PTG_CUDA(launch_coarse_setup(op->g.nx, op->g.ny, op->W, op->tl_m, Ac, op->dirichlet, op->tl_Ac, op->tl_band,
                                  op->tl_X, op->tl_Ainv, stream));
+    if (op->tl3_m > 0)
+      PTG_CUDA(launch_threelevel_setup(op->g.nx, op->g.ny, op->W, Ac, op->dirichlet, op->tl3_m, op->tl3_A1,
+                                       op->tl3_Ac, op->tl3_band, op->tl3_X, op->tl3_Ainv, stream));
   }
   if (op->mesh) {                // the 2h-mesh op on the averaged design
     PTG_CUDA(mesh_design(op->g.nx, op->g.ny, rho_d, op->mesh_rho, stream));
@@ -861,19 +1029,29 @@ int ptg_fine_propagate_slices(ptg_op* op, int schedule, int s0, int ns, const do
 
 int ptg_coarse_sweep(ptg_op* op, int direction, const double* X_field, const double* X_aux, const double* T_hist,
                      const double* Theta_d, double* G_field, double* G_aux, cudaStream_t stream) {
+  if (!op) return PTG_EINVAL;
+  return ptg_coarse_sweep_slices(op, direction, 0, op->tm.Ntau, X_field, X_aux, T_hist, Theta_d, G_field, G_aux,
+                                 stream);
+}
+
+int ptg_coarse_sweep_slices(ptg_op* op, int direction, int s0, int ns, const double* X_field, const double* X_aux,
+                            const double* T_hist, const double* Theta_d, double* G_field, double* G_aux,
+                            cudaStream_t stream) {
   if (!op || !X_field || !X_aux || !G_field || !G_aux) return PTG_EINVAL;
   if (direction != PTG_PRIMAL && direction != PTG_ADJOINT) return PTG_EINVAL;
   if (direction == PTG_ADJOINT && (!T_hist || !Theta_d)) return PTG_EINVAL;
+  if (s0 < 0 || ns < 1 || s0 + ns > op->tm.Ntau) return PTG_EINVAL;
   DeviceGuard dg(op->device);
   if (op->mesh) {
+    if (s0 != 0 || ns != op->tm.Ntau) return PTG_EINVAL;   // the 2h-mesh G runs every slice
     op->last_stream = stream;
     return mesh_coarse_sweep(op, direction, X_field, X_aux, T_hist, Theta_d, G_field, G_aux, stream);
   }
   StepParams P;
   base_params(op, P);
   P.kind = direction == PTG_PRIMAL ? KIND_COARSE_PRI : KIND_COARSE_ADJ;
-  P.s0 = 0;
-  P.ns = op->tm.Ntau;
+  P.s0 = s0;
+  P.ns = ns;
   P.in_field = X_field;
   P.in_aux = X_aux;
   P.out_field = G_field;
@@ -882,7 +1060,63 @@ int ptg_coarse_sweep(ptg_op* op, int direction, const double* X_field, const dou
   P.hist_j0 = 0;
   P.hist_rows = T_hist ? op->tm.Nt + 1 : 0;
   P.Theta = Theta_d;
-  return run(op, P, op->tm.Ntau, stream);
+  return run(op, P, ns, stream);
+}
+
+int ptg_coarse_adjoint_split(ptg_op* op, int s0, int ns, const double* V_lam, const double* V_g, const double* T_hist,
+                             double* H_lam, double* H_g, double* S_lam, double* S_g, cudaStream_t stream) {
+  if (!op || !V_lam || !V_g || !T_hist || !H_lam || !H_g || !S_lam || !S_g) return PTG_EINVAL;
+  if (s0 < 0 || ns < 1 || s0 + ns > op->tm.Ntau) return PTG_EINVAL;
+  if (op->mesh) return PTG_EINVAL;                       // the 2h-mesh G has its own adjoint path
+  DeviceGuard dg(op->device);
+  for (int part = 1; part <= 2; ++part) {
+    StepParams P;
+    base_params(op, P);
+    P.kind = KIND_COARSE_ADJ;
+    P.s0 = s0;
+    P.ns = ns;
+    P.src_mode = part;
+    P.in_field = V_lam;
+    P.in_aux = V_g;
+    P.out_field = part == 1 ? H_lam : S_lam;
+    P.out_aux = part == 1 ? H_g : S_g;
+    P.hist = const_cast<double*>(T_hist);
+    P.hist_j0 = 0;
+    P.hist_rows = op->tm.Nt + 1;
+    P.Theta = nullptr;
+    const int rc = run(op, P, ns, stream);
+    if (rc != PTG_OK) return rc;
+  }
+  return PTG_OK;
+}
+
+int ptg_op_overlap_ok(ptg_op* op, int* ok) {
+  if (!op || !ok) return PTG_EINVAL;
+  *ok = 0;
+  if (op->M < 2 || op->mesh) return PTG_OK;
+  DeviceGuard dg(op->device);
+  Plan pc, pa;
+  int rc = choose_plan(op, kind_precision(op->sv.precision, KIND_CORRECT_PRI), KIND_CORRECT_PRI, 1, &pc);
+  if (rc == PTG_OK)
+    rc = choose_plan(op, kind_precision(op->sv.precision, KIND_COARSE_ADJ), KIND_COARSE_ADJ, op->tm.Ntau, &pa);
+  if (rc != PTG_OK) return rc;
+  *ok = !pc.wide && !pa.wide;
+  return PTG_OK;
+}
+
+int ptg_coarse_adjoint_combine(ptg_op* op, int s0, int ns, const double* Theta_d, const double* H_lam,
+                               const double* H_g, const double* S_lam, const double* S_g, double* G_lam, double* G_g,
+                               cudaStream_t stream) {
+  if (!op || !Theta_d || !H_lam || !H_g || !S_lam || !S_g || !G_lam || !G_g) return PTG_EINVAL;
+  if (s0 < 0 || ns < 1 || s0 + ns > op->tm.Ntau) return PTG_EINVAL;
+  DeviceGuard dg(op->device);
+  const long long Nn = op->Nn, Ne = (long long)op->g.nx * op->g.ny;
+  const long long ol = (long long)s0 * Nn, og = (long long)s0 * Ne;
+  op->last_stream = stream;
+  PTG_CUDA(launch_adjoint_combine((long long)ns * Nn, (long long)ns * Ne, Theta_d, op->tm.p, (int)Ne,
+                                  op->tm.objective == PTG_OBJ_MODIFIED, H_lam + ol, H_g + og, S_lam + ol, S_g + og,
+                                  G_lam + ol, G_g + og, stream));
+  return PTG_OK;
 }
 
 int ptg_parareal_correct(ptg_op* op, int direction, const double* F_field, const double* F_aux, const double* G_field,
@@ -982,6 +1216,13 @@ int ptg_get_stats(ptg_op* op, ptg_stats* out) {
     out->kind_cg_iters[k] = (long long)s.kind_cg_iters[k];
     out->kind_refinements[k] = (long long)s.kind_refinements[k];
   }
+  return PTG_OK;
+}
+
+int ptg_op_set_wait_limit(ptg_op* op, long long polls) {
+  if (!op || polls < 0) return PTG_EINVAL;
+  std::lock_guard<std::mutex> lk(op->mu);
+  op->wait_limit = polls;
   return PTG_OK;
 }
 
@@ -1211,7 +1452,7 @@ int batch_twolevel_mode(const ptg_batch* b, int ph) {
   int mode = TL_NONE;
   for (const ptg_op* op : b->ops)
     if (twolevel_rows(op, b->precision, phase_kind(ph), 1) > 0) mode = std::max(mode, strongest_mode(op));
-  return mode;
+  return std::min(mode, (int)TL_VCYCLE);   // batches run at most the two-grid cycle
 }
 
 int batch_default(ptg_batch* b, int ph) {

@@ -1,4 +1,5 @@
 // assemble.cu -- a1 (SIMP coefficients and element weights) and a6 (sensitivity reduction).
+#include <algorithm>
 #include <cstdint>
 #include "ptg_device.cuh"
 #include "ptg_internal.h"
@@ -143,9 +144,8 @@ cudaError_t launch_assemble(int nx, int ny, double h, const ptg_material& m, dou
 }
 
 // a6, Eq. 4.7: per element e and time chunk, sum over j of
-//   lambda_j,e^T ( dk_e Ke T_j,e + dc_e/dt Me (T_j - T_{j-1})_e ).
-// One thread per element; blockIdx.y selects a contiguous chunk of time steps.  T_{j-1} is
-// carried in registers from the previous step, so each step reads lambda_j and T_j once.
+//   lambda_j,e^T ( dk_e Ke T_j,e + dc_e/dt Me (T_j - T_{j-1})_e )   (sens_element_sum).
+// One thread per element; blockIdx.y selects a contiguous chunk of time steps.
 __global__ void sens_kernel(int nx, int ny, double h, double dt, int has_dc, const double* __restrict__ dk,
                             const double* __restrict__ dc, const double* __restrict__ lam, int j0, int j1,
                             const double* __restrict__ T, int hist_j0, int steps_per_chunk,
@@ -157,35 +157,10 @@ __global__ void sens_kernel(int nx, int ny, double h, double dt, int has_dc, con
   const int ja = j0 + chunk * steps_per_chunk;
   const int jb = min(j1, ja + steps_per_chunk - 1);
   const int ey = e / nx, ex = e % nx;
-  const int g0 = ey * nn + ex;
-  const double h2 = h * h / 36.0;
   const double dke = dk[e], dce = has_dc ? dc[e] / dt : 0.0;
-  double acc = 0.0;
-  if (ja <= jb) {
-    const double* Tp = T + (size_t)(ja - 1 - hist_j0) * Nn;
-    double psw = Tp[g0], pse = Tp[g0 + 1], pne = Tp[g0 + nn + 1], pnw = Tp[g0 + nn];
-    for (int j = ja; j <= jb; ++j) {
-      const double* Tj = T + (size_t)(j - hist_j0) * Nn;
-      const double* Lj = lam + (size_t)(j - j0) * Nn;
-      const double tsw = Tj[g0], tse = Tj[g0 + 1], tne = Tj[g0 + nn + 1], tnw = Tj[g0 + nn];
-      const double lsw = Lj[g0], lse = Lj[g0 + 1], lne = Lj[g0 + nn + 1], lnw = Lj[g0 + nn];
-      const double ksw = 4.0 * tsw - tse - 2.0 * tne - tnw;
-      const double kse = -tsw + 4.0 * tse - tne - 2.0 * tnw;
-      const double kne = -2.0 * tsw - tse + 4.0 * tne - tnw;
-      const double knw = -tsw - 2.0 * tse - tne + 4.0 * tnw;
-      double term = dke * (lsw * ksw + lse * kse + lne * kne + lnw * knw) / 6.0;
-      if (has_dc) {
-        const double dsw = tsw - psw, dse = tse - pse, dne = tne - pne, dnw = tnw - pnw;
-        const double msw = 4.0 * dsw + 2.0 * dse + dne + 2.0 * dnw;
-        const double mse = 2.0 * dsw + 4.0 * dse + 2.0 * dne + dnw;
-        const double mne = dsw + 2.0 * dse + 4.0 * dne + 2.0 * dnw;
-        const double mnw = 2.0 * dsw + dse + 2.0 * dne + 4.0 * dnw;
-        term += dce * (lsw * msw + lse * mse + lne * mne + lnw * mnw) * h2;
-      }
-      acc += term;
-      psw = tsw; pse = tse; pne = tne; pnw = tnw;
-    }
-  }
+  const double acc = ja <= jb ? sens_element_sum(ey * nn + ex, nn, Nn, h * h / 36.0, dke, dce, has_dc != 0, lam, j0,
+                                                 T, hist_j0, ja, jb)
+                              : 0.0;
   partial[(size_t)chunk * Ne + e] = acc;
 }
 
@@ -237,6 +212,65 @@ cudaError_t launch_sensitivities(int nx, int ny, int Nt, double h, double dt, in
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   sens_reduce_kernel<<<(Ne + 255) / 256, 256, 0, stream>>>(Ne, used, 1.0 / Nt, partial, grad);
+  return cudaGetLastError();
+}
+
+// G_adj = H + c S on rows [0, n_l) of a lambda block and [0, n_g) of a g block, with the
+// adjoint source scale c of Eq. 4.6 (Theta^(1-p)/Ne, or p/Ne for the modified objective of
+// Sec. 7.1) read from the device scalar Theta.
+__global__ void adjoint_combine_kernel(long long n_l, long long n_g, const double* __restrict__ Theta, double p,
+                                       int Ne, int modified, const double* __restrict__ H_l,
+                                       const double* __restrict__ H_g, const double* __restrict__ S_l,
+                                       const double* __restrict__ S_g, double* __restrict__ G_l,
+                                       double* __restrict__ G_g) {
+  const double c = (modified ? p : pow(*Theta, 1.0 - p)) / (double)Ne;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_l + n_g; i += stride) {
+    if (i < n_l)
+      G_l[i] = fma(c, S_l[i], H_l[i]);
+    else
+      G_g[i - n_l] = fma(c, S_g[i - n_l], H_g[i - n_l]);
+  }
+}
+
+cudaError_t launch_adjoint_combine(long long n_l, long long n_g, const double* Theta, double p, int Ne, int modified,
+                                   const double* H_l, const double* H_g, const double* S_l, const double* S_g,
+                                   double* G_l, double* G_g, cudaStream_t stream) {
+  const long long n = n_l + n_g;
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 4 * 152);
+  adjoint_combine_kernel<<<blocks, 256, 0, stream>>>(n_l, n_g, Theta, p, Ne, modified, H_l, H_g, S_l, S_g, G_l, G_g);
+  return cudaGetLastError();
+}
+
+// FP32 node weights of C/dt + K and 1/C for the streamed fine propagators, on the n = (ny+3) W
+// entries of the padded node grid (rows iy = -1..ny+1); arrays `stride` floats apart.  1/C is 0
+// on Dirichlet and out-of-grid nodes (so z = r / C vanishes there).
+__global__ void stream_weights_kernel(int n, int stride, NodeWeights A, const uint8_t* __restrict__ dirichlet, int nx,
+                                      int ny, int W, float* __restrict__ w32, double* __restrict__ w64_inv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int iy = i / W - 1, ix = i % W - 1;
+  const bool unknown = iy >= 0 && iy <= ny && ix >= 0 && ix <= nx && dirichlet[iy * (nx + 1) + ix] == 0;
+  w32[i] = (float)A.C[i];
+  w32[stride + i] = (float)A.E[i];
+  w32[2 * stride + i] = (float)A.N[i];
+  w32[3 * stride + i] = (float)A.NE[i];
+  w32[4 * stride + i] = (float)A.NW[i];
+  const double inv = unknown ? 1.0 / A.C[i] : 0.0;
+  w32[5 * stride + i] = (float)inv;
+  w64_inv[i] = inv;
+}
+
+cudaError_t launch_stream_weights(int stride, const NodeWeights& A, const uint8_t* dirichlet, int nx, int ny, int W,
+                                  float* w32, double* w64_inv, cudaStream_t stream) {
+  const int n = (ny + 3) * W;
+  stream_weights_kernel<<<(n + 255) / 256, 256, 0, stream>>>(n, stride, A, dirichlet, nx, ny, W, w32, w64_inv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sens_reduce(int Ne, int nchunks, double inv_nt, const double* partial, double* grad,
+                               cudaStream_t stream) {
+  sens_reduce_kernel<<<(Ne + 255) / 256, 256, 0, stream>>>(Ne, nchunks, inv_nt, partial, grad);
   return cudaGetLastError();
 }
 

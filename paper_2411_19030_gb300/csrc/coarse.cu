@@ -174,6 +174,125 @@ __global__ void pack_inverse_kernel(int nax, int nay, const float* __restrict__ 
   Ainv[(size_t)Pi * ncp + Q] = v;
 }
 
+// ---------------------------------------------------------------------------- three levels
+// The 2h level of the three-level cycle: node (I, J), I = 0..nx1, J = 0..ny1 (nx = 2 nx1,
+// ny = 2 ny1) sits on fine node (2I, 2J); P1 interpolates bilinearly, so the fine node
+// (2I + di, 2J + dj), |di|, |dj| <= 1, takes the weight w(di) w(dj) of 2h node (I, J), with
+// w(0) = 1 and w(+-1) = 1/2; rows of P1 at Dirichlet fine nodes are zero.  A1 = P1^T A P1 is a
+// 9-point operator; one thread per (2h node a, neighbour b) sums P1(i, a) A(i, j) P1(j, b) over
+// the free fine nodes i in the support of a and their free fine neighbours j (fixed order).
+// A 2h node whose support holds no free fine node gets the identity row.
+__device__ __forceinline__ double p1_weight(int d) { return d == 0 ? 1.0 : 0.5; }
+
+__global__ void galerkin_l1_kernel(int nx, int ny, int W, NodeWeights A, const uint8_t* __restrict__ dirichlet,
+                                   int nx1, int ny1, double* __restrict__ A1) {
+  const int n1 = (nx1 + 1) * (ny1 + 1);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 9 * n1) return;
+  const int k = t / n1, a = t - k * n1;
+  const int I = a % (nx1 + 1), J = a / (nx1 + 1);
+  const int dI = k % 3 - 1, dJ = k / 3 - 1;
+  const int Ib = I + dI, Jb = J + dJ;
+  double sum = 0.0;
+  auto free_node = [&](int iy, int ix) {
+    return iy >= 0 && iy <= ny && ix >= 0 && ix <= nx && !dirichlet[iy * (nx + 1) + ix];
+  };
+  if (Ib >= 0 && Ib <= nx1 && Jb >= 0 && Jb <= ny1) {
+    for (int dj = -1; dj <= 1; ++dj) {
+      for (int di = -1; di <= 1; ++di) {
+        const int iy = 2 * J + dj, ix = 2 * I + di;
+        if (!free_node(iy, ix)) continue;
+        const double wa = p1_weight(di) * p1_weight(dj);
+        const int go = (iy + 1) * W + ix + 1;
+        // the 9 couplings of fine node i: C, E, W, N, S, NE, SW, NW, SE
+        const int dyv[9] = {0, 0, 0, 1, -1, 1, -1, 1, -1};
+        const int dxv[9] = {0, 1, -1, 0, 0, 1, -1, -1, 1};
+        const double wv[9] = {A.C[go], A.E[go], A.E[go - 1], A.N[go], A.N[go - W],
+                              A.NE[go], A.NE[go - W - 1], A.NW[go], A.NW[go - W + 1]};
+        for (int n = 0; n < 9; ++n) {
+          const int jy = iy + dyv[n], jx = ix + dxv[n];
+          if (!free_node(jy, jx)) continue;
+          const int ox = jx - 2 * Ib, oy = jy - 2 * Jb;
+          if (ox < -1 || ox > 1 || oy < -1 || oy > 1) continue;
+          sum += wa * wv[n] * (p1_weight(ox) * p1_weight(oy));
+        }
+      }
+    }
+  }
+  if (k == 4 && !(sum > 0.0)) sum = 1.0;   // no free fine node in the support
+  A1[(size_t)k * n1 + a] = sum;
+}
+
+// A2 = P2^T A1 P2 for aggregates of m x m 2h nodes (nax x nay, the last of a direction
+// absorbing the remainder): one CTA per aggregate a, fixed-order block sums into the dense
+// [nc][nc] FP64 matrix (as galerkin_kernel on the fine grid).
+__global__ void galerkin_l2_kernel(int nx1, int ny1, int m, int nax, int nay, const double* __restrict__ A1,
+                                   double* __restrict__ Ac) {
+  const int a = blockIdx.x;
+  const int ax = a % nax, ay = a / nax;
+  const int nc = nax * nay, n1 = (nx1 + 1) * (ny1 + 1);
+  const int y0 = ay * m, y1 = (ay == nay - 1) ? ny1 : ay * m + m - 1;
+  const int x0 = ax * m, x1 = (ax == nax - 1) ? nx1 : ax * m + m - 1;
+  const int wx = x1 - x0 + 1, cnt = wx * (y1 - y0 + 1);
+  __shared__ double part[9][32];
+  double acc[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc[k] = 0.0;
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    const int J = y0 + t / wx, I = x0 + t % wx;
+    const int i = J * (nx1 + 1) + I;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const int Jb = J + k / 3 - 1, Ib = I + k % 3 - 1;
+      if (Jb < 0 || Jb > ny1 || Ib < 0 || Ib > nx1) continue;
+      const int kk = (l3_agg(Jb, m, nay) - ay + 1) * 3 + (l3_agg(Ib, m, nax) - ax + 1);
+      const double v = A1[(size_t)k * n1 + i];
+#pragma unroll
+      for (int q = 0; q < 9; ++q)
+        if (q == kk) acc[q] += v;
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    double v = acc[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) part[k][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    const int k = threadIdx.x;
+    double v = 0.0;
+    for (int w = 0; w < nw; ++w) v += part[k][w];
+    const int bx = ax + k % 3 - 1, by = ay + k / 3 - 1;
+    if (bx >= 0 && bx < nax && by >= 0 && by < nay) Ac[(size_t)a * nc + by * nax + bx] = v;
+  }
+}
+
+cudaError_t launch_threelevel_setup(int nx, int ny, int W, const NodeWeights& A, const uint8_t* dirichlet, int m,
+                                    double* A1, double* Ac, float* band, float* X, float* Ainv, cudaStream_t stream) {
+  const int nx1 = nx / 2, ny1 = ny / 2, n1 = (nx1 + 1) * (ny1 + 1);
+  const int nax = coarse_aggregates(nx1, m), nay = coarse_aggregates(ny1, m);   // (n1 + 1) / m 2h nodes
+  const int nc = nax * nay, ncp = coarse_row_stride(nax) * nay;
+  const int b = nax + 1;
+  galerkin_l1_kernel<<<(9 * n1 + 255) / 256, 256, 0, stream>>>(nx, ny, W, A, dirichlet, nx1, ny1, A1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(Ac, 0, sizeof(double) * nc * nc, stream)) != cudaSuccess) return e;
+  galerkin_l2_kernel<<<nc, 128, 0, stream>>>(nx1, ny1, m, nax, nay, A1, Ac);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const size_t ldlt_smem = sizeof(float) * nc * (b + 1);
+  const size_t inv_smem = sizeof(float) * (nc * (kBandMax + 1) + (nc + kBandMax) * 32);
+  if ((e = configure_kernel((const void*)band_ldlt_kernel, ldlt_smem, false)) != cudaSuccess) return e;
+  if ((e = configure_kernel((const void*)band_inverse_kernel, inv_smem, false)) != cudaSuccess) return e;
+  band_ldlt_kernel<<<1, 32, ldlt_smem, stream>>>(nc, b, Ac, band);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  band_inverse_kernel<<<(nc + 31) / 32, 32, inv_smem, stream>>>(nc, b, band, X);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  pack_inverse_kernel<<<dim3((ncp + 127) / 128, ncp), 128, 0, stream>>>(nax, nay, X, Ainv);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_coarse_setup(int nx, int ny, int W, int m, const NodeWeights& A, const uint8_t* dirichlet,
                                 double* Ac, float* band, float* X, float* Ainv, cudaStream_t stream) {
   const int nax = coarse_aggregates(nx, m), nay = coarse_aggregates(ny, m);

@@ -41,6 +41,23 @@ struct ClusterComm {
   __device__ void push_halos(T* buf, const Slab& sb) {
     ptg::push_halos(buf, sb, cl);
   }
+  // The same for a buffer on the 2h level of the three-level cycle: rows of W1 floats, R1 owned
+  // rows here, R1b owned rows in the CTA below (whose halo row lr = R1b receives row 0).
+  __device__ void push_halos_rows(float* buf, int W1, int R1, int R1b, int rank, int cs) {
+    const int nv = W1 / 4;
+    if (rank > 0) {
+      float* dst = cl.map_shared_rank(buf, (unsigned)(rank - 1));
+      const uint4* s = reinterpret_cast<const uint4*>(buf + 1 * W1);
+      uint4* d = reinterpret_cast<uint4*>(dst + (R1b + 1) * W1);
+      for (int i = threadIdx.x; i < nv; i += blockDim.x) d[i] = s[i];
+    }
+    if (rank < cs - 1) {
+      float* dst = cl.map_shared_rank(buf, (unsigned)(rank + 1));
+      const uint4* s = reinterpret_cast<const uint4*>(buf + R1 * W1);
+      uint4* d = reinterpret_cast<uint4*>(dst);
+      for (int i = threadIdx.x; i < nv; i += blockDim.x) d[i] = s[i];
+    }
+  }
   // Edge rows sent straight from registers: the thread holding columns [col, col+4) of the
   // owned row lr (0 or R-1) stores them into the neighbour's two-row buffer `edge` ([0]: the
   // row below that CTA's slab, [1]: the row above); visible after the next barrier.
@@ -107,7 +124,8 @@ struct GridComm {
   // Counting barrier over all CTAs of the launch (co-resident: cooperative launch).  Thread 0
   // of each CTA makes the CTA's global writes visible, arrives, and waits for the generation
   // to move on; the last arriver resets the count and releases the next generation.  A wait
-  // that exceeds kGridSpinLimit polls records PTG_ETIMEOUT and returns; once any CTA has
+  // that reaches P.wait_limit polls (kGridSpinLimit if not positive) without the release
+  // records PTG_ETIMEOUT and returns; once any CTA has
   // recorded it (the launch's status word, P.g_bar[2]), every later wait returns at once, so a
   // broken launch ends quickly with the error instead of waiting out every barrier.
   __device__ void barrier() {
@@ -124,10 +142,11 @@ struct GridComm {
         __threadfence();
         st_release_gpu(gen, g0 + 1u);
       } else {
-        long spins = 0;
+        const long long limit = P.wait_limit > 0 ? P.wait_limit : (long long)kGridSpinLimit;
+        long long spins = 0;
         while (ld_acquire_gpu(gen) == g0) {
           if ((++spins & 255) == 0 && ld_acquire_gpu(broken) != 0u) break;
-          if (spins > kGridSpinLimit) {
+          if (spins >= limit) {
             record_error(P.stats, PTG_ETIMEOUT, P.stats_kind, -1);
             atomicExch(broken, 1u);
             break;
@@ -226,6 +245,24 @@ struct GridComm {
     __threadfence();                                // each writer orders its own stores
     pending_lo = reinterpret_cast<unsigned char*>(buf);
     pending_hi = reinterpret_cast<unsigned char*>(buf + (sb.R + 1) * sb.W);
+    pending_bytes = nb;
+  }
+  // 2h-level rows (see ClusterComm::push_halos_rows) through the global halo slots.
+  __device__ void push_halos_rows(float* buf, int W1, int R1, int /*R1b*/, int /*rank*/, int /*cs*/) {
+    const int nb = W1 * (int)sizeof(float);
+    hset ^= 1;
+    unsigned char* out = reinterpret_cast<unsigned char*>(P.g_halo) + halo_slot(hset, (int)blockIdx.x);
+    const uint4* s0 = reinterpret_cast<const uint4*>(buf + 1 * W1);
+    const uint4* s1 = reinterpret_cast<const uint4*>(buf + R1 * W1);
+    uint4* d0 = reinterpret_cast<uint4*>(out);
+    uint4* d1 = reinterpret_cast<uint4*>(out + P.g_halo_row_bytes);
+    for (int i = threadIdx.x; i < nb / 16; i += blockDim.x) {
+      d0[i] = s0[i];
+      d1[i] = s1[i];
+    }
+    __threadfence();
+    pending_lo = reinterpret_cast<unsigned char*>(buf);
+    pending_hi = reinterpret_cast<unsigned char*>(buf + (R1 + 1) * W1);
     pending_bytes = nb;
   }
   // Edge rows from registers (see ClusterComm::put_edge): into this CTA's slots of the next set.

@@ -135,4 +135,26 @@ int ptg_mma_update(ptg_mma* m, const double* x, double f0, const double* df0, do
   return PTG_OK;
 }
 
+int ptg_mma_get_state(const ptg_mma* m, long long* k, double* x1, double* x2, double* L, double* U) {
+  if (!m || !k || !x1 || !x2 || !L || !U) return PTG_EINVAL;
+  *k = m->k;
+  for (int j = 0; j < m->n; ++j) {
+    x1[j] = m->x1[j];
+    x2[j] = m->x2[j];
+    L[j] = m->L[j];
+    U[j] = m->U[j];
+  }
+  return PTG_OK;
+}
+
+int ptg_mma_set_state(ptg_mma* m, long long k, const double* x1, const double* x2, const double* L, const double* U) {
+  if (!m || k < 0 || !x1 || !x2 || !L || !U) return PTG_EINVAL;
+  m->k = (long)k;
+  m->x1.assign(x1, x1 + m->n);
+  m->x2.assign(x2, x2 + m->n);
+  m->L.assign(L, L + m->n);
+  m->U.assign(U, U + m->n);
+  return PTG_OK;
+}
+
 }  // extern "C"

@@ -99,6 +99,8 @@ struct StepParams {
   const double* src_field;   // coarse kinds: [Ntau][Nn] right-hand-side source per slice instead of q_j f
   int objective;             // PTG_OBJ_POWER_MEAN or PTG_OBJ_MODIFIED
   int plt;                   // correction kinds: coarse propagators identically zero (copy F)
+  int src_mode;              // coarse adjoint: 0 source scale Theta^(1-p)/Ne (or p/Ne); 1 no source (the part
+                             // driven by the state); 2 unit source scale from zero lambda and zero g
   // two-level preconditioner of the coarse-step solves (Ainv == null: Jacobi)
   const float* Ainv;         // [ncp][ncp] inverse of the Galerkin coarse matrix (padded layout)
   int cm, nax, nay;          // aggregate size m and aggregate counts per direction
@@ -114,11 +116,31 @@ struct StepParams {
                              // states (or null: every step starts from the last state)
   int tl_nu;                 // V-cycle smoothing: <= 1 one global Jacobi step before and after; k >= 2 k
                              // slab-local steps before and after
+  // three-level cycle (P.tl_l3): the V-cycle's coarse correction becomes a two-grid cycle of its
+  // own on the 2h level (node (I, J) at fine node (2I, 2J), operator A1 = P1^T A P1 with bilinear
+  // P1), whose coarse level is the aggregates of m x m 2h nodes (cm, nax, nay, Ainv, tl_naj then
+  // describe that aggregation)
+  int tl_l3;
+  int l3_nx1, l3_ny1;        // 2h nodes per direction minus one (nx / 2, ny / 2)
+  int l3_W1;                 // padded row width of the 2h buffers
+  int l3_r1max;              // most 2h rows owned by a CTA of the launch
+  const double* A1;          // [9][(ny1 + 1) (nx1 + 1)] 2h stencil, k = (dJ + 1) * 3 + (dI + 1)
+  // streamed fine propagators (stream.cuh): per group of P.cs CTAs, [3][Nn] FP64 (x, x, b) and
+  // [4][Nn] CG vectors (r, p, q, d) in the kernel's precision; the FP32 operator C/dt + K as
+  // per-node weights C, E, N, NE, NW then 1/C (0 off the unknowns), each w32_stride floats in the
+  // padded node layout; its FP64 inverse diagonal for FP64 CG
+  double* st_w64;
+  void* st_wr;
+  const float* w32;
+  const float* w32_inv;
+  int w32_stride;
+  const double* w64_inv;
   // one system over a whole cooperative grid (GridComm): global scratch of the op
   int wide;                  // 1: launched as stepper_wide_kernel, groups of cs CTAs
   int wide_tasks;            // tasks of a grid-wide launch (group g runs g, g + groups, ...)
   double* g_red;             // [2][kMaxGrid][4] reduction partials
   unsigned* g_bar;           // [4 per group] barrier: arrival count, generation, broken flag (zeroed per launch)
+  long long wait_limit;      // polls of a grid barrier before it reports PTG_ETIMEOUT (<= 0: kGridSpinLimit)
   void* g_halo;              // [2 sets][kMaxGrid][2] rows of g_halo_row_bytes: first / last owned row
   int g_halo_row_bytes;      // W * 8 (a row of doubles; float rows use the first half)
   float* g_tl;               // [kMaxGrid][ncp] restricted partials of the two-level preconditioner
@@ -187,6 +209,46 @@ inline size_t twolevel_smem_bytes(int W, int rmax, int cs, int nax, int nay, int
   return (b + 15) & ~size_t(15);
 }
 
+// Three-level cycle: the 2h rows J owned by the slab of fine rows r0 .. r0+R-1 are those with
+// r0 <= 2J < r0 + R, i.e. J0 = ceil(r0 / 2) .. ceil((r0 + R) / 2) - 1 (R >= 2 gives at least one).
+inline __host__ __device__ void l1_rows_of_slab(int r0, int R, int& J0, int& R1) {
+  J0 = (r0 + 1) / 2;
+  R1 = (r0 + R + 1) / 2 - J0;
+}
+// aggregate of 2h node index I (or J) among na aggregates of m nodes (the last absorbs the rest)
+inline __host__ __device__ int l3_agg(int I, int m, int na) {
+  const int a = I / m;
+  return a < na - 1 ? a : na - 1;
+}
+// Shared-memory bytes of the three-level cycle for one CTA: the aggregate level as in
+// twolevel_smem_bytes (naj aggregate rows, partials of every rank for a cluster), the fine
+// V-cycle buffers, the fine residual with halos, and on the 2h level (r1max owned rows of W1
+// entries): five buffers with halo rows, the restricted residual, nine stencil weights and
+// omega / diag per owned node, and the per-aggregate partial sums.
+inline size_t threelevel_smem_bytes(int W, int rmax, int cs, int W1, int r1max, int nax, int nay, int naj,
+                                    bool slots, int real_bytes, int nu) {
+  const size_t naxp = (size_t)coarse_row_stride(nax), ncp = naxp * nay;
+  const size_t halo = (size_t)(rmax + 2) * W + 2 * kSlack;
+  const size_t elems = (size_t)(rmax + 1) * W + 2 * kSlack;
+  const size_t halo1 = (size_t)(r1max + 2) * W1 + 2 * kSlack;
+  const size_t own1 = (size_t)r1max * W1 + 2 * kSlack;
+  size_t b = 0;
+  b += (size_t)naj * naxp * ncp * 4;        // rows of Ainv for the CTA's aggregates
+  if (slots) b += (size_t)cs * ncp * 4;     // restricted partials of every rank
+  b += ncp * 4;                             // their sum over the covering ranks
+  b += (size_t)naj * naxp * 4;              // coarse correction of the CTA's aggregates
+  b += 4 * (size_t)W * real_bytes;          // (the V-cycle's halo rows of q and r, unused here)
+  b += 2 * halo * 4;                        // fine smoother iterate and omega D^-1
+  if (real_bytes == 8) b += 3 * elems * 4;  // FP32 (D, S, T) element weights
+  if (nu >= 2) b += 2 * halo * 4;           // the slab-local smoother's two iterates
+  b += halo * 4;                            // fine residual with halo rows
+  b += 5 * halo1 * 4;                       // 2h: e1, u1, z1, two smoother iterates
+  b += 11 * own1 * 4;                       // 2h: restricted residual, 9 weights, omega / diag
+  b += (size_t)naj * naxp * 4;              // per-aggregate partial sums
+  b += (size_t)nay * 2 * 4;                 // covering rank range per aggregate row
+  return (b + 15) & ~size_t(15);
+}
+
 // Shared-memory footprint (bytes) of one CTA of the stepper.
 inline size_t stepper_smem_bytes(int nx, int rmax, int real_bytes, bool keep_ax = true) {
   const size_t W = (size_t)padded_width(nx);
@@ -210,8 +272,10 @@ struct Plan {
   int max_active_clusters = 0;
   bool twolevel = false;     // coarse kinds: two-level preconditioner (its shared memory is in smem)
   bool vc = false;           // ... in the V(1,1) cycle form (else additive)
+  bool l3 = false;           // ... as the three-level cycle
   bool keep_ax = true;       // the saved A x of the last residual is in smem
   bool wide = false;         // one task over a cooperative grid of cs CTAs (GridComm), no clusters
+  bool stream = false;       // fine kinds: the streamed propagator (stream.cuh), cs CTAs per slice
 };
 
 // CTAs of a grid-wide launch at most (>= the SM count of the chip).
@@ -223,6 +287,11 @@ cudaError_t launch_stepper_batch(int precision, int kind, const Plan& plan, cons
 cudaError_t query_batch_occupancy(int precision, int kind, int cs, int ng, int nthreads, size_t smem, int* nclusters);
 cudaError_t launch_coarse_setup(int nx, int ny, int W, int m, const NodeWeights& A, const uint8_t* dirichlet,
                                 double* Ac, float* band, float* X, float* Ainv, cudaStream_t stream);
+// Three-level set-up from the coarse-step operator's node weights: the 2h Galerkin stencil A1
+// ([9][(ny/2 + 1)(nx/2 + 1)]), then the aggregates of m x m 2h nodes: A2 = P2^T A1 P2 (dense FP64
+// in Ac), its band LDL^T and dense inverse in FP32, packed as for the fine aggregates.
+cudaError_t launch_threelevel_setup(int nx, int ny, int W, const NodeWeights& A, const uint8_t* dirichlet, int m,
+                                    double* A1, double* Ac, float* band, float* X, float* Ainv, cudaStream_t stream);
 // Raise a kernel's dynamic shared-memory limit (and allow non-portable cluster sizes) once per
 // device; later calls with no larger footprint make no attribute call.
 cudaError_t configure_kernel(const void* k, size_t smem, bool cluster);
@@ -251,6 +320,19 @@ cudaError_t launch_objective_from_modified(int Ne, double p, const double* Theta
 cudaError_t launch_sensitivities(int nx, int ny, int Nt, double h, double dt, int has_dc, const double* dk,
                                  const double* dc, const double* lam, int j0, int j1, const double* T, int hist_j0,
                                  double* partial, int nchunks, double* grad, cudaStream_t stream);
+
+// FP32 copies of the node weights of C/dt + K (C, E, N, NE, NW) and 1/C (0 off the unknowns), and
+// the FP64 1/C, for the streamed fine propagators (padded node layout, PN entries each)
+cudaError_t launch_stream_weights(int stride, const NodeWeights& A, const uint8_t* dirichlet, int nx, int ny, int W,
+                                  float* w32, double* w64_inv, cudaStream_t stream);
+cudaError_t launch_stream(const StepParams& P, int precision, int ngroups, int nthreads, cudaStream_t stream);
+// G_l = H_l + c S_l ([n_l]) and G_g = H_g + c S_g ([n_g]), c the adjoint source scale of Theta
+cudaError_t launch_adjoint_combine(long long n_l, long long n_g, const double* Theta, double p, int Ne, int modified,
+                                   const double* H_l, const double* H_g, const double* S_l, const double* S_g,
+                                   double* G_l, double* G_g, cudaStream_t stream);
+// grad[e] -= inv_nt * (sum of partial[c][e] over c = 0..nchunks-1, in that order)
+cudaError_t launch_sens_reduce(int Ne, int nchunks, double inv_nt, const double* partial, double* grad,
+                               cudaStream_t stream);
 
 void set_last_error(const char* msg);
 

@@ -189,6 +189,20 @@ struct Stepper {
   float* vsd = nullptr;      // S = omega D^-1, rows -1..R (0 off the unknowns)
   float* ve0 = nullptr;      // slab-local smoothing (P.tl_nu >= 2): ping-pong iterates, rows -1..R,
   float* ve1 = nullptr;      // halo rows kept at zero
+  // three-level cycle (P.tl_l3, see vcycle3): the 2h rows [J0, J0 + R1) of this CTA (R1b: those
+  // of the CTA below), padded 2h row width W1, stride own1s of the owned-row 2h arrays
+  bool l3 = false;
+  int J0 = 0, R1 = 0, R1b = 0, W1 = 0, own1s = 0;
+  float* vw = nullptr;       // fine residual w0 = r - A e0, rows -1..R
+  float* b1x = nullptr;      // 2h rows -1..R1: e1 = S1 r1 (halo rows from the neighbours)
+  float* b1u = nullptr;      //                 u1 = e1 + P2 ec (owned and halo rows, computed here)
+  float* b1z = nullptr;      //                 z1 = u1 + S1 (r1 - A1 u1) (halo rows from the neighbours)
+  float* s1a = nullptr;      //                 slab-local smoothing iterates (halo rows kept at zero)
+  float* s1b = nullptr;
+  float* r1 = nullptr;       // owned 2h rows: restricted residual r1 = P1^T w0 (then r1 - A1 u1)
+  float* a1w = nullptr;      // [9][own1s] A1 weights of the owned 2h nodes, k = (dJ + 1) * 3 + (dI + 1)
+  float* s1d = nullptr;      // omega / diag(A1) of the owned 2h nodes
+  float* l3_items = nullptr; // partial sums of the 2h residual per aggregate of the owned rows
 
   __device__ Stepper(const StepParams& P_, Comm& comm_, unsigned char* dyn) : P(P_), comm(comm_) {
     sb.nx = P.nx;
@@ -253,6 +267,49 @@ struct Stepper {
           }
           for (float* z = v0 + threadIdx.x; z < t; z += blockDim.x) *z = 0.f;
         }
+        if (P.tl_l3) {
+          float* l0 = t;
+          vw = t + kSlack;  t += halo;
+          W1 = P.l3_W1;
+          const int halo1 = (P.l3_r1max + 2) * W1 + 2 * kSlack;
+          own1s = P.l3_r1max * W1 + 2 * kSlack;
+          b1x = t + kSlack;  t += halo1;
+          b1u = t + kSlack;  t += halo1;
+          b1z = t + kSlack;  t += halo1;
+          s1a = t + kSlack;  t += halo1;
+          s1b = t + kSlack;  t += halo1;
+          r1 = t + kSlack - W1;  t += own1s;     // r1[lr1 * W1 + I + 1]: owned rows from lr1 = 0
+          a1w = t + kSlack - W1; t += 9 * own1s;
+          s1d = t + kSlack - W1; t += own1s;
+          l3_items = t;      t += P.tl_naj * naxp;
+          for (float* z = l0 + threadIdx.x; z < t; z += blockDim.x) *z = 0.f;
+          tl_cov = reinterpret_cast<int*>(t);
+          l1_rows_of_slab(sb.r0, sb.R, J0, R1);
+          if (sb.rank > 0) {
+            int r0b, Rb, J0b;
+            slab_rows(P.ny + 1, P.cs, sb.rank - 1, r0b, Rb);
+            l1_rows_of_slab(r0b, Rb, J0b, R1b);
+          }
+          const int ny1 = P.l3_ny1;
+          aj0 = l3_agg(J0 > 0 ? J0 - 1 : 0, P.cm, P.nay);
+          naj = l3_agg(J0 + R1 <= ny1 ? J0 + R1 : ny1, P.cm, P.nay) - aj0 + 1;
+          ajo0 = l3_agg(J0, P.cm, P.nay);
+          najo = l3_agg(J0 + R1 - 1, P.cm, P.nay) - ajo0 + 1;
+          for (int J = threadIdx.x; J < P.nay; J += blockDim.x) {
+            int lo = -1, hi = -1;
+            for (int q = 0; q < P.cs; ++q) {
+              int r0q, Rq, J0q, R1q;
+              slab_rows(P.ny + 1, P.cs, q, r0q, Rq);
+              l1_rows_of_slab(r0q, Rq, J0q, R1q);
+              if (R1q > 0 && J >= l3_agg(J0q, P.cm, P.nay) && J <= l3_agg(J0q + R1q - 1, P.cm, P.nay)) {
+                if (lo < 0) lo = q;
+                hi = q;
+              }
+            }
+            tl_cov[2 * J] = lo;
+            tl_cov[2 * J + 1] = hi;
+          }
+        } else {
         tl_gs = t;    t += groups;
         tl_gagg = reinterpret_cast<int*>(t);  t += P.tl_vc ? groups + 2 * (W / kGroup) : groups;
         tl_cov = reinterpret_cast<int*>(t);
@@ -290,6 +347,7 @@ struct Stepper {
           }
           tl_cov[2 * J] = lo;
           tl_cov[2 * J + 1] = hi;
+        }
         }
       }
     }
@@ -337,6 +395,7 @@ struct Stepper {
     ax_valid = false;
     tl = coarse && P.tl_naj > 0 && P.Ainv != nullptr;
     vc = tl && P.tl_vc;
+    l3 = vc && P.tl_l3;
     if (tl && !tl_loaded) {        // rows of the aggregate rows aj0 .. aj0+naj-1 of Ainv, 16-byte copies
       const int naxp = coarse_row_stride(P.nax), ncp = naxp * P.nay;
       const int n4 = naj * naxp * ncp / 4;
@@ -372,6 +431,17 @@ struct Stepper {
           fmask |= 1u << (kGroup * k + j);
         }
         dinv[l0 + j] = v;
+      }
+    }
+    if (l3) {
+      // the 2h stencil and omega / diag of the owned 2h nodes (FP32)
+      const int n1 = P.l3_nx1 + 1, nn1 = n1 * (P.l3_ny1 + 1);
+      for (int t = threadIdx.x; t < R1 * n1; t += blockDim.x) {
+        const int lr1 = t / n1, I = t - lr1 * n1, o = lr1 * W1 + I + 1;
+        const int g = (J0 + lr1) * n1 + I;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) a1w[k * own1s + o] = (float)P.A1[(size_t)k * nn1 + g];
+        s1d[o] = (float)((double)P.tl_omega / P.A1[(size_t)4 * nn1 + g]);
       }
     }
     if (vc) {
@@ -851,7 +921,204 @@ struct Stepper {
       float t[4];
       stencil_elem32(vy, wd, ws, wt, l0, W, t);
 #pragma unroll
-      for (int j = 0; j < kGroup; ++j) w[k][j] = unknown(k, j) ? rf[k][j] - t[j] : 0.f;
+      for (int j = 0; j < kGroup; ++j) w[k][j] = unknown(k, j) ? (float)r[k][j] - t[j] : 0.f;
+    }
+    smooth_local(w, e);
+    Real rz = Real(0);
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+      if (l0 < 0) continue;
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) {
+        const float z = vy[l0 + j] + e[k][j];
+        zbuf[l0 + j] = (Real)z;
+        rz = fma(r[k][j], (Real)z, rz);
+      }
+    }
+    return rz;
+  }
+
+  // ---------------------------------------------------------------- three-level cycle
+  // 2h buffers: halo buffers (rows -1..R1) at (lr1 + 1) W1 + I + 1, owned-row arrays at lr1 W1 + I + 1
+  __device__ __forceinline__ int h1(int lr1, int I) const { return (lr1 + 1) * W1 + I + 1; }
+  __device__ __forceinline__ int o1(int lr1, int I) const { return lr1 * W1 + I + 1; }
+
+  // (A1 x) at the owned 2h node (lr1, I) from a halo buffer x (zero outside the 2h grid)
+  __device__ __forceinline__ float a1_apply(const float* __restrict__ x, int lr1, int I) const {
+    const int c = h1(lr1, I), o = o1(lr1, I);
+    float y = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) y = fmaf(a1w[k * own1s + o], x[c + (k / 3 - 1) * W1 + (k % 3 - 1)], y);
+    return y;
+  }
+
+  // refresh the 2h halo rows of every CTA from the neighbours' owned rows
+  __device__ void exchange_l1(float* buf) {
+    __syncthreads();
+    comm.push_halos_rows(buf, W1, R1, R1b, sb.rank, sb.cs);
+    comm.sync();
+  }
+
+  // P.tl_nu damped-Jacobi steps of A1_s e = s from e = 0 on the owned 2h rows, with the 2h halo
+  // rows held at zero (the diagonal block of A1 of this CTA's rows: a fixed polynomial in
+  // S1 A1_s times S1, symmetric, no communication); e goes to the owned rows of `out`.
+  __device__ void smooth_l1(const float* __restrict__ s, float* __restrict__ out) {
+    const int n1 = P.l3_nx1 + 1, n = R1 * n1;
+    float* cur = s1a;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const int lr1 = t / n1, I = t - lr1 * n1;
+      cur[h1(lr1, I)] = s1d[o1(lr1, I)] * s[o1(lr1, I)];
+    }
+    __syncthreads();
+    for (int it = 1; it < P.tl_nu; ++it) {
+      float* nxt = cur == s1a ? s1b : s1a;
+      for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const int lr1 = t / n1, I = t - lr1 * n1;
+        nxt[h1(lr1, I)] = fmaf(s1d[o1(lr1, I)], s[o1(lr1, I)] - a1_apply(cur, lr1, I), cur[h1(lr1, I)]);
+      }
+      __syncthreads();
+      cur = nxt;
+    }
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const int lr1 = t / n1, I = t - lr1 * n1;
+      out[h1(lr1, I)] = cur[h1(lr1, I)];
+    }
+    __syncthreads();
+  }
+
+  // The 2h part of the three-level cycle, from the fine residual w0 in vw (halo rows exchanged):
+  //   r1 = P1^T w0;  e1 = S1 r1;  ec = A2^-1 P2^T (r1 - A1 e1);  u1 = e1 + P2 ec;
+  //   z1 = u1 + S1 (r1 - A1 u1) into b1z with its halo rows exchanged.
+  __device__ __forceinline__ void l1_correct() {
+    const int W = sb.W, n1 = P.l3_nx1 + 1, ny1 = P.l3_ny1;
+    const int naxp = coarse_row_stride(P.nax), ncp = naxp * P.nay;
+    // r1 = P1^T w0 on the owned 2h rows: fine rows 2J-1 .. 2J+1 lie in -1 .. R
+    for (int t = threadIdx.x; t < R1 * n1; t += blockDim.x) {
+      const int lr1 = t / n1, I = t - lr1 * n1;
+      const int lr = 2 * (J0 + lr1) - sb.r0;
+      const float* c = vw + (lr + 1) * W + 2 * I + 1;
+      const float mid = fmaf(0.5f, c[-1] + c[1], c[0]);
+      const float lo = fmaf(0.5f, c[-W - 1] + c[-W + 1], c[-W]);
+      const float hi = fmaf(0.5f, c[W - 1] + c[W + 1], c[W]);
+      r1[o1(lr1, I)] = fmaf(0.5f, lo + hi, mid);
+    }
+    __syncthreads();
+    // 2h pre-smoothing e1 = S1 r1, exchanged
+    smooth_l1(r1, b1x);
+    exchange_l1(b1x);
+    // 2h residual r1 - A1 e1 (in s1a's owned rows), summed per aggregate of the owned rows and
+    // published to every CTA (16-byte chunks of 4 aggregates)
+    for (int t = threadIdx.x; t < R1 * n1; t += blockDim.x) {
+      const int lr1 = t / n1, I = t - lr1 * n1;
+      s1a[h1(lr1, I)] = r1[o1(lr1, I)] - a1_apply(b1x, lr1, I);
+    }
+    __syncthreads();
+    const int items = najo * naxp;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+      const int ay = ajo0 + it / naxp, ax = it % naxp;
+      float acc = 0.f;
+      if (ax < P.nax) {
+        const int ya = max(ay * P.cm, J0), yb = min(ay == P.nay - 1 ? ny1 : ay * P.cm + P.cm - 1, J0 + R1 - 1);
+        const int xa = ax * P.cm, xb = ax == P.nax - 1 ? n1 - 1 : ax * P.cm + P.cm - 1;
+        for (int J = ya; J <= yb; ++J)
+          for (int I = xa; I <= xb; ++I) acc += s1a[h1(J - J0, I)];
+      }
+      l3_items[it] = acc;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < (items / 4) * 16; t += blockDim.x) {
+      const int c = t >> 4;
+      const float4 chunk = reinterpret_cast<const float4*>(l3_items)[c];
+      const int item0 = 4 * c, ajl0 = item0 / naxp, ax0 = item0 - ajl0 * naxp;
+      comm.publish_tl(tl_slot, sb.rank * ncp + (ajo0 + ajl0) * naxp + ax0, chunk, t & 15, sb.cs);
+    }
+    comm.sync();
+    coarse_gather(true, 0.f);
+    // u1 = e1 + P2 ec on the owned and halo 2h rows
+    for (int t = threadIdx.x; t < (R1 + 2) * n1; t += blockDim.x) {
+      const int lr1 = t / n1 - 1, I = t - (lr1 + 1) * n1, J = J0 + lr1;
+      if (J < 0 || J > ny1) continue;
+      const float ec = tl_ec[(l3_agg(J, P.cm, P.nay) - aj0) * naxp + l3_agg(I, P.cm, P.nax)];
+      b1u[h1(lr1, I)] = b1x[h1(lr1, I)] + ec;
+    }
+    __syncthreads();
+    // 2h post-smoothing z1 = u1 + S1 (r1 - A1 u1), exchanged
+    for (int t = threadIdx.x; t < R1 * n1; t += blockDim.x) {
+      const int lr1 = t / n1, I = t - lr1 * n1;
+      r1[o1(lr1, I)] -= a1_apply(b1u, lr1, I);
+    }
+    __syncthreads();
+    smooth_l1(r1, b1z);
+    for (int t = threadIdx.x; t < R1 * n1; t += blockDim.x) {
+      const int lr1 = t / n1, I = t - lr1 * n1;
+      b1z[h1(lr1, I)] += b1u[h1(lr1, I)];
+    }
+    exchange_l1(b1z);
+  }
+
+  // Three-level cycle z = M^-1 r in FP32 over the fine, 2h and aggregate levels:
+  //   e0 = S0 r;  w0 = r - A e0;  r1 = P1^T w0;
+  //   e1 = S1 r1;  ec = A2^-1 P2^T (r1 - A1 e1);  u1 = e1 + P2 ec;  z1 = u1 + S1 (r1 - A1 u1);
+  //   u0 = e0 + P1 z1;  z = u0 + S0 (r - A u0),
+  // S0, S1 the slab-local damped-Jacobi smoothers of smooth_local / smooth_l1, P1 bilinear from
+  // the 2h nodes (2I, 2J), P2 piecewise constant on the aggregates, A1 = P1^T A P1,
+  // A2 = P2^T A1 P2.  Each level's correction is the exact adjoint of its restriction and every
+  // smoother is symmetric, so M^-1 is symmetric.  Values on halo rows equal the owners' (e0 and
+  // e1 exchanged, ec from the same restricted vector in every CTA, z1 exchanged), so M^-1 is one
+  // operator across the CTAs.  Five cluster barriers.  z goes to zbuf; returns the local (r, z).
+  __device__ Real vcycle3(const Real (&r)[NG][4]) {
+    const int W = sb.W;
+    float e[NG][4], w[NG][4];
+    // fine pre-smoothing e0 = S0 r, exchanged (r in FP32 in w)
+#pragma unroll
+    for (int k = 0; k < NG; ++k)
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) w[k][j] = (float)r[k][j];
+    smooth_local(w, e);
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+      if (l0 < 0) continue;
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) vy[l0 + j] = e[k][j];
+    }
+    exchange(vy);
+    // fine residual w0 = r - A e0 on the owned rows, exchanged
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+      if (l0 < 0) continue;
+      float t[4];
+      stencil_elem32(vy, wd, ws, wt, l0, W, t);
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) vw[l0 + j] = unknown(k, j) ? w[k][j] - t[j] : 0.f;
+    }
+    exchange(vw);
+    l1_correct();
+    // u0 = e0 + P1 z1 on the owned and halo fine rows (in vy); 0 off the unknowns
+    for (int i = threadIdx.x; i < (sb.R + 2) * W; i += blockDim.x) {
+      if (vsd[i] == 0.f) {
+        vy[i] = 0.f;
+        continue;
+      }
+      const int lr = i / W - 1, ix = i - (lr + 1) * W - 1, y = sb.r0 + lr;
+      const int ja = y / 2 - J0, jb = (y + 1) / 2 - J0, ia = ix / 2, ib = (ix + 1) / 2;
+      const float z = 0.25f * ((b1z[h1(ja, ia)] + b1z[h1(ja, ib)]) + (b1z[h1(jb, ia)] + b1z[h1(jb, ib)]));
+      vy[i] += z;
+    }
+    __syncthreads();
+    // fine post-smoothing z = u0 + S0 (r - A u0)
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int l0 = loc0[k];
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) w[k][j] = 0.f;
+      if (l0 < 0) continue;
+      float t[4];
+      stencil_elem32(vy, wd, ws, wt, l0, W, t);
+#pragma unroll
+      for (int j = 0; j < kGroup; ++j) w[k][j] = unknown(k, j) ? (float)r[k][j] - t[j] : 0.f;
     }
     smooth_local(w, e);
     Real rz = Real(0);
@@ -949,6 +1216,8 @@ struct Stepper {
       }
       if (local2) {
         v[0] = precond_local2(r);
+      } else if (l3) {
+        v[0] = vcycle3(r);
       } else if (vc && P.tl_nu >= 2) {
         v[0] = vcycle_local(r);
       } else if (vc) {
@@ -988,7 +1257,7 @@ struct Stepper {
           pq[0] = fma(p[k][j], q[k][j], pq[0]);
         }
       }
-      if (vc && P.tl_nu < 2) {
+      if (vc && !l3 && P.tl_nu < 2) {
         // q's owned edge rows to the neighbours, whose copies of r on their halo rows follow
         // the same recurrence (visible after the all-reduce's barrier)
         put_edges(vqh, q);
@@ -1019,6 +1288,8 @@ struct Stepper {
       }
       if (local2) {
         v[0] = precond_local2(r);
+      } else if (l3) {
+        v[0] = vcycle3(r);
       } else if (vc && P.tl_nu >= 2) {
         v[0] = vcycle_local(r);
       } else if (vc) {
@@ -1149,7 +1420,7 @@ struct Stepper {
         const double cterm = (lsw * msw + lse * mse + lne * mne + lnw * mnw) * h2;
         term += P.dc[e] * cterm / dt_step;
       }
-      double g = gsrc[e] - term / nnorm;
+      double g = (gsrc ? gsrc[e] : 0.0) - term / nnorm;
       if (addF) g += addF[e] - subG[e];
       gdst[e] = g;
     }
@@ -1253,7 +1524,7 @@ struct Stepper {
   }
 
   __device__ void coarse_primal(int task) {
-    const int s = task;
+    const int s = P.s0 + task;
     set_operator(true);
     load_x64(P.in_field + (size_t)s * P.Nn);
     const double theta0 = P.in_aux[s];
@@ -1365,21 +1636,27 @@ struct Stepper {
     }
   }
 
+  // G_adj of slice s; with P.src_mode 1 or 2 one of its two parts (G_adj is affine in the source
+  // scale c of Eq. 4.6): 1 the solve and g update driven by v_{s+1} with c = 0, 2 those of the
+  // unit source (c = 1) from lambda = 0 and g = 0.  The parts start from the state they
+  // propagate (zero for part 2).
   __device__ void coarse_adjoint(int task) {
-    const int s = task;
+    const int s = P.s0 + task;
     const int kidx = P.M * s + 1;
     const int kprev = max(kidx - P.M, 0);
-    const double Theta = *P.Theta;
-    const double scale = adjoint_scale(Theta);
+    const double scale = P.src_mode == 0 ? adjoint_scale(*P.Theta) : (P.src_mode == 1 ? 0.0 : 1.0);
     const double* Tk = P.hist + (size_t)kidx * P.Nn;
     const double* Tkm = P.hist + (size_t)kprev * P.Nn;
     set_operator(true);
-    load_x64(P.in_field + (size_t)(s + 1) * P.Nn);
+    if (P.src_mode == 2)
+      zero_x64();
+    else
+      load_x64(P.in_field + (size_t)(s + 1) * P.Nn);
     build_rhs([&](int g) { return scale * ipow(Tk[g], P.p_int - 1); });
-    if (P.guess_next) load_x64(P.in_field + (size_t)s * P.Nn);   // start from the guess lambda_s
+    if (P.guess_next && P.src_mode == 0) load_x64(P.in_field + (size_t)s * P.Nn);   // start from the guess lambda_s
     solve(kidx);
-    accumulate_g(Tk, Tkm, P.dtau, (double)P.Ntau, P.in_aux + (size_t)(s + 1) * P.Ne, P.out_aux + (size_t)s * P.Ne,
-                 nullptr, nullptr);
+    accumulate_g(Tk, Tkm, P.dtau, (double)P.Ntau, P.src_mode == 2 ? nullptr : P.in_aux + (size_t)(s + 1) * P.Ne,
+                 P.out_aux + (size_t)s * P.Ne, nullptr, nullptr);
     store_x64(P.out_field + (size_t)s * P.Nn);
   }
 

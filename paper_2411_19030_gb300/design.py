@@ -92,6 +92,20 @@ class MMAUpdate:
                                      out.ctypes.data), "ptg_mma_update")
         return out
 
+    def get_state(self) -> dict:
+        """The update count and the last two iterates and asymptotes (host copies)."""
+        k = ctypes.c_longlong()
+        arrs = {name: np.empty(self.n) for name in ("x1", "x2", "L", "U")}
+        _check(_lib().ptg_mma_get_state(self._h, ctypes.byref(k), *(a.ctypes.data for a in arrs.values())),
+               "ptg_mma_get_state")
+        return dict(k=k.value, **arrs)
+
+    def set_state(self, st: dict):
+        arrs = [np.ascontiguousarray(st[name], dtype=np.float64) for name in ("x1", "x2", "L", "U")]
+        if any(a.size != self.n for a in arrs):
+            raise ValueError("MMA state of another size")
+        _check(_lib().ptg_mma_set_state(self._h, int(st["k"]), *(a.ctypes.data for a in arrs)), "ptg_mma_set_state")
+
 
 class OneShotLoop:
     """Alg. 3 for one design: ``op`` holds the problem (its precision is the pass's), ``design``
@@ -143,10 +157,41 @@ class OneShotLoop:
         Theta, _ = sequential_pass(top, tb)
         return float(Theta.item())
 
-    def run(self, chi0: np.ndarray, iterations: int, true_every: int = 0) -> dict:
+    # ------------------------------------------------------------------ save / resume
+    def save(self, path: str, chi: np.ndarray, iteration: int):
+        """Write everything the loop carries from one design iteration to the next: the design
+        variable chi to be evaluated next, the number of iterations done, the objective scale
+        Theta_1, the coarse states of the warm start (u^old = (T, theta), v^old = (lambda, g)),
+        and the MMA state; plus the problem sizes, which load() checks."""
+        torch.cuda.synchronize(self.op.device)
+        op, b = self.op, self.buf
+        np.savez(path, chi=np.asarray(chi, dtype=np.float64), iteration=int(iteration),
+                 theta1=np.nan if self.theta1 is None else self.theta1,
+                 U_T=b.U_T.cpu().numpy(), U_th=b.U_th.cpu().numpy(), V_l=b.V_l.cpu().numpy(),
+                 V_g=b.V_g.cpu().numpy(), sizes=np.array([op.nx, op.ny, op.Nt, op.Ntau]),
+                 **{"mma_" + k: v for k, v in self.mma.get_state().items()})
+
+    def load(self, path: str) -> tuple[np.ndarray, int]:
+        """Restore a state written by save() into this loop (same problem sizes); returns
+        (chi, iterations done) to pass to run(..., start=iterations done)."""
+        d = np.load(path)
+        op, b = self.op, self.buf
+        if list(d["sizes"]) != [op.nx, op.ny, op.Nt, op.Ntau]:
+            raise ValueError(f"saved state is for sizes {list(d['sizes'])}, not {[op.nx, op.ny, op.Nt, op.Ntau]}")
+        for t, name in ((b.U_T, "U_T"), (b.U_th, "U_th"), (b.V_l, "V_l"), (b.V_g, "V_g")):
+            t.copy_(torch.from_numpy(d[name]))
+        th1 = float(d["theta1"])
+        self.theta1 = None if np.isnan(th1) else th1
+        self.mma.set_state({k: d["mma_" + k] for k in ("k", "x1", "x2", "L", "U")})
+        torch.cuda.synchronize(op.device)
+        return d["chi"].copy(), int(d["iteration"])
+
+    def run(self, chi0: np.ndarray, iterations: int, true_every: int = 0, start: int = 0) -> dict:
+        """Design iterations start .. iterations-1 from chi0 (iteration 0 is the sequential one;
+        a resumed loop passes the state's iteration count as start)."""
         chi = np.ascontiguousarray(chi0, dtype=np.float64)
         hist = dict(Theta=[], volume=[], ms=[], true_Theta={})
-        for k in range(iterations):
+        for k in range(start, iterations):
             torch.cuda.synchronize(self.op.device)
             t0 = time.perf_counter()
             out = self.iterate(chi, first=(k == 0))

@@ -61,3 +61,35 @@ def test_design_loop_matches_oracle(precision, tol):
         assert abs(out["volume"] - ref["volume"][k]) <= tol, k
         assert np.max(np.abs(chi - ref["chi"][k])) <= 10 * tol, k
     assert op.stats()["status"] == 0
+
+
+def test_design_loop_resumes_from_a_saved_state(tmp_path):
+    """A loop saved after two design iterations and resumed in fresh objects (a new operator,
+    buffers and MMA) continues exactly as the uninterrupted loop: the state it carries is the
+    design chi, the warm-start coarse states u^old and v^old, Theta_1 and the MMA history."""
+    Nt = 32
+    prob = make_problem(20, 16, Nt=Nt, Ntau=4, dt=1.0 / Nt, material="table1", sink="bottom", p=8.0,
+                        q_time=W.q_time_paper(Nt, 1.0 / Nt))
+    r_fil, beta, a_max = 0.12, 8.0, 0.3
+    chi0 = np.full(prob.Ne, a_max)
+
+    def new_loop():
+        op = gpu_operator(prob, "fp32_refine", rtol=1e-10)
+        return OneShotLoop(op, DesignMap(prob.nx, prob.ny, prob.h, r_fil, beta, 0.5), a_max)
+
+    full = new_loop().run(chi0, 5)
+    first = new_loop().run(chi0, 2)
+    saver = new_loop()
+    saver.run(chi0, 2)
+    path = str(tmp_path / "loop_state.npz")
+    saver.save(path, first["chi"], 2)
+    resumed = new_loop()
+    chi, done = resumed.load(path)
+    assert done == 2 and np.array_equal(chi, first["chi"])
+    rest = resumed.run(chi, 5, start=done)
+    assert rest["Theta"] == full["Theta"][2:]
+    assert rest["volume"] == full["volume"][2:]
+    assert np.array_equal(rest["chi"], full["chi"])
+    with pytest.raises(ValueError):
+        op2 = gpu_operator(make_problem(12, 10, Nt=Nt, Ntau=4, dt=1.0 / Nt), "fp32_refine")
+        OneShotLoop(op2, DesignMap(12, 10, 1 / 12, r_fil, beta, 0.5), a_max).load(path)

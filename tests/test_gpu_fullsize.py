@@ -63,6 +63,36 @@ def test_oneshot128_pass_matches_oracle():
     assert op.stats()["status"] == 0
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_loop512_grouped_pass_matches_oracle_on_a_short_time_grid(precision):
+    """512 x 512 with the design loop's step size (dt = 1/4096), on a short time grid (Nt = 64 in
+    8 slices): no slab of this grid fits a 16-CTA cluster, so every kind runs in groups of a
+    cooperative launch, as in the full 512 x 512 loop.  The one-shot pass against the oracle's,
+    element by element (warm start of a design 1% away)."""
+    prob = make_problem(512, Nt=64, Ntau=8, dt=1 / 4096)
+    rho = W.rho_uniform(512, 512, 5, 0.2, 0.8)
+    rho_old = W.rho_warm_perturb(rho, seed=6, amp=0.01)
+    U_old, V_old, _ = coarse_states_from_sequential(OracleOp(prob, rho_old))
+    ref = o_oneshot(OracleOp(prob, rho), U_old, V_old)
+    fp64 = precision == "fp64"
+    # FP64: rtol 1e-12, the floor of the FP64 coarse-step CG with an FP32 preconditioner
+    op = gpu_operator(prob, precision, **dict(BENCH_SOLVE, rtol=1e-12 if fp64 else 1e-10))
+    assert op.plan(0, 8)["cs"] > 16 and op.plan(2, 1)["cs"] > 16
+    buf = PassBuffers(op)
+    buf.U_T.copy_(dev(U_old[0])); buf.U_th.copy_(dev(U_old[1]))
+    buf.V_l.copy_(dev(V_old[0])); buf.V_g.copy_(dev(V_old[1]))
+    op.assemble(dev(rho))
+    Theta, grad = oneshot_pass(op, buf)
+    torch.cuda.synchronize()
+    tol_t, tol_g = (FP64_TOL, FP64_TOL) if fp64 else (MIXED_T_TOL, MIXED_G_TOL)
+    assert_close("T_hist", host(buf.T_hist), ref["T_hist"], tol_t)
+    assert_close("U_new", host(buf.U_T_new), ref["U"][0], tol_t)
+    assert_close("Theta", host(Theta), [ref["Theta"]], tol_t)
+    assert_close("V_lam", host(buf.V_l_new), ref["V"][0], tol_g)
+    assert_close("grad", host(grad), ref["grad"], tol_g)
+    assert op.stats()["status"] == 0, op.stats()
+
+
 def test_diff256_autograd_gradient():
     prob, _ = workload("diff256")
     rho_np = W.rho_uniform(256, 256, 1, 0.0, 1.0)
