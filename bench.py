@@ -146,7 +146,8 @@ def run_gpu(args):
     n, Nt, Ntau, dt, p = w["n"], w["Nt"], w["Ntau"], w["dt"], w["p"]
     N_free = (n + 1) ** 2 - int(sink.sum())
     solve = SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=2000, refine_max=8,
-                        twolevel=args.twolevel, smooth_steps=args.smooth, local_steps=args.local, initial_guess=args.initial_guess)
+                        twolevel=args.twolevel, smooth_steps=args.smooth, local_steps=args.local, initial_guess=args.initial_guess,
+                        fine_stream=args.fine_stream)
     op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink, solve=solve, device=local)
     seq_op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink,
                       solve=SolveConfig("fp64", rtol=1e-13, cg_iters_max=4000, refine_max=8), device=local)
@@ -620,7 +621,7 @@ def streaming_256(args, flush, stream, device) -> dict:
     rho_np = W.rho_warm_perturb(rho_old_np, seed=1000, amp=0.01)
     solve = SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=4000, refine_max=8,
                         twolevel=args.twolevel, smooth_steps=args.smooth, local_steps=args.local,
-                        initial_guess=args.initial_guess)
+                        initial_guess=args.initial_guess, fine_stream=args.fine_stream)
     op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink, solve=solve, device=device.index)
     wop = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink,
                    solve=SolveConfig("fp64", rtol=1e-12, cg_iters_max=8000, refine_max=8), device=device.index)
@@ -720,7 +721,8 @@ def run_loop(args):
     a_max, r_fil, beta, eta = 0.4, 0.03, 32.0, 0.5
     op = Operator(n, n, h, w["material"], Nt, Ntau, dt, w["p"], sink,
                   solve=SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=4000, refine_max=8,
-                                    twolevel=args.twolevel, smooth_steps=args.smooth, local_steps=args.local, initial_guess=args.initial_guess, coarse_mesh=args.coarse_mesh))
+                                    twolevel=args.twolevel, smooth_steps=args.smooth, local_steps=args.local, initial_guess=args.initial_guess, coarse_mesh=args.coarse_mesh,
+                                    fine_stream=args.fine_stream))
     true_op = Operator(n, n, h, w["material"], Nt, Ntau, dt, w["p"], sink,
                        solve=SolveConfig("fp64", rtol=1e-12, cg_iters_max=8000, refine_max=8,
                                          initial_guess=args.initial_guess))
@@ -1028,6 +1030,9 @@ def main():
                     help="time the passes only: no end-to-end run, comparator, accuracy checks or G = 0 probe "
                          "(for profiling the launch sequence of the timed steps)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--fine-stream", type=int, default=0, choices=[0, 1, 2],
+                    help="fine propagators with their CG vectors in global memory, every slice at once "
+                         "(ptg_solve.fine_stream): 2 always, 0/1 on chip")
     ap.add_argument("--no-overlap", dest="overlap", action="store_false",
                     help="run the adjoint coarse propagators after the forward correction sweep instead of as "
                          "two Theta-free parts beside it on a second stream")

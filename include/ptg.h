@@ -169,9 +169,11 @@ typedef struct {
                           0 the library's default (4).  Other values: PTG_EINVAL. */
     int fine_stream;   /* fine propagators of the parallel schedule (a2, a5): 2 with the Krylov vectors
                           in global memory, one group of CTAs per slice and every slice at once
-                          (the FP32 operator stays in L2); 0 or 1 on chip (one thread-block
-                          cluster, or a cooperative group, per slice with its vectors on chip).
-                          Other values: PTG_EINVAL. */
+                          (the FP32 operator stays in L2); 1 on chip (one thread-block cluster,
+                          or a cooperative group, per slice with its vectors on chip); 0 the
+                          library's choice: streamed where no cluster holds a slice (grids of
+                          roughly 300 x 300 and more), on chip elsewhere.  Other values:
+                          PTG_EINVAL. */
 } ptg_solve;
 
 typedef struct {

@@ -36,11 +36,12 @@ struct ptg_op {
   float *tl3_band = nullptr, *tl3_X = nullptr, *tl3_Ainv = nullptr;
   // streamed fine propagators (ptg_solve.fine_stream, stream.cuh): FP32 weights of C/dt + K and
   // 1/C ([6][PN]), the FP64 1/C ([PN]), and the workspace of st_groups concurrent slices
-  float* w32 = nullptr;
-  double* w64_inv = nullptr;
-  double* st_w64 = nullptr;    // [st_groups][3][Nn]
-  void* st_wr = nullptr;       // [st_groups][4][Nn] in the fine CG precision
-  int st_groups = 0;           // 0: the op has no streaming workspace
+  float* w32 = nullptr;         // [3][PEe] FP32 element weights (D, S, T) of C/dt + K
+  float* w32_inv = nullptr;     // [PN] FP32 1/C
+  double* w64_inv = nullptr;    // [PN] FP64 1/C
+  double* st_w64 = nullptr;     // [st_groups][3][PN] (x, x, b), padded node layout
+  void* st_wr = nullptr;        // [st_groups][5][PN] (r, z, p, q, d) in the fine CG precision
+  int st_groups = 0;            // 0: the op has no streaming workspace
   // device workspace
   double *k = nullptr, *c = nullptr, *dk = nullptr, *dc = nullptr;
   double* wE = nullptr;     // [2][3][PEe]: element (D, S, T) weights for dt and dtau (padded)
@@ -325,13 +326,21 @@ int choose_plan(ptg_op* op, int precision, int kind, int ntasks, Plan* out) {
     return PTG_OK;
   }
   // Fine kinds of the parallel schedule (ntasks >= 2 slices at once) on the streamed propagator
-  // when ptg_solve.fine_stream = 2.  One CTA of 1024 threads per SM; G = SMs / slices CTAs per
-  // slice (at least 2 node rows each), all slices at once.
+  // (ptg_solve.fine_stream).  One CTA of 512 threads per SM; G = SMs / slices CTAs per slice (at
+  // least 2 node rows each), all slices at once.
   if ((kind == KIND_FINE_PRI || kind == KIND_FINE_ADJ) && op->st_groups > 0 && ntasks >= 2 &&
       op->sv.fine_stream != 1) {
-    // fine_stream 0 keeps the on-chip path: measured at 256 x 256 (64 slices) the streamed
-    // propagators took 134 ms against 59 ms on chip
-    const bool want = op->sv.fine_stream == 2;
+    // fine_stream 0: streamed where no cluster holds a slice (the grouped launches of large
+    // grids run only a few slices at a time: at 512 x 512, 3 of 128); measured there the one-shot
+    // design iteration takes 4.4-4.8 s streamed against 7.6-9.0 s on chip.  Where clusters fit
+    // (256 x 256) both take the same time and the on-chip path stays.
+    bool want = op->sv.fine_stream == 2;
+    if (!want && op->sv.fine_stream == 0) {
+      Plan c;
+      long w = best_plan(op, precision, kind, ntasks, TL_NONE, &c);
+      if (w < 0) w = best_plan(op, precision, kind, ntasks, TL_NONE, &c, false);
+      want = w < 0;
+    }
     if (want) {
       int dev = 0, nsm = 0;
       cudaGetDevice(&dev);
@@ -341,7 +350,7 @@ int choose_plan(ptg_op* op, int precision, int kind, int ntasks, Plan* out) {
       G = std::min(G, std::max(1, (op->g.ny + 1) / 2));
       Plan sp;
       sp.cs = G;
-      sp.nthreads = 1024;
+      sp.nthreads = 512;
       sp.ng = 1;
       sp.rmax = (op->g.ny + 1 + G - 1) / G;
       sp.smem = 0;
@@ -458,9 +467,10 @@ void base_params(const ptg_op* op, StepParams& P) {
   P.mass = nw(10);
   if (op->w32) {
     P.w32 = op->w32 + kSlack;
-    P.w32_inv = op->w32 + 5 * PN + kSlack;
-    P.w32_stride = (int)PN;
+    P.w32_stride = (int)PEe;
+    P.w32_inv = op->w32_inv + kSlack;
     P.w64_inv = op->w64_inv + kSlack;
+    P.st_pv = (long long)PN;
   }
   P.dk = op->dk;
   P.dc = op->dc;
@@ -529,7 +539,7 @@ void free_all(ptg_op* op) {
                   op->g_red, op->g_bar, op->g_halo, op->g_tl,
                   op->tl_Ac, op->tl_band, op->tl_X, op->tl_Ainv,
                   op->tl3_A1, op->tl3_Ac, op->tl3_band, op->tl3_X, op->tl3_Ainv,
-                  op->w32, op->w64_inv, op->st_w64, op->st_wr,
+                  op->w32, op->w32_inv, op->w64_inv, op->st_w64, op->st_wr,
                   op->mesh_rho, op->mesh_XH, op->mesh_FH, op->mesh_GH, op->mesh_SH, op->mesh_YH,
                   op->mesh_zero, op->mesh_aux, op->mesh_pn, op->mesh_lam, op->mesh_dg};
   for (void* p : ptrs)
@@ -821,17 +831,23 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
       A(&op->tl3_Ainv, ncp3 * ncp3 * sizeof(float));
     }
   }
-  // streamed fine propagators (fine_stream = 2)
-  if (solve->fine_stream == 2) {
+  // streamed fine propagators: fine_stream = 2, or 0 on grids of kWideMinNodes nodes or more
+  // (the plan streams only where no cluster holds a slice)
+  if (solve->fine_stream == 2 || (solve->fine_stream == 0 && op->Nn >= kWideMinNodes)) {
     int dev_sm = 0;
     cudaDeviceGetAttribute(&dev_sm, cudaDevAttrMultiProcessorCount, device);
     op->st_groups = std::max(1, std::min(time->Ntau, std::min(dev_sm, kMaxGrid)));
     const size_t PNs = (size_t)(grid->ny + 3) * op->W + 2 * kSlack;
+    const size_t PEs = (size_t)(grid->ny + 2) * op->W + 2 * kSlack;
     const size_t rb = kind_precision(solve->precision, KIND_FINE_PRI) == PTG_FP64 ? 8 : 4;
-    A(&op->w32, 6 * PNs * sizeof(float));
+    A(&op->w32, 3 * PEs * sizeof(float));
+    A(&op->w32_inv, PNs * sizeof(float));
     A(&op->w64_inv, PNs * sizeof(double));
-    A(&op->st_w64, (size_t)op->st_groups * 3 * op->Nn * sizeof(double));
-    A(&op->st_wr, (size_t)op->st_groups * 4 * op->Nn * rb);
+    A(&op->st_w64, (size_t)op->st_groups * 3 * PNs * sizeof(double));
+    A(&op->st_wr, (size_t)op->st_groups * 5 * PNs * rb);
+    // the padded vectors are zero outside the unknowns; only unknowns are ever written
+    if (e == cudaSuccess) e = cudaMemset(op->st_w64, 0, (size_t)op->st_groups * 3 * PNs * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(op->st_wr, 0, (size_t)op->st_groups * 5 * PNs * rb);
   }
   A(&op->scratch, 2 * sizeof(double));
   A(&op->g_red, 2 * kMaxGrid * 4 * sizeof(double));
@@ -973,16 +989,9 @@ int ptg_fe_assemble_operator(ptg_op* op, const double* rho_d, cudaStream_t strea
   out.fload = op->fload;
   PTG_CUDA(launch_assemble(op->g.nx, op->g.ny, op->g.h, op->mat, op->tm.dt, op->dtau, rho_d, op->q_elem,
                            op->dirichlet, out, op->stats, stream));
-  if (op->w32) {
-    NodeWeights Af;
-    Af.C = out.node[0];
-    Af.E = out.node[1];
-    Af.N = out.node[2];
-    Af.NE = out.node[3];
-    Af.NW = out.node[4];
-    PTG_CUDA(launch_stream_weights((int)PN, Af, op->dirichlet, op->g.nx, op->g.ny, op->W, op->w32 + kSlack,
-                                   op->w64_inv + kSlack, stream));
-  }
+  if (op->w32)
+    PTG_CUDA(launch_stream_weights((int)PEe, (int)PN, op->wE, op->nodew, op->dirichlet, op->g.nx, op->g.ny, op->W,
+                                   op->w32, op->w32_inv, op->w64_inv, stream));
   if (op->tl_m) {
     NodeWeights Ac;
     Ac.C = out.node[5];

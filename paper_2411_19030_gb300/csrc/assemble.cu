@@ -242,29 +242,31 @@ cudaError_t launch_adjoint_combine(long long n_l, long long n_g, const double* T
   return cudaGetLastError();
 }
 
-// FP32 node weights of C/dt + K and 1/C for the streamed fine propagators, on the n = (ny+3) W
-// entries of the padded node grid (rows iy = -1..ny+1); arrays `stride` floats apart.  1/C is 0
-// on Dirichlet and out-of-grid nodes (so z = r / C vanishes there).
-__global__ void stream_weights_kernel(int n, int stride, NodeWeights A, const uint8_t* __restrict__ dirichlet, int nx,
-                                      int ny, int W, float* __restrict__ w32, double* __restrict__ w64_inv) {
+// FP32 element weights and the inverse diagonal for the streamed fine propagators (see
+// ptg_internal.h).  Node entry i of the padded layout (slack included) is row i / W - 1 after the
+// kSlack leading entries.
+__global__ void stream_weights_kernel(int PE, int PN, const double* __restrict__ wE, const double* __restrict__ C,
+                                      const uint8_t* __restrict__ dirichlet, int nx, int ny, int W,
+                                      float* __restrict__ w32, float* __restrict__ w32_inv,
+                                      double* __restrict__ w64_inv) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int iy = i / W - 1, ix = i % W - 1;
-  const bool unknown = iy >= 0 && iy <= ny && ix >= 0 && ix <= nx && dirichlet[iy * (nx + 1) + ix] == 0;
-  w32[i] = (float)A.C[i];
-  w32[stride + i] = (float)A.E[i];
-  w32[2 * stride + i] = (float)A.N[i];
-  w32[3 * stride + i] = (float)A.NE[i];
-  w32[4 * stride + i] = (float)A.NW[i];
-  const double inv = unknown ? 1.0 / A.C[i] : 0.0;
-  w32[5 * stride + i] = (float)inv;
-  w64_inv[i] = inv;
+  if (i < 3 * PE) w32[i] = (float)wE[i];
+  if (i < PN) {
+    const int k = i - kSlack;
+    const int iy = k >= 0 ? k / W - 1 : -2, ix = k >= 0 ? k % W - 1 : -2;
+    const bool unknown = iy >= 0 && iy <= ny && ix >= 0 && ix <= nx && dirichlet[iy * (nx + 1) + ix] == 0;
+    const double inv = unknown ? 1.0 / C[i] : 0.0;
+    w32_inv[i] = (float)inv;
+    w64_inv[i] = inv;
+  }
 }
 
-cudaError_t launch_stream_weights(int stride, const NodeWeights& A, const uint8_t* dirichlet, int nx, int ny, int W,
-                                  float* w32, double* w64_inv, cudaStream_t stream) {
-  const int n = (ny + 3) * W;
-  stream_weights_kernel<<<(n + 255) / 256, 256, 0, stream>>>(n, stride, A, dirichlet, nx, ny, W, w32, w64_inv);
+cudaError_t launch_stream_weights(int PE, int PN, const double* wE, const double* C_node, const uint8_t* dirichlet,
+                                  int nx, int ny, int W, float* w32, float* w32_inv, double* w64_inv,
+                                  cudaStream_t stream) {
+  const int n = 3 * PE > PN ? 3 * PE : PN;
+  stream_weights_kernel<<<(n + 255) / 256, 256, 0, stream>>>(PE, PN, wE, C_node, dirichlet, nx, ny, W, w32, w32_inv,
+                                                             w64_inv);
   return cudaGetLastError();
 }
 

@@ -125,15 +125,16 @@ struct StepParams {
   int l3_W1;                 // padded row width of the 2h buffers
   int l3_r1max;              // most 2h rows owned by a CTA of the launch
   const double* A1;          // [9][(ny1 + 1) (nx1 + 1)] 2h stencil, k = (dJ + 1) * 3 + (dI + 1)
-  // streamed fine propagators (stream.cuh): per group of P.cs CTAs, [3][Nn] FP64 (x, x, b) and
-  // [4][Nn] CG vectors (r, p, q, d) in the kernel's precision; the FP32 operator C/dt + K as
-  // per-node weights C, E, N, NE, NW then 1/C (0 off the unknowns), each w32_stride floats in the
-  // padded node layout; its FP64 inverse diagonal for FP64 CG
+  // streamed fine propagators (stream.cuh): per group of P.cs CTAs, three FP64 vectors (x, x, b)
+  // and five CG vectors (r, z, p, q, d) in the kernel's precision, each st_pv entries in the padded
+  // node layout with its slack; the FP32 element weights (D, S, T) of C/dt + K, w32_stride floats
+  // apart in the padded element layout; 1/C (0 off the unknowns) in FP32 and FP64, padded node layout
   double* st_w64;
   void* st_wr;
+  long long st_pv;
   const float* w32;
-  const float* w32_inv;
   int w32_stride;
+  const float* w32_inv;
   const double* w64_inv;
   // one system over a whole cooperative grid (GridComm): global scratch of the op
   int wide;                  // 1: launched as stepper_wide_kernel, groups of cs CTAs
@@ -321,10 +322,12 @@ cudaError_t launch_sensitivities(int nx, int ny, int Nt, double h, double dt, in
                                  const double* dc, const double* lam, int j0, int j1, const double* T, int hist_j0,
                                  double* partial, int nchunks, double* grad, cudaStream_t stream);
 
-// FP32 copies of the node weights of C/dt + K (C, E, N, NE, NW) and 1/C (0 off the unknowns), and
-// the FP64 1/C, for the streamed fine propagators (padded node layout, PN entries each)
-cudaError_t launch_stream_weights(int stride, const NodeWeights& A, const uint8_t* dirichlet, int nx, int ny, int W,
-                                  float* w32, double* w64_inv, cudaStream_t stream);
+// For the streamed fine propagators: FP32 copies of the 3 x PE FP64 element weights (D, S, T) of
+// C/dt + K (slack included), and 1/C in FP32 and FP64 (0 off the unknowns) on the PN entries of
+// the padded node layout (slack included; C the node weight array with its slack).
+cudaError_t launch_stream_weights(int PE, int PN, const double* wE, const double* C_node, const uint8_t* dirichlet,
+                                  int nx, int ny, int W, float* w32, float* w32_inv, double* w64_inv,
+                                  cudaStream_t stream);
 cudaError_t launch_stream(const StepParams& P, int precision, int ngroups, int nthreads, cudaStream_t stream);
 // G_l = H_l + c S_l ([n_l]) and G_g = H_g + c S_g ([n_g]), c the adjoint source scale of Theta
 cudaError_t launch_adjoint_combine(long long n_l, long long n_g, const double* Theta, double p, int Ne, int modified,

@@ -28,122 +28,6 @@
 
 namespace ptg {
 
-// 6-entry window of a row around a group: w[0] = offset b-1, w[1..4] = b..b+3, w[5] = b+4
-// (b a multiple of 4).  One 16-byte load for the centre in float, two in double.
-template <class T>
-__device__ __forceinline__ void load_window(const T* __restrict__ x, int b, T (&w)[6]) {
-  w[0] = x[b - 1];
-  if constexpr (sizeof(T) == 4) {
-    const float4 c = *reinterpret_cast<const float4*>(x + b);
-    w[1] = c.x; w[2] = c.y; w[3] = c.z; w[4] = c.w;
-  } else {
-    const double2 c0 = *reinterpret_cast<const double2*>(x + b);
-    const double2 c1 = *reinterpret_cast<const double2*>(x + b + 2);
-    w[1] = c0.x; w[2] = c0.y; w[3] = c1.x; w[4] = c1.y;
-  }
-  w[5] = x[b + 4];
-}
-
-// 5-entry window of an element row: e[0] = offset b-1, e[1..4] = b..b+3 (b a multiple of 4).
-__device__ __forceinline__ void load_ewindow(const float* __restrict__ w, int b, float (&e)[5]) {
-  e[0] = w[b - 1];
-  const float4 c = *reinterpret_cast<const float4*>(w + b);
-  e[1] = c.x; e[2] = c.y; e[3] = c.z; e[4] = c.w;
-}
-
-__device__ __forceinline__ void load4(const double* __restrict__ p, double (&v)[4]) {
-  const double2 a = *reinterpret_cast<const double2*>(p);
-  const double2 b = *reinterpret_cast<const double2*>(p + 2);
-  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-}
-
-// y = A x for the 4 nodes of a group, FP64 per-node weights (global memory).
-// x: node buffer (rows -1..R); loc0: offset of the group's first node in x;
-// go: offset of the same node in the padded global node arrays; W: row width.
-template <class T>
-__device__ __forceinline__ void stencil_node64(const T* __restrict__ x, int loc0, const NodeWeights& nw, int go, int W,
-                                               double (&y)[4]) {
-  T xl[6], xm[6], xh[6];
-  load_window(x, loc0 - W, xl);
-  load_window(x, loc0, xm);
-  load_window(x, loc0 + W, xh);
-  double C[4], No[4], Nb[4], NEo[4], NWo[4];
-  load4(nw.C + go, C);
-  load4(nw.N + go, No);
-  load4(nw.N + go - W, Nb);
-  load4(nw.NE + go, NEo);
-  load4(nw.NW + go, NWo);
-  double E[5];
-  E[0] = nw.E[go - 1];
-  {
-    double e4[4];
-    load4(nw.E + go, e4);
-    E[1] = e4[0]; E[2] = e4[1]; E[3] = e4[2]; E[4] = e4[3];
-  }
-  const double* neb = nw.NE + go - W - 1;      // NE weights of the row below, shifted left
-  const double* nwb = nw.NW + go - W + 1;      // NW weights of the row below, shifted right
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    double a = C[j] * (double)xm[j + 1];
-    a = fma(E[j + 1], (double)xm[j + 2], a);   // east
-    a = fma(E[j], (double)xm[j], a);           // west  = east weight of the west neighbour
-    a = fma(No[j], (double)xh[j + 1], a);      // north
-    a = fma(Nb[j], (double)xl[j + 1], a);      // south = north weight of the south neighbour
-    a = fma(NEo[j], (double)xh[j + 2], a);     // north-east
-    a = fma(neb[j], (double)xl[j], a);         // south-west = NE weight of the SW neighbour
-    a = fma(NWo[j], (double)xh[j], a);         // north-west
-    a = fma(nwb[j], (double)xl[j + 2], a);     // south-east = NW weight of the SE neighbour
-    y[j] = a;
-  }
-}
-
-// y = A z for the 4 nodes of a group, FP32 element weights (D, S, T) in shared memory.
-// For the node at window position c = j+1: elements a, b below-left / below-right and c, d
-// above-left / above-right, i.e. element windows lower[j], lower[j+1], upper[j], upper[j+1].
-// no_lo / no_hi: the node row below / above is left out (taken as zero), which applies the
-// slab's diagonal block of the operator on its first / last row.
-__device__ __forceinline__ void stencil_elem32(const float* __restrict__ z, const float* __restrict__ wd,
-                                               const float* __restrict__ ws, const float* __restrict__ wt, int loc0,
-                                               int W, float (&y)[4], bool no_lo = false, bool no_hi = false) {
-  float zl[6], zm[6], zh[6];
-  if (no_lo) {
-#pragma unroll
-    for (int i = 0; i < 6; ++i) zl[i] = 0.f;
-  } else {
-    load_window(z, loc0 - W, zl);
-  }
-  load_window(z, loc0, zm);
-  if (no_hi) {
-#pragma unroll
-    for (int i = 0; i < 6; ++i) zh[i] = 0.f;
-  } else {
-    load_window(z, loc0 + W, zh);
-  }
-  float dl[5], sl[5], tl[5], du[5], su[5], tu[5];
-  const int el = loc0 - W, eu = loc0;   // element windows share the node buffers' row offsets
-  load_ewindow(wd, el, dl);
-  load_ewindow(ws, el, sl);
-  load_ewindow(wt, el, tl);
-  load_ewindow(wd, eu, du);
-  load_ewindow(ws, eu, su);
-  load_ewindow(wt, eu, tu);
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const float Da = dl[j], Db = dl[j + 1], Dc = du[j], Dd = du[j + 1];
-    const float Sa = sl[j], Sb = sl[j + 1], Sc = su[j], Sd = su[j + 1];
-    float a = ((Da + Db) + (Dc + Dd)) * zm[j + 1];
-    a = fmaf(Sa + Sc, zm[j], a);           // west:  shared by a, c
-    a = fmaf(Sb + Sd, zm[j + 2], a);       // east:  shared by b, d
-    a = fmaf(Sa + Sb, zl[j + 1], a);       // south: shared by a, b
-    a = fmaf(Sc + Sd, zh[j + 1], a);       // north: shared by c, d
-    a = fmaf(tl[j], zl[j], a);             // south-west corner of a
-    a = fmaf(tl[j + 1], zl[j + 2], a);     // south-east corner of b
-    a = fmaf(tu[j], zh[j], a);             // north-west corner of c
-    a = fmaf(tu[j + 1], zh[j + 2], a);     // north-east corner of d
-    y[j] = a;
-  }
-}
-
 template <class Real, int NG, class Comm>
 struct Stepper {
   static constexpr bool kMixed = std::is_same<Real, float>::value;

@@ -3,9 +3,11 @@
 
 namespace ptg {
 
+constexpr int kStreamThreads = 512;   // one CTA per SM, 128 registers per thread
+
 // ngroups groups of P.cs CTAs; group g runs tasks g, g + ngroups, ... < P.wide_tasks.
 template <class Real, int KIND>
-__global__ void __launch_bounds__(1024, 1) stream_kernel(const __grid_constant__ StepParams P) {
+__global__ void __launch_bounds__(kStreamThreads, 1) stream_kernel(const __grid_constant__ StepParams P) {
   __shared__ RedSmem rs;
   GridComm comm(P, rs);
   Streamer<Real, KIND> st(P, comm);
@@ -31,7 +33,7 @@ cudaError_t launch_stream(const StepParams& P, int precision, int ngroups, int n
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   cfg.gridDim = dim3((unsigned)(ngroups * P.cs), 1, 1);
-  cfg.blockDim = dim3((unsigned)nthreads, 1, 1);
+  cfg.blockDim = dim3((unsigned)(nthreads < kStreamThreads ? nthreads : kStreamThreads), 1, 1);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = stream;
   attr[0].id = cudaLaunchAttributeCooperative;

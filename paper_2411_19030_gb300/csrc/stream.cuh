@@ -26,105 +26,112 @@ struct Streamer {
   GridComm& comm;
   int rank = 0, r0 = 0, R = 0;   // this CTA's node rows [r0, r0 + R) of the group's system
   int nn = 0;                    // nodes per row (nx + 1)
-  int cpr = 0;                   // 32-node chunks per row
-  double *xa = nullptr, *xb = nullptr, *b = nullptr;   // group workspace, [Nn] each
-  Real *r = nullptr, *p = nullptr, *q = nullptr, *d = nullptr;
+  int G4 = 0;                    // groups of 4 nodes per padded row (W / 4)
+  // group workspace, padded node layout (node (iy, ix) at (iy + 1) W + ix + 1, the layout of the
+  // per-node weights), zero off the unknowns
+  double *xa = nullptr, *xb = nullptr, *b = nullptr;
+  Real *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *d = nullptr;
   double step_dt = 0.0, inv_dt = 0.0;
 
   __device__ Streamer(const StepParams& P_, GridComm& comm_) : P(P_), comm(comm_) {
     rank = comm.rank();
     slab_rows(P.ny + 1, P.cs, rank, r0, R);
     nn = P.nx + 1;
-    cpr = (nn + 31) / 32;
+    G4 = P.W / kGroup;
     const int grp = (int)blockIdx.x / P.cs;
-    double* w64 = P.st_w64 + (size_t)grp * 3 * P.Nn;
+    const size_t pv = (size_t)P.st_pv;                 // entries of one padded vector incl. slack
+    double* w64 = P.st_w64 + (size_t)grp * 3 * pv + kSlack;
     xa = w64;
-    xb = w64 + P.Nn;
-    b = w64 + 2 * (size_t)P.Nn;
-    Real* wr = reinterpret_cast<Real*>(P.st_wr) + (size_t)grp * 4 * P.Nn;
+    xb = w64 + pv;
+    b = w64 + 2 * pv;
+    Real* wr = reinterpret_cast<Real*>(P.st_wr) + (size_t)grp * 5 * pv + kSlack;
     r = wr;
-    p = wr + P.Nn;
-    q = wr + 2 * (size_t)P.Nn;
-    d = wr + 3 * (size_t)P.Nn;
+    z = wr + pv;
+    p = wr + 2 * pv;
+    q = wr + 3 * pv;
+    d = wr + 4 * pv;
     step_dt = P.dt;
     inv_dt = 1.0 / P.dt;
   }
 
-  // Visit this CTA's nodes: warps take 32-node chunks of a row, f(g, iy, ix, go) for the nodes
-  // inside the grid (g the node index, go its index in the padded weight arrays).
+  // Visit this CTA's groups of 4 nodes (columns 4g-1 .. 4g+2 of an owned row): f(loc, iy, g) with
+  // loc the padded index of the group's first node (16-byte aligned).
   template <class F>
-  __device__ __forceinline__ void for_nodes(F f) const {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int c = warp; c < R * cpr; c += nwarps) {
-      const int lr = c / cpr, ix = (c - lr * cpr) * 32 + lane;
-      if (ix >= nn) continue;
-      const int iy = r0 + lr;
-      f(iy * nn + ix, iy, ix, (iy + 1) * P.W + ix + 1);
+  __device__ __forceinline__ void for_groups(F f) const {
+    for (int t = threadIdx.x; t < R * G4; t += blockDim.x) {
+      const int lr = t / G4, g = t - lr * G4, iy = r0 + lr;
+      f((iy + 1) * P.W + kGroup * g, iy, g);
     }
   }
 
-  __device__ __forceinline__ bool free_node(int g) const { return P.dirichlet[g] == 0; }
-
-  // value of v at the node offset (dy, dx) from (iy, ix), 0 outside the grid
-  template <class T>
-  __device__ __forceinline__ T at(const T* __restrict__ v, int g, int iy, int ix, int dy, int dx) const {
-    const int y = iy + dy, x = ix + dx;
-    return (y >= 0 && y <= P.ny && x >= 0 && x <= P.nx) ? v[g + dy * nn + dx] : T(0);
+  // Two groups per loop trip (t and t + blockDim.x): f(loc[2], ok[2]) loads both groups' operands
+  // before it computes, so each thread keeps twice the memory requests in flight.
+  template <class F>
+  __device__ __forceinline__ void for_group_pairs(F f) const {
+    const int n = R * G4;
+    for (int t0 = threadIdx.x; t0 < n; t0 += 2 * blockDim.x) {
+      int loc[2];
+      bool ok[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int t = t0 + u * (int)blockDim.x;
+        ok[u] = t < n;
+        const int lr = ok[u] ? t / G4 : 0, g = ok[u] ? t - lr * G4 : 0;
+        loc[u] = (r0 + lr + 1) * P.W + kGroup * g;
+      }
+      f(loc, ok);
+    }
   }
 
-  // (A v)(g) with FP64 per-node weights W (padded layout)
-  __device__ __forceinline__ double stencil64(const NodeWeights& A, const double* __restrict__ v, int g, int iy, int ix,
-                                              int go) const {
-    const int Wp = P.W;
-    double y = A.C[go] * v[g];
-    y = fma(A.E[go], at(v, g, iy, ix, 0, 1), y);
-    y = fma(A.E[go - 1], at(v, g, iy, ix, 0, -1), y);
-    y = fma(A.N[go], at(v, g, iy, ix, 1, 0), y);
-    y = fma(A.N[go - Wp], at(v, g, iy, ix, -1, 0), y);
-    y = fma(A.NE[go], at(v, g, iy, ix, 1, 1), y);
-    y = fma(A.NE[go - Wp - 1], at(v, g, iy, ix, -1, -1), y);
-    y = fma(A.NW[go], at(v, g, iy, ix, 1, -1), y);
-    y = fma(A.NW[go - Wp + 1], at(v, g, iy, ix, -1, 1), y);
-    return y;
+  // node index of column 4g-1+j of row iy, or -1 for a pad column
+  __device__ __forceinline__ int gnode(int iy, int g, int j) const {
+    const int ix = kGroup * g - 1 + j;
+    return (ix >= 0 && ix <= P.nx) ? iy * nn + ix : -1;
   }
 
-  // weight k (C, E, N, NE, NW) of C/dt + K at a padded node index, in the CG precision (the FP32
-  // copies for FP32 CG, the FP64 weights for FP64 CG), and 1/C (0 off the unknowns)
-  __device__ __forceinline__ Real wgt(int k, int idx) const {
+  // 1/C of the 4 nodes (0 off the unknowns) in the CG precision
+  __device__ __forceinline__ void dinv4(int loc, Real (&v)[4]) const {
     if constexpr (sizeof(Real) == 8) {
-      const NodeWeights& A = P.A_fine;
-      return (k == 0 ? A.C : k == 1 ? A.E : k == 2 ? A.N : k == 3 ? A.NE : A.NW)[idx];
+      load4(P.w64_inv + loc, v);
     } else {
-      return P.w32[k * P.w32_stride + idx];
+      const float4 c = *reinterpret_cast<const float4*>(P.w32_inv + loc);
+      v[0] = c.x; v[1] = c.y; v[2] = c.z; v[3] = c.w;
     }
   }
-  __device__ __forceinline__ Real winv(int idx) const {
-    if constexpr (sizeof(Real) == 8)
-      return P.w64_inv[idx];
-    else
-      return P.w32_inv[idx];
+  __device__ __forceinline__ void ld4(const Real* __restrict__ a, int loc, Real (&v)[4]) const {
+    if constexpr (sizeof(Real) == 8) {
+      load4(a + loc, v);
+    } else {
+      const float4 c = *reinterpret_cast<const float4*>(a + loc);
+      v[0] = c.x; v[1] = c.y; v[2] = c.z; v[3] = c.w;
+    }
+  }
+  __device__ __forceinline__ void st4(Real* __restrict__ a, int loc, const Real (&v)[4]) const {
+    if constexpr (sizeof(Real) == 8) {
+      *reinterpret_cast<double2*>(a + loc) = make_double2(v[0], v[1]);
+      *reinterpret_cast<double2*>(a + loc + 2) = make_double2(v[2], v[3]);
+    } else {
+      *reinterpret_cast<float4*>(a + loc) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+  }
+  __device__ __forceinline__ void st4d(double* __restrict__ a, int loc, const double (&v)[4]) const {
+    *reinterpret_cast<double2*>(a + loc) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(a + loc + 2) = make_double2(v[2], v[3]);
   }
 
-  // z = D^-1 r at (g + offset), 0 outside the grid (the inverse diagonal is 0 off the unknowns)
-  __device__ __forceinline__ Real zat(int g, int iy, int ix, int dy, int dx, int go) const {
-    const int y = iy + dy, x = ix + dx;
-    if (y < 0 || y > P.ny || x < 0 || x > P.nx) return Real(0);
-    return winv(go + dy * P.W + dx) * r[g + dy * nn + dx];
-  }
-
-  // (A z)(g) in the CG precision, z = D^-1 r formed on the fly
-  __device__ __forceinline__ Real stencil_z(int g, int iy, int ix, int go) const {
-    const int Wp = P.W;
-    Real y = wgt(0, go) * zat(g, iy, ix, 0, 0, go);
-    y = fma(wgt(1, go), zat(g, iy, ix, 0, 1, go), y);
-    y = fma(wgt(1, go - 1), zat(g, iy, ix, 0, -1, go), y);
-    y = fma(wgt(2, go), zat(g, iy, ix, 1, 0, go), y);
-    y = fma(wgt(2, go - Wp), zat(g, iy, ix, -1, 0, go), y);
-    y = fma(wgt(3, go), zat(g, iy, ix, 1, 1, go), y);
-    y = fma(wgt(3, go - Wp - 1), zat(g, iy, ix, -1, -1, go), y);
-    y = fma(wgt(4, go), zat(g, iy, ix, 1, -1, go), y);
-    y = fma(wgt(4, go - Wp + 1), zat(g, iy, ix, -1, 1, go), y);
-    return y;
+  // (A z) on a group in the CG precision
+  __device__ __forceinline__ void apply_z(int loc, Real (&w)[4]) const {
+    if constexpr (sizeof(Real) == 8) {
+      double y[4];
+      stencil_node64<double>(z, loc, P.A_fine, loc, P.W, y);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) w[j] = y[j];
+    } else {
+      float y[4];
+      stencil_elem32(z, P.w32, P.w32 + P.w32_stride, P.w32 + 2 * P.w32_stride, loc, P.W, y);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) w[j] = y[j];
+    }
   }
 
   template <class T, int NV, int NX = 0, class Post = NoPost>
@@ -132,22 +139,29 @@ struct Streamer {
     comm.template allreduce<T, NV, NX, Post>(v, P.cs, post);
   }
 
-  // r = b - A x (FP64, stored in Real unscaled); returns the local (b, b) and (r, r)
+  // r = b - A x (FP64, stored in the CG precision unscaled, 0 off the unknowns); the local
+  // (b, b) and (r, r)
   __device__ void residual(const double* __restrict__ x, double& bb, double& rr) const {
     bb = 0.0;
     rr = 0.0;
-    for_nodes([&](int g, int iy, int ix, int go) {
-      double rv = 0.0;
-      if (free_node(g)) {
-        rv = b[g] - stencil64(P.A_fine, x, g, iy, ix, go);
-        bb = fma(b[g], b[g], bb);
-        rr = fma(rv, rv, rr);
+    for_groups([&](int loc, int, int) {
+      double y[4], bv[4];
+      Real di[4], rv[4];
+      stencil_node64<double>(x, loc, P.A_fine, loc, P.W, y);
+      load4(b + loc, bv);
+      dinv4(loc, di);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const double t = di[j] != Real(0) ? bv[j] - y[j] : 0.0;
+        bb = fma(bv[j], bv[j], bb);
+        rr = fma(t, t, rr);
+        rv[j] = (Real)t;
       }
-      r[g] = (Real)rv;
+      st4(r, loc, rv);
     });
   }
 
-  // Solve (C/dt + K) x = b from the start in x (the group's rows of x, every row readable).
+  // Solve (C/dt + K) x = b from the start in x (every row of x readable).
   __device__ void solve(double* __restrict__ x, int step) {
     double v2[2];
     residual(x, v2[0], v2[1]);
@@ -160,15 +174,23 @@ struct Streamer {
       const double nrm = sqrt(rr);
       const Real scale = (Real)(1.0 / nrm);
       const Real target2 = (Real)fmax(P.inner_rtol * P.inner_rtol, 0.25 * tol2 / rr);
-      // r /= ||r||, d = p = q = 0; (r, z)
+      // r /= ||r||, z = D^-1 r, d = p = q = 0; (r, z)
       Real a[1] = {Real(0)};
-      for_nodes([&](int g, int iy, int ix, int go) {
-        const Real rv = r[g] * scale;
-        r[g] = rv;
-        d[g] = Real(0);
-        p[g] = Real(0);
-        q[g] = Real(0);
-        a[0] = fma(rv, winv(go) * rv, a[0]);
+      for_groups([&](int loc, int, int) {
+        Real rv[4], di[4], zv[4], zero[4] = {Real(0), Real(0), Real(0), Real(0)};
+        ld4(r, loc, rv);
+        dinv4(loc, di);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          rv[j] *= scale;
+          zv[j] = di[j] * rv[j];
+          a[0] = fma(rv[j], zv[j], a[0]);
+        }
+        st4(r, loc, rv);
+        st4(z, loc, zv);
+        st4(d, loc, zero);
+        st4(p, loc, zero);
+        st4(q, loc, zero);
       });
       allreduce<Real, 1>(a);
       Real rz = a[0], beta = Real(0);
@@ -177,27 +199,54 @@ struct Streamer {
       while (!done && it < P.itmax) {
         // q = A z + beta q, p = z + beta p, (p, q); alpha = rz / (p, q)
         Real pq[1] = {Real(0)};
-        for_nodes([&](int g, int iy, int ix, int go) {
-          Real pv = Real(0), qv = Real(0);
-          if (free_node(g)) {
-            qv = fma(beta, q[g], stencil_z(g, iy, ix, go));
-            pv = fma(beta, p[g], winv(go) * r[g]);
+        for_groups([&](int loc, int, int) {
+          Real w[4], qv[4], pv[4], zv[4], di[4];
+          apply_z(loc, w);
+          ld4(q, loc, qv);
+          ld4(p, loc, pv);
+          ld4(z, loc, zv);
+          dinv4(loc, di);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            qv[j] = di[j] != Real(0) ? fma(beta, qv[j], w[j]) : Real(0);
+            pv[j] = fma(beta, pv[j], zv[j]);
+            pq[0] = fma(pv[j], qv[j], pq[0]);
           }
-          q[g] = qv;
-          p[g] = pv;
-          pq[0] = fma(pv, qv, pq[0]);
+          st4(q, loc, qv);
+          st4(p, loc, pv);
         });
         const Real rz_c = rz;
         allreduce<Real, 1>(pq, [rz_c](Real* t) { t[0] = rz_c / t[0]; });
         const Real alpha = pq[0];
-        // d += alpha p, r -= alpha q; (r, z), (r, r), beta = (r, z)_new / (r, z)
+        // d += alpha p, r -= alpha q, z = D^-1 r; (r, z), (r, r), beta = (r, z)_new / (r, z)
         Real v[3] = {Real(0), Real(0), Real(0)};
-        for_nodes([&](int g, int iy, int ix, int go) {
-          d[g] = fma(alpha, p[g], d[g]);
-          const Real rv = fma(-alpha, q[g], r[g]);
-          r[g] = rv;
-          v[0] = fma(rv, winv(go) * rv, v[0]);
-          v[1] = fma(rv, rv, v[1]);
+        for_group_pairs([&](const int (&loc)[2], const bool (&ok)[2]) {
+          Real dv[2][4], pv[2][4], rv[2][4], qv[2][4], di[2][4];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            if (!ok[u]) continue;
+            ld4(d, loc[u], dv[u]);
+            ld4(p, loc[u], pv[u]);
+            ld4(r, loc[u], rv[u]);
+            ld4(q, loc[u], qv[u]);
+            dinv4(loc[u], di[u]);
+          }
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            if (!ok[u]) continue;
+            Real zv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              dv[u][j] = fma(alpha, pv[u][j], dv[u][j]);
+              rv[u][j] = fma(-alpha, qv[u][j], rv[u][j]);
+              zv[j] = di[u][j] * rv[u][j];
+              v[0] = fma(rv[u][j], zv[j], v[0]);
+              v[1] = fma(rv[u][j], rv[u][j], v[1]);
+            }
+            st4(d, loc[u], dv[u]);
+            st4(r, loc[u], rv[u]);
+            st4(z, loc[u], zv);
+          }
         });
         allreduce<Real, 2, 1>(v, [rz_c](Real* t) { t[2] = t[0] / rz_c; });
         ++it;
@@ -208,8 +257,14 @@ struct Streamer {
       its += it;
       ++sweeps;
       // x += ||r|| d on the own rows, then the FP64 residual of the whole system
-      for_nodes([&](int g, int iy, int ix, int go) {
-        if (free_node(g)) x[g] = fma((double)d[g], nrm, x[g]);
+      for_groups([&](int loc, int, int) {
+        double xv[4];
+        Real dv[4];
+        load4(x + loc, xv);
+        ld4(d, loc, dv);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) xv[j] = fma((double)dv[j], nrm, xv[j]);
+        st4d(x, loc, xv);
       });
       comm.sync();
       residual(x, v2[0], v2[1]);
@@ -246,48 +301,112 @@ struct Streamer {
     return (P.objective == PTG_OBJ_MODIFIED ? P.p : pow(Theta, 1.0 - P.p)) / (double)P.Ne;
   }
 
-  // b = (C/dt) xp + src(g) on the own rows; xn = the start of the step: the extrapolation through
-  // xp and the ring rows X[0..n-2] (n = 1: xp itself); the ring row wr receives xp.
+  // b = (C/dt) xp + src(node) on the own rows; xn = the start of the step: the extrapolation
+  // through xp and the ring rows X[0..n-2] (n = 1: xp itself); the ring row wr receives xp.
+  // The ring rows are node vectors ([Nn], unpadded).
   template <class Src>
   __device__ void begin_step(const double* __restrict__ xp, double* __restrict__ xn, int n, const double* const* X,
                              double* __restrict__ wr, Src src) {
-    for_nodes([&](int g, int iy, int ix, int go) {
-      const double x1 = xp[g];
-      if (wr) wr[g] = x1;
-      double bv = 0.0, xv = 0.0;
-      if (free_node(g)) {
-        bv = fma(stencil64(P.mass, xp, g, iy, ix, go), inv_dt, src(g));
+    for_groups([&](int loc, int iy, int g) {
+      double y[4], x1[4], bv[4], xv[4];
+      stencil_node64<double>(xp, loc, P.mass, loc, P.W, y);
+      load4(xp + loc, x1);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int gi = gnode(iy, g, j);
+        bv[j] = 0.0;
+        xv[j] = 0.0;
+        if (gi < 0) continue;
+        if (wr) wr[gi] = x1[j];
+        if (P.dirichlet[gi]) continue;
+        bv[j] = fma(y[j], inv_dt, src(gi));
         if (n <= 1)
-          xv = x1;
+          xv[j] = x1[j];
         else if (n == 2)
-          xv = fma(2.0, x1, -X[0][g]);
+          xv[j] = fma(2.0, x1[j], -X[0][gi]);
         else if (n == 3)
-          xv = fma(3.0, x1 - X[0][g], X[1][g]);
+          xv[j] = fma(3.0, x1[j] - X[0][gi], X[1][gi]);
         else
-          xv = fma(4.0, x1 + X[1][g], -fma(6.0, X[0][g], X[2][g]));
+          xv[j] = fma(4.0, x1[j] + X[1][gi], -fma(6.0, X[0][gi], X[2][gi]));
       }
-      b[g] = bv;
-      xn[g] = xv;
+      st4d(b, loc, bv);
+      st4d(xn, loc, xv);
     });
     comm.sync();
   }
 
-  // copy a node vector of the system into the own rows of dst (Dirichlet nodes 0)
+  // a node vector ([Nn]) into the own rows of a padded vector (0 off the unknowns), and back
   __device__ void load(const double* __restrict__ src, double* __restrict__ dst) const {
-    for_nodes([&](int g, int, int, int) { dst[g] = free_node(g) ? src[g] : 0.0; });
+    for_groups([&](int loc, int iy, int g) {
+      double v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int gi = gnode(iy, g, j);
+        v[j] = (gi >= 0 && !P.dirichlet[gi]) ? src[gi] : 0.0;
+      }
+      st4d(dst, loc, v);
+    });
   }
   __device__ void store(const double* __restrict__ src, double* __restrict__ dst) const {
     if (!dst) return;
-    for_nodes([&](int g, int, int, int) { dst[g] = src[g]; });
+    for_groups([&](int loc, int iy, int g) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int gi = gnode(iy, g, j);
+        if (gi >= 0) dst[gi] = src[loc + j];
+      }
+    });
   }
 
   __device__ double pnorm_p(const double* __restrict__ x) {
     double v[1] = {0.0};
-    for_nodes([&](int g, int, int, int) {
-      if (free_node(g)) v[0] += ipow(x[g], P.p_int);
+    for_groups([&](int loc, int iy, int g) {
+      double xv[4];
+      load4(x + loc, xv);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (gnode(iy, g, j) >= 0) v[0] += ipow(xv[j], P.p_int);   // 0 on Dirichlet nodes
     });
     allreduce<double, 1>(v);
     return v[0];
+  }
+
+  // Eq. 4.7 element sums of the own element rows (rows r0 .. r0 + R - 1 below ny); lam padded,
+  // Tj and Tjm node vectors
+  __device__ void accumulate_g(const double* __restrict__ lam, const double* __restrict__ Tj,
+                               const double* __restrict__ Tjm, const double* __restrict__ gsrc,
+                               double* __restrict__ gdst) const {
+    const int nx = P.nx, Wp = P.W;
+    const int er = min(R, P.ny - r0);
+    const int nel = er > 0 ? er * nx : 0;
+    const double h2 = P.h * P.h / 36.0;
+    const double nnorm = (double)P.Nt;
+    for (int t = threadIdx.x; t < nel; t += blockDim.x) {
+      const int ler = t / nx, ex = t - ler * nx;
+      const int ey = r0 + ler;
+      const int e = ey * nx + ex;
+      const int g0 = ey * nn + ex;
+      const int l0 = (ey + 1) * Wp + ex + 1;
+      const double lsw = lam[l0], lse = lam[l0 + 1], lne = lam[l0 + Wp + 1], lnw = lam[l0 + Wp];
+      const double tsw = Tj[g0], tse = Tj[g0 + 1], tne = Tj[g0 + nn + 1], tnw = Tj[g0 + nn];
+      const double ksw = 4.0 * tsw - tse - 2.0 * tne - tnw;
+      const double kse = -tsw + 4.0 * tse - tne - 2.0 * tnw;
+      const double kne = -2.0 * tsw - tse + 4.0 * tne - tnw;
+      const double knw = -tsw - 2.0 * tse - tne + 4.0 * tnw;
+      const double kterm = (lsw * ksw + lse * kse + lne * kne + lnw * knw) / 6.0;
+      double term = P.dk[e] * kterm;
+      if (P.has_dc) {
+        const double dsw = tsw - Tjm[g0], dse = tse - Tjm[g0 + 1], dne = tne - Tjm[g0 + nn + 1],
+                     dnw = tnw - Tjm[g0 + nn];
+        const double msw = 4.0 * dsw + 2.0 * dse + dne + 2.0 * dnw;
+        const double mse = 2.0 * dsw + 4.0 * dse + 2.0 * dne + dnw;
+        const double mne = dsw + 2.0 * dse + 4.0 * dne + 2.0 * dnw;
+        const double mnw = 2.0 * dsw + dse + 2.0 * dne + 4.0 * dnw;
+        const double cterm = (lsw * msw + lse * mse + lne * mne + lnw * mnw) * h2;
+        term += P.dc[e] * cterm / step_dt;
+      }
+      gdst[e] = gsrc[e] - term / nnorm;
+    }
   }
 
   // ------------------------------------------------------------------ task bodies
@@ -325,42 +444,6 @@ struct Streamer {
     }
     store(x_prev, P.out_field + (size_t)s * P.Nn);
     if (threadIdx.x == 0 && rank == 0) P.out_aux[s] = theta;
-  }
-
-  // Eq. 4.7 element sums of the own element rows (rows r0 .. r0 + R - 1 below ny)
-  __device__ void accumulate_g(const double* __restrict__ lam, const double* __restrict__ Tj,
-                               const double* __restrict__ Tjm, const double* __restrict__ gsrc,
-                               double* __restrict__ gdst) const {
-    const int nx = P.nx;
-    const int er = min(R, P.ny - r0);
-    const int nel = er > 0 ? er * nx : 0;
-    const double h2 = P.h * P.h / 36.0;
-    const double nnorm = (double)P.Nt;
-    for (int t = threadIdx.x; t < nel; t += blockDim.x) {
-      const int ler = t / nx, ex = t - ler * nx;
-      const int ey = r0 + ler;
-      const int e = ey * nx + ex;
-      const int g0 = ey * nn + ex;
-      const double lsw = lam[g0], lse = lam[g0 + 1], lne = lam[g0 + nn + 1], lnw = lam[g0 + nn];
-      const double tsw = Tj[g0], tse = Tj[g0 + 1], tne = Tj[g0 + nn + 1], tnw = Tj[g0 + nn];
-      const double ksw = 4.0 * tsw - tse - 2.0 * tne - tnw;
-      const double kse = -tsw + 4.0 * tse - tne - 2.0 * tnw;
-      const double kne = -2.0 * tsw - tse + 4.0 * tne - tnw;
-      const double knw = -tsw - 2.0 * tse - tne + 4.0 * tnw;
-      const double kterm = (lsw * ksw + lse * kse + lne * kne + lnw * knw) / 6.0;
-      double term = P.dk[e] * kterm;
-      if (P.has_dc) {
-        const double dsw = tsw - Tjm[g0], dse = tse - Tjm[g0 + 1], dne = tne - Tjm[g0 + nn + 1],
-                     dnw = tnw - Tjm[g0 + nn];
-        const double msw = 4.0 * dsw + 2.0 * dse + dne + 2.0 * dnw;
-        const double mse = 2.0 * dsw + 4.0 * dse + 2.0 * dne + dnw;
-        const double mne = dsw + 2.0 * dse + 4.0 * dne + 2.0 * dnw;
-        const double mnw = 2.0 * dsw + dse + 2.0 * dne + 4.0 * dnw;
-        const double cterm = (lsw * msw + lse * mse + lne * mne + lnw * mnw) * h2;
-        term += P.dc[e] * cterm / step_dt;
-      }
-      gdst[e] = gsrc[e] - term / nnorm;
-    }
   }
 
   __device__ void fine_adjoint(int task) {

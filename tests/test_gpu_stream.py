@@ -56,7 +56,7 @@ def test_streamed_fine_propagators_match_oracle(name, precision):
     U_old, V_old, _ = coarse_states_from_sequential(OracleOp(prob, rho_old))
     ref = o_oneshot(OracleOp(prob, rho), U_old, V_old)
     op, buf, Theta, grad = run(prob, rho, U_old, V_old, precision, 2)
-    assert op.plan(0, prob.Ntau)["nthreads"] == 1024           # the streamed plan ran
+    assert op.plan(0, prob.Ntau)["nthreads"] == 512            # the streamed plan ran
     tol_t, tol_g = (FP64_TOL, FP64_TOL) if precision == "fp64" else (MIXED_T_TOL, MIXED_G_TOL)
     assert_close("F_T", host(buf.F_T), ref["F_pri"][0], tol_t)
     assert_close("F_theta", host(buf.F_th), ref["F_pri"][1], tol_t)
@@ -78,3 +78,18 @@ def test_streamed_path_is_deterministic():
     a = run(prob, rho, U, V, "fp32_refine", 2)
     b = run(prob, rho, U, V, "fp32_refine", 2)
     assert np.array_equal(host(a[3]), host(b[3])) and np.array_equal(host(a[1].T_hist), host(b[1].T_hist))
+
+
+def _plans(prob, stream):
+    op = gpu_operator(prob, "fp32_refine", fine_stream=stream)
+    return [op.plan(kind, prob.Ntau) for kind in (0, 3)]
+
+
+def test_library_streams_only_where_no_cluster_holds_a_slice():
+    # 512 x 512: slabs of a slice fit no 16-CTA cluster, so fine_stream 0 takes the streamed plan
+    big = make_problem(512, 512, Nt=16, Ntau=8, dt=1 / 16, material="table1", sink="left_wide")
+    auto, forced = _plans(big, 0), _plans(big, 2)
+    assert auto == forced and all(p["nthreads"] == 512 for p in auto)
+    # 128 x 128: clusters hold a slice and the on-chip plan stays
+    small = make_problem(128, 128, Nt=16, Ntau=8, dt=1 / 16, material="table1", sink="left_wide")
+    assert _plans(small, 0) == _plans(small, 1)
