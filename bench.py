@@ -147,7 +147,7 @@ def run_gpu(args):
     N_free = (n + 1) ** 2 - int(sink.sum())
     solve = SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=2000, refine_max=8,
                         twolevel=args.twolevel, smooth_steps=args.smooth, local_steps=args.local, initial_guess=args.initial_guess,
-                        fine_stream=args.fine_stream)
+                        fine_stream=args.fine_stream, coarse_stream=args.coarse_stream)
     op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink, solve=solve, device=local)
     seq_op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink,
                       solve=SolveConfig("fp64", rtol=1e-13, cg_iters_max=4000, refine_max=8), device=local)
@@ -602,18 +602,19 @@ def roofline(kind_ms: dict, stats: dict, N_free: int, launches: int, precision: 
     return out
 
 
-def streaming_256(args, flush, stream, device) -> dict:
+def streaming_256(args, flush, stream, device, name="diff256") -> dict:
     """The one-shot pass on the 256x256 workload (Nt = 2048 in 64 slices, rho ~ U(0, 1) seed 1, the
     timed design 1% away from the warm start's, seed 1000), the grid size at which the history
     (1.08 GB) and a slice batch no longer fit in L2: per-kernel CUDA-event times and each stepper
     kernel's algorithmic bandwidth against the measured HBM copy bandwidth.  Warm start from the
-    sequential FP64 coarse states of the nearby design (untimed)."""
+    sequential FP64 coarse states of the nearby design (untimed).  name = "loop512" takes the
+    512x512 sizes (Nt = 4096 in 128 slices) with the same design recipe."""
     import torch
 
     from paper_2411_19030_gb300 import Operator, PassBuffers, SolveConfig, sequential_pass
     from paper_2411_19030_gb300 import PTG_ADJOINT, PTG_PRIMAL
 
-    w = W.workload("diff256")
+    w = W.workload(name)
     n, Nt, Ntau, dt, p = w["n"], w["Nt"], w["Ntau"], w["dt"], w["p"]
     sink = W.dirichlet_left_centre(n, n, w["h"])
     N_free = (n + 1) ** 2 - int(sink.sum())
@@ -621,7 +622,7 @@ def streaming_256(args, flush, stream, device) -> dict:
     rho_np = W.rho_warm_perturb(rho_old_np, seed=1000, amp=0.01)
     solve = SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=4000, refine_max=8,
                         twolevel=args.twolevel, smooth_steps=args.smooth, local_steps=args.local,
-                        initial_guess=args.initial_guess, fine_stream=args.fine_stream)
+                        initial_guess=args.initial_guess, fine_stream=args.fine_stream, coarse_stream=args.coarse_stream)
     op = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink, solve=solve, device=device.index)
     wop = Operator(n, n, w["h"], w["material"], Nt, Ntau, dt, p, sink,
                    solve=SolveConfig("fp64", rtol=1e-12, cg_iters_max=8000, refine_max=8), device=device.index)
@@ -675,7 +676,7 @@ def streaming_256(args, flush, stream, device) -> dict:
     st = op.stats()
     ms = float(np.mean(tot))
     roof = roofline(kind_ms, st, N_free, steps, args.precision)
-    out = {"workload": f"diff256: {n}x{n} grid, Nt={Nt}, Ntau={Ntau} (M={Nt // Ntau}), p={p:g}, rho ~ U(0,1) seed 1, "
+    out = {"workload": f"{name}: {n}x{n} grid, Nt={Nt}, Ntau={Ntau} (M={Nt // Ntau}), p={p:g}, rho ~ U(0,1) seed 1, "
                        "timed design 1% away (seed 1000), warm start from the sequential FP64 coarse states",
            "precision": args.precision, "rtol": args.rtol, "steps": steps, "ms_per_step": ms,
            "value": 2.0 * N_free * Nt / (ms * 1e-3), "unit": UNIT, "per_kernel_ms": kind_ms,
@@ -693,7 +694,8 @@ def run_c3_only(args):
     device = torch.device("cuda", 0)
     torch.cuda.set_device(device)
     flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device=device)
-    print(json.dumps(streaming_256(args, flush, torch.cuda.current_stream(device), device)), flush=True)
+    print(json.dumps(streaming_256(args, flush, torch.cuda.current_stream(device), device, args.c3_workload)),
+          flush=True)
 
 
 # ---------------------------------------------------------------------------- full design loop
@@ -722,7 +724,7 @@ def run_loop(args):
     op = Operator(n, n, h, w["material"], Nt, Ntau, dt, w["p"], sink,
                   solve=SolveConfig(args.precision, rtol=args.rtol, inner_rtol=1e-4, cg_iters_max=4000, refine_max=8,
                                     twolevel=args.twolevel, smooth_steps=args.smooth, local_steps=args.local, initial_guess=args.initial_guess, coarse_mesh=args.coarse_mesh,
-                                    fine_stream=args.fine_stream))
+                                    fine_stream=args.fine_stream, coarse_stream=args.coarse_stream))
     true_op = Operator(n, n, h, w["material"], Nt, Ntau, dt, w["p"], sink,
                        solve=SolveConfig("fp64", rtol=1e-12, cg_iters_max=8000, refine_max=8,
                                          initial_guess=args.initial_guess))
@@ -1030,6 +1032,9 @@ def main():
                     help="time the passes only: no end-to-end run, comparator, accuracy checks or G = 0 probe "
                          "(for profiling the launch sequence of the timed steps)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--coarse-stream", type=int, default=0, choices=[0, 1, 2],
+                    help="coarse-step solves streamed with the multigrid V-cycle: 2 always, 1 never, "
+                         "0 the library's choice (large grids)")
     ap.add_argument("--fine-stream", type=int, default=0, choices=[0, 1, 2],
                     help="fine propagators with their CG vectors in global memory, every slice at once "
                          "(ptg_solve.fine_stream): 2 always, 0/1 on chip")
@@ -1039,6 +1044,8 @@ def main():
     ap.add_argument("--no-c3", dest="c3", action="store_false",
                     help="leave out the 256x256 pass (Nt=2048, 64 slices) with its per-kernel roofline")
     ap.add_argument("--c3-steps", type=int, default=2, help="timed passes of the 256x256 line")
+    ap.add_argument("--c3-workload", default="diff256", choices=["diff256", "loop512"],
+                    help="--c3-only: the grid of the per-kernel line (256x256 or 512x512)")
     ap.add_argument("--c3-only", action="store_true",
                     help="only the 256x256 line (its JSON object), e.g. to capture its kernels under a profiler")
     ap.add_argument("--loop", type=int, default=0, metavar="ITERATIONS",

@@ -149,9 +149,13 @@ typedef struct {
     int local_steps;   /* preconditioner of the FP32 CG solves that use no two-level form (the fine
                           steps): 1 Jacobi; 2 two damped-Jacobi steps (omega = 0.8) on each CTA's
                           slab alone, z = (2S - S A_s S) r with S = omega D^-1 and A_s the slab's
-                          diagonal block of A (symmetric, no communication); 0 the library's
-                          default: 1 on cluster launches, 2 on cooperative-grid launches (whose
-                          reductions go through global memory).  Other values: PTG_EINVAL. */
+                          diagonal block of A (symmetric, no communication); 3 on the streamed
+                          fine propagators (fine_stream) of grids that coarsen at least once: the
+                          multigrid V(1,1)-cycle of coarse_stream, built on C/dt + K (elsewhere as
+                          0); 0 the library's default: the multigrid cycle on streamed fine
+                          propagators of grids with at least three levels, else 1 on cluster
+                          launches and 2 on cooperative-grid launches (whose reductions go through
+                          global memory).  Other values: PTG_EINVAL. */
     int initial_guess; /* where each CG of a time step starts (only iteration counts change):
                           1 plain: a fine step from the state it steps from, a batched coarse step
                           (ptg_coarse_sweep) from the state it propagates;
@@ -174,6 +178,19 @@ typedef struct {
                           library's choice: streamed where no cluster holds a slice (grids of
                           roughly 300 x 300 and more), on chip elsewhere.  Other values:
                           PTG_EINVAL. */
+    int coarse_stream; /* coarse-step solves (G_pri, G_adj and the correction sweeps, a3 and a4) with
+                          the Krylov vectors in global memory: FP64 CG (FP32 under
+                          PTG_FP32_REFINE_ALL) preconditioned by one V(1,1)-cycle of geometric
+                          multigrid in FP32: level l+1 the nodes (2I, 2J) of level l down to a
+                          grid of at most 8 elements across (while nx and ny stay even), Galerkin
+                          operators P^T A P of bilinear interpolation P, damped-Jacobi smoothing
+                          (omega = 0.8), ten damped-Jacobi steps on the coarsest level; symmetric.
+                          The batched coarse propagators run every slice at once, one group of
+                          CTAs per slice; a correction sweep runs as one group of about one CTA
+                          per four node rows.  2 wherever the grid coarsens at least once; 1
+                          never (the on-chip stepper with ptg_solve.twolevel); 0 the library's
+                          choice: grids of 40000 nodes or more with at least three levels.
+                          Other values: PTG_EINVAL. */
 } ptg_solve;
 
 typedef struct {
@@ -303,10 +320,11 @@ int ptg_coarse_sweep_slices(ptg_op* op, int direction, int s0, int ns, const dou
  * (H_lam, S_lam [Ntau][Nn]; H_g, S_g [Ntau][Ne]; only rows s0 .. s0+ns-1 written).  The parts read
  * only the history rows M s + 1 and M(s-1) + 1 (row 0 for s = 0), which ptg_fine_propagate_slices
  * writes and, for M > 1, the forward correction sweep does not, so they can run before Theta is
- * known: beside ptg_parareal_correct(PTG_PRIMAL) of the same op on another stream, when M > 1 and
- * neither call runs on a cooperative grid (ptg_op_overlap_ok).  That is
- * the one exception to the rule that calls on one op do not overlap; the parts touch no op
- * workspace but the counters.  Ops with the 2h-mesh coarse propagators: PTG_EINVAL.
+ * known: beside ptg_parareal_correct(PTG_PRIMAL) of the same op on another stream, when
+ * ptg_op_overlap_ok allows it.  That is the one exception to the rule that calls on one op do not
+ * overlap: a streamed sweep (ptg_solve.coarse_stream) keeps a workspace of its own, and parts on
+ * cluster launches touch no op workspace but the counters.  Ops with the 2h-mesh coarse
+ * propagators: PTG_EINVAL.
  * ptg_coarse_adjoint_combine then forms G_lam = H_lam + c S_lam and G_g = H_g + c S_g on the same
  * rows, with c from the device scalar Theta_d.
  */
@@ -315,10 +333,12 @@ int ptg_coarse_adjoint_split(ptg_op* op, int s0, int ns, const double* V_lam, co
 int ptg_coarse_adjoint_combine(ptg_op* op, int s0, int ns, const double* Theta_d, const double* H_lam,
                                const double* H_g, const double* S_lam, const double* S_g, double* G_lam, double* G_g,
                                cudaStream_t stream);
-/* *ok = 1 when ptg_coarse_adjoint_split may run beside ptg_parareal_correct(PTG_PRIMAL) of this op:
- * M > 1, coarse propagators on the fine mesh, and neither the forward sweep nor the batched
- * coarse adjoint (Ntau tasks) planned as a cooperative-grid launch (those share the op's grid
- * workspace); else *ok = 0. */
+/* Whether ptg_coarse_adjoint_split may run beside ptg_parareal_correct(PTG_PRIMAL) of this op:
+ * M > 1, coarse propagators on the fine mesh, the forward sweep on a cluster or streamed, and the
+ * batched coarse adjoint (Ntau tasks) on clusters or streamed (cooperative-grid stepper plans
+ * share the op's grid workspace).  *ok = 1: the parts may also overlap ptg_adjoint_sweep;
+ * *ok = 2: streamed parts share their workspace with the fine adjoint propagator, which must
+ * start after them; *ok = 0: no overlap. */
 int ptg_op_overlap_ok(ptg_op* op, int* ok);
 
 /*

@@ -37,7 +37,8 @@ class ptg_solve(ctypes.Structure):
     _fields_ = [("precision", c_int), ("rtol", c_double), ("inner_rtol", c_double),
                 ("cg_iters_max", c_int), ("refine_max", c_int), ("twolevel", c_int), ("grid_wide", c_int),
                 ("smooth_steps", c_int), ("coarse_mesh", c_int),
-                ("local_steps", c_int), ("initial_guess", c_int), ("fine_stream", c_int)]
+                ("local_steps", c_int), ("initial_guess", c_int), ("fine_stream", c_int),
+                ("coarse_stream", c_int)]
 
 
 class ptg_stats(ctypes.Structure):

@@ -73,11 +73,15 @@ class SolveConfig:
     #                                  steps, 0 the library default
     coarse_mesh: bool = False        # coarse propagators on the 2h mesh (Sec. 7.3 future work)
     local_steps: int = 0             # FP32 CG without two-level: 1 Jacobi, 2 two slab-local Jacobi
-    #                                  steps, 0 the library default
+    #                                  steps, 3 the multigrid cycle on streamed fine propagators,
+    #                                  0 the library default
     initial_guess: int = 0           # CG start of a step: 1 plain, 2 extrapolated / the neighbouring
     #                                  guess state, 0 the library default (2)
     fine_stream: int = 0             # fine propagators with the CG vectors in global memory, every
     #                                  slice at once: 2 always, 1 never, 0 the library's choice
+    coarse_stream: int = 0           # coarse-step solves (G and the correction sweeps) with the CG
+    #                                  vectors in global memory and a multigrid V-cycle: 2 always
+    #                                  (even grids), 1 never, 0 the library's choice (large grids)
 
 
 class Operator:
@@ -117,7 +121,7 @@ class Operator:
         s = _ffi.ptg_solve(prec, solve.rtol, solve.inner_rtol, solve.cg_iters_max, solve.refine_max,
                            twolevel_code(solve.twolevel), int(solve.grid_wide), int(solve.smooth_steps),
                            int(solve.coarse_mesh), int(solve.local_steps), int(solve.initial_guess),
-                           int(solve.fine_stream))
+                           int(solve.fine_stream), int(solve.coarse_stream))
         self._dir = np.ascontiguousarray(dirichlet, dtype=np.uint8).reshape(-1)
         if self._dir.size != self.Nn:
             raise ValueError("dirichlet mask must have (nx+1)(ny+1) entries")
@@ -206,12 +210,20 @@ class Operator:
                                                  _ptr(S_lam, d), _ptr(S_g, d), _ptr(G_lam, d), _ptr(G_g, d),
                                                  self._stream(stream)), "ptg_coarse_adjoint_combine")
 
+    def overlap_mode(self) -> int:
+        """ptg_op_overlap_ok: 0 the split G_adj may not run beside the forward correction sweep;
+        1 it may (and beside F_adj); 2 it may, but F_adj must start after it (shared streaming
+        workspace)."""
+        if getattr(self, "_overlap_mode", None) is None:
+            ok = ctypes.c_int()
+            _check(_lib().ptg_op_overlap_ok(self._h, ctypes.byref(ok)), "ptg_op_overlap_ok")
+            self._overlap_mode = int(ok.value)
+        return self._overlap_mode
+
     def can_overlap_adjoint_coarse(self) -> bool:
         """Whether the split G_adj may run beside the forward correction sweep (ptg_op_overlap_ok):
-        M > 1, fine-mesh G, and neither kind on a cooperative grid."""
-        ok = ctypes.c_int()
-        _check(_lib().ptg_op_overlap_ok(self._h, ctypes.byref(ok)), "ptg_op_overlap_ok")
-        return bool(ok.value)
+        M > 1, fine-mesh G, and neither kind on a cooperative-grid stepper launch."""
+        return self.overlap_mode() > 0
 
     def side_stream(self):
         """Stream of the work that runs beside the forward correction sweep (default priority)."""
@@ -286,6 +298,7 @@ class Operator:
     def set_plan(self, kind: int, cs: int, ng: int = 1):
         """Force the cluster size and groups per thread of one task kind (cs = 0 clears it)."""
         _check(_lib().ptg_op_set_plan(self._h, kind, cs, ng), "ptg_op_set_plan")
+        self._overlap_mode = None         # the plans decide it
 
 
 # ---------------------------------------------------------------------- state buffers
@@ -400,6 +413,8 @@ def _oneshot_pass_overlapped(op: Operator, buf: PassBuffers, stream=None):
     parts_done.record(side)
     Theta = buf.U_th_new[Ntau:Ntau + 1]
     main.wait_event(sweep_done)
+    if op.overlap_mode() == 2:            # streamed parts and F_adj share the streaming workspace
+        main.wait_event(parts_done)
     op.adjoint_sweep(buf.T_hist, Theta, buf.V_l, buf.V_g, buf.F_l, buf.F_g, stream=main)
     main.wait_event(parts_done)
     op.coarse_adjoint_combine(Theta, H_l, H_g, S_l, S_g, buf.G_l, buf.G_g, stream=main)

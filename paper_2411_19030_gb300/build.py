@@ -37,8 +37,10 @@ def _units() -> list[tuple[str, list[str], str]]:
             units.append((os.path.join(CSRC, "stepper_inst.cu"),
                           [f"-DPTG_REAL={real}", f"-DPTG_TAG={tag}", f"-DPTG_KIND={kind}"],
                           f"stepper_{tag}_k{kind}.o"))
+    for kind in range(6):
+        units.append((os.path.join(CSRC, "stream_inst.cu"), [f"-DPTG_KIND={kind}"], f"stream_k{kind}.o"))
     for name in ("plan.cu", "assemble.cu", "coarse.cu", "api.cu", "noalloc.cu", "design.cu", "mesh.cu", "stream.cu",
-                 "mma.cpp"):
+                 "mg.cu", "mma.cpp"):
         units.append((os.path.join(CSRC, name), [], name.rsplit(".", 1)[0] + ".o"))
     return units
 

@@ -40,8 +40,22 @@ struct ptg_op {
   float* w32_inv = nullptr;     // [PN] FP32 1/C
   double* w64_inv = nullptr;    // [PN] FP64 1/C
   double* st_w64 = nullptr;     // [st_groups][3][PN] (x, x, b), padded node layout
-  void* st_wr = nullptr;        // [st_groups][5][PN] (r, z, p, q, d) in the fine CG precision
-  int st_groups = 0;            // 0: the op has no streaming workspace
+  void* st_wr = nullptr;        // [st_groups][5][PN] (r, z, p, q, d) of the FP64 CG kinds
+  void* st_wr32 = nullptr;      // the same for the FP32 CG kinds: the two layouts never share
+                                // memory, whose padding rows must stay zero for both
+  int st_groups = 0;            // 0: the op has no streaming workspace; the workspace holds
+                                // st_groups + 1 groups, the last one the correction sweeps'
+  // streamed coarse-step solves (ptg_solve.coarse_stream, mg.cu): the multigrid hierarchy of
+  // C/dtau + K and its workspace (st_groups + 1 groups); mg_L == 0: the coarse kinds stay on chip
+  int mg_L = 0;
+  MgLevel mg_lv[kMgMaxLevels] = {};
+  float* mg_w = nullptr;
+  float* mg_wf = nullptr;       // the same hierarchy of C/dt + K for the streamed fine propagators
+  int mg_Lf = 0;                // its levels (0: the fine kinds stream with Jacobi)
+  float* mg_ws = nullptr;
+  long long mg_ws_stride = 0;
+  double* sw_red = nullptr;     // the correction sweeps' reduction partials and barrier, so that the
+  unsigned* sw_bar = nullptr;   // adjoint coarse parts may run beside the forward sweep
   // device workspace
   double *k = nullptr, *c = nullptr, *dk = nullptr, *dc = nullptr;
   double* wE = nullptr;     // [2][3][PEe]: element (D, S, T) weights for dt and dtau (padded)
@@ -216,6 +230,14 @@ constexpr int kThreeLevelSmoothSteps = 3;
 
 // Node count from which a single FP64 system runs grid-wide (see choose_plan).
 constexpr int kWideMinNodes = 40000;
+// Streamed coarse-step solves (stream.cuh, mg.cu): node rows per CTA of a correction sweep's
+// group, the multigrid's smoothing steps, the damped-Jacobi steps on its coarsest level (at most
+// 9 x 9 nodes), and the levels with at most kMgSoloRows node rows, which the group's first CTA
+// runs alone (block barriers instead of the group's).
+constexpr int kSweepRowsPerCta = 4;
+constexpr int kMgNu = 1;
+constexpr int kMgCoarseSteps = 10;
+constexpr int kMgSoloRows = 33;
 
 // two-level bytes of a grid-wide launch of G CTAs (the partials live in global memory)
 struct WideCtx {
@@ -244,7 +266,9 @@ void twolevel_params(const ptg_op* op, int precision, StepParams& P, int tl_mode
   P.tl_vc = P.tl_naj > 0 && uses_vcycle(op, tl_mode);
   P.tl_omega = kVcycleOmega;
   P.tl_nu = op->tl_nu;
-  P.local_steps = op->sv.local_steps > 0 ? op->sv.local_steps : kLocalSteps;
+  // local_steps 3 (multigrid) applies to streamed fine propagators only: the default elsewhere
+  const int ls = op->sv.local_steps == 3 ? 0 : op->sv.local_steps;
+  P.local_steps = ls > 0 ? ls : kLocalSteps;
   // FP32 CG: the op's inner tolerance; FP64 CG: to the final tolerance in one go, or in
   // kTwoLevelInnerFp64 steps with the additive two-level preconditioner
   if (precision == PTG_FP64)
@@ -323,6 +347,30 @@ int choose_plan(ptg_op* op, int precision, int kind, int ntasks, Plan* out) {
   auto it = op->plans.find(key);
   if (it != op->plans.end()) {
     *out = it->second;
+    return PTG_OK;
+  }
+  // Coarse-step solves (a3 and a4) of ops with a multigrid hierarchy (ptg_solve.coarse_stream):
+  // streamed, FP64 CG with the V-cycle of mg.cu.  Batched coarse kinds: G = SMs / slices CTAs per
+  // slice, every slice at once; a correction sweep (one system): one group of a CTA per
+  // kSweepRowsPerCta node rows, at most one per SM.
+  if (coarse_kind(kind) && op->mg_L > 0 && op->st_groups > 0) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    nsm = std::min(nsm, kMaxGrid);
+    const bool sweep = kind == KIND_CORRECT_PRI || kind == KIND_CORRECT_ADJ;
+    int G = sweep ? (op->g.ny + 1) / kSweepRowsPerCta : nsm / ntasks;
+    G = std::max(1, std::min({G, nsm, std::max(1, (op->g.ny + 1) / 2)}));
+    Plan sp;
+    sp.cs = G;
+    sp.nthreads = 512;
+    sp.ng = 1;
+    sp.rmax = (op->g.ny + 1 + G - 1) / G;
+    sp.smem = 0;
+    sp.max_active_clusters = sweep ? 1 : std::max(1, std::min({ntasks, nsm / G, op->st_groups}));
+    sp.stream = true;
+    op->plans[key] = sp;
+    *out = sp;
     return PTG_OK;
   }
   // Fine kinds of the parallel schedule (ntasks >= 2 slices at once) on the streamed propagator
@@ -502,8 +550,30 @@ int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream, int stats_ki
     P.g_bar = op->g_bar;
     P.wait_limit = op->wait_limit;
     P.st_w64 = op->st_w64;
-    P.st_wr = op->st_wr;
+    P.st_wr = prec == PTG_FP64 ? op->st_wr : op->st_wr32;
+    const size_t rbytes = prec == PTG_FP64 ? sizeof(double) : sizeof(float);
+    if (!P.st_wr) return PTG_EINVAL;           // (allocated for every precision a streamed kind uses)
     twolevel_params(op, prec, P, TL_NONE);
+    const int L = coarse_kind(P.kind) ? op->mg_L : op->mg_Lf;
+    if (L > 0) {
+      P.mg_levels = L;
+      P.mg_nu = kMgNu;
+      P.mg_coarse_steps = kMgCoarseSteps;
+      P.mg_solo_rows = kMgSoloRows;
+      for (int l = 0; l < L; ++l) P.mg[l] = op->mg_lv[l];
+      P.mg_w = coarse_kind(P.kind) ? op->mg_w : op->mg_wf;
+      P.mg_ws = op->mg_ws;
+      P.mg_ws_stride = op->mg_ws_stride;
+      if (P.kind == KIND_CORRECT_PRI || P.kind == KIND_CORRECT_ADJ) {
+        // the sweep's own group of the workspace, partials and barrier
+        const size_t g = (size_t)op->st_groups;
+        P.st_w64 = op->st_w64 + g * 3 * (size_t)P.st_pv;
+        P.st_wr = static_cast<char*>(P.st_wr) + g * 5 * (size_t)P.st_pv * rbytes;
+        P.mg_ws = op->mg_ws + g * (size_t)op->mg_ws_stride;
+        P.g_red = op->sw_red;
+        P.g_bar = op->sw_bar;
+      }
+    }
     op->last_stream = stream;
     PTG_CUDA(launch_stream(P, prec, plan.max_active_clusters, plan.nthreads, stream));
     return PTG_OK;
@@ -523,7 +593,7 @@ int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream, int stats_ki
   P.keep_ax = plan.keep_ax ? 1 : 0;
   // on cooperative-grid launches every reduction is a global-memory round trip of several
   // microseconds, so the default trades two slab-local sweeps for fewer CG iterations there
-  if (op->sv.local_steps == 0 && plan.wide) P.local_steps = 2;
+  if ((op->sv.local_steps == 0 || op->sv.local_steps == 3) && plan.wide) P.local_steps = 2;
   op->last_stream = stream;
   PTG_CUDA(launch_stepper(P, plan, prec, ntasks, stream));
   return PTG_OK;
@@ -539,7 +609,8 @@ void free_all(ptg_op* op) {
                   op->g_red, op->g_bar, op->g_halo, op->g_tl,
                   op->tl_Ac, op->tl_band, op->tl_X, op->tl_Ainv,
                   op->tl3_A1, op->tl3_Ac, op->tl3_band, op->tl3_X, op->tl3_Ainv,
-                  op->w32, op->w32_inv, op->w64_inv, op->st_w64, op->st_wr,
+                  op->w32, op->w32_inv, op->w64_inv, op->st_w64, op->st_wr, op->st_wr32, op->mg_w, op->mg_wf, op->mg_ws, op->sw_red,
+                  op->sw_bar,
                   op->mesh_rho, op->mesh_XH, op->mesh_FH, op->mesh_GH, op->mesh_SH, op->mesh_YH,
                   op->mesh_zero, op->mesh_aux, op->mesh_pn, op->mesh_lam, op->mesh_dg};
   for (void* p : ptrs)
@@ -744,9 +815,10 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
     return PTG_EINVAL;
   if (solve->twolevel < PTG_TWOLEVEL_NONE || solve->twolevel > PTG_TWOLEVEL_THREELEVEL) return PTG_EINVAL;
   if (solve->fine_stream < 0 || solve->fine_stream > 2) return PTG_EINVAL;
+  if (solve->coarse_stream < 0 || solve->coarse_stream > 2) return PTG_EINVAL;
   if (solve->smooth_steps < 0 || solve->smooth_steps > 16) return PTG_EINVAL;
   if (solve->coarse_mesh != 0 && solve->coarse_mesh != 1) return PTG_EINVAL;
-  if (solve->local_steps < 0 || solve->local_steps > 2) return PTG_EINVAL;
+  if (solve->local_steps < 0 || solve->local_steps > 3) return PTG_EINVAL;
   if (solve->initial_guess < 0 || solve->initial_guess > kMaxExtrap) return PTG_EINVAL;
   if (solve->coarse_mesh && (grid->nx % 2 || grid->ny % 2 || grid->nx < 4 || grid->ny < 4)) return PTG_EINVAL;
   if (!(solve->rtol > 0.0) || solve->cg_iters_max < 1 || solve->refine_max < 1 || !(solve->inner_rtol >= 0.0))
@@ -831,23 +903,53 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
       A(&op->tl3_Ainv, ncp3 * ncp3 * sizeof(float));
     }
   }
+  // streamed coarse-step solves: coarse_stream = 2 where the grid coarsens at least once, or 0 on
+  // grids of kWideMinNodes nodes or more with at least three levels
+  const int mgL = mg_level_count(grid->nx, grid->ny);
+  if ((solve->coarse_stream == 2 && mgL >= 2) || (solve->coarse_stream == 0 && op->Nn >= kWideMinNodes && mgL >= 3))
+    op->mg_L = mgL;
   // streamed fine propagators: fine_stream = 2, or 0 on grids of kWideMinNodes nodes or more
-  // (the plan streams only where no cluster holds a slice)
-  if (solve->fine_stream == 2 || (solve->fine_stream == 0 && op->Nn >= kWideMinNodes)) {
+  // (the plan streams only where no cluster holds a slice); their CG preconditioned by the
+  // multigrid cycle of C/dt + K with local_steps = 3 (at least two levels), or by default with at
+  // least three levels
+  const bool fine_st = solve->fine_stream == 2 || (solve->fine_stream == 0 && op->Nn >= kWideMinNodes);
+  if (fine_st && ((solve->local_steps == 3 && mgL >= 2) || (solve->local_steps == 0 && mgL >= 3))) op->mg_Lf = mgL;
+  if (fine_st || op->mg_L > 0) {
     int dev_sm = 0;
     cudaDeviceGetAttribute(&dev_sm, cudaDevAttrMultiProcessorCount, device);
     op->st_groups = std::max(1, std::min(time->Ntau, std::min(dev_sm, kMaxGrid)));
+    const size_t ng = (size_t)op->st_groups + 1;
     const size_t PNs = (size_t)(grid->ny + 3) * op->W + 2 * kSlack;
     const size_t PEs = (size_t)(grid->ny + 2) * op->W + 2 * kSlack;
-    const size_t rb = kind_precision(solve->precision, KIND_FINE_PRI) == PTG_FP64 ? 8 : 4;
+    // CG vectors in the precision of each streamed kind's CG
+    const int pf = kind_precision(solve->precision, KIND_FINE_PRI), pc = kind_precision(solve->precision, KIND_COARSE_PRI);
+    const bool f64 = (fine_st && pf == PTG_FP64) || (op->mg_L > 0 && pc == PTG_FP64);
+    const bool f32 = (fine_st && pf != PTG_FP64) || (op->mg_L > 0 && pc != PTG_FP64);
     A(&op->w32, 3 * PEs * sizeof(float));
     A(&op->w32_inv, PNs * sizeof(float));
     A(&op->w64_inv, PNs * sizeof(double));
-    A(&op->st_w64, (size_t)op->st_groups * 3 * PNs * sizeof(double));
-    A(&op->st_wr, (size_t)op->st_groups * 5 * PNs * rb);
+    A(&op->st_w64, ng * 3 * PNs * sizeof(double));
+    if (f64) A(&op->st_wr, ng * 5 * PNs * sizeof(double));
+    if (f32) A(&op->st_wr32, ng * 5 * PNs * sizeof(float));
     // the padded vectors are zero outside the unknowns; only unknowns are ever written
-    if (e == cudaSuccess) e = cudaMemset(op->st_w64, 0, (size_t)op->st_groups * 3 * PNs * sizeof(double));
-    if (e == cudaSuccess) e = cudaMemset(op->st_wr, 0, (size_t)op->st_groups * 5 * PNs * rb);
+    if (e == cudaSuccess) e = cudaMemset(op->st_w64, 0, ng * 3 * PNs * sizeof(double));
+    if (e == cudaSuccess && f64) e = cudaMemset(op->st_wr, 0, ng * 5 * PNs * sizeof(double));
+    if (e == cudaSuccess && f32) e = cudaMemset(op->st_wr32, 0, ng * 5 * PNs * sizeof(float));
+    if (op->mg_L > 0 || op->mg_Lf > 0) {
+      long long wsf = 0;
+      const long long wf = mg_layout(grid->nx, grid->ny, op->mg_lv, std::max(op->mg_L, op->mg_Lf), &wsf);
+      op->mg_ws_stride = wsf;
+      A(&op->mg_ws, ng * (size_t)wsf * sizeof(float));
+      A(&op->sw_red, 2 * kMaxGrid * 4 * sizeof(double));
+      A(&op->sw_bar, 4 * sizeof(unsigned));
+      // rows and columns outside each level's grid and the slack stay zero
+      if (e == cudaSuccess) e = cudaMemset(op->mg_ws, 0, ng * (size_t)wsf * sizeof(float));
+      for (float** w : {op->mg_L > 0 ? &op->mg_w : nullptr, op->mg_Lf > 0 ? &op->mg_wf : nullptr}) {
+        if (!w) continue;
+        A(w, (size_t)wf * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemset(*w, 0, (size_t)wf * sizeof(float));
+      }
+    }
   }
   A(&op->scratch, 2 * sizeof(double));
   A(&op->g_red, 2 * kMaxGrid * 4 * sizeof(double));
@@ -992,6 +1094,14 @@ int ptg_fe_assemble_operator(ptg_op* op, const double* rho_d, cudaStream_t strea
   if (op->w32)
     PTG_CUDA(launch_stream_weights((int)PEe, (int)PN, op->wE, op->nodew, op->dirichlet, op->g.nx, op->g.ny, op->W,
                                    op->w32, op->w32_inv, op->w64_inv, stream));
+  if (op->mg_L > 0) {
+    NodeWeights Ac{out.node[5], out.node[6], out.node[7], out.node[8], out.node[9]};
+    PTG_CUDA(launch_mg_setup(Ac, op->dirichlet, op->mg_lv, op->mg_L, op->mg_w, stream));
+  }
+  if (op->mg_Lf > 0) {
+    NodeWeights Af{out.node[0], out.node[1], out.node[2], out.node[3], out.node[4]};
+    PTG_CUDA(launch_mg_setup(Af, op->dirichlet, op->mg_lv, op->mg_Lf, op->mg_wf, stream));
+  }
   if (op->tl_m) {
     NodeWeights Ac;
     Ac.C = out.node[5];
@@ -1109,7 +1219,17 @@ int ptg_op_overlap_ok(ptg_op* op, int* ok) {
   if (rc == PTG_OK)
     rc = choose_plan(op, kind_precision(op->sv.precision, KIND_COARSE_ADJ), KIND_COARSE_ADJ, op->tm.Ntau, &pa);
   if (rc != PTG_OK) return rc;
-  *ok = !pc.wide && !pa.wide;
+  // a streamed sweep has its own workspace, partials and barrier; a streamed G_adj shares the op's
+  // grid partials with cooperative-grid stepper plans, and its workspace and partials with a
+  // streamed F_adj, which must then wait for it (2)
+  if (!((!pc.wide || pc.stream) && !pa.wide)) return PTG_OK;
+  *ok = 1;
+  if (pa.stream) {
+    Plan pf;
+    rc = choose_plan(op, kind_precision(op->sv.precision, KIND_FINE_ADJ), KIND_FINE_ADJ, op->tm.Ntau, &pf);
+    if (rc != PTG_OK) return rc;
+    if (pf.stream || pf.wide) *ok = 2;
+  }
   return PTG_OK;
 }
 

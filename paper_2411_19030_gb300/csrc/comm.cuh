@@ -97,6 +97,9 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
 __device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ void red_release_add_gpu(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 // The CTAs of a cooperative launch form groups of G = P.cs consecutive CTAs; each group runs
 // one system at a time.  Reduction partials, halo rows and two-level partials are indexed by
@@ -116,41 +119,42 @@ struct GridComm {
   unsigned char* pending_hi = nullptr;   // where the row above goes
   int pending_bytes = 0;         // bytes of one row
   int hset = 0;                  // slot set of the latest push
+  unsigned epoch = 0;            // barriers this CTA has passed in the launch
 
   __device__ GridComm(const StepParams& P_, RedSmem& rs_)
       : P(P_), rs(rs_), G(P_.cs), gid((int)blockIdx.x / P_.cs), base(((int)blockIdx.x / P_.cs) * P_.cs) {}
   __device__ int rank() const { return (int)blockIdx.x - base; }
 
-  // Counting barrier over all CTAs of the launch (co-resident: cooperative launch).  Thread 0
-  // of each CTA makes the CTA's global writes visible, arrives, and waits for the generation
-  // to move on; the last arriver resets the count and releases the next generation.  A wait
-  // that reaches P.wait_limit polls (kGridSpinLimit if not positive) without the release
-  // records PTG_ETIMEOUT and returns; once any CTA has
-  // recorded it (the launch's status word, P.g_bar[2]), every later wait returns at once, so a
-  // broken launch ends quickly with the error instead of waiting out every barrier.
+  // Counting barrier over the CTAs of the group (co-resident: cooperative launch).  The group's
+  // arrival count (zeroed before the launch) only grows: thread 0 of each CTA adds 1 with release
+  // semantics, which publishes the CTA's global writes ordered before it by the block barrier, and
+  // polls with acquire loads until the count reaches G times the barriers passed, which makes
+  // every other CTA's writes before its arrival visible.  One global round trip after the last
+  // arrival; no reset.  A wait that reaches P.wait_limit polls (kGridSpinLimit if not positive)
+  // records PTG_ETIMEOUT and returns; once any CTA has recorded it (the group's broken flag,
+  // P.g_bar[4 gid + 2]), every later wait returns at once, so a broken launch ends quickly with
+  // the error instead of waiting out every barrier.
   __device__ void barrier() {
     __syncthreads();
+    if (G == 1) {                // a group of one CTA: the block barrier orders its global accesses
+      pull_halos();
+      return;
+    }
     if (threadIdx.x == 0) {
       unsigned* count = P.g_bar + 4 * gid;
-      unsigned* gen = count + 1;
       unsigned* broken = count + 2;
-      const unsigned g0 = ld_acquire_gpu(gen);
+      ++epoch;
+      const unsigned target = epoch * (unsigned)G;
       __threadfence();
-      const unsigned arrived = atomicAdd(count, 1u);
-      if (arrived == (unsigned)G - 1u) {
-        atomicExch(count, 0u);
-        __threadfence();
-        st_release_gpu(gen, g0 + 1u);
-      } else {
-        const long long limit = P.wait_limit > 0 ? P.wait_limit : (long long)kGridSpinLimit;
-        long long spins = 0;
-        while (ld_acquire_gpu(gen) == g0) {
-          if ((++spins & 255) == 0 && ld_acquire_gpu(broken) != 0u) break;
-          if (spins >= limit) {
-            record_error(P.stats, PTG_ETIMEOUT, P.stats_kind, -1);
-            atomicExch(broken, 1u);
-            break;
-          }
+      red_release_add_gpu(count, 1u);
+      const long long limit = P.wait_limit > 0 ? P.wait_limit : (long long)kGridSpinLimit;
+      long long spins = 0;
+      while ((int)(ld_acquire_gpu(count) - target) < 0) {
+        if ((++spins & 255) == 0 && ld_acquire_gpu(broken) != 0u) break;
+        if (spins >= limit) {
+          record_error(P.stats, PTG_ETIMEOUT, P.stats_kind, -1);
+          atomicExch(broken, 1u);
+          break;
         }
       }
       __threadfence();

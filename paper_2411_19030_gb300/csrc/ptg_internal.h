@@ -53,6 +53,18 @@ struct NodeWeights {
   const double* NW;
 };
 
+// Geometric multigrid hierarchy of the coarse-step operator (mg.cu): level l has nx, ny
+// elements (halved per level), the padded width W, arrays of plen floats each (slack included),
+// its six weight arrays (C, E, N, NE, NW, omega/diag) at woff in the op's weight buffer, and its
+// vectors at voff in a group's workspace (level 0: u, res; coarser: f, u, res, e).
+constexpr int kMgMaxLevels = 10;
+constexpr int kMgMinCells = 8;       // a level with min(nx, ny) <= 8 is the coarsest
+constexpr float kMgOmega = 0.8f;     // Jacobi damping: omega lambda_max(D^-1 A) <= 1.8 on every level
+struct MgLevel {
+  int nx, ny, W, pad;
+  long long plen, woff, voff;
+};
+
 // Everything one stepper launch needs (passed by value in parameter space).
 struct StepParams {
   // problem
@@ -140,11 +152,22 @@ struct StepParams {
   int wide;                  // 1: launched as stepper_wide_kernel, groups of cs CTAs
   int wide_tasks;            // tasks of a grid-wide launch (group g runs g, g + groups, ...)
   double* g_red;             // [2][kMaxGrid][4] reduction partials
-  unsigned* g_bar;           // [4 per group] barrier: arrival count, generation, broken flag (zeroed per launch)
+  unsigned* g_bar;           // [4 per group] barrier: arrival count, unused, broken flag (zeroed per launch)
   long long wait_limit;      // polls of a grid barrier before it reports PTG_ETIMEOUT (<= 0: kGridSpinLimit)
   void* g_halo;              // [2 sets][kMaxGrid][2] rows of g_halo_row_bytes: first / last owned row
   int g_halo_row_bytes;      // W * 8 (a row of doubles; float rows use the first half)
   float* g_tl;               // [kMaxGrid][ncp] restricted partials of the two-level preconditioner
+  // streamed coarse-step solves (stream.cuh): FP64 CG preconditioned by one V(nu, nu)-cycle of the
+  // multigrid hierarchy (mg_levels = 0: Jacobi); mg_ws + group * mg_ws_stride is a group's
+  // workspace; levels with at most mg_solo_rows node rows run on the group's first CTA alone
+  int mg_levels;
+  int mg_nu;                 // damped-Jacobi steps before and after the coarse correction
+  int mg_coarse_steps;       // damped-Jacobi steps on the coarsest level (from zero)
+  int mg_solo_rows;
+  MgLevel mg[kMgMaxLevels];
+  const float* mg_w;
+  float* mg_ws;
+  long long mg_ws_stride;
 };
 
 // Two-level preconditioner of the coarse-step solves: aggregates of m x m nodes (m a multiple
@@ -329,6 +352,14 @@ cudaError_t launch_stream_weights(int PE, int PN, const double* wE, const double
                                   int nx, int ny, int W, float* w32, float* w32_inv, double* w64_inv,
                                   cudaStream_t stream);
 cudaError_t launch_stream(const StepParams& P, int precision, int ngroups, int nthreads, cudaStream_t stream);
+// Multigrid hierarchy: the number of levels of an nx x ny grid (1: no coarsening), the layout of
+// L levels (returns the floats of the weight buffer; *ws_floats the floats of one group's
+// workspace), and the set-up of every level's weights from the FP64 node weights A (buffer
+// zeroed beforehand: the slack and the rows outside the grid stay zero).
+int mg_level_count(int nx, int ny);
+long long mg_layout(int nx, int ny, MgLevel* lv, int L, long long* ws_floats);
+cudaError_t launch_mg_setup(NodeWeights A, const uint8_t* dirichlet, const MgLevel* lv, int L, float* w,
+                            cudaStream_t stream);
 // G_l = H_l + c S_l ([n_l]) and G_g = H_g + c S_g ([n_g]), c the adjoint source scale of Theta
 cudaError_t launch_adjoint_combine(long long n_l, long long n_g, const double* Theta, double p, int Ne, int modified,
                                    const double* H_l, const double* H_g, const double* S_l, const double* S_g,

@@ -1,32 +1,21 @@
-// stream.cu -- kernels and launch of the streamed fine propagators (stream.cuh).
+// stream.cu -- launch of the streamed propagators (stream.cuh); the kernels are instantiated
+// per task kind in stream_inst.cu.
 #include "stream.cuh"
 
 namespace ptg {
 
-constexpr int kStreamThreads = 512;   // one CTA per SM, 128 registers per thread
-
-// ngroups groups of P.cs CTAs; group g runs tasks g, g + ngroups, ... < P.wide_tasks.
-template <class Real, int KIND>
-__global__ void __launch_bounds__(kStreamThreads, 1) stream_kernel(const __grid_constant__ StepParams P) {
-  __shared__ RedSmem rs;
-  GridComm comm(P, rs);
-  Streamer<Real, KIND> st(P, comm);
-  const int ngroups = (int)gridDim.x / P.cs;
-  for (int task = comm.gid; task < P.wide_tasks; task += ngroups) {
-    if constexpr (KIND == KIND_FINE_PRI)
-      st.fine_primal(task);
-    else
-      st.fine_adjoint(task);
-    comm.sync();                           // the group's workspace is free for its next task
-  }
-}
-
 cudaError_t launch_stream(const StepParams& P, int precision, int ngroups, int nthreads, cudaStream_t stream) {
-  using K = void (*)(const StepParams);
-  K k = nullptr;
-  const bool f32 = precision == PTG_FP32_REFINE;
-  if (P.kind == KIND_FINE_PRI) k = f32 ? &stream_kernel<float, KIND_FINE_PRI> : &stream_kernel<double, KIND_FINE_PRI>;
-  if (P.kind == KIND_FINE_ADJ) k = f32 ? &stream_kernel<float, KIND_FINE_ADJ> : &stream_kernel<double, KIND_FINE_ADJ>;
+  StreamKernels ks{nullptr, nullptr};
+  switch (P.kind) {
+    case KIND_FINE_PRI: ks = stream_select_0(); break;
+    case KIND_COARSE_PRI: ks = stream_select_1(); break;
+    case KIND_CORRECT_PRI: ks = stream_select_2(); break;
+    case KIND_FINE_ADJ: ks = stream_select_3(); break;
+    case KIND_COARSE_ADJ: ks = stream_select_4(); break;
+    case KIND_CORRECT_ADJ: ks = stream_select_5(); break;
+    default: break;
+  }
+  const StreamKernel k = precision == PTG_FP32_REFINE ? ks.f32 : ks.f64;
   if (!k || ngroups < 1 || ngroups * P.cs > kMaxGrid) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaMemsetAsync(P.g_bar, 0, 4 * sizeof(unsigned) * ngroups, stream);
   if (e != cudaSuccess) return e;

@@ -54,7 +54,7 @@ def _args(nx=4, ny=4, Nt=4, Ntau=2, p=8.0, prec=0):
 
 
 @pytest.mark.parametrize("bad", ["ntau", "p_odd", "p_frac", "nx", "precision", "objective", "guess_high",
-                                 "guess_negative", "local_steps"])
+                                 "guess_negative", "local_steps", "coarse_stream"])
 def test_invalid_problem_rejected_on_host(lib, bad):
     g, m, t, s, d = _args()
     if bad == "ntau":
@@ -74,7 +74,9 @@ def test_invalid_problem_rejected_on_host(lib, bad):
     elif bad == "guess_negative":
         s.initial_guess = -1
     elif bad == "local_steps":
-        s.local_steps = 3
+        s.local_steps = 4
+    elif bad == "coarse_stream":
+        s.coarse_stream = 3
     h = ctypes.c_void_p()
     rc = lib.ptg_op_create(ctypes.byref(g), ctypes.byref(m), ctypes.byref(t), ctypes.byref(s), d.ctypes.data,
                            None, None, 0, ctypes.byref(h))

@@ -37,8 +37,8 @@ CASES = {
 }
 
 
-def run(prob, rho, U_old, V_old, precision, stream):
-    op = gpu_operator(prob, precision, rtol=1e-13 if precision == "fp64" else 1e-10, fine_stream=stream)
+def run(prob, rho, U_old, V_old, precision, stream, **kw):
+    op = gpu_operator(prob, precision, rtol=1e-13 if precision == "fp64" else 1e-10, fine_stream=stream, **kw)
     buf = PassBuffers(op)
     buf.U_T.copy_(dev(U_old[0])); buf.U_th.copy_(dev(U_old[1]))
     buf.V_l.copy_(dev(V_old[0])); buf.V_g.copy_(dev(V_old[1]))
@@ -93,3 +93,36 @@ def test_library_streams_only_where_no_cluster_holds_a_slice():
     # 128 x 128: clusters hold a slice and the on-chip plan stays
     small = make_problem(128, 128, Nt=16, Ntau=8, dt=1 / 16, material="table1", sink="left_wide")
     assert _plans(small, 0) == _plans(small, 1)
+
+
+MG_CASES = {
+    # three levels (40 x 32 -> 20 x 16 -> 10 x 8), several CTAs per slice
+    "table1_40x32": lambda: (make_problem(40, 32, Nt=24, Ntau=4, dt=0.6 / 24, material="table1", sink="left_wide",
+                                          q_time=W.q_time_paper(24, 0.6 / 24)), W.rho_uniform(40, 32, 85, 0.05, 0.95)),
+    # two levels, one CTA per slice
+    "one_cta_16": lambda: (make_problem(16, 16, Nt=160, Ntau=160, dt=1 / 160, material="simp_k", sink="left_wide"),
+                           W.rho_uniform(16, 16, 86, 0.2, 0.8)),
+}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+@pytest.mark.parametrize("name", list(MG_CASES))
+def test_streamed_fine_propagators_with_multigrid_match_oracle(name, precision):
+    """local_steps = 3: the streamed fine CG preconditioned by the multigrid V-cycle of C/dt + K."""
+    prob, rho = MG_CASES[name]()
+    rho_old = W.rho_warm_perturb(rho, seed=87, amp=0.05)
+    U_old, V_old, _ = coarse_states_from_sequential(OracleOp(prob, rho_old))
+    ref = o_oneshot(OracleOp(prob, rho), U_old, V_old)
+    its = {}
+    for ls in (3, 1):
+        op, buf, Theta, grad = run(prob, rho, U_old, V_old, precision, 2, local_steps=ls)
+        tol_t, tol_g = (FP64_TOL, FP64_TOL) if precision == "fp64" else (MIXED_T_TOL, MIXED_G_TOL)
+        assert_close(f"F_T[{ls}]", host(buf.F_T), ref["F_pri"][0], tol_t)
+        assert_close(f"T_hist[{ls}]", host(buf.T_hist), ref["T_hist"], tol_t)
+        assert_close(f"F_lam[{ls}]", host(buf.F_l), ref["F_adj"][0], tol_g)
+        assert_close(f"F_g[{ls}]", host(buf.F_g), ref["F_adj"][1], tol_g)
+        assert_close(f"grad[{ls}]", host(grad), ref["grad"], tol_g)
+        st = op.stats()
+        assert st["status"] == 0, st
+        its[ls] = st["kind_cg_iters"][0] / st["kind_solves"][0]
+    assert its[3] < its[1], its                  # the cycle cuts the fine-step iterations
