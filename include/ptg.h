@@ -187,7 +187,7 @@ typedef struct {
                           (omega = 0.8), ten damped-Jacobi steps on the coarsest level; symmetric.
                           The batched coarse propagators run every slice at once, one group of
                           CTAs per slice; a correction sweep runs as one group of about one CTA
-                          per four node rows.  2 wherever the grid coarsens at least once; 1
+                          per two node rows (at most one per SM).  2 wherever the grid coarsens at least once; 1
                           never (the on-chip stepper with ptg_solve.twolevel); 0 the library's
                           choice: grids of 40000 nodes or more with at least three levels.
                           Other values: PTG_EINVAL. */
@@ -238,6 +238,14 @@ void ptg_op_destroy(ptg_op* op);
 /* Sizes of the op: Nn, Ne, Nt, Ntau, M (any pointer may be NULL). */
 int ptg_op_sizes(const ptg_op* op, int* Nn, int* Ne, int* Nt, int* Ntau, int* M);
 
+/* Tuning of the multigrid cycle of the streamed solves (ptg_solve.coarse_stream, local_steps = 3)
+ * for the launches that follow: solo_rows, levels with at most this many node rows run on the
+ * first CTA of a group alone (block barriers instead of the group's); coarse_steps, damped-Jacobi
+ * steps on the coarsest level (1..64); fused, 1 prolongation and post-smoothing in one pass, 0 in
+ * two.  0 (solo_rows, coarse_steps) and -1 (fused) restore the library's defaults (33, 10, 1).
+ * Results change only within the solver tolerance.  PTG_EINVAL on other values. */
+int ptg_op_set_multigrid(ptg_op* op, int solo_rows, int coarse_steps, int fused);
+
 /*
  * Launch plan of the cluster stepper.  Every solve runs on one thread-block cluster of
  * `cs` CTAs (1, 2, 4, 8 or 16) that split the node rows; each CTA has `nthreads` (256)
@@ -245,7 +253,9 @@ int ptg_op_sizes(const ptg_op* op, int* Nn, int* Ne, int* Nt, int* Ntau, int* M)
  * 1 coarse primal, 2 primal correction, 3 fine adjoint, 4 coarse adjoint, 5 adjoint correction.
  * ptg_op_get_plan reports the plan used for `ntasks` concurrent clusters (chosen for the
  * fewest waves, then the largest cluster).  ptg_op_set_plan forces a plan for a kind
- * (cs = 0 removes the override); PTG_EINVAL if the plan does not fit the grid or device.
+ * (cs = 0 removes the override); PTG_EINVAL if the plan does not fit the grid or device.  For a
+ * streamed correction sweep (ptg_solve.coarse_stream) cs is the number of CTAs of its group
+ * (1 .. SMs, at least two node rows each) and ng is ignored.
  */
 int ptg_op_get_plan(ptg_op* op, int kind, int ntasks, int* cs, int* nthreads, int* ng, int* max_active_clusters);
 int ptg_op_set_plan(ptg_op* op, int kind, int cs, int ng);

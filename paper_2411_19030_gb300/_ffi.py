@@ -62,6 +62,7 @@ SIGNATURES = {
     "ptg_op_create": (c_int, [POINTER(ptg_grid), POINTER(ptg_material), POINTER(ptg_time), POINTER(ptg_solve),
                               _P, _P, _P, c_int, POINTER(c_void_p)]),
     "ptg_op_destroy": (None, [_P]),
+    "ptg_op_set_multigrid": (c_int, [_P, c_int, c_int, c_int]),
     "ptg_op_sizes": (c_int, [_P, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "ptg_op_get_plan": (c_int, [_P, c_int, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "ptg_op_set_plan": (c_int, [_P, c_int, c_int, c_int]),

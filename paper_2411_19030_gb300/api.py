@@ -295,6 +295,11 @@ class Operator:
                                       ctypes.byref(mac)), "ptg_op_get_plan")
         return dict(cs=cs.value, nthreads=nt.value, ng=ng.value, max_active_clusters=mac.value)
 
+    def set_multigrid(self, solo_rows: int = 0, coarse_steps: int = 0, fused: int = -1):
+        """Tune the multigrid cycle of the streamed solves (ptg_op_set_multigrid; 0 / -1 restore
+        the defaults)."""
+        _check(_lib().ptg_op_set_multigrid(self._h, solo_rows, coarse_steps, fused), "ptg_op_set_multigrid")
+
     def set_plan(self, kind: int, cs: int, ng: int = 1):
         """Force the cluster size and groups per thread of one task kind (cs = 0 clears it)."""
         _check(_lib().ptg_op_set_plan(self._h, kind, cs, ng), "ptg_op_set_plan")

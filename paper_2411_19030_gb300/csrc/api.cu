@@ -54,6 +54,7 @@ struct ptg_op {
   int mg_Lf = 0;                // its levels (0: the fine kinds stream with Jacobi)
   float* mg_ws = nullptr;
   long long mg_ws_stride = 0;
+  int mg_solo = 0, mg_csteps = 0, mg_fuse = -1;   // ptg_op_set_multigrid (0 / -1: the defaults)
   double* sw_red = nullptr;     // the correction sweeps' reduction partials and barrier, so that the
   unsigned* sw_bar = nullptr;   // adjoint coarse parts may run beside the forward sweep
   // device workspace
@@ -232,12 +233,13 @@ constexpr int kThreeLevelSmoothSteps = 3;
 constexpr int kWideMinNodes = 40000;
 // Streamed coarse-step solves (stream.cuh, mg.cu): node rows per CTA of a correction sweep's
 // group, the multigrid's smoothing steps, the damped-Jacobi steps on its coarsest level (at most
-// 9 x 9 nodes), and the levels with at most kMgSoloRows node rows, which the group's first CTA
+// 9 x 9 nodes) where no dense inverse applies, and the levels with at most kMgSoloRows node rows, which the group's first CTA
 // runs alone (block barriers instead of the group's).
-constexpr int kSweepRowsPerCta = 4;
+constexpr int kSweepRowsPerCta = 2;
 constexpr int kMgNu = 1;
 constexpr int kMgCoarseSteps = 10;
 constexpr int kMgSoloRows = 33;
+constexpr int kMgFuse = 1;
 
 // two-level bytes of a grid-wide launch of G CTAs (the partials live in global memory)
 struct WideCtx {
@@ -558,8 +560,9 @@ int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream, int stats_ki
     if (L > 0) {
       P.mg_levels = L;
       P.mg_nu = kMgNu;
-      P.mg_coarse_steps = kMgCoarseSteps;
-      P.mg_solo_rows = kMgSoloRows;
+      P.mg_coarse_steps = op->mg_csteps > 0 ? op->mg_csteps : kMgCoarseSteps;
+      P.mg_solo_rows = op->mg_solo > 0 ? op->mg_solo : kMgSoloRows;
+      P.mg_fuse = op->mg_fuse >= 0 ? op->mg_fuse : kMgFuse;
       for (int l = 0; l < L; ++l) P.mg[l] = op->mg_lv[l];
       P.mg_w = coarse_kind(P.kind) ? op->mg_w : op->mg_wf;
       P.mg_ws = op->mg_ws;
@@ -1031,6 +1034,22 @@ int ptg_op_set_plan(ptg_op* op, int kind, int cs, int ng) {
     op->plan_override.erase(kind);
     return PTG_OK;
   }
+  if ((kind == KIND_CORRECT_PRI || kind == KIND_CORRECT_ADJ) && op->mg_L > 0 && op->st_groups > 0) {
+    // a streamed correction sweep: one group of cs CTAs (at most one per SM, >= 2 rows each)
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cs < 1 || cs > std::min(nsm, kMaxGrid) || cs > (op->g.ny + 1) / 2) return PTG_EINVAL;
+    Plan sp;
+    sp.cs = cs;
+    sp.nthreads = 512;
+    sp.ng = 1;
+    sp.rmax = (op->g.ny + 1 + cs - 1) / cs;
+    sp.max_active_clusters = 1;
+    sp.stream = true;
+    op->plan_override[kind] = sp;
+    return PTG_OK;
+  }
   if (cs != 1 && cs != 2 && cs != 4 && cs != 8 && cs != 16) return PTG_EINVAL;
   const int rmax = (op->g.ny + 1 + cs - 1) / cs;
   if (rmax < 2) return PTG_EINVAL;
@@ -1059,6 +1078,14 @@ int ptg_op_set_plan(ptg_op* op, int kind, int cs, int ng) {
     }
   }
   return PTG_EINVAL;
+}
+
+int ptg_op_set_multigrid(ptg_op* op, int solo_rows, int coarse_steps, int fused) {
+  if (!op || solo_rows < 0 || coarse_steps < 0 || coarse_steps > 64 || fused < -1 || fused > 1) return PTG_EINVAL;
+  op->mg_solo = solo_rows;
+  op->mg_csteps = coarse_steps;
+  op->mg_fuse = fused;
+  return PTG_OK;
 }
 
 int ptg_op_get_plan(ptg_op* op, int kind, int ntasks, int* cs, int* nthreads, int* ng, int* max_active_clusters) {

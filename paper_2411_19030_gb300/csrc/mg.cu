@@ -154,4 +154,5 @@ cudaError_t launch_mg_setup(NodeWeights A, const uint8_t* dirichlet, const MgLev
   return cudaGetLastError();
 }
 
+
 }  // namespace ptg

@@ -164,6 +164,8 @@ struct StepParams {
   int mg_nu;                 // damped-Jacobi steps before and after the coarse correction
   int mg_coarse_steps;       // damped-Jacobi steps on the coarsest level (from zero)
   int mg_solo_rows;
+  int mg_fuse;               // nu = 1: prolongation and post-smoothing in one pass (one barrier less
+                             // per level)
   MgLevel mg[kMgMaxLevels];
   const float* mg_w;
   float* mg_ws;

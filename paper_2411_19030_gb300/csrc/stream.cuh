@@ -418,6 +418,93 @@ struct Streamer {
     }
     return rz;
   }
+  // nu = 1: the prolongation and the post-smoothing step in one pass, out = u' + S (f - A u') with
+  // u' = u + P e_{l+1} formed on the window from u and the coarse e (no barrier between them);
+  // level 0 writes z in the CG precision and returns the local (r, z)
+  template <class T>
+  __device__ Real mg_prolong_post(int l, const T* __restrict__ f) {
+    const int c = l + 1, Wl = P.mg[l].W, Wc = P.mg[c].W;
+    const float* ec = lv(c, 3);
+    const float* wd = lw(l, 5);
+    const float* u = lv(l, l == 0 ? 0 : 1);
+    const float *C = lw(l, 0), *E = lw(l, 1), *N = lw(l, 2), *NE = lw(l, 3), *NW = lw(l, 4);
+    Real rz = Real(0);
+    for_lgroups(l, [&](int loc) {
+      const int y = loc / Wl - 1, x0 = loc - (y + 1) * Wl - 1;   // first node of the group
+      // A u' accumulated row by row (rows y-1, y, y+1) from the window of u' = u + P e_{l+1};
+      // x0 = 4g - 1 is odd, so window column i (node x0 - 1 + i) lies between coarse columns
+      // cx0 + i/2 and cx0 + (i+1)/2 (equal for even i)
+      const int cx0 = (x0 - 1) >> 1;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f}, uc[4];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const int row = loc + (r - 1) * Wl;
+        float v[6], d[6];
+        load_window(u, row, v);
+        load_window(wd, row, d);
+        const int yy = y - 1 + r, Ja = yy >> 1, Jb = (yy + 1) >> 1;
+        const float* ra = ec + (Ja + 1) * Wc + 1 + cx0;
+        const float* rb = ec + (Jb + 1) * Wc + 1 + cx0;
+        float ca[4], cb[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          ca[q] = ra[q];
+          cb[q] = rb[q];
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+          const int Ia = i >> 1, Ib = (i + 1) >> 1;
+          const float pv = 0.25f * ((ca[Ia] + ca[Ib]) + (cb[Ia] + cb[Ib]));
+          if (d[i] != 0.f) v[i] += pv;
+        }
+        if (r == 0) {          // the row below: N of the node below, NE of the SW, NW of the SE node
+          float nb[4];
+          ld4f(N, loc - Wl, nb);
+          const float* neb = NE + loc - Wl - 1;
+          const float* nwb = NW + loc - Wl + 1;
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            acc[j] = fmaf(nb[j], v[j + 1], fmaf(neb[j], v[j], fmaf(nwb[j], v[j + 2], acc[j])));
+        } else if (r == 1) {   // the node's row: C, E of the node, E of the west neighbour
+          float c4[4], e5[5];
+          ld4f(C, loc, c4);
+          load_ewindow(E, loc, e5);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            acc[j] = fmaf(c4[j], v[j + 1], fmaf(e5[j + 1], v[j + 2], fmaf(e5[j], v[j], acc[j])));
+            uc[j] = v[j + 1];
+          }
+        } else {               // the row above: the node's N, NE, NW
+          float n4[4], ne4[4], nw4[4];
+          ld4f(N, loc, n4);
+          ld4f(NE, loc, ne4);
+          ld4f(NW, loc, nw4);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            acc[j] = fmaf(n4[j], v[j + 1], fmaf(ne4[j], v[j + 2], fmaf(nw4[j], v[j], acc[j])));
+        }
+      }
+      float dv[4], o[4];
+      T fv[4];
+      ld4f(wd, loc, dv);
+      ldv(f, loc, fv);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) o[j] = fmaf(dv[j], (float)fv[j] - acc[j], uc[j]);
+      if (l == 0) {
+        Real zv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          zv[j] = (Real)o[j];
+          rz = fma((Real)fv[j], zv[j], rz);
+        }
+        st4(z, loc, zv);
+      } else {
+        st4f(lv(l, 3), loc, o);
+      }
+    });
+    return rz;
+  }
+
   // z = M^-1 r from r (every row of r visible); returns the local (r, z).  z is visible to the
   // group after the next group barrier.
   __device__ Real vcycle() {
@@ -436,6 +523,13 @@ struct Streamer {
     for (int l = L - 2; l >= 0; --l) {
       if (l < L - 2) xsync(l + 1, l);   // e_{l+1} of the level above is visible
       else if (!(solo(l + 1) && solo(l))) comm.sync();
+      if (P.mg_nu == 1 && P.mg_fuse) {
+        if (l == 0)
+          rz = mg_prolong_post(0, r);
+        else
+          mg_prolong_post(l, (const float*)lv(l, 0));
+        continue;
+      }
       mg_prolong(l);
       xsync(l, l);
       if (l == 0)
