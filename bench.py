@@ -437,6 +437,16 @@ def run_gpu(args):
 
     roof = roofline(kind_ms, stats, N_free, args.steps, args.precision)
     streaming = streaming_256(args, flush, stream, device) if (args.extras and args.c3) else None
+    loop512 = None
+    if args.extras and args.c5 and world == 1:
+        ll = loop_line(args, 3)
+        loop512 = {"what": "Alg. 3 at 512x512 (Nt = 4096, 128 slices), 3 design iterations (1 sequential, 2 one-shot); "
+                           "the comparator is sequential FP64 time stepping of the last design",
+                   "workload": ll["config"]["workload"], "ms_per_oneshot_iteration": ll["value"],
+                   "iteration_ms": ll["history"]["ms"], "sequential_fp64_ms": ll["sequential_fp64_ms_last_design"],
+                   "speedup_vs_sequential_fp64": ll["speedup_last_iteration_vs_sequential_fp64"],
+                   "Theta_estimate": ll["final"]["Theta_estimate"],
+                   "Theta_true_fp64_sequential": ll["final"]["Theta_true_fp64_sequential"]}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -445,7 +455,7 @@ def run_gpu(args):
         "config": {"workload": f"{WORKLOAD}: 128x128 grid, Nt=1024, Ntau=32 (M=32), p=8, SIMP k, warm start from "
                                "the sequential coarse states of a design 1% away",
                    "overlap_adjoint_coarse": overlap,
-                   "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel, "smooth_steps": args.smooth, "local_steps": args.local, "initial_guess": args.initial_guess, "l2": "flushed between steps (256 MB write)",
+                   "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel, "smooth_steps": args.smooth, "local_steps": args.local, "initial_guess": args.initial_guess, "fine_stream": args.fine_stream, "coarse_stream": args.coarse_stream, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "wall_s": wall},
         "per_kernel_ms": kind_ms,
@@ -477,10 +487,14 @@ def run_gpu(args):
         "precision_variant": variant,
         "fp64_oneshot": fp64_arm,
         "streaming_256": streaming,
+        "loop512": loop512,
         "e2e": None if e2e is None else {"value": world * dof_steps / (e2e * 1e-3), "unit": UNIT, "ms": e2e,
                                          "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": (1 + n * n) * 8},
-        # per pass: assembly 3 kernels (+ 4 for the two-level coarse set-up) + 6 stepper launches
-        "gpu_launches": (9 + (4 if args.twolevel != "none" else 0)) * args.steps,
+        # per pass: assembly 3 kernels, the two-level set-up 4 (+ 5 for the three-level one), and
+        # the pass: F_pri, G_pri, the two sweeps, F_adj and G_adj (overlapped: its two parts and
+        # the combination)
+        "gpu_launches": (3 + (4 if args.twolevel != "none" else 0) + (5 if args.twolevel == "threelevel" else 0)
+                         + (8 if overlap else 6)) * args.steps,
         "roofline": roof,
         "clocks": clk.summary(),
     }
@@ -499,10 +513,12 @@ def run_gpu(args):
 # differently reports traffic as null.
 NCU_TRAFFIC = {
     "captured": "2026-12-03",
-    "sources_sha16": None,
-    "bytes": {"fine_primal": 7.991040e6 + 107.795712e6, "coarse_primal": 6.969088e6 + 0.0,
-              "correct_primal": 11.175168e6 + 0.0, "fine_adjoint": 148.516608e6 + 2.119936e6,
-              "coarse_adjoint": 15.237376e6 + 0.0, "correct_adjoint": 24.019200e6 + 0.0},
+    "sources_sha16": "bf2c76ac53ffac87",
+    # the adjoint coarse propagator runs as its two Theta-free parts (two launches per pass)
+    "bytes": {"fine_primal": 8.028928e6 + 108.199936e6, "coarse_primal": 7.425536e6 + 0.0,
+              "correct_primal": 11.869696e6 + 1536.0, "fine_adjoint": 148.818688e6 + 1.789184e6,
+              "coarse_adjoint": (15.687680e6 + 0.0) + (7.088640e6 + 768.0),
+              "correct_adjoint": 24.059136e6 + 768.0},
 }
 STEPPER_SOURCES = ("stepper.cuh", "comm.cuh", "ptg_device.cuh", "stepper_inst.cu", "stepper_launch.cuh", "plan.cu")
 
@@ -701,6 +717,10 @@ def run_c3_only(args):
 # ---------------------------------------------------------------------------- full design loop
 
 def run_loop(args):
+    print(json.dumps(loop_line(args, args.loop)), flush=True)
+
+
+def loop_line(args, iterations):
     """Alg. 3 at 512 x 512, Nt = 4096 in 128 slices (M = 32): rho(0) = a_max = 0.4 uniform, the
     paper's filter and projection (r_fil = 0.03, beta = 32, eta = 0.5, no continuation), host MMA
     (move 0.2); design iteration 1 sequential, the rest one-shot.  Reports the time of every
@@ -735,7 +755,7 @@ def run_loop(args):
     chi0 = np.full(n * n, eta + np.arctanh(a_max * den - np.tanh(beta * eta)) / beta)
     with ClockSampler(0) as clk:
         t0 = time.perf_counter()
-        hist = loop.run(chi0, args.loop, true_every=0)
+        hist = loop.run(chi0, iterations, true_every=0)
         wall = time.perf_counter() - t0
     torch.cuda.synchronize()
     # the comparator on the design of the last iteration: sequential FP64 time stepping (the
@@ -759,7 +779,7 @@ def run_loop(args):
         "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
         "config": {"workload": f"loop{n}: {n}x{n} grid, Nt={Nt}, Ntau={Ntau}, p=8, SIMP k, a_max={a_max}, "
                                f"r_fil={r_fil}, beta={beta}, eta={eta}, MMA move 0.2",
-                   "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel, "smooth_steps": args.smooth, "local_steps": args.local, "initial_guess": args.initial_guess,
+                   "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel, "smooth_steps": args.smooth, "local_steps": args.local, "initial_guess": args.initial_guess, "fine_stream": args.fine_stream, "coarse_stream": args.coarse_stream,
                    "coarse_propagator": "2h mesh (Sec. 7.3 future work)" if args.coarse_mesh else "h mesh"},
         "first_iteration_sequential_ms": ms[0],
         "fine_dof_steps_per_s": 2.0 * N_free * Nt / (np.mean(oneshot) * 1e-3),
@@ -770,7 +790,9 @@ def run_loop(args):
         "speedup_last_iteration_vs_sequential_fp64": seq_ms / ms[-1],
         "wall_s": wall, "clocks": clk.summary(),
     }
-    print(json.dumps(line), flush=True)
+    del loop, op, true_op
+    torch.cuda.synchronize()
+    return line
 
 
 # ---------------------------------------------------------------------------- batching
@@ -1044,6 +1066,8 @@ def main():
     ap.add_argument("--no-c3", dest="c3", action="store_false",
                     help="leave out the 256x256 pass (Nt=2048, 64 slices) with its per-kernel roofline")
     ap.add_argument("--c3-steps", type=int, default=2, help="timed passes of the 256x256 line")
+    ap.add_argument("--no-c5", dest="c5", action="store_false",
+                    help="leave out the 512x512 design loop summary (3 design iterations)")
     ap.add_argument("--c3-workload", default="diff256", choices=["diff256", "loop512"],
                     help="--c3-only: the grid of the per-kernel line (256x256 or 512x512)")
     ap.add_argument("--c3-only", action="store_true",
