@@ -121,3 +121,87 @@ def test_autotuner_installs_valid_plans_and_keeps_results():
     for d, (prob, rho) in enumerate(ds):
         seq = o_sequential(OracleOp(prob, rho))
         assert_close(f"grad[{d}]", host(batch.buffers(d)["V_g_new"][0]), seq["grad"], FP64_TOL)
+
+
+# ---------------------------------------------------------------- designs on their own path
+
+def make_mixed_batch(precision="fp64", **kw):
+    """The same designs, the even ones (24^2, 40^2, 32^2) with streamed coarse-step solves
+    (coarse_stream = 2): the batch runs those through their ops' own launches and the rest in the
+    persistent launches."""
+    ds = designs()
+    ops = [gpu_operator(p, precision, coarse_stream=2 if d in (0, 2, 4) else 1, **kw) for d, (p, _) in enumerate(ds)]
+    return ds, ops, Batch(ops)
+
+
+def _warm(ds, batch, seed):
+    refs = []
+    for d, (prob, rho) in enumerate(ds):
+        rho_old = W.rho_warm_perturb(rho, seed=seed + d, amp=0.05)
+        U_old, V_old, _ = coarse_states_from_sequential(OracleOp(prob, rho_old))
+        refs.append((U_old, V_old))
+        b = batch.buffers(d)
+        b["U_T"].copy_(dev(U_old[0])); b["U_theta"].copy_(dev(U_old[1]))
+        b["V_lam"].copy_(dev(V_old[0])); b["V_g"].copy_(dev(V_old[1]))
+        b["rho"].copy_(dev(rho))
+    return refs
+
+
+@pytest.mark.parametrize("precision,tol_t,tol_g", [("fp64", FP64_TOL, FP64_TOL),
+                                                   ("fp32_refine", MIXED_T_TOL, MIXED_G_TOL)])
+@pytest.mark.parametrize("plt", [False, True])
+def test_batch_with_designs_on_their_own_path_matches_oracle(precision, tol_t, tol_g, plt):
+    from paper_2411_19030_gb300 import PassBuffers, oneshot_pass
+    kw = {"rtol": 1e-12} if precision == "fp64" else {"rtol": 1e-10}
+    ds, ops, batch = make_mixed_batch(precision, **kw)
+    warm = _warm(ds, batch, 300)
+    batch.assemble()
+    batch.oneshot_pass(plt=plt)
+    torch.cuda.synchronize()
+    for d, (prob, rho) in enumerate(ds):
+        U_old, V_old = warm[d]
+        ref = o_oneshot(OracleOp(prob, rho), U_old, V_old, plt=plt)
+        b = batch.buffers(d)
+        assert_close(f"T_hist[{d}]", host(b["T_hist"]), ref["T_hist"], tol_t)
+        assert_close(f"U_new[{d}]", host(b["U_T_new"]), ref["U"][0], tol_t)
+        assert_close(f"Theta[{d}]", host(b["U_theta_new"][prob.Ntau:]), [ref["Theta"]], tol_t)
+        assert_close(f"V_new[{d}]", host(b["V_lam_new"]), ref["V"][0], tol_g)
+        assert_close(f"grad[{d}]", host(b["V_g_new"][0]), ref["grad"], tol_g)
+    for op in ops:
+        assert op.stats()["status"] == 0
+    # a design on its own path equals the single-design pass of its op, bit for bit, with the
+    # sweep group the batch gives it (16 CTAs: the batch runs its large designs' sweeps side by side)
+    d = 2
+    op, b = ops[d], batch.buffers(d)
+    G = min(16, (op.ny + 1) // 2)
+    op.set_plan(2, G)
+    op.set_plan(5, G)
+    buf = PassBuffers(op)
+    U_old, V_old = warm[d]
+    buf.U_T.copy_(dev(U_old[0])); buf.U_th.copy_(dev(U_old[1]))
+    buf.V_l.copy_(dev(V_old[0])); buf.V_g.copy_(dev(V_old[1]))
+    op.assemble(b["rho"].clone())
+    oneshot_pass(op, buf, plt=plt, overlap=False)
+    torch.cuda.synchronize()
+    assert torch.equal(buf.T_hist, b["T_hist"]) and torch.equal(buf.V_g_new, b["V_g_new"])
+    op.set_plan(2, 0)
+    op.set_plan(5, 0)
+
+
+def test_graph_replay_of_a_batch_with_designs_on_their_own_path():
+    ds, ops, batch = make_mixed_batch("fp32_refine", rtol=1e-10)
+    for d, (_, rho) in enumerate(ds):
+        batch.buffers(d)["rho"].copy_(dev(rho))
+    batch.assemble()
+    batch.sequential_pass()
+    batch.assemble()
+    batch.oneshot_pass()
+    torch.cuda.synchronize()
+    direct = [host(batch.buffers(d)["V_g_new"][0]).copy() for d in range(len(ds))]
+    batch.capture()
+    for d in range(len(ds)):
+        batch.buffers(d)["V_g_new"].zero_()
+    batch.replay()
+    torch.cuda.synchronize()
+    for d in range(len(ds)):
+        assert np.array_equal(host(batch.buffers(d)["V_g_new"][0]), direct[d])
