@@ -1694,7 +1694,52 @@ int batch_own_phase(ptg_batch* b, int d, int ph, cudaStream_t st) {
   }
 }
 
+// The fine phases of the designs on their own path, beside the persistent launch: cluster
+// launches, which need no co-residency with it (a streamed or cooperative-grid plan does, so
+// such designs wait for it instead).  Returns whether the fine phase was forked off.
+bool own_fine_beside(ptg_batch* b, int ph, const std::vector<int>& own) {
+  if ((ph != 0 && ph != 3) || own.empty() || b->side.empty()) return false;
+  for (int d : own) {
+    ptg_op* op = b->ops[d];
+    Plan p;
+    if (choose_plan(op, kind_precision(op->sv.precision, phase_kind(ph)), phase_kind(ph), op->tm.Ntau, &p) != PTG_OK ||
+        p.stream || p.wide)
+      return false;
+  }
+  return true;
+}
+
 int batch_run(ptg_batch* b, int ph, cudaStream_t stream) {
+  std::vector<int> own;
+  for (int d : b->order)
+    if (!in_launch(b, d, ph)) own.push_back(d);
+  if (own_fine_beside(b, ph, own)) {
+    PTG_CUDA(cudaEventRecord(b->fork, stream));
+    const int ns = std::min((int)own.size(), (int)b->side.size());
+    for (int k = 0; k < ns; ++k) PTG_CUDA(cudaStreamWaitEvent(b->side[k], b->fork, 0));
+    for (size_t i = 0; i < own.size(); ++i) {
+      int rc = batch_own_phase(b, own[i], ph, b->side[i % ns]);
+      if (rc != PTG_OK) return rc;
+    }
+    {
+      std::lock_guard<std::mutex> lk(b->mu);
+      if (!phase_tasks(b, ph).empty()) {
+        if (!b->ph[ph].ready) {
+          int rc = batch_default(b, ph);
+          if (rc != PTG_OK) return rc;
+        }
+        const PhasePlan& pp = b->ph[ph];
+        PTG_CUDA(launch_stepper_batch(kind_precision(b->precision, phase_kind(ph)), phase_kind(ph), pp.plan,
+                                      pp.table, pp.tasks, pp.ntasks, b->queue + ph, pp.nclusters, stream));
+      }
+    }
+    for (int k = 0; k < ns; ++k) {
+      PTG_CUDA(cudaEventRecord(b->join[k], b->side[k]));
+      PTG_CUDA(cudaStreamWaitEvent(stream, b->join[k], 0));
+    }
+    for (ptg_op* op : b->ops) op->last_stream = stream;
+    return PTG_OK;
+  }
   {
     std::lock_guard<std::mutex> lk(b->mu);
     if (!phase_tasks(b, ph).empty()) {
@@ -1708,9 +1753,6 @@ int batch_run(ptg_batch* b, int ph, cudaStream_t stream) {
                                     pp.tasks, pp.ntasks, b->queue + ph, pp.nclusters, stream));
     }
   }
-  std::vector<int> own;
-  for (int d : b->order)
-    if (!in_launch(b, d, ph)) own.push_back(d);
   const bool sweep = ph == 2 || ph == 5;
   if (!sweep || own.size() < 2 || b->side.empty()) {
     for (int d : own) {
@@ -1782,7 +1824,8 @@ int ptg_batch_create(ptg_op* const* ops, int nops, ptg_batch** out) {
     b->own.push_back(op->mg_L > 0 ? 1 : 0);
     nown += op->mg_L > 0 ? 1 : 0;
   }
-  // an op that holds two designs would run two sweeps on its one sweep workspace: no side streams
+  // an op that holds two designs would run two of its launches at once on its one workspace:
+  // no side streams
   for (int x = 0; x < nops; ++x)
     for (int y = x + 1; y < nops; ++y)
       if (b->own[x] && ops[x] == ops[y]) nown = 0;
@@ -1807,7 +1850,7 @@ int ptg_batch_create(ptg_op* const* ops, int nops, ptg_batch** out) {
     b->bufs.push_back(B);
   }
   if (e == cudaSuccess) e = cudaMalloc(&b->queue, kPhases * sizeof(int));
-  if (nown >= 2) {
+  if (nown >= 1) {
     // as many side streams as sweeps fit the chip at once
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
