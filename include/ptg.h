@@ -448,6 +448,11 @@ int ptg_sensitivities_noalloc(int nx, int ny, double h, int Nt, double dt, const
  * adjoint, 5 adjoint correction (the one-shot pass, the iteration body of Alg. 3); 6 sequential primal,
  * 7 sequential adjoint (the initialisation of Alg. 3, writing the warm start U/V); 8 and 9 the
  * primal and adjoint corrections of the PLT variant (G = 0, Sec. 7).
+ * A design whose op streams its coarse-step solves (ptg_solve.coarse_stream) takes no part in
+ * the persistent launches of phases 0-5, 8 and 9: each of those phases runs it through its op's
+ * own entry points on the batch's buffers, as a single-design pass does.  Their fine phases run
+ * beside the persistent launch and their correction sweeps side by side (groups of 16 CTAs), on
+ * streams forked from and joined to `stream`.  ptg_batch_design_path reports which designs.
  * Every call is asynchronous on `stream`; after a first call of each phase (which uploads the
  * plan) the launch sequence can be captured into a CUDA graph.
  */
@@ -480,10 +485,14 @@ int ptg_batch_oneshot_pass(ptg_batch* b, int variant, cudaStream_t stream);
 int ptg_batch_commit(ptg_batch* b, cudaStream_t stream);
 /* One phase alone (its inputs must be current), e.g. to time it. */
 int ptg_batch_run_phase(ptg_batch* b, int phase, cudaStream_t stream);
-/* Plan of a phase: cluster size (2..16), groups per thread (1..6), threads per CTA (32..512,
- * multiple of 32); PTG_EINVAL if it does not fit every design or the device. */
+/* Plan of a phase's persistent launch: cluster size (2..16), groups per thread (1..6), threads per
+ * CTA (32..512, multiple of 32); PTG_EINVAL if it does not fit every design of the launch or the
+ * device. */
 int ptg_batch_set_plan(ptg_batch* b, int phase, int cs, int ng, int nthreads);
 int ptg_batch_get_plan(ptg_batch* b, int phase, int* cs, int* ng, int* nthreads, int* nclusters);
+/* *own = 1 if design d runs the pass phases through its op's own launches, 0 if in the
+ * persistent launches. */
+int ptg_batch_design_path(ptg_batch* b, int design, int* own);
 
 /*
  * Design parametrisation (Sec. 2.1) and area constraint (Sec. 3), on the device, FP64.

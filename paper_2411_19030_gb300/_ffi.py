@@ -90,6 +90,7 @@ SIGNATURES = {
     "ptg_batch_run_phase": (c_int, [_P, c_int, _P]),
     "ptg_batch_set_plan": (c_int, [_P, c_int, c_int, c_int, c_int]),
     "ptg_batch_get_plan": (c_int, [_P, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+    "ptg_batch_design_path": (c_int, [_P, c_int, POINTER(c_int)]),
     "ptg_design_create": (c_int, [c_int, c_int, c_double, c_double, c_double, c_double, c_int, POINTER(c_void_p)]),
     "ptg_design_destroy": (None, [_P]),
     "ptg_design_forward": (c_int, [_P, _P, _P, _P, _P]),

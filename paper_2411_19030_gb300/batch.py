@@ -101,6 +101,13 @@ class Batch:
     def set_plan(self, phase: int, cs: int, ng: int, nthreads: int):
         _check(_lib().ptg_batch_set_plan(self._h, phase, cs, ng, nthreads), "ptg_batch_set_plan")
 
+    def own_path(self, d: int) -> bool:
+        """Whether design d runs the pass phases through its op's own launches (streamed
+        coarse-step solves) rather than in the persistent launches."""
+        own = ctypes.c_int()
+        _check(_lib().ptg_batch_design_path(self._h, d, ctypes.byref(own)), "ptg_batch_design_path")
+        return bool(own.value)
+
     def plan(self, phase: int) -> dict:
         cs, ng, nt, ncl = (ctypes.c_int() for _ in range(4))
         _check(_lib().ptg_batch_get_plan(self._h, phase, ctypes.byref(cs), ctypes.byref(ng), ctypes.byref(nt),
@@ -135,13 +142,15 @@ class Batch:
 
 def candidate_plans(batch: Batch):
     """Valid (cluster size, groups per thread, threads per CTA) candidates: for every cluster
-    size and NG the smallest block that holds the largest design's slab, and twice that."""
+    size and NG the smallest block that holds the slab of the largest design of the persistent
+    launches, and twice that."""
     out = []
+    ops = [op for d, op in enumerate(batch.ops) if not batch.own_path(d)] or batch.ops
     for cs in (16, 8, 4, 2):
-        rows = [(op.ny + 1 + cs - 1) // cs for op in batch.ops]
+        rows = [(op.ny + 1 + cs - 1) // cs for op in ops]
         if min(rows) < 2:
             continue
-        groups = max(r * (((op.nx + 3 + 3) // 4 * 4) // 4) for r, op in zip(rows, batch.ops))
+        groups = max(r * (((op.nx + 3 + 3) // 4 * 4) // 4) for r, op in zip(rows, ops))
         for ng in range(1, 7):
             nt = -(-groups // ng)
             nt = -(-nt // 32) * 32

@@ -1438,7 +1438,7 @@ struct ptg_batch {
   // their correction sweeps run side by side, each on a group of kBatchSweepCtas CTAs, on
   // streams forked from and joined to the caller's stream
   std::vector<cudaStream_t> side;
-  cudaEvent_t fork = nullptr;
+  cudaEvent_t fork = nullptr, fork2 = nullptr;
   std::vector<cudaEvent_t> join;
   std::vector<BatchBuf> bufs;
   std::vector<void*> allocs;
@@ -1461,7 +1461,8 @@ void batch_free(ptg_batch* b) {
     if (e) cudaEventDestroy(e);
   b->join.clear();
   if (b->fork) cudaEventDestroy(b->fork);
-  b->fork = nullptr;
+  if (b->fork2) cudaEventDestroy(b->fork2);
+  b->fork = b->fork2 = nullptr;
   for (auto& p : b->ph) {
     if (p.table) cudaFree(p.table);
     if (p.tasks) cudaFree(p.tasks);
@@ -1663,6 +1664,10 @@ int batch_default(ptg_batch* b, int ph) {
 // chip side by side (measured at 256 x 256: 71 ms for 64 steps on 16 CTAs, against 45 ms alone
 // on 128 CTAs, one after the other).
 constexpr int kBatchSweepCtas = 16;
+// Designs of this many nodes or more take their own path in a batch even with on-chip solves:
+// the persistent launch's geometry is sized by its largest design, and their own cluster
+// launches run beside it.
+constexpr int kBatchOwnMinNodes = 30000;
 
 // Phase ph of design d through its op's own launches (the per-op entry points on the batch's
 // buffers), as a single-design pass runs it.
@@ -1694,51 +1699,39 @@ int batch_own_phase(ptg_batch* b, int d, int ph, cudaStream_t st) {
   }
 }
 
-// The fine phases of the designs on their own path, beside the persistent launch: cluster
-// launches, which need no co-residency with it (a streamed or cooperative-grid plan does, so
-// such designs wait for it instead).  Returns whether the fine phase was forked off.
-bool own_fine_beside(ptg_batch* b, int ph, const std::vector<int>& own) {
-  if ((ph != 0 && ph != 3) || own.empty() || b->side.empty()) return false;
-  for (int d : own) {
-    ptg_op* op = b->ops[d];
-    Plan p;
-    if (choose_plan(op, kind_precision(op->sv.precision, phase_kind(ph)), phase_kind(ph), op->tm.Ntau, &p) != PTG_OK ||
-        p.stream || p.wide)
-      return false;
-  }
-  return true;
+// A design's own launches of phase ph are cluster launches (no cooperative grid): they can run
+// beside the persistent launch, which they need not be co-resident with.
+bool own_beside(ptg_batch* b, int d, int ph) {
+  if (ph == 8 || ph == 9) return true;   // the PLT corrections: copies
+  ptg_op* op = b->ops[d];
+  const int kind = phase_kind(ph);
+  const int ntasks = (kind == KIND_CORRECT_PRI || kind == KIND_CORRECT_ADJ) ? 1 : op->tm.Ntau;
+  Plan p;
+  return choose_plan(op, kind_precision(op->sv.precision, kind), kind, ntasks, &p) == PTG_OK && !p.stream && !p.wide;
 }
 
+// Phase ph: the persistent launch of the designs in it on `stream`; the designs on their own path
+// (a) with cluster launches beside it on the side streams, forked before it, and (b) with
+// streamed launches after it: correction sweeps side by side on the side streams (each on a
+// group of kBatchSweepCtas CTAs, a plan override of its op for that launch only), the rest one
+// after the other on `stream`.  Every side stream used joins `stream` at the end.
 int batch_run(ptg_batch* b, int ph, cudaStream_t stream) {
-  std::vector<int> own;
-  for (int d : b->order)
-    if (!in_launch(b, d, ph)) own.push_back(d);
-  if (own_fine_beside(b, ph, own)) {
+  std::vector<int> beside, after;
+  for (int d : b->order) {
+    if (in_launch(b, d, ph)) continue;
+    (!b->side.empty() && own_beside(b, d, ph) ? beside : after).push_back(d);
+  }
+  const int nside = (int)b->side.size();
+  std::vector<char> used(nside, 0);
+  if (!beside.empty()) {
     PTG_CUDA(cudaEventRecord(b->fork, stream));
-    const int ns = std::min((int)own.size(), (int)b->side.size());
-    for (int k = 0; k < ns; ++k) PTG_CUDA(cudaStreamWaitEvent(b->side[k], b->fork, 0));
-    for (size_t i = 0; i < own.size(); ++i) {
-      int rc = batch_own_phase(b, own[i], ph, b->side[i % ns]);
+    for (size_t i = 0; i < beside.size(); ++i) {
+      const int k = (int)(i % nside);
+      if (!used[k]) PTG_CUDA(cudaStreamWaitEvent(b->side[k], b->fork, 0));
+      used[k] = 1;
+      int rc = batch_own_phase(b, beside[i], ph, b->side[k]);
       if (rc != PTG_OK) return rc;
     }
-    {
-      std::lock_guard<std::mutex> lk(b->mu);
-      if (!phase_tasks(b, ph).empty()) {
-        if (!b->ph[ph].ready) {
-          int rc = batch_default(b, ph);
-          if (rc != PTG_OK) return rc;
-        }
-        const PhasePlan& pp = b->ph[ph];
-        PTG_CUDA(launch_stepper_batch(kind_precision(b->precision, phase_kind(ph)), phase_kind(ph), pp.plan,
-                                      pp.table, pp.tasks, pp.ntasks, b->queue + ph, pp.nclusters, stream));
-      }
-    }
-    for (int k = 0; k < ns; ++k) {
-      PTG_CUDA(cudaEventRecord(b->join[k], b->side[k]));
-      PTG_CUDA(cudaStreamWaitEvent(stream, b->join[k], 0));
-    }
-    for (ptg_op* op : b->ops) op->last_stream = stream;
-    return PTG_OK;
   }
   {
     std::lock_guard<std::mutex> lk(b->mu);
@@ -1748,56 +1741,58 @@ int batch_run(ptg_batch* b, int ph, cudaStream_t stream) {
         if (rc != PTG_OK) return rc;
       }
       const PhasePlan& pp = b->ph[ph];
-      for (ptg_op* op : b->ops) op->last_stream = stream;
       PTG_CUDA(launch_stepper_batch(kind_precision(b->precision, phase_kind(ph)), phase_kind(ph), pp.plan, pp.table,
                                     pp.tasks, pp.ntasks, b->queue + ph, pp.nclusters, stream));
     }
   }
   const bool sweep = ph == 2 || ph == 5;
-  if (!sweep || own.size() < 2 || b->side.empty()) {
-    for (int d : own) {
+  if (sweep && after.size() >= 2 && nside > 0) {
+    PTG_CUDA(cudaEventRecord(b->fork2, stream));
+    const int kind = phase_kind(ph);
+    for (size_t i = 0; i < after.size(); ++i) {
+      const int k = (int)(i % nside);
+      PTG_CUDA(cudaStreamWaitEvent(b->side[k], b->fork2, 0));
+      used[k] = 1;
+      ptg_op* op = b->ops[after[i]];
+      Plan saved;
+      bool had = false;
+      {
+        std::lock_guard<std::mutex> lk(op->mu);
+        auto it = op->plan_override.find(kind);
+        had = it != op->plan_override.end();
+        if (had) saved = it->second;
+        Plan sp;
+        sp.cs = std::max(1, std::min(kBatchSweepCtas, (op->g.ny + 1) / 2));
+        sp.nthreads = 512;
+        sp.ng = 1;
+        sp.rmax = (op->g.ny + 1 + sp.cs - 1) / sp.cs;
+        sp.max_active_clusters = 1;
+        sp.stream = true;
+        op->plan_override[kind] = sp;
+      }
+      const int rc = batch_own_phase(b, after[i], ph, b->side[k]);
+      {
+        std::lock_guard<std::mutex> lk(op->mu);
+        if (had)
+          op->plan_override[kind] = saved;
+        else
+          op->plan_override.erase(kind);
+      }
+      if (rc != PTG_OK) return rc;
+    }
+  } else {
+    for (int d : after) {
       int rc = batch_own_phase(b, d, ph, stream);
       if (rc != PTG_OK) return rc;
     }
-    return PTG_OK;
   }
-  // the sweeps side by side: design i on side stream i mod (streams), each with a group of
-  // kBatchSweepCtas CTAs (a plan override of its op for this launch only)
-  PTG_CUDA(cudaEventRecord(b->fork, stream));
-  const int ns = std::min((int)own.size(), (int)b->side.size());
-  for (int k = 0; k < ns; ++k) PTG_CUDA(cudaStreamWaitEvent(b->side[k], b->fork, 0));
-  const int kind = phase_kind(ph);
-  int rc = PTG_OK;
-  for (size_t i = 0; i < own.size() && rc == PTG_OK; ++i) {
-    ptg_op* op = b->ops[own[i]];
-    Plan saved;
-    bool had = false;
-    {
-      std::lock_guard<std::mutex> lk(op->mu);
-      auto it = op->plan_override.find(kind);
-      had = it != op->plan_override.end();
-      if (had) saved = it->second;
-      Plan sp;
-      sp.cs = std::max(1, std::min(kBatchSweepCtas, (op->g.ny + 1) / 2));
-      sp.nthreads = 512;
-      sp.ng = 1;
-      sp.rmax = (op->g.ny + 1 + sp.cs - 1) / sp.cs;
-      sp.max_active_clusters = 1;
-      sp.stream = true;
-      op->plan_override[kind] = sp;
-    }
-    rc = batch_own_phase(b, own[i], ph, b->side[i % ns]);
-    std::lock_guard<std::mutex> lk(op->mu);
-    if (had)
-      op->plan_override[kind] = saved;
-    else
-      op->plan_override.erase(kind);
-  }
-  for (int k = 0; k < ns; ++k) {
+  for (int k = 0; k < nside; ++k) {
+    if (!used[k]) continue;
     PTG_CUDA(cudaEventRecord(b->join[k], b->side[k]));
     PTG_CUDA(cudaStreamWaitEvent(stream, b->join[k], 0));
   }
-  return rc;
+  for (ptg_op* op : b->ops) op->last_stream = stream;
+  return PTG_OK;
 }
 
 }  // namespace
@@ -1821,8 +1816,9 @@ int ptg_batch_create(ptg_op* const* ops, int nops, ptg_batch** out) {
   b->ops.assign(ops, ops + nops);
   int nown = 0;
   for (ptg_op* op : b->ops) {
-    b->own.push_back(op->mg_L > 0 ? 1 : 0);
-    nown += op->mg_L > 0 ? 1 : 0;
+    const bool own = op->mg_L > 0 || op->Nn >= kBatchOwnMinNodes;
+    b->own.push_back(own ? 1 : 0);
+    nown += own ? 1 : 0;
   }
   // an op that holds two designs would run two of its launches at once on its one workspace:
   // no side streams
@@ -1856,6 +1852,7 @@ int ptg_batch_create(ptg_op* const* ops, int nops, ptg_batch** out) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
     const int nside = std::max(1, std::min(nown, nsm / kBatchSweepCtas));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork2, cudaEventDisableTiming);
     for (int k = 0; k < nside && e == cudaSuccess; ++k) {
       cudaStream_t st = nullptr;
       cudaEvent_t ev = nullptr;
@@ -1966,6 +1963,12 @@ int ptg_batch_set_plan(ptg_batch* b, int phase, int cs, int ng, int nthreads) {
       if (batch_install(b, phase, cs, ng, nthreads, mode, keep_ax) == PTG_OK) return PTG_OK;
   if (batch_install(b, phase, cs, ng, nthreads, TL_NONE) == PTG_OK) return PTG_OK;
   return batch_install(b, phase, cs, ng, nthreads, TL_NONE, false);
+}
+
+int ptg_batch_design_path(ptg_batch* b, int design, int* own) {
+  if (!b || !own || design < 0 || design >= (int)b->ops.size()) return PTG_EINVAL;
+  *own = b->own[design] ? 1 : 0;
+  return PTG_OK;
 }
 
 int ptg_batch_get_plan(ptg_batch* b, int phase, int* cs, int* ng, int* nthreads, int* nclusters) {

@@ -190,6 +190,7 @@ def test_batch_with_designs_on_their_own_path_matches_oracle(precision, tol_t, t
 
 def test_graph_replay_of_a_batch_with_designs_on_their_own_path():
     ds, ops, batch = make_mixed_batch("fp32_refine", rtol=1e-10)
+    assert [batch.own_path(d) for d in range(len(ds))] == [True, False, True, False, True]
     for d, (_, rho) in enumerate(ds):
         batch.buffers(d)["rho"].copy_(dev(rho))
     batch.assemble()
