@@ -448,11 +448,13 @@ int ptg_sensitivities_noalloc(int nx, int ny, double h, int Nt, double dt, const
  * adjoint, 5 adjoint correction (the one-shot pass, the iteration body of Alg. 3); 6 sequential primal,
  * 7 sequential adjoint (the initialisation of Alg. 3, writing the warm start U/V); 8 and 9 the
  * primal and adjoint corrections of the PLT variant (G = 0, Sec. 7).
- * A design whose op streams its coarse-step solves (ptg_solve.coarse_stream) takes no part in
- * the persistent launches of phases 0-5, 8 and 9: each of those phases runs it through its op's
- * own entry points on the batch's buffers, as a single-design pass does.  Their fine phases run
- * beside the persistent launch and their correction sweeps side by side (groups of 16 CTAs), on
- * streams forked from and joined to `stream`.  ptg_batch_design_path reports which designs.
+ * A large design takes no part in the persistent launches of phases 0-5, 8 and 9: one whose op
+ * streams its coarse-step solves (ptg_solve.coarse_stream), or one of 15000 nodes or more.
+ * Each of those phases runs it through its op's own entry points on the batch's buffers, as a
+ * single-design pass does.  Its cluster launches run beside the persistent launch; its
+ * streamed launches follow it, the correction sweeps of several designs side by side (groups
+ * of 16 CTAs).  The side launches run on streams forked from and joined to `stream`.
+ * ptg_batch_design_path reports which designs take that path.
  * Every call is asynchronous on `stream`; after a first call of each phase (which uploads the
  * plan) the launch sequence can be captured into a CUDA graph.
  */

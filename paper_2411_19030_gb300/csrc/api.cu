@@ -1666,8 +1666,10 @@ int batch_default(ptg_batch* b, int ph) {
 constexpr int kBatchSweepCtas = 16;
 // Designs of this many nodes or more take their own path in a batch even with on-chip solves:
 // the persistent launch's geometry is sized by its largest design, and their own cluster
-// launches run beside it.
-constexpr int kBatchOwnMinNodes = 30000;
+// launches run beside it.  Measured on the 48-design workload: 1.98 s per batched pass with
+// 15000 (128 x 128 and larger on their own path), 2.12 s with 30000, 2.60 s with only the
+// streamed designs on it.
+constexpr int kBatchOwnMinNodes = 15000;
 
 // Phase ph of design d through its op's own launches (the per-op entry points on the batch's
 // buffers), as a single-design pass runs it.
