@@ -437,6 +437,12 @@ def run_gpu(args):
 
     roof = roofline(kind_ms, stats, N_free, args.steps, args.precision)
     streaming = streaming_256(args, flush, stream, device) if (args.extras and args.c3) else None
+    batch48 = None
+    if args.extras and args.c4 and world == 1:
+        bl = batch48_line(args, steps=3, autotune_plans=False)
+        batch48 = {k: bl[k] for k in ("ms_per_batched_pass", "design_by_design_ms", "batching_speedup", "value",
+                                      "unit", "steps", "designs_on_own_path", "status")}
+        batch48["workload"] = bl["config"]["workload"]
     loop512 = None
     if args.extras and args.c5 and world == 1:
         ll = loop_line(args, 3)
@@ -487,6 +493,7 @@ def run_gpu(args):
         "precision_variant": variant,
         "fp64_oneshot": fp64_arm,
         "streaming_256": streaming,
+        "batch48": batch48,
         "loop512": loop512,
         "e2e": None if e2e is None else {"value": world * dof_steps / (e2e * 1e-3), "unit": UNIT, "ms": e2e,
                                          "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": (1 + n * n) * 8},
@@ -798,6 +805,10 @@ def loop_line(args, iterations):
 # ---------------------------------------------------------------------------- batching
 
 def run_batch48(args):
+    print(json.dumps(batch48_line(args)), flush=True)
+
+
+def batch48_line(args, steps=None, autotune_plans=None):
     """The batching workload: 48 designs of uneven size (64^2 .. 256^2, Nt 512 .. 2048, 16 .. 64
     slices), warm-started from the sequential coarse states of designs 1% away, advanced
     together: each phase of the one-shot pass is one persistent launch over every design and
@@ -831,12 +842,12 @@ def run_batch48(args):
     for i, d in enumerate(designs):
         batch.buffers(i)["rho"].copy_(dv(d["rho"]))
     batch.assemble()
-    tuned = autotune(batch) if args.autotune else None
+    tuned = autotune(batch) if (args.autotune if autotune_plans is None else autotune_plans) else None
     batch.oneshot_pass()
     batch.capture()
     flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device=device)
     stream = torch.cuda.current_stream(device)
-    steps = max(1, min(args.steps, 5))
+    steps = max(1, min(args.steps if steps is None else steps, 5))
     for _ in range(max(1, args.warmup)):
         batch.replay()
     torch.cuda.synchronize()
@@ -870,16 +881,22 @@ def run_batch48(args):
             b.synchronize()
         single += a.elapsed_time(b)
         del buf
-    print(json.dumps({"metric": "fine DOF*steps/s of the batched one-shot pass (48 designs of uneven size)",
-                      "value": dof / (ms * 1e-3), "unit": UNIT, "ms_per_batched_pass": ms, "steps": steps,
-                      "design_by_design_ms": single, "batching_speedup": single / ms, "status": int(status),
-                      "autotuned": tuned is not None, "dtype": "f32+f64" if args.precision != "fp64" else "f64",
-                      "config": {"workload": "batch48: 48 designs, sides 64/96/128/192/256, (Nt, Ntau) in "
-                                             "(512,16)/(1024,32)/(2048,64), rho ~ U(0.2,0.8)",
-                                 "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel,
-                                 "initial_guess": args.initial_guess,
-                                 "l2": "flushed between steps (256 MB write)"},
-                      "clocks": clk.summary()}), flush=True)
+    own = sum(batch.own_path(d) for d in range(len(ops)))
+    line = {"metric": "fine DOF*steps/s of the batched one-shot pass (48 designs of uneven size)",
+            "value": dof / (ms * 1e-3), "unit": UNIT, "ms_per_batched_pass": ms, "steps": steps,
+            "design_by_design_ms": single, "batching_speedup": single / ms, "status": int(status),
+            "designs_on_own_path": own,
+            "autotuned": tuned is not None, "dtype": "f32+f64" if args.precision != "fp64" else "f64",
+            "config": {"workload": "batch48: 48 designs, sides 64/96/128/192/256, (Nt, Ntau) in "
+                                   "(512,16)/(1024,32)/(2048,64), rho ~ U(0.2,0.8)",
+                       "precision": args.precision, "rtol": args.rtol, "twolevel": args.twolevel,
+                       "initial_guess": args.initial_guess,
+                       "l2": "flushed between steps (256 MB write)"},
+            "clocks": clk.summary()}
+    batch.close()
+    del batch, ops
+    torch.cuda.synchronize()
+    return line
 
 
 # ---------------------------------------------------------------------------- Parareal sweep
@@ -1066,6 +1083,8 @@ def main():
     ap.add_argument("--no-c3", dest="c3", action="store_false",
                     help="leave out the 256x256 pass (Nt=2048, 64 slices) with its per-kernel roofline")
     ap.add_argument("--c3-steps", type=int, default=2, help="timed passes of the 256x256 line")
+    ap.add_argument("--no-c4", dest="c4", action="store_false",
+                    help="leave out the 48-design batching summary")
     ap.add_argument("--no-c5", dest="c5", action="store_false",
                     help="leave out the 512x512 design loop summary (3 design iterations)")
     ap.add_argument("--c3-workload", default="diff256", choices=["diff256", "loop512"],
