@@ -167,9 +167,12 @@ typedef struct {
                           batched coarse step from the guess state at the other end of its slice
                           (u_{s+1} for G_pri, lambda_{Ms+1} for G_adj), which the previous
                           one-shot iteration left close to the answer, and a correction-sweep
-                          step (ptg_parareal_correct) from G_old[s] plus the previous step's
-                          increment G(x^new) - G(x^old), i.e. u_s - F[s-1] (primal) or
-                          v_{s+1} - F[s+1] (adjoint), instead of G_old[s] alone;
+                          step (ptg_parareal_correct) from G_old[s] plus the polynomial
+                          extrapolation, through the increments G(x^new) - G(x^old) of the last
+                          n - 1 steps of the sweep (fewer at its start), of the next one; the
+                          increment of a step is the corrected state it produced minus the fine
+                          result of its slice, e.g. u_s - F[s-1] (primal) or v_{s+1} - F[s+1]
+                          (adjoint);
                           0 the library's default (4).  Other values: PTG_EINVAL. */
     int fine_stream;   /* fine propagators of the parallel schedule (a2, a5): 2 with the Krylov vectors
                           in global memory, one group of CTAs per slice and every slice at once

@@ -368,11 +368,16 @@ struct Stepper {
     __syncthreads();
   }
 
-  // Correction sweeps: x64 = G + (x64 - Fm) on the owned and both halo rows, with x64 holding
-  // the corrected state the step propagates and Fm the fine result of the step before it.
-  // Every CTA evaluates the same expression on the same operands (x64's halos are exact), so
-  // the halos stay exact.  Ends with __syncthreads.
-  __device__ void load_x64_increment(const double* __restrict__ G, const double* __restrict__ Fm) {
+  // Correction sweeps: the start of a step is G_old plus the polynomial extrapolation of the
+  // sweep's increments G(x^new) - G(x^old) through the last m of them (1 <= m <= 3):
+  //   x64 = G + inc,  inc = d0 (m = 1), 2 d0 - d1 (m = 2), 3 (d0 - d1) + d2 (m = 3),
+  // with d_i = X_i - Fm[i] the increment of the i-th step before, which by the correction itself
+  // is the corrected state X_i that step produced minus the fine result Fm[i] of its slice; X_0
+  // is x64 (the state the step propagates), X_1, X_2 node vectors of earlier corrected states.
+  // On the owned and both halo rows: every CTA evaluates the same expression on the same
+  // operands (x64's halos are exact), so the halos stay exact.  Ends with __syncthreads.
+  __device__ void load_x64_increment(const double* __restrict__ G, int m, const double* const* Fm,
+                                     const double* const* X) {
     ax_valid = false;
     __syncthreads();
     const int nn = P.nx + 1;
@@ -383,7 +388,11 @@ struct Stepper {
       if (g >= 0 && g <= P.ny) {
         const int gi = g * nn + ix;
         double& x = x64[row * sb.W + ix + 1];
-        x = P.dirichlet[gi] ? 0.0 : G[gi] + (x - Fm[gi]);
+        const double d0 = x - Fm[0][gi];
+        double inc = d0;
+        if (m == 2) inc = fma(2.0, d0, -(X[1][gi] - Fm[1][gi]));
+        if (m == 3) inc = fma(3.0, d0 - (X[1][gi] - Fm[1][gi]), X[2][gi] - Fm[2][gi]);
+        x = P.dirichlet[gi] ? 0.0 : G[gi] + inc;
       }
     }
     __syncthreads();
@@ -1456,12 +1465,19 @@ struct Stepper {
         const double qj = P.q_time[j];
         build_rhs([&](int g) { return qj * P.fload[g]; });
       }
-      // initial guess G(u_s^old) + (G(u_{s-1}^new) - G(u_{s-1}^old)): the previous step's
-      // increment, which is u_s^new - F[s-1] by the correction itself (plain: G(u_s^old))
-      if (P.extrap > 1 && s > 0)
-        load_x64_increment(P.G_field + (size_t)s * P.Nn, P.F_field + (size_t)(s - 1) * P.Nn);
-      else
+      // initial guess G(u_s^old) plus the extrapolation of the increments G(u^new) - G(u^old) of
+      // the last min(extrap - 1, s) steps, the increment of step s-1-i being u_{s-i}^new - F[s-1-i]
+      // by the correction itself (plain: G(u_s^old))
+      const int m = min(P.extrap - 1, min(s, 3));
+      if (m >= 1) {
+        const double* Fm[3];
+        const double* X[3] = {nullptr, nullptr, nullptr};
+        for (int i = 0; i < m; ++i) Fm[i] = P.F_field + (size_t)(s - 1 - i) * P.Nn;
+        for (int i = 1; i < m; ++i) X[i] = P.out_field + (size_t)(s - i) * P.Nn;
+        load_x64_increment(P.G_field + (size_t)s * P.Nn, m, Fm, X);
+      } else {
         load_x64(P.G_field + (size_t)s * P.Nn);
+      }
       solve(j);
       const double sp = pnorm_p();
       apply_correction(P.F_field + (size_t)s * P.Nn, P.G_field + (size_t)s * P.Nn,
@@ -1581,12 +1597,19 @@ struct Stepper {
       const double* Tk = P.hist + (size_t)kidx * P.Nn;
       const double* Tkm = P.hist + (size_t)kprev * P.Nn;
       build_rhs([&](int g) { return scale * ipow(Tk[g], P.p_int - 1); });
-      // initial guess G(v_{s+1}^old) + (G(v_{s+2}^new) - G(v_{s+2}^old)) = G[s] + v_{s+1}^new - F[s+1]
-      // (plain: G(v_{s+1}^old))
-      if (P.extrap > 1 && s + 1 < P.Ntau)
-        load_x64_increment(P.G_field + (size_t)s * P.Nn, P.F_field + (size_t)(s + 1) * P.Nn);
-      else
+      // initial guess G(v_{s+1}^old) plus the extrapolation of the increments of the last
+      // min(extrap - 1, Ntau - 1 - s) steps, the increment of step s+1+i being
+      // v_{s+1+i}^new - F[s+1+i] (plain: G(v_{s+1}^old))
+      const int m = min(P.extrap - 1, min(P.Ntau - 1 - s, 3));
+      if (m >= 1) {
+        const double* Fm[3];
+        const double* X[3] = {nullptr, nullptr, nullptr};
+        for (int i = 0; i < m; ++i) Fm[i] = P.F_field + (size_t)(s + 1 + i) * P.Nn;
+        for (int i = 1; i < m; ++i) X[i] = P.out_field + (size_t)(s + 1 + i) * P.Nn;
+        load_x64_increment(P.G_field + (size_t)s * P.Nn, m, Fm, X);
+      } else {
         load_x64(P.G_field + (size_t)s * P.Nn);
+      }
       solve(kidx);
       // g_s = g_{s+1} - (1/Ntau) term(lambda_G) + F_g[s] - G_g[s]
       accumulate_g(Tk, Tkm, P.dtau, (double)P.Ntau, P.out_aux + (size_t)(s + 1) * P.Ne, P.out_aux + (size_t)s * P.Ne,

@@ -836,17 +836,28 @@ struct Streamer {
       st4d(b, loc, bv);
     });
   }
-  // x = Gs + (xc - Fm) on the own rows (node vectors Gs, Fm; xc padded): the start G(u^old) plus
-  // the increment of the previous correction step; 0 off the unknowns
-  __device__ void load_increment(const double* __restrict__ Gs, const double* __restrict__ Fm,
-                                 const double* __restrict__ xc, double* __restrict__ x) const {
+  // x = Gs + inc on the own rows, 0 off the unknowns: the start G(u^old) plus the polynomial
+  // extrapolation of the last m (1..3) increments of the correction sweep (as the stepper's
+  // load_x64_increment): d_i = X_i - Fm[i], X_0 = xc (padded, the state the step propagates),
+  // X_1, X_2 node vectors of earlier corrected states; inc = d0, 2 d0 - d1 or 3 (d0 - d1) + d2
+  __device__ void load_increment(const double* __restrict__ Gs, int m, const double* const* Fm,
+                                 const double* const* X, const double* __restrict__ xc,
+                                 double* __restrict__ x) const {
     for_groups([&](int loc, int iy, int g) {
       double v[4], c[4];
       load4(xc + loc, c);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int gi = gnode(iy, g, j);
-        v[j] = (gi >= 0 && !P.dirichlet[gi]) ? Gs[gi] + (c[j] - Fm[gi]) : 0.0;
+        if (gi < 0 || P.dirichlet[gi]) {
+          v[j] = 0.0;
+          continue;
+        }
+        const double d0 = c[j] - Fm[0][gi];
+        double inc = d0;
+        if (m == 2) inc = fma(2.0, d0, -(X[1][gi] - Fm[1][gi]));
+        if (m == 3) inc = fma(3.0, d0 - (X[1][gi] - Fm[1][gi]), X[2][gi] - Fm[2][gi]);
+        v[j] = Gs[gi] + inc;
       }
       st4d(x, loc, v);
     });
@@ -1038,11 +1049,17 @@ struct Streamer {
         const double qj = P.q_time[j];
         build_rhs(xa, [&](int g) { return qj * P.fload[g]; });
       }
-      // start G(u_s^old) + (G(u_{s-1}^new) - G(u_{s-1}^old)) = G[s] + u_s^new - F[s-1]
-      if (P.extrap > 1 && s > 0)
-        load_increment(P.G_field + (size_t)s * P.Nn, P.F_field + (size_t)(s - 1) * P.Nn, xa, xb);
-      else
+      // start G(u_s^old) plus the extrapolated increments of the last min(extrap - 1, s) steps
+      const int m = min(P.extrap - 1, min(s, 3));
+      if (m >= 1) {
+        const double* Fm[3];
+        const double* X[3] = {nullptr, nullptr, nullptr};
+        for (int i = 0; i < m; ++i) Fm[i] = P.F_field + (size_t)(s - 1 - i) * P.Nn;
+        for (int i = 1; i < m; ++i) X[i] = P.out_field + (size_t)(s - i) * P.Nn;
+        load_increment(P.G_field + (size_t)s * P.Nn, m, Fm, X, xa, xb);
+      } else {
         load(P.G_field + (size_t)s * P.Nn, xb);
+      }
       comm.sync();
       solve(xb, j);
       const double sp = pnorm_p(xb);
@@ -1090,11 +1107,18 @@ struct Streamer {
       const double* Tk = P.hist + (size_t)kidx * P.Nn;
       const double* Tkm = P.hist + (size_t)kprev * P.Nn;
       build_rhs(xa, [&](int g) { return scale * ipow(Tk[g], P.p_int - 1); });
-      // start G(v_{s+1}^old) + (G(v_{s+2}^new) - G(v_{s+2}^old)) = G[s] + v_{s+1}^new - F[s+1]
-      if (P.extrap > 1 && s + 1 < P.Ntau)
-        load_increment(P.G_field + (size_t)s * P.Nn, P.F_field + (size_t)(s + 1) * P.Nn, xa, xb);
-      else
+      // start G(v_{s+1}^old) plus the extrapolated increments of the last min(extrap - 1,
+      // Ntau - 1 - s) steps
+      const int m = min(P.extrap - 1, min(P.Ntau - 1 - s, 3));
+      if (m >= 1) {
+        const double* Fm[3];
+        const double* X[3] = {nullptr, nullptr, nullptr};
+        for (int i = 0; i < m; ++i) Fm[i] = P.F_field + (size_t)(s + 1 + i) * P.Nn;
+        for (int i = 1; i < m; ++i) X[i] = P.out_field + (size_t)(s + 1 + i) * P.Nn;
+        load_increment(P.G_field + (size_t)s * P.Nn, m, Fm, X, xa, xb);
+      } else {
         load(P.G_field + (size_t)s * P.Nn, xb);
+      }
       comm.sync();
       solve(xb, kidx);
       // g_s = g_{s+1} - (1/Ntau) term(lambda_G) + F_g[s] - G_g[s]
