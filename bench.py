@@ -520,12 +520,12 @@ def run_gpu(args):
 # differently reports traffic as null.
 NCU_TRAFFIC = {
     "captured": "2026-12-03",
-    "sources_sha16": "bf2c76ac53ffac87",
+    "sources_sha16": "a6f7f5ec6bb57ab9",
     # the adjoint coarse propagator runs as its two Theta-free parts (two launches per pass)
-    "bytes": {"fine_primal": 8.028928e6 + 108.199936e6, "coarse_primal": 7.425536e6 + 0.0,
-              "correct_primal": 11.869696e6 + 1536.0, "fine_adjoint": 148.818688e6 + 1.789184e6,
-              "coarse_adjoint": (15.687680e6 + 0.0) + (7.088640e6 + 768.0),
-              "correct_adjoint": 24.059136e6 + 768.0},
+    "bytes": {"fine_primal": 8.002304e6 + 108.280064e6, "coarse_primal": 7.368448e6 + 256.0,
+              "correct_primal": 11.627264e6 + 768.0, "fine_adjoint": 149.358848e6 + 2.136320e6,
+              "coarse_adjoint": (15.459840e6 + 0.0) + (7.042304e6 + 512.0),
+              "correct_adjoint": 24.212224e6 + 0.0},
 }
 STEPPER_SOURCES = ("stepper.cuh", "comm.cuh", "ptg_device.cuh", "stepper_inst.cu", "stepper_launch.cuh", "plan.cu")
 
