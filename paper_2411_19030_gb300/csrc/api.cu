@@ -1438,6 +1438,7 @@ struct ptg_batch {
   // their correction sweeps run side by side, each on a group of kBatchSweepCtas CTAs, on
   // streams forked from and joined to the caller's stream
   std::vector<cudaStream_t> side;
+  int nsweep_side = 0;           // side streams the streamed sweeps use (as many as fit the chip)
   cudaEvent_t fork = nullptr, fork2 = nullptr;
   std::vector<cudaEvent_t> join;
   std::vector<BatchBuf> bufs;
@@ -1664,6 +1665,7 @@ int batch_default(ptg_batch* b, int ph) {
 // chip side by side (measured at 256 x 256: 71 ms for 64 steps on 16 CTAs, against 45 ms alone
 // on 128 CTAs, one after the other).
 constexpr int kBatchSweepCtas = 16;
+constexpr int kBatchSideStreams = 24;
 // Designs of this many nodes or more take their own path in a batch even with on-chip solves:
 // the persistent launch's geometry is sized by its largest design, and their own cluster
 // launches run beside it.  Measured on the 48-design workload: 1.98 s per batched pass with
@@ -1748,11 +1750,11 @@ int batch_run(ptg_batch* b, int ph, cudaStream_t stream) {
     }
   }
   const bool sweep = ph == 2 || ph == 5;
-  if (sweep && after.size() >= 2 && nside > 0) {
+  if (sweep && after.size() >= 2 && b->nsweep_side > 0) {
     PTG_CUDA(cudaEventRecord(b->fork2, stream));
     const int kind = phase_kind(ph);
     for (size_t i = 0; i < after.size(); ++i) {
-      const int k = (int)(i % nside);
+      const int k = (int)(i % b->nsweep_side);
       PTG_CUDA(cudaStreamWaitEvent(b->side[k], b->fork2, 0));
       used[k] = 1;
       ptg_op* op = b->ops[after[i]];
@@ -1849,10 +1851,12 @@ int ptg_batch_create(ptg_op* const* ops, int nops, ptg_batch** out) {
   }
   if (e == cudaSuccess) e = cudaMalloc(&b->queue, kPhases * sizeof(int));
   if (nown >= 1) {
-    // as many side streams as sweeps fit the chip at once
+    // side streams: up to kBatchSideStreams for the cluster launches beside the persistent
+    // launch; the first SMs / kBatchSweepCtas of them carry the streamed sweeps side by side
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
-    const int nside = std::max(1, std::min(nown, nsm / kBatchSweepCtas));
+    const int nside = std::max(1, std::min(nown, kBatchSideStreams));
+    b->nsweep_side = std::max(1, std::min(nside, nsm / kBatchSweepCtas));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork2, cudaEventDisableTiming);
     for (int k = 0; k < nside && e == cudaSuccess; ++k) {
