@@ -190,10 +190,10 @@ typedef struct {
                           (omega = 0.8), ten damped-Jacobi steps on the coarsest level; symmetric.
                           The batched coarse propagators run every slice at once, one group of
                           CTAs per slice; a correction sweep runs as one group of about one CTA
-                          per two node rows (at most one per SM).  2 wherever the grid coarsens at least once; 1
-                          never (the on-chip stepper with ptg_solve.twolevel); 0 the library's
-                          choice: grids of 40000 nodes or more with at least three levels.
-                          Other values: PTG_EINVAL. */
+                          per two node rows (at most one per SM).  2 wherever the grid coarsens
+                          at least once; 1 never (the on-chip stepper with ptg_solve.twolevel);
+                          0 the library's choice: grids of 40000 nodes or more with at least
+                          three levels.  Other values: PTG_EINVAL. */
 } ptg_solve;
 
 typedef struct {
