@@ -192,7 +192,7 @@ typedef struct {
                           CTAs per slice; a correction sweep runs as one group of about one CTA
                           per two node rows (at most one per SM).  2 wherever the grid coarsens
                           at least once; 1 never (the on-chip stepper with ptg_solve.twolevel);
-                          0 the library's choice: grids of 40000 nodes or more with at least
+                          0 the library's choice: grids of 30000 nodes or more with at least
                           three levels.  Other values: PTG_EINVAL. */
 } ptg_solve;
 

@@ -231,6 +231,10 @@ constexpr int kThreeLevelSmoothSteps = 3;
 
 // Node count from which a single FP64 system runs grid-wide (see choose_plan).
 constexpr int kWideMinNodes = 40000;
+// Node count from which the coarse-step solves stream by default (multigrid-preconditioned FP64 CG
+// with the vectors in HBM): 192 x 192 (37 249 nodes) and up.  On chip, a 192 x 192 one-shot pass
+// took longer than a 256 x 256 one with the same slices (214 against 187 ms at 64 slices).
+constexpr int kCoarseStreamMinNodes = 30000;
 // Streamed coarse-step solves (stream.cuh, mg.cu): node rows per CTA of a correction sweep's
 // group, the multigrid's smoothing steps, the damped-Jacobi steps on its coarsest level (at most
 // 9 x 9 nodes) where no dense inverse applies, and the levels with at most kMgSoloRows node rows, which the group's first CTA
@@ -907,9 +911,10 @@ int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time*
     }
   }
   // streamed coarse-step solves: coarse_stream = 2 where the grid coarsens at least once, or 0 on
-  // grids of kWideMinNodes nodes or more with at least three levels
+  // grids of kCoarseStreamMinNodes nodes or more with at least three levels
   const int mgL = mg_level_count(grid->nx, grid->ny);
-  if ((solve->coarse_stream == 2 && mgL >= 2) || (solve->coarse_stream == 0 && op->Nn >= kWideMinNodes && mgL >= 3))
+  if ((solve->coarse_stream == 2 && mgL >= 2) ||
+      (solve->coarse_stream == 0 && op->Nn >= kCoarseStreamMinNodes && mgL >= 3))
     op->mg_L = mgL;
   // streamed fine propagators: fine_stream = 2, or 0 on grids of kWideMinNodes nodes or more
   // (the plan streams only where no cluster holds a slice); their CG preconditioned by the
