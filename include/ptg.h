@@ -214,7 +214,9 @@ typedef struct {
 
 typedef struct ptg_op ptg_op;   /* opaque: operator coefficients, launch plan, workspace */
 
-/* Library version string ("ptg <major>.<minor> sm_103a"). */
+/* Library version string ("ptg <major>.<minor> sm_103a"; the build with NVTX ranges, libptg_nvtx.so,
+ * appends " nvtx").  That build wraps every call that enqueues GPU work in an NVTX range of the
+ * domain "ptg" named after the call, and each batch phase in a nested range. */
 const char* ptg_version(void);
 
 /* Text of the last CUDA error seen by this thread's calls (static storage). */

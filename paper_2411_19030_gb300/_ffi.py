@@ -6,7 +6,7 @@ import ctypes
 import os
 from ctypes import POINTER, c_char_p, c_double, c_int, c_longlong, c_void_p
 
-from .build import LIB
+from .build import library_path
 
 PTG_OK, PTG_EINVAL, PTG_ENOCONV, PTG_ENONFINITE, PTG_ETIMEOUT, PTG_ECUDA, PTG_ENOMEM = 0, -1, -2, -3, -4, -5, -6
 PTG_FP64, PTG_FP32_REFINE, PTG_FP32_REFINE_ALL = 0, 1, 2
@@ -108,13 +108,19 @@ SIGNATURES = {
 _lib = None
 
 
+def default_library() -> str:
+    """The library ``load()`` opens: the build variant named by the environment variable
+    PTG_LIBRARY ("release", the default, is libptg.so; "nvtx" is libptg_nvtx.so)."""
+    return library_path(os.environ.get("PTG_LIBRARY") or "release")
+
+
 def load(path: str | None = None):
-    """Load libptg.so (built by ``build.build_library``) and declare every signature.
+    """Load the library (built by ``build.build_library``) and declare every signature.
     Raises OSError if the library is missing: there is no fallback implementation."""
     global _lib
     if _lib is not None and path is None:
         return _lib
-    p = path or LIB
+    p = path or default_library()
     if not os.path.exists(p):
         raise OSError(f"{p} is missing: run paper_2411_19030_gb300.build.build_library() first")
     lib = ctypes.CDLL(p)

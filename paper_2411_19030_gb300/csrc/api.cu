@@ -10,6 +10,7 @@
 #include "mesh.h"
 #include "ptg_internal.h"
 #include "stepper_launch.cuh"
+#include "trace.h"
 
 using namespace ptg;
 
@@ -803,13 +804,14 @@ void set_last_error(const char* msg) { std::snprintf(g_last_error, sizeof(g_last
 
 extern "C" {
 
-const char* ptg_version(void) { return "ptg 0.1 sm_103a"; }
+const char* ptg_version(void) { return PTG_TRACE_ENABLED ? "ptg 0.1 sm_103a nvtx" : "ptg 0.1 sm_103a"; }
 
 const char* ptg_last_error(void) { return g_last_error; }
 
 int ptg_op_create(const ptg_grid* grid, const ptg_material* mat, const ptg_time* time, const ptg_solve* solve,
                   const uint8_t* dirichlet_h, const double* q_elem_h, const double* q_time_h, int device,
                   ptg_op** out) {
+  PTG_TRACE(__func__);
   if (!out) return PTG_EINVAL;
   *out = nullptr;
   if (!grid || !mat || !time || !solve || !dirichlet_h) return PTG_EINVAL;
@@ -1107,6 +1109,7 @@ int ptg_op_get_plan(ptg_op* op, int kind, int ntasks, int* cs, int* nthreads, in
 }
 
 int ptg_fe_assemble_operator(ptg_op* op, const double* rho_d, cudaStream_t stream) {
+  PTG_TRACE(__func__);
   if (!op || !rho_d) return PTG_EINVAL;
   DeviceGuard dg(op->device);
   op->last_stream = stream;
@@ -1157,6 +1160,7 @@ int ptg_fe_assemble_operator(ptg_op* op, const double* rho_d, cudaStream_t strea
 int ptg_fine_propagate_slices(ptg_op* op, int schedule, int s0, int ns, const double* U_T, const double* U_theta,
                               double* T_hist, int hist_j0, int hist_rows, double* F_T, double* F_theta,
                               cudaStream_t stream) {
+  PTG_TRACE(__func__);
   if (!op || !U_T || !U_theta || !F_T || !F_theta) return PTG_EINVAL;
   if (schedule != PTG_SLICES_PARALLEL && schedule != PTG_SLICES_CHAINED) return PTG_EINVAL;
   if (s0 < 0 || ns < 1 || s0 + ns > op->tm.Ntau) return PTG_EINVAL;
@@ -1180,6 +1184,7 @@ int ptg_fine_propagate_slices(ptg_op* op, int schedule, int s0, int ns, const do
 
 int ptg_coarse_sweep(ptg_op* op, int direction, const double* X_field, const double* X_aux, const double* T_hist,
                      const double* Theta_d, double* G_field, double* G_aux, cudaStream_t stream) {
+  PTG_TRACE(__func__);
   if (!op) return PTG_EINVAL;
   return ptg_coarse_sweep_slices(op, direction, 0, op->tm.Ntau, X_field, X_aux, T_hist, Theta_d, G_field, G_aux,
                                  stream);
@@ -1188,6 +1193,7 @@ int ptg_coarse_sweep(ptg_op* op, int direction, const double* X_field, const dou
 int ptg_coarse_sweep_slices(ptg_op* op, int direction, int s0, int ns, const double* X_field, const double* X_aux,
                             const double* T_hist, const double* Theta_d, double* G_field, double* G_aux,
                             cudaStream_t stream) {
+  PTG_TRACE(__func__);
   if (!op || !X_field || !X_aux || !G_field || !G_aux) return PTG_EINVAL;
   if (direction != PTG_PRIMAL && direction != PTG_ADJOINT) return PTG_EINVAL;
   if (direction == PTG_ADJOINT && (!T_hist || !Theta_d)) return PTG_EINVAL;
@@ -1216,6 +1222,7 @@ int ptg_coarse_sweep_slices(ptg_op* op, int direction, int s0, int ns, const dou
 
 int ptg_coarse_adjoint_split(ptg_op* op, int s0, int ns, const double* V_lam, const double* V_g, const double* T_hist,
                              double* H_lam, double* H_g, double* S_lam, double* S_g, cudaStream_t stream) {
+  PTG_TRACE(__func__);
   if (!op || !V_lam || !V_g || !T_hist || !H_lam || !H_g || !S_lam || !S_g) return PTG_EINVAL;
   if (s0 < 0 || ns < 1 || s0 + ns > op->tm.Ntau) return PTG_EINVAL;
   if (op->mesh) return PTG_EINVAL;                       // the 2h-mesh G has its own adjoint path
@@ -1268,6 +1275,7 @@ int ptg_op_overlap_ok(ptg_op* op, int* ok) {
 int ptg_coarse_adjoint_combine(ptg_op* op, int s0, int ns, const double* Theta_d, const double* H_lam,
                                const double* H_g, const double* S_lam, const double* S_g, double* G_lam, double* G_g,
                                cudaStream_t stream) {
+  PTG_TRACE(__func__);
   if (!op || !Theta_d || !H_lam || !H_g || !S_lam || !S_g || !G_lam || !G_g) return PTG_EINVAL;
   if (s0 < 0 || ns < 1 || s0 + ns > op->tm.Ntau) return PTG_EINVAL;
   DeviceGuard dg(op->device);
@@ -1283,6 +1291,7 @@ int ptg_coarse_adjoint_combine(ptg_op* op, int s0, int ns, const double* Theta_d
 int ptg_parareal_correct(ptg_op* op, int direction, const double* F_field, const double* F_aux, const double* G_field,
                          const double* G_aux, double* X_field, double* X_aux, double* T_hist, const double* Theta_d,
                          cudaStream_t stream) {
+  PTG_TRACE(__func__);
   if (!op || !F_field || !F_aux || !X_field || !X_aux) return PTG_EINVAL;
   if ((G_field == nullptr) != (G_aux == nullptr)) return PTG_EINVAL;   // both NULL: PLT (G = 0)
   if (direction != PTG_PRIMAL && direction != PTG_ADJOINT) return PTG_EINVAL;
@@ -1313,6 +1322,7 @@ int ptg_parareal_correct(ptg_op* op, int direction, const double* F_field, const
 
 int ptg_objective_from_modified(ptg_op* op, const double* Theta_mod_d, const double* grad_mod_d, double* Theta_d,
                                 double* grad_d, cudaStream_t stream) {
+  PTG_TRACE(__func__);
   if (!op || !Theta_mod_d || !grad_mod_d || !Theta_d || !grad_d) return PTG_EINVAL;
   DeviceGuard dg(op->device);
   op->last_stream = stream;
@@ -1324,6 +1334,7 @@ int ptg_objective_from_modified(ptg_op* op, const double* Theta_mod_d, const dou
 int ptg_adjoint_sweep(ptg_op* op, int schedule, int s0, int ns, const double* T_hist, int hist_j0, int hist_rows,
                       const double* Theta_d, const double* V_lam, const double* V_g, double* F_lam, double* F_g,
                       cudaStream_t stream) {
+  PTG_TRACE(__func__);
   if (!op || !T_hist || !Theta_d || !V_lam || !V_g || !F_lam || !F_g) return PTG_EINVAL;
   if (schedule != PTG_SLICES_PARALLEL && schedule != PTG_SLICES_CHAINED) return PTG_EINVAL;
   if (s0 < 0 || ns < 1 || s0 + ns > op->tm.Ntau) return PTG_EINVAL;
@@ -1348,6 +1359,7 @@ int ptg_adjoint_sweep(ptg_op* op, int schedule, int s0, int ns, const double* T_
 
 int ptg_sensitivities(ptg_op* op, const double* lam_hist, int j0, int j1, const double* T_hist, int hist_j0,
                       int hist_rows, double* grad_d, cudaStream_t stream) {
+  PTG_TRACE(__func__);
   if (!op || !lam_hist || !T_hist || !grad_d) return PTG_EINVAL;
   if (j0 < 1 || j1 < j0 || j1 > op->tm.Nt) return PTG_EINVAL;
   if (!window_covers(hist_j0, hist_rows, j0 - 1, j1)) return PTG_EINVAL;
@@ -1388,6 +1400,7 @@ int ptg_op_set_wait_limit(ptg_op* op, long long polls) {
 }
 
 int ptg_reset_stats(ptg_op* op, cudaStream_t stream) {
+  PTG_TRACE(__func__);
   if (!op) return PTG_EINVAL;
   DeviceGuard dg(op->device);
   op->last_stream = stream;
@@ -1724,7 +1737,17 @@ bool own_beside(ptg_batch* b, int d, int ph) {
 // streamed launches after it: correction sweeps side by side on the side streams (each on a
 // group of kBatchSweepCtas CTAs, a plan override of its op for that launch only), the rest one
 // after the other on `stream`.  Every side stream used joins `stream` at the end.
+#if PTG_TRACE_ENABLED
+const char* const kPhaseTrace[kPhases] = {"fine primal",  "coarse primal",      "primal correction",
+                                          "fine adjoint", "coarse adjoint",     "adjoint correction",
+                                          "sequential primal", "sequential adjoint", "primal copy (G = 0)",
+                                          "adjoint copy (G = 0)"};
+#endif
+
 int batch_run(ptg_batch* b, int ph, cudaStream_t stream) {
+#if PTG_TRACE_ENABLED
+  PTG_TRACE(kPhaseTrace[ph]);
+#endif
   std::vector<int> beside, after;
   for (int d : b->order) {
     if (in_launch(b, d, ph)) continue;
@@ -1809,6 +1832,7 @@ int batch_run(ptg_batch* b, int ph, cudaStream_t stream) {
 extern "C" {
 
 int ptg_batch_create(ptg_op* const* ops, int nops, ptg_batch** out) {
+  PTG_TRACE(__func__);
   if (!out) return PTG_EINVAL;
   *out = nullptr;
   if (!ops || nops < 1) return PTG_EINVAL;
@@ -1910,6 +1934,7 @@ int ptg_batch_buffers(ptg_batch* b, int d, ptg_pass_buffers* out) {
 }
 
 int ptg_batch_assemble(ptg_batch* b, cudaStream_t stream) {
+  PTG_TRACE(__func__);
   if (!b) return PTG_EINVAL;
   for (int d = 0; d < (int)b->ops.size(); ++d) {
     int rc = ptg_fe_assemble_operator(b->ops[d], b->bufs[d].rho, stream);
@@ -1919,6 +1944,7 @@ int ptg_batch_assemble(ptg_batch* b, cudaStream_t stream) {
 }
 
 int ptg_batch_sequential_pass(ptg_batch* b, cudaStream_t stream) {
+  PTG_TRACE(__func__);
   if (!b) return PTG_EINVAL;
   DeviceGuard dg(b->device);
   int rc = batch_run(b, 6, stream);
@@ -1927,6 +1953,7 @@ int ptg_batch_sequential_pass(ptg_batch* b, cudaStream_t stream) {
 }
 
 int ptg_batch_oneshot_pass(ptg_batch* b, int variant, cudaStream_t stream) {
+  PTG_TRACE(__func__);
   if (!b || (variant != PTG_PARAREAL && variant != PTG_PLT)) return PTG_EINVAL;
   DeviceGuard dg(b->device);
   static const int parareal[] = {0, 1, 2, 3, 4, 5};
@@ -1941,6 +1968,7 @@ int ptg_batch_oneshot_pass(ptg_batch* b, int variant, cudaStream_t stream) {
 }
 
 int ptg_batch_commit(ptg_batch* b, cudaStream_t stream) {
+  PTG_TRACE(__func__);
   if (!b) return PTG_EINVAL;
   DeviceGuard dg(b->device);
   for (int d = 0; d < (int)b->ops.size(); ++d) {
@@ -1956,6 +1984,7 @@ int ptg_batch_commit(ptg_batch* b, cudaStream_t stream) {
 }
 
 int ptg_batch_run_phase(ptg_batch* b, int phase, cudaStream_t stream) {
+  PTG_TRACE(__func__);
   if (!b || phase < 0 || phase >= kPhases) return PTG_EINVAL;
   DeviceGuard dg(b->device);
   return batch_run(b, phase, stream);

@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <new>
 #include "ptg_internal.h"
+#include "trace.h"
 
 struct ptg_design {
   int device = 0;
@@ -123,6 +124,7 @@ extern "C" {
 
 int ptg_design_create(int nx, int ny, double h, double r_fil, double beta, double eta, int device,
                       ptg_design** out) {
+  PTG_TRACE(__func__);
   if (!out) return PTG_EINVAL;
   *out = nullptr;
   if (nx < 1 || ny < 1 || nx > 4096 || ny > 4096 || !(h > 0.0) || !(r_fil > 0.0) || !(beta > 0.0) ||
@@ -193,6 +195,7 @@ void ptg_design_destroy(ptg_design* d) {
 static int grid_for(int n) { return (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096; }
 
 int ptg_design_forward(ptg_design* d, const double* chi_d, double* rho_d, double* dproj_d, cudaStream_t stream) {
+  PTG_TRACE(__func__);
   if (!d || !chi_d || !rho_d || !dproj_d) return PTG_EINVAL;
   int prev = 0;
   cudaGetDevice(&prev);
@@ -206,6 +209,7 @@ int ptg_design_forward(ptg_design* d, const double* chi_d, double* rho_d, double
 
 int ptg_design_backward(ptg_design* d, const double* dproj_d, const double* df_drho_d, double* df_dchi_d,
                         cudaStream_t stream) {
+  PTG_TRACE(__func__);
   if (!d || !dproj_d || !df_dchi_d) return PTG_EINVAL;
   int prev = 0;
   cudaGetDevice(&prev);
@@ -218,6 +222,7 @@ int ptg_design_backward(ptg_design* d, const double* dproj_d, const double* df_d
 }
 
 int ptg_design_volume(ptg_design* d, const double* rho_d, double* vol_d, cudaStream_t stream) {
+  PTG_TRACE(__func__);
   if (!d || !rho_d || !vol_d) return PTG_EINVAL;
   int prev = 0;
   cudaGetDevice(&prev);

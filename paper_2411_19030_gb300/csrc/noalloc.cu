@@ -15,6 +15,7 @@
 #include <mutex>
 #include "ptg_device.cuh"
 #include "ptg_internal.h"
+#include "trace.h"
 
 namespace {
 
@@ -79,6 +80,7 @@ extern "C" {
 int ptg_sensitivities_noalloc(int nx, int ny, double h, int Nt, double dt, const ptg_material* mat,
                               const double* rho_d, const double* lam_hist, int j0, int j1, const double* T_hist,
                               int hist_j0, int hist_rows, double* grad_d, cudaStream_t stream) {
+  PTG_TRACE(__func__);
   if (!mat || !rho_d || !lam_hist || !T_hist || !grad_d) return PTG_EINVAL;
   if (nx < 1 || ny < 1 || Nt < 1 || !(h > 0.0) || !(dt > 0.0)) return PTG_EINVAL;
   if (j0 < 1 || j1 < j0 || j1 > Nt) return PTG_EINVAL;
