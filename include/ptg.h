@@ -54,6 +54,8 @@ extern "C" {
 #define PTG_ETIMEOUT   -4   /* a bounded device wait gave up */
 #define PTG_ECUDA      -5   /* a CUDA runtime call failed (see ptg_last_error) */
 #define PTG_ENOMEM     -6   /* device allocation failed */
+#define PTG_EBOUNDS    -7   /* debug build (libptg_debug.so) only: a launch check found an index range
+                                outside the op's allocations; the launch was skipped */
 
 /* precision of the fine-propagator CG (Sec. 2.2 solves; precision pattern of the port) */
 #define PTG_FP64            0  /* CG and every accumulation in FP64 */
@@ -200,8 +202,11 @@ typedef struct {
     int status;             /* PTG_OK or the first device-side error code recorded */
     int fail_kind;          /* who recorded status: 1 assemble; 10 + task kind for the stepper
                                (10 fine primal, 11 coarse primal, 12 correct primal,
-                                13 fine adjoint, 14 coarse adjoint, 15 correct adjoint) */
-    int fail_step;          /* fine time index j of the failing step (or -1) */
+                                13 fine adjoint, 14 coarse adjoint, 15 correct adjoint);
+                               30 + task kind for a launch check of the debug build */
+    int fail_step;          /* fine time index j of the failing step (or -1); for PTG_EBOUNDS
+                               the failed check: 1 slices, 2 history rows, 3 streamed groups,
+                               4 streamed workspace, 5 multigrid levels, 6 row ownership */
     int reserved;
     long long solves;       /* linear solves since the last reset */
     long long cg_iters;     /* CG iterations since the last reset */
@@ -215,8 +220,12 @@ typedef struct {
 typedef struct ptg_op ptg_op;   /* opaque: operator coefficients, launch plan, workspace */
 
 /* Library version string ("ptg <major>.<minor> sm_103a"; the build with NVTX ranges, libptg_nvtx.so,
- * appends " nvtx").  That build wraps every call that enqueues GPU work in an NVTX range of the
- * domain "ptg" named after the call, and each batch phase in a nested range. */
+ * appends " nvtx", the debug build, libptg_debug.so, " debug").  The NVTX build wraps every call
+ * that enqueues GPU work in an NVTX range of the domain "ptg" named after the call, and each batch
+ * phase in a nested range.  The debug build checks, before every launch of an op's task kinds,
+ * that the index ranges the launch will touch (slices, history rows, workspace groups, multigrid
+ * levels, node rows) lie inside the op's allocations; a failed check skips the launch, the call
+ * returns PTG_EBOUNDS, and ptg_get_stats reports it with the check in fail_step. */
 const char* ptg_version(void);
 
 /* Text of the last CUDA error seen by this thread's calls (static storage). */

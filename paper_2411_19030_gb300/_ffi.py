@@ -9,6 +9,7 @@ from ctypes import POINTER, c_char_p, c_double, c_int, c_longlong, c_void_p
 from .build import library_path
 
 PTG_OK, PTG_EINVAL, PTG_ENOCONV, PTG_ENONFINITE, PTG_ETIMEOUT, PTG_ECUDA, PTG_ENOMEM = 0, -1, -2, -3, -4, -5, -6
+PTG_EBOUNDS = -7
 PTG_FP64, PTG_FP32_REFINE, PTG_FP32_REFINE_ALL = 0, 1, 2
 PTG_SLICES_PARALLEL, PTG_SLICES_CHAINED = 0, 1
 PTG_PRIMAL, PTG_ADJOINT = 1, -1
@@ -17,7 +18,7 @@ PTG_PARAREAL, PTG_PLT = 0, 1
 PTG_TWOLEVEL_NONE, PTG_TWOLEVEL_ADDITIVE, PTG_TWOLEVEL_VCYCLE, PTG_TWOLEVEL_THREELEVEL = 0, 1, 2, 3
 
 ERROR_NAMES = {0: "PTG_OK", -1: "PTG_EINVAL", -2: "PTG_ENOCONV", -3: "PTG_ENONFINITE",
-               -4: "PTG_ETIMEOUT", -5: "PTG_ECUDA", -6: "PTG_ENOMEM"}
+               -4: "PTG_ETIMEOUT", -5: "PTG_ECUDA", -6: "PTG_ENOMEM", -7: "PTG_EBOUNDS"}
 
 
 class ptg_grid(ctypes.Structure):
@@ -110,7 +111,8 @@ _lib = None
 
 def default_library() -> str:
     """The library ``load()`` opens: the build variant named by the environment variable
-    PTG_LIBRARY ("release", the default, is libptg.so; "nvtx" is libptg_nvtx.so)."""
+    PTG_LIBRARY ("release", the default, is libptg.so; "nvtx" libptg_nvtx.so; "debug"
+    libptg_debug.so)."""
     return library_path(os.environ.get("PTG_LIBRARY") or "release")
 
 

@@ -5,10 +5,11 @@ build in parallel; the objects are linked with the assembly kernels and the C AB
 into ``paper_2411_19030_gb300/libptg.so``.  Objects go to ``paper_2411_19030_gb300/_build``.
 A rebuild happens only when a source or header is newer than the library.
 
-Variants: ``release`` (the default, ``libptg.so``) and ``nvtx`` (``libptg_nvtx.so``, compiled
-with ``-DPTG_NVTX``: NVTX ranges around every C-ABI call, for a profiler's timeline).  The
-binding loads the variant named by the environment variable ``PTG_LIBRARY`` (default
-``release``).
+Variants: ``release`` (the default, ``libptg.so``), ``nvtx`` (``libptg_nvtx.so``, compiled with
+``-DPTG_NVTX``: NVTX ranges around every C-ABI call, for a profiler's timeline) and ``debug``
+(``libptg_debug.so``, ``-DPTG_DEBUG``: every launch's index ranges checked against the op's
+allocations first; a failed check skips the launch and reports PTG_EBOUNDS).  The binding loads
+the variant named by the environment variable ``PTG_LIBRARY`` (default ``release``).
 """
 from __future__ import annotations
 
@@ -23,10 +24,11 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libptg.so")
-VARIANTS = {"release": [], "nvtx": ["-DPTG_NVTX"]}
-# the translation units whose code depends on a variant's macros (those that include trace.h);
-# a variant compiles these and links them with the release objects of the others
-VARIANT_SOURCES = {"nvtx": ("api.cu", "design.cu", "noalloc.cu")}
+VARIANTS = {"release": [], "nvtx": ["-DPTG_NVTX"], "debug": ["-DPTG_DEBUG"]}
+# the translation units whose code depends on a variant's macros (trace.h reads PTG_NVTX; the
+# launch checks of launch_check.h run in api.cu); a variant compiles these and links them with
+# the release objects of the others
+VARIANT_SOURCES = {"nvtx": ("api.cu", "design.cu", "noalloc.cu"), "debug": ("api.cu",)}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -10,6 +10,7 @@
 #include "mesh.h"
 #include "ptg_internal.h"
 #include "stepper_launch.cuh"
+#include "launch_check.h"
 #include "trace.h"
 
 using namespace ptg;
@@ -92,6 +93,9 @@ struct ptg_op {
   double* mesh_lam = nullptr;    // [Ntau][Nn] prolongated adjoint states of G
   double* mesh_dg = nullptr;     // [Ntau][Ne] g increments of G
   cudaStream_t last_stream = nullptr;
+  // the first failed launch check of the debug build (launch_check.h): PTG_EBOUNDS, the task
+  // kind and the check's site; reported by ptg_get_stats when the device status is clear
+  int dbg_status = 0, dbg_kind = 0, dbg_site = 0;
   std::mutex mu;
   std::map<std::tuple<int, int, int>, Plan> plans;   // (precision, kind, ntasks) -> plan
   std::map<int, Plan> plan_override;                   // kind -> forced plan
@@ -541,6 +545,50 @@ void base_params(const ptg_op* op, StepParams& P) {
   P.prev_field = op->lam_prev;
 }
 
+#ifdef PTG_DEBUG
+static_assert(kCheckMaxLevels == kMgMaxLevels && kCheckSlack == kSlack, "launch_check.h constants");
+
+// The debug build's launch checks (launch_check.h): PTG_OK, or PTG_EBOUNDS with the first failed
+// check recorded on the op (the launch is then skipped).
+int debug_check(ptg_op* op, const StepParams& P, const Plan& plan, int ntasks) {
+  LaunchFacts f;
+  f.kind = P.kind;
+  f.s0 = P.s0;
+  f.ns = P.ns;
+  f.chained = P.chained;
+  f.ntasks = ntasks;
+  f.Ntau = op->tm.Ntau;
+  f.M = op->M;
+  f.plt = P.plt;
+  f.has_hist = P.hist != nullptr;
+  f.hist_j0 = P.hist_j0;
+  f.hist_rows = P.hist_rows;
+  f.ny = op->g.ny;
+  f.W = op->W;
+  f.cs = plan.cs;
+  f.rmax = plan.rmax;
+  f.streamed = plan.stream;
+  f.wide = plan.wide;
+  f.groups = plan.max_active_clusters;
+  f.st_groups = op->st_groups;
+  f.st_pv = P.st_pv;
+  f.mg_levels = plan.stream ? P.mg_levels : 0;
+  for (int l = 0; l < f.mg_levels && l < kCheckMaxLevels; ++l) {
+    f.mg_voff[l] = P.mg[l].voff;
+    f.mg_plen[l] = P.mg[l].plen;
+  }
+  f.mg_ws_stride = P.mg_ws_stride;
+  const int site = launch_check_site(f);
+  if (site == kSiteNone) return PTG_OK;
+  if (op->dbg_status == 0) {
+    op->dbg_status = PTG_EBOUNDS;
+    op->dbg_kind = 30 + P.stats_kind;
+    op->dbg_site = site;
+  }
+  return PTG_EBOUNDS;
+}
+#endif
+
 int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream, int stats_kind = -1) {
   P.stats_kind = stats_kind >= 0 ? stats_kind : P.kind;
   Plan plan;
@@ -582,6 +630,9 @@ int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream, int stats_ki
         P.g_bar = op->sw_bar;
       }
     }
+#ifdef PTG_DEBUG
+    if (const int site = debug_check(op, P, plan, ntasks)) return site;
+#endif
     op->last_stream = stream;
     PTG_CUDA(launch_stream(P, prec, plan.max_active_clusters, plan.nthreads, stream));
     return PTG_OK;
@@ -602,6 +653,9 @@ int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream, int stats_ki
   // on cooperative-grid launches every reduction is a global-memory round trip of several
   // microseconds, so the default trades two slab-local sweeps for fewer CG iterations there
   if ((op->sv.local_steps == 0 || op->sv.local_steps == 3) && plan.wide) P.local_steps = 2;
+#ifdef PTG_DEBUG
+  if (const int site = debug_check(op, P, plan, ntasks)) return site;
+#endif
   op->last_stream = stream;
   PTG_CUDA(launch_stepper(P, plan, prec, ntasks, stream));
   return PTG_OK;
@@ -804,7 +858,13 @@ void set_last_error(const char* msg) { std::snprintf(g_last_error, sizeof(g_last
 
 extern "C" {
 
-const char* ptg_version(void) { return PTG_TRACE_ENABLED ? "ptg 0.1 sm_103a nvtx" : "ptg 0.1 sm_103a"; }
+const char* ptg_version(void) {
+#ifdef PTG_DEBUG
+  return "ptg 0.1 sm_103a debug";
+#else
+  return PTG_TRACE_ENABLED ? "ptg 0.1 sm_103a nvtx" : "ptg 0.1 sm_103a";
+#endif
+}
 
 const char* ptg_last_error(void) { return g_last_error; }
 
@@ -1379,6 +1439,11 @@ int ptg_get_stats(ptg_op* op, ptg_stats* out) {
   out->status = s.status;
   out->fail_kind = s.fail_kind;
   out->fail_step = s.fail_step;
+  if (s.status == PTG_OK && op->dbg_status != PTG_OK) {
+    out->status = op->dbg_status;
+    out->fail_kind = op->dbg_kind;
+    out->fail_step = op->dbg_site;
+  }
   out->reserved = 0;
   out->solves = (long long)s.solves;
   out->cg_iters = (long long)s.cg_iters;
@@ -1404,6 +1469,7 @@ int ptg_reset_stats(ptg_op* op, cudaStream_t stream) {
   if (!op) return PTG_EINVAL;
   DeviceGuard dg(op->device);
   op->last_stream = stream;
+  op->dbg_status = op->dbg_kind = op->dbg_site = 0;
   PTG_CUDA(cudaMemsetAsync(op->stats, 0, sizeof(DevStats), stream));
   return PTG_OK;
 }
