@@ -43,9 +43,13 @@ optima; for the coarse-mesh propagators, bilinear reproduction by the interpolat
 the restricted load and the Galerkin products against the operators assembled on 2h,
 Galerkin orthogonality of a coarse step, the one-shot fixed point, exactness after N_tau
 iterations, and second-order agreement with the fine-mesh coarse step.
-The one-shot estimate for a design that differs from the warm-start design has
-no closed form: beyond the fixed point it is "parity unpinned" (it is the literal
-algorithm, checked only for consistency with the pinned pieces it is made of).
+The one-shot estimate for a design that differs from the warm-start design is pinned in
+closed form where the problem reduces to scalars: uniform designs, no load, Dirichlet sinks on
+the whole boundary and a sine mode, with the old design's exact states as the warm start.
+There every state is a multiple of the mode, and T, Theta~, lambda and the gradient of the pass
+(p = 2 for the adjoint half) are explicit sums over the slices; planted mistakes in the
+propagators fail them.  For a non-uniform design there is no closed form: beyond the fixed point
+the same code runs unpinned.
 """
 from .fem import Material, Problem, element_matrices, simp, assemble
 from .stepping import (Operator, objective, objective_from_modified, sequential_primal, sequential_adjoint,
