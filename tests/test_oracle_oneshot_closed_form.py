@@ -39,7 +39,7 @@ KE = np.array([[4, -1, -2, -1], [-1, 4, -1, -2], [-2, -1, 4, -1], [-1, -2, -1, 4
 ME1 = np.array([[4, 2, 1, 2], [2, 4, 2, 1], [1, 2, 4, 2], [2, 1, 2, 4]]) / 36.0   # times h^2
 
 
-def _setup(nx, ny, mx, my, Nt, Ntau, p, dt, rho_a, rho_b):
+def _setup(nx, ny, mx, my, Nt, Ntau, p, dt, rho_a, rho_b, modified=True):
     h = 1.0 / max(nx, ny)
     x = np.arange(nx + 1) * h
     y = np.arange(ny + 1) * h
@@ -48,14 +48,14 @@ def _setup(nx, ny, mx, my, Nt, Ntau, p, dt, rho_a, rho_b):
     sink[0, :] = sink[-1, :] = sink[:, 0] = sink[:, -1] = True
     v[sink.reshape(-1)] = 0.0
     prob = make_problem(nx, ny, Nt=Nt, Ntau=Ntau, dt=dt, p=p, material="table1", sink=sink.reshape(-1),
-                        q_time=np.zeros(Nt + 1), T0=v, h=h, modified_objective=True)
+                        q_time=np.zeros(Nt + 1), T0=v, h=h, modified_objective=modified)
     mat = prob.material
     k = lambda r: mat.kmin + (mat.k0 - mat.kmin) * r ** mat.pk
     c = lambda r: mat.cmin + (mat.c0 - mat.cmin) * r ** mat.pc
     tx, ty = mx * np.pi / nx, my * np.pi / ny
     m1x, m1y = h * (2 + np.cos(tx)) / 3, h * (2 + np.cos(ty)) / 3
     k1x, k1y = 2 * (1 - np.cos(tx)) / h, 2 * (1 - np.cos(ty)) / h
-    S = dict(h=h, v=v, prob=prob, mh=m1x * m1y, kh=k1x * m1y + m1x * k1y,
+    S = dict(h=h, v=v, prob=prob, mh=m1x * m1y, kh=k1x * m1y + m1x * k1y, modified=modified,
              ka=k(rho_a), ca=c(rho_a), kb=k(rho_b), cb=c(rho_b),
              dkb=mat.pk * (mat.k0 - mat.kmin) * rho_b ** (mat.pk - 1),
              dcb=mat.pc * (mat.c0 - mat.cmin) * rho_b ** (mat.pc - 1))
@@ -82,17 +82,33 @@ def _closed_form(S, Nt, Ntau, p, dt):
         for i in range(1, M):
             tau[M * s + i] = r ** i * alpha[s]
         tau[M * (s + 1)] = beta[s + 1]
-    # Theta~ (plain sum of Sec. 7.1): G(new) + F(old) - G(old) increments of every slice
-    Theta = sum(Pp / Ne * ((R * beta[s]) ** p / Ntau
-                           + sum((r ** i * alpha[s]) ** p for i in range(1, M + 1)) / Nt
-                           - (R * alpha[s]) ** p / Ntau) for s in range(Ntau))
+    if S["modified"]:
+        # Theta~ (plain sum of Sec. 7.1): G(new) + F(old) - G(old) increments of every slice
+        Theta = sum(Pp / Ne * ((R * beta[s]) ** p / Ntau
+                               + sum((r ** i * alpha[s]) ** p for i in range(1, M + 1)) / Nt
+                               - (R * alpha[s]) ** p / Ntau) for s in range(Ntau))
+        Theta_a = None
+    else:
+        # the power mean of Eq. 2.11 carried as theta itself (Sec. 4.4): each propagator adds
+        # its increment under the p-th power, the correction acts on theta
+        th_old = [(sum(ra ** (p * j) for j in range(1, M * s + 1)) * Pp / (Nt * Ne)) ** (1 / p)
+                  for s in range(Ntau + 1)]
+        thG = lambda th, amp: (th ** p + (R * amp) ** p * Pp / (Ntau * Ne)) ** (1 / p)
+        th = 0.0
+        for s in range(Ntau):
+            thF = (th_old[s] ** p + sum((r ** i * alpha[s]) ** p for i in range(1, M + 1)) * Pp / (Nt * Ne)) ** (1 / p)
+            th = thG(th, beta[s]) + thF - thG(th_old[s], alpha[s])
+        Theta, Theta_a = th, th_old[Ntau]
     if p != 2:
         return dict(tau=tau, Theta=Theta)
-    sig = 2.0 / Ne                                      # adjoint source scale p / Ne (Sec. 7.1)
+    # adjoint source scale: p / Ne (Sec. 7.1), or Theta^(1-p) / Ne (Eq. 4.6) with the pass's
+    # corrected Theta (and the old design's exact Theta for its sequential adjoint)
+    sig = 2.0 / Ne if S["modified"] else Theta ** (1 - p) / Ne
+    sig_a = 2.0 / Ne if S["modified"] else Theta_a ** (1 - p) / Ne
     # old adjoint (exact sequential, design a): lambda_j = sum_{i >= j} ra^(i-j+1) dt sig ra^i / (ca mh)
     lam_a = np.zeros(Nt + 2)
     for j in range(1, Nt + 1):
-        lam_a[j] = sum(ra ** (i - j + 1) * dt * sig * ra ** i / (S["ca"] * S["mh"]) for i in range(j, Nt + 1))
+        lam_a[j] = sum(ra ** (i - j + 1) * dt * sig_a * ra ** i / (S["ca"] * S["mh"]) for i in range(j, Nt + 1))
     lam_old = np.array([lam_a[M * n + 1] if n < Ntau else 0.0 for n in range(Ntau + 1)])
     cb_mh = S["cb"] * S["mh"]
 
@@ -146,25 +162,30 @@ def _old_states(S, Nt, Ntau, p, dt, lam_old, rng):
     Pp = float(np.sum(np.abs(S["v"]) ** p))
     U_T = np.array([ra ** (M * s) * S["v"] for s in range(Ntau + 1)])
     U_th = np.array([sum(ra ** (p * j) for j in range(1, M * s + 1)) * Pp / (Nt * prob.Ne) for s in range(Ntau + 1)])
+    if not S["modified"]:
+        U_th = U_th ** (1 / p)
     V_l = np.array([lam_old[n] * S["v"] for n in range(Ntau + 1)]) if lam_old is not None else np.zeros_like(U_T)
     V_g = rng.standard_normal((Ntau + 1, prob.Ne))
     V_g[Ntau] = 0.0
     return (U_T, U_th), (V_l, V_g)
 
 
-CASES = [  # nx, ny, mx, my, Nt, Ntau, p
-    (8, 6, 1, 1, 12, 3, 2.0),
-    (8, 6, 2, 1, 12, 4, 2.0),
-    (7, 9, 1, 2, 10, 5, 2.0),
-    (8, 6, 1, 1, 12, 3, 8.0),
-    (6, 6, 1, 1, 8, 2, 8.0),
+CASES = [  # nx, ny, mx, my, Nt, Ntau, p, modified objective (Sec. 7.1) or the power mean
+    (8, 6, 1, 1, 12, 3, 2.0, True),
+    (8, 6, 2, 1, 12, 4, 2.0, True),
+    (7, 9, 1, 2, 10, 5, 2.0, True),
+    (8, 6, 1, 1, 12, 3, 8.0, True),
+    (6, 6, 1, 1, 8, 2, 8.0, True),
+    (8, 6, 1, 1, 12, 3, 2.0, False),
+    (7, 9, 2, 1, 10, 5, 2.0, False),
+    (8, 6, 1, 1, 12, 4, 8.0, False),
 ]
 
 
-@pytest.mark.parametrize("nx,ny,mx,my,Nt,Ntau,p", CASES)
-def test_oneshot_pass_with_a_changed_design_matches_the_closed_form(nx, ny, mx, my, Nt, Ntau, p):
+@pytest.mark.parametrize("nx,ny,mx,my,Nt,Ntau,p,modified", CASES)
+def test_oneshot_pass_with_a_changed_design_matches_the_closed_form(nx, ny, mx, my, Nt, Ntau, p, modified):
     dt, rho_a, rho_b = 0.011, 0.6, 0.75
-    S = _setup(nx, ny, mx, my, Nt, Ntau, p, dt, rho_a, rho_b)
+    S = _setup(nx, ny, mx, my, Nt, Ntau, p, dt, rho_a, rho_b, modified)
     cf = _closed_form(S, Nt, Ntau, p, dt)
     U_old, V_old = _old_states(S, Nt, Ntau, p, dt, cf.get("lam_old"), np.random.default_rng(3))
     out = oneshot_pass(Operator(S["prob"], np.full(nx * ny, rho_b)), U_old, V_old)
@@ -203,15 +224,21 @@ def test_gradient_does_not_depend_on_the_old_g_states():
 # ------------------------------------------------------------------ planted mistakes
 
 def _planted(name):
-    """Plausible mistakes, each planted in the oracle's propagators: G_adj reading T_{M(s+1)}
-    instead of T_{Ms+1}; the coarse theta increment divided by Nt Ne instead of Ntau Ne; the
-    fine adjoint's sensitivity divided by Ntau instead of Nt; a coarse step of dt."""
+    """Plausible mistakes, each planted in the oracle: G_adj reading T_{M(s+1)} instead of
+    T_{Ms+1}; the coarse theta increment divided by Nt Ne instead of Ntau Ne; the fine adjoint's
+    sensitivity divided by Ntau instead of Nt; a coarse step of dt; the adjoint source scale
+    Theta^(-p) / Ne instead of Theta^(1-p) / Ne (Eq. 4.6)."""
     import importlib
     import sys
 
     importlib.import_module("oracle.parareal")
     PR = sys.modules["oracle.parareal"]
     from oracle.stepping import accumulate_theta, sensitivity_term
+
+    ST = sys.modules["oracle.stepping"]
+
+    def source_scale(prob, Theta):
+        return prob.p / prob.Ne if prob.modified_objective else Theta ** (-prob.p) / prob.Ne
 
     def G_adj_row(op, s, lam, g, T_hist, Theta):
         prob = op.prob
@@ -237,15 +264,16 @@ def _planted(name):
             g = g - sensitivity_term(op, lam, T_hist[j], T_hist[j - 1], prob.dt) / prob.Ntau
         return lam, g
 
-    table = {"G_adj_row": ("G_adj", G_adj_row), "G_pri_divisor": ("G_pri", G_pri_divisor),
-             "G_pri_step": ("G_pri", G_pri_step), "F_adj_divisor": ("F_adj", F_adj_divisor)}
-    return PR, table[name]
+    table = {"G_adj_row": (PR, "G_adj", G_adj_row), "G_pri_divisor": (PR, "G_pri", G_pri_divisor),
+             "G_pri_step": (PR, "G_pri", G_pri_step), "F_adj_divisor": (PR, "F_adj", F_adj_divisor),
+             "source_exponent": (ST, "adjoint_source_scale", source_scale)}
+    return table[name]
 
 
-@pytest.mark.parametrize("name", ["G_adj_row", "G_pri_divisor", "G_pri_step", "F_adj_divisor"])
+@pytest.mark.parametrize("name", ["G_adj_row", "G_pri_divisor", "G_pri_step", "F_adj_divisor", "source_exponent"])
 def test_a_planted_mistake_fails_the_closed_form(monkeypatch, name):
-    PR, (attr, fn) = _planted(name)
-    monkeypatch.setattr(PR, attr, fn)
+    module, attr, fn = _planted(name)
+    monkeypatch.setattr(module, attr, fn)
     failed = False
     for case in CASES:
         try:
