@@ -515,12 +515,14 @@ def run_gpu(args):
 
 
 # DRAM bytes per launch (read + write) of the 128x128 pass in the default precision, from one
-# ncu capture (profiles/).  They hold only for the kernel source they were taken from: the hash
-# of the stepper sources at capture time is stored beside them, and a run whose sources hash
-# differently reports traffic as null.
+# ncu capture (profiles/).  They hold only for that workload and precision, and only for the
+# kernel source they were taken from: the hash of the stepper sources at capture time is stored
+# beside them.  Any other workload, precision or source hash reports traffic as null.
 NCU_TRAFFIC = {
     "captured": "2026-12-03",
     "sources_sha16": "a6f7f5ec6bb57ab9",
+    "workload": WORKLOAD,
+    "precision": "fp32_refine",
     # the adjoint coarse propagator runs as its two Theta-free parts (two launches per pass)
     "bytes": {"fine_primal": 8.002304e6 + 108.280064e6, "coarse_primal": 7.368448e6 + 256.0,
               "correct_primal": 11.627264e6 + 768.0, "fine_adjoint": 149.358848e6 + 2.136320e6,
@@ -539,8 +541,11 @@ def stepper_sources_sha16() -> str:
     return hsh.hexdigest()[:16]
 
 
-def ncu_traffic(kind: str):
+def ncu_traffic(kind: str, workload: str = WORKLOAD, precision: str = "fp32_refine"):
     """(bytes per launch or None, provenance) of the stored ncu DRAM figure of a kernel."""
+    if workload != NCU_TRAFFIC["workload"] or precision != NCU_TRAFFIC["precision"]:
+        return None, (f"no ncu capture of this workload and precision ({workload}, {precision}); the stored one "
+                      f"is of {NCU_TRAFFIC['workload']}, {NCU_TRAFFIC['precision']}")
     sha = stepper_sources_sha16()
     if NCU_TRAFFIC["sources_sha16"] != sha or kind not in NCU_TRAFFIC["bytes"]:
         return None, f"no ncu capture of the current stepper sources ({sha})"
@@ -587,7 +592,8 @@ def algorithmic_bytes(kind: str, st: dict, N_free: int, launches: int) -> float:
     return N_free * per_dof / max(1, launches)
 
 
-def roofline(kind_ms: dict, stats: dict, N_free: int, launches: int, precision: str) -> dict:
+def roofline(kind_ms: dict, stats: dict, N_free: int, launches: int, precision: str,
+             workload: str = WORKLOAD) -> dict:
     """Roofline entry of the dominant kernel (largest share of the step) against the measured
     HBM copy bandwidth, with the algorithmic bytes of algorithmic_bytes(); beside it every
     stepper kernel's figure, and for an FP64-CG kernel its algorithmic FP64 FLOP rate against
@@ -605,7 +611,7 @@ def roofline(kind_ms: dict, stats: dict, N_free: int, launches: int, precision: 
                   "refine_per_solve": st["refinements"] / max(1, st["solves"])}
     dom = max(per, key=lambda k: per[k]["ms"])
     d = per[dom]
-    traffic, tsrc = ncu_traffic(dom)
+    traffic, tsrc = ncu_traffic(dom, workload, precision)
     out = {"kernel": dom, "bound": "hbm", "achieved": d["achieved_gbs"], "peak": hbm, "unit": "GB/s",
            "frac": d["frac"], "traffic": traffic, "traffic_source": tsrc, "peak_source": source,
            "algorithmic_bytes_per_launch": d["algorithmic_bytes"],
@@ -698,7 +704,7 @@ def streaming_256(args, flush, stream, device, name="diff256") -> dict:
     kind_ms = {k: float(v / steps) for k, v in zip(kinds, per)}
     st = op.stats()
     ms = float(np.mean(tot))
-    roof = roofline(kind_ms, st, N_free, steps, args.precision)
+    roof = roofline(kind_ms, st, N_free, steps, args.precision, name)
     out = {"workload": f"{name}: {n}x{n} grid, Nt={Nt}, Ntau={Ntau} (M={Nt // Ntau}), p={p:g}, rho ~ U(0,1) seed 1, "
                        "timed design 1% away (seed 1000), warm start from the sequential FP64 coarse states",
            "precision": args.precision, "rtol": args.rtol, "steps": steps, "ms_per_step": ms,

@@ -60,3 +60,34 @@ def test_reference_arm_is_silent_on_other_ranks(monkeypatch):
     with redirect_stdout(out):
         bench.run_reference(_args())
     assert out.getvalue().strip() == ""
+
+
+def _fake_counters():
+    kinds = ("fine_primal", "coarse_primal", "correct_primal", "fine_adjoint", "coarse_adjoint", "correct_adjoint")
+    stats = {"by_kind": {k: {"solves": 32.0, "cg_iters": 320.0, "refinements": 32.0} for k in kinds}}
+    kind_ms = {k: 1.0 + i for i, k in enumerate(kinds)}          # correct_adjoint dominates
+    return kind_ms, stats
+
+
+def test_roofline_bytes_follow_the_per_dof_rule(monkeypatch):
+    monkeypatch.setattr(bench, "stepper_sources_sha16", lambda: bench.NCU_TRAFFIC["sources_sha16"])
+    kind_ms, stats = _fake_counters()
+    r = bench.roofline(kind_ms, stats, 1000, 2, "fp32_refine")
+    assert r["kernel"] == "correct_adjoint" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    per_launch = 1000 * ((16 + 8) * 32 + 36 * 320 + 28 * 32) / 2   # adjoint solves read T_j too
+    assert r["algorithmic_bytes_per_launch"] == per_launch
+    assert abs(r["achieved"] - per_launch / 6e-3 / 1e9) < 1e-9 * r["achieved"]
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-15
+    assert r["per_kernel"]["fine_primal"]["algorithmic_bytes"] == 1000 * (16 * 32 + 36 * 320 + 28 * 32) / 2
+    assert r["traffic"] == bench.NCU_TRAFFIC["bytes"]["correct_adjoint"]
+
+
+def test_stored_traffic_is_reported_only_for_its_workload_and_precision(monkeypatch):
+    monkeypatch.setattr(bench, "stepper_sources_sha16", lambda: bench.NCU_TRAFFIC["sources_sha16"])
+    kind_ms, stats = _fake_counters()
+    for workload, precision in (("diff256", "fp32_refine"), ("loop512", "fp32_refine"), (bench.WORKLOAD, "fp64")):
+        r = bench.roofline(kind_ms, stats, 1000, 1, precision, workload)
+        assert r["traffic"] is None and "no ncu capture of this workload" in r["traffic_source"]
+    monkeypatch.setattr(bench, "stepper_sources_sha16", lambda: "0000000000000000")
+    r = bench.roofline(kind_ms, stats, 1000, 1, "fp32_refine")
+    assert r["traffic"] is None and "current stepper sources" in r["traffic_source"]
