@@ -161,13 +161,13 @@ def test_gradient_matches_central_differences(material, p):
 
 
 def test_gradient_fd_on_plain32_sample():
-    """32x32, 100 steps (the plain FP64 workload): central differences on 6 random elements."""
+    """32x32, 100 steps (the plain FP64 workload): central differences on 32 random elements."""
     w = W.workload("plain32")
     prob = make_problem(32, Nt=w["Nt"], dt=w["dt"], p=w["p"])
     rho = W.rho_plain(32, 32, 0)
     g = sequential_pass(Operator(prob, rho))["grad"]
     eps = 1e-6
-    for e in W.fd_elements(prob.Ne, 6, seed=3):
+    for e in W.fd_elements(prob.Ne, 32, seed=3):
         rp, rm = rho.copy(), rho.copy()
         rp[e] += eps
         rm[e] -= eps
