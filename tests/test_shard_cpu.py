@@ -159,3 +159,52 @@ def test_slice_range_partitions_contiguously():
                 s += ns
             assert s == Ntau
             assert max(n for _, n in got) - min(n for _, n in got) <= 1
+
+
+def _failing_worker(rank, world, port, q):
+    """Rank 1's fine propagation raises (a host-side injected failure) before the first exchange;
+    rank 1 then leaves.  Rank 0 must learn of it from its next collective, which ends with an error
+    within the process group's timeout instead of waiting for ever."""
+    import datetime
+    import time
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    prob, rho, rho_old = _case(4)
+    U_old, V_old, _ = coarse_states_from_sequential(OracleOp(prob, rho_old))
+    op = OracleSliceOp(OracleOp(prob, rho))
+    buf = Buffers(prob)
+    buf.U_T.copy_(torch.from_numpy(U_old[0])); buf.U_th.copy_(torch.from_numpy(U_old[1]))
+    buf.V_l.copy_(torch.from_numpy(V_old[0])); buf.V_g.copy_(torch.from_numpy(V_old[1]))
+    if rank == 1:
+        def fail(*args, **kwargs):
+            raise RuntimeError("injected failure of the fine propagation")
+        op.fine_propagate_slices = fail
+    t0 = time.monotonic()
+    try:
+        sharded_oneshot_pass(op, buf)
+        q.put((rank, "finished", "", time.monotonic() - t0))
+    except Exception as e:                                  # noqa: BLE001 -- reported to the test
+        q.put((rank, "error", f"{type(e).__name__}: {str(e)[:120]}", time.monotonic() - t0))
+    q.close()
+    q.join_thread()
+    os._exit(0)                                             # leave without a closing collective
+
+
+def test_a_failing_rank_ends_the_others_collectives_with_an_error():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        results = {r: (status, msg, secs) for r, status, msg, secs in (q.get(timeout=120) for _ in range(2))}
+    finally:
+        for p in procs:
+            p.join(timeout=30)
+            if p.is_alive():
+                p.kill()
+    assert results[1][0] == "error" and "injected failure" in results[1][1]
+    assert results[0][0] == "error", results[0]             # rank 0's all-gather did not complete
+    assert results[0][2] < 60.0                             # bounded by the process group's timeout
