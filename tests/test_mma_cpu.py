@@ -72,3 +72,35 @@ def test_design_and_mma_argument_checks(lib):
     assert lib.ptg_design_create(8, 8, 0.1, -1.0, 8.0, 0.5, 0, ctypes.byref(h)) == _ffi.PTG_EINVAL
     assert lib.ptg_design_create(8, 8, 0.1, 0.2, 8.0, 1.5, 0, ctypes.byref(h)) == _ffi.PTG_EINVAL
     assert lib.ptg_design_forward(None, None, None, None, None) == _ffi.PTG_EINVAL
+
+
+def test_mma_state_saved_to_a_file_resumes_bit_for_bit(lib, tmp_path):
+    """The optimiser half of the design loop's save / resume: the MMA state (update count, last
+    two iterates, asymptotes) written with np.savez, as the loop's save() does, and restored into
+    a fresh optimiser continues with the same iterates as the optimiser that never stopped."""
+    from paper_2411_19030_gb300.design import MMAUpdate
+
+    rng = np.random.default_rng(9)
+    n, V = 200, 0.45
+    t = rng.uniform(-0.2, 1.2, n)
+
+    def grads(x, k):
+        w = 1.0 + 0.5 * np.sin(0.4 * k)
+        return float(w * np.sum((x - t) ** 2)), 2 * w * (x - t), float(x.mean() - V), np.full(n, 1.0 / n)
+
+    a = MMAUpdate(n, 0.0, 1.0, 0.15)
+    x = rng.uniform(0.2, 0.8, n)
+    for k in range(7):
+        x = a.update(x, *grads(x, k))
+    path = tmp_path / "state.npz"
+    np.savez(path, x=x, **{"mma_" + key: v for key, v in a.get_state().items()})
+    d = np.load(path)
+    b = MMAUpdate(n, 0.0, 1.0, 0.15)
+    b.set_state({key: d["mma_" + key] for key in ("k", "x1", "x2", "L", "U")})
+    xa, xb = x, d["x"].copy()
+    for k in range(7, 15):
+        xa = a.update(xa, *grads(xa, k))
+        xb = b.update(xb, *grads(xb, k))
+        assert np.array_equal(xa, xb), k
+    with pytest.raises(ValueError):
+        MMAUpdate(n + 1, 0.0, 1.0, 0.15).set_state(a.get_state())
