@@ -48,8 +48,10 @@ closed form where the problem reduces to scalars: uniform designs, no load, Diri
 the whole boundary and a sine mode, with the old design's exact states as the warm start.
 There every state is a multiple of the mode, and T, Theta~, lambda and the gradient of the pass
 (p = 2 for the adjoint half) are explicit sums over the slices; planted mistakes in the
-propagators fail them.  For a non-uniform design there is no closed form: beyond the fixed point
-the same code runs unpinned.
+propagators fail them.  The same reduction pins the coarse-mesh propagators and k-iteration
+Parareal (the binomial iterates of Gander and Vandewalle, 2007; the reverse iterations in
+matrix form).  For a non-uniform design there is no closed form: beyond the fixed point the
+same code runs unpinned.
 """
 from .fem import Material, Problem, element_matrices, simp, assemble
 from .stepping import (Operator, objective, objective_from_modified, sequential_primal, sequential_adjoint,
