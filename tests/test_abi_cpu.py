@@ -102,3 +102,15 @@ def test_noalloc_rejects_non_positive_materials_on_host(lib, field):
     rc = lib.ptg_sensitivities_noalloc(4, 4, 0.25, 4, 0.1, ctypes.byref(m), fake, fake, 1, 4, fake, 0, 5, fake, None)
     assert rc == _ffi.PTG_EINVAL
     assert b"positive" in lib.ptg_last_error()
+
+
+def test_binding_constants_match_the_header():
+    """Every integer constant of include/ptg.h has the same value in the ctypes binding, and every
+    error code has a name there (the header's PTG_NOALLOC_SCRATCH_DOUBLES is a size, not a code)."""
+    src = open(os.path.join(ROOT, "include", "ptg.h")).read()
+    defs = dict(re.findall(r"^#define (PTG_[A-Z0-9_]+)\s+(-?\d+)\b", src, flags=re.M))
+    assert len(defs) >= 20
+    for name, value in defs.items():
+        assert getattr(_ffi, name) == int(value), name
+        if name.startswith("PTG_E") or name == "PTG_OK":
+            assert _ffi.ERROR_NAMES[int(value)] == name
