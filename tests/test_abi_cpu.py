@@ -114,3 +114,37 @@ def test_binding_constants_match_the_header():
         assert getattr(_ffi, name) == int(value), name
         if name.startswith("PTG_E") or name == "PTG_OK":
             assert _ffi.ERROR_NAMES[int(value)] == name
+
+
+def test_ctypes_structures_match_the_header_layout(tmp_path):
+    """The ctypes mirrors of the header's structures have the C layout: for every field of every
+    mirror, the offset that g++ gives it through include/ptg.h, and the size of the whole struct
+    (a field missing on either side changes one of them or fails the compile)."""
+    import shutil
+    import subprocess
+
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no host C++ compiler")
+    structs = [_ffi.ptg_grid, _ffi.ptg_material, _ffi.ptg_time, _ffi.ptg_solve, _ffi.ptg_stats,
+               _ffi.ptg_pass_buffers]
+    lines = ['#include <cstdio>', '#include <cstddef>', '#include "ptg.h"', "int main() {"]
+    for st in structs:
+        lines.append(f'  std::printf("{st.__name__} size %zu\\n", sizeof({st.__name__}));')
+        for f in st._fields_:
+            lines.append(f'  std::printf("{st.__name__} {f[0]} %zu\\n", offsetof({st.__name__}, {f[0]}));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.cpp"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    if not os.path.exists(os.path.join(cuda_inc, "cuda_runtime_api.h")):
+        pytest.skip("no CUDA headers for ptg.h")
+    subprocess.run([gxx, "-std=c++17", "-I", os.path.join(ROOT, "include"), "-I", cuda_inc, str(src), "-o", str(exe)],
+                   check=True, timeout=120)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True, timeout=60).stdout.split("\n")
+    got = {(a, b): int(c) for a, b, c in (ln.split() for ln in out if ln.strip())}
+    for st in structs:
+        assert got[(st.__name__, "size")] == ctypes.sizeof(st), st.__name__
+        for f in st._fields_:
+            assert got[(st.__name__, f[0])] == getattr(st, f[0]).offset, (st.__name__, f[0])
