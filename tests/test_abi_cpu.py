@@ -148,3 +148,18 @@ def test_ctypes_structures_match_the_header_layout(tmp_path):
         assert got[(st.__name__, "size")] == ctypes.sizeof(st), st.__name__
         for f in st._fields_:
             assert got[(st.__name__, f[0])] == getattr(st, f[0]).offset, (st.__name__, f[0])
+
+
+def test_product_path_fails_loudly_without_its_library_or_a_gpu(tmp_path):
+    """There is no CPU fallback: a missing library raises OSError on load, and an operator cannot
+    be made without a CUDA device (this test runs where torch sees none)."""
+    import torch
+
+    with pytest.raises(OSError, match="missing"):
+        _ffi.load(str(tmp_path / "libptg.so"))
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2411_19030_gb300 import Operator
+    with pytest.raises(Exception):
+        Operator(4, 4, 0.25, dict(k0=1.0, kmin=1e-3, pk=3.0, c0=1.0, cmin=1.0, pc=1.0), 4, 2, 0.1, 8.0,
+                 np.zeros(25, np.uint8))
