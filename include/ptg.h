@@ -262,8 +262,8 @@ int ptg_op_set_multigrid(ptg_op* op, int solo_rows, int coarse_steps, int fused)
 
 /*
  * Launch plan of the cluster stepper.  Every solve runs on one thread-block cluster of
- * `cs` CTAs (1, 2, 4, 8 or 16) that split the node rows; each CTA has `nthreads` (256)
- * threads, each holding `ng` aligned groups of 4 nodes (1..6).  kind: 0 fine primal,
+ * `cs` CTAs (1, 2, 4, 8 or 16) that split the node rows; each CTA has `nthreads` threads
+ * (a multiple of 32, at most 512), each holding `ng` aligned groups of 4 nodes (1..6).  kind: 0 fine primal,
  * 1 coarse primal, 2 primal correction, 3 fine adjoint, 4 coarse adjoint, 5 adjoint correction.
  * ptg_op_get_plan reports the plan used for `ntasks` concurrent clusters (chosen for the
  * fewest waves, then the largest cluster).  ptg_op_set_plan forces a plan for a kind
@@ -483,6 +483,14 @@ typedef struct {
 
 typedef struct ptg_batch ptg_batch;
 
+/* ptg_batch_create: a batch of nops >= 1 ops (the same device and precision; ops with the 2h-mesh
+ * coarse propagators are refused), each one design.  An op may hold several designs; if such an
+ * op takes the designs' own path, the batch runs without side streams.  The batch allocates and
+ * owns every design's pass buffers, zeroed; the ops
+ * stay the caller's and must outlive the batch.  PTG_EINVAL on such arguments, PTG_ENOMEM when
+ * device memory runs out (nothing is left allocated).  ptg_batch_destroy synchronises the device
+ * and frees the buffers.  ptg_batch_buffers: the device pointers of design `design`'s buffers,
+ * valid until ptg_batch_destroy; PTG_EINVAL for a design out of range. */
 int ptg_batch_create(ptg_op* const* ops, int nops, ptg_batch** out);
 void ptg_batch_destroy(ptg_batch* b);
 int ptg_batch_buffers(ptg_batch* b, int design, ptg_pass_buffers* out);
@@ -505,6 +513,9 @@ int ptg_batch_run_phase(ptg_batch* b, int phase, cudaStream_t stream);
  * CTA (32..512, multiple of 32); PTG_EINVAL if it does not fit every design of the launch or the
  * device. */
 int ptg_batch_set_plan(ptg_batch* b, int phase, int cs, int ng, int nthreads);
+/* The plan of a phase's persistent launch (the default one is chosen and installed on first use)
+ * and the number of clusters it launches; NULL outputs are skipped.  PTG_EINVAL for a phase out of
+ * range. */
 int ptg_batch_get_plan(ptg_batch* b, int phase, int* cs, int* ng, int* nthreads, int* nclusters);
 /* *own = 1 if design d runs the pass phases through its op's own launches, 0 if in the
  * persistent launches. */
@@ -521,7 +532,8 @@ int ptg_batch_design_path(ptg_batch* b, int design, int* own);
  *             rho); df_drho == NULL stands for the constant 1/Ne (the area-fraction gradient).
  * ptg_design_volume: *vol_d = mean(rho) (the area fraction on the uniform grid).
  * Element arrays are row-major (ey, ex), caller-owned device memory; calls are asynchronous.
- * r_fil must be positive and at most 64 h; 0 < eta < 1; beta > 0.
+ * r_fil must be positive and at most 64 h; 0 < eta < 1; beta > 0; 1 <= nx, ny <= 4096; a valid
+ * device.  PTG_EINVAL otherwise (and for NULL arrays), PTG_ENOMEM or PTG_ECUDA from the set-up.
  */
 typedef struct ptg_design ptg_design;
 int ptg_design_create(int nx, int ny, double h, double r_fil, double beta, double eta, int device,
@@ -539,6 +551,7 @@ int ptg_design_volume(ptg_design* d, const double* rho_d, double* vol_d, cudaStr
  * on monotone progress), move limit `move`, convex separable models, and the single-multiplier
  * dual solved by bisection.  ptg_mma_update takes host arrays of length n (x, df0, df1) and
  * writes the next iterate to x_new (host); it keeps the last two iterates and asymptotes.
+ * PTG_EINVAL for n < 1, x_max <= x_min, move <= 0 or NULL arrays; PTG_ENOMEM from create.
  */
 typedef struct ptg_mma ptg_mma;
 int ptg_mma_create(int n, double x_min, double x_max, double move, ptg_mma** out);
