@@ -631,7 +631,7 @@ int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream, int stats_ki
       }
     }
 #ifdef PTG_DEBUG
-    if (const int site = debug_check(op, P, plan, ntasks)) return site;
+    if (const int rc = debug_check(op, P, plan, ntasks)) return rc;
 #endif
     op->last_stream = stream;
     PTG_CUDA(launch_stream(P, prec, plan.max_active_clusters, plan.nthreads, stream));
@@ -654,7 +654,7 @@ int run(ptg_op* op, StepParams& P, int ntasks, cudaStream_t stream, int stats_ki
   // microseconds, so the default trades two slab-local sweeps for fewer CG iterations there
   if ((op->sv.local_steps == 0 || op->sv.local_steps == 3) && plan.wide) P.local_steps = 2;
 #ifdef PTG_DEBUG
-  if (const int site = debug_check(op, P, plan, ntasks)) return site;
+  if (const int rc = debug_check(op, P, plan, ntasks)) return rc;
 #endif
   op->last_stream = stream;
   PTG_CUDA(launch_stepper(P, plan, prec, ntasks, stream));
