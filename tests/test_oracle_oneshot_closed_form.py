@@ -227,7 +227,8 @@ def _planted(name):
     """Plausible mistakes, each planted in the oracle: G_adj reading T_{M(s+1)} instead of
     T_{Ms+1}; the coarse theta increment divided by Nt Ne instead of Ntau Ne; the fine adjoint's
     sensitivity divided by Ntau instead of Nt; a coarse step of dt; the adjoint source scale
-    Theta^(-p) / Ne instead of Theta^(1-p) / Ne (Eq. 4.6)."""
+    Theta^(-p) / Ne instead of Theta^(1-p) / Ne (Eq. 4.6); the capacity term of Eq. 4.7 dropped
+    or with its sign flipped."""
     import importlib
     import sys
 
@@ -264,13 +265,24 @@ def _planted(name):
             g = g - sensitivity_term(op, lam, T_hist[j], T_hist[j - 1], prob.dt) / prob.Ntau
         return lam, g
 
+    def sens_without_capacity(op, lam, T_j, T_jm1, dt):
+        return sensitivity_term(op, lam, T_j, T_jm1, dt) - op.dc * np.einsum(
+            "ei,ij,ej->e", lam[op.en], op.Me, (T_j - T_jm1)[op.en] / dt)
+
+    def sens_capacity_sign(op, lam, T_j, T_jm1, dt):
+        return sensitivity_term(op, lam, T_j, T_jm1, dt) - 2.0 * op.dc * np.einsum(
+            "ei,ij,ej->e", lam[op.en], op.Me, (T_j - T_jm1)[op.en] / dt)
+
     table = {"G_adj_row": (PR, "G_adj", G_adj_row), "G_pri_divisor": (PR, "G_pri", G_pri_divisor),
              "G_pri_step": (PR, "G_pri", G_pri_step), "F_adj_divisor": (PR, "F_adj", F_adj_divisor),
-             "source_exponent": (ST, "adjoint_source_scale", source_scale)}
+             "source_exponent": (ST, "adjoint_source_scale", source_scale),
+             "sens_without_capacity": (PR, "sensitivity_term", sens_without_capacity),
+             "sens_capacity_sign": (PR, "sensitivity_term", sens_capacity_sign)}
     return table[name]
 
 
-@pytest.mark.parametrize("name", ["G_adj_row", "G_pri_divisor", "G_pri_step", "F_adj_divisor", "source_exponent"])
+@pytest.mark.parametrize("name", ["G_adj_row", "G_pri_divisor", "G_pri_step", "F_adj_divisor", "source_exponent",
+                                  "sens_without_capacity", "sens_capacity_sign"])
 def test_a_planted_mistake_fails_the_closed_form(monkeypatch, name):
     module, attr, fn = _planted(name)
     monkeypatch.setattr(module, attr, fn)
