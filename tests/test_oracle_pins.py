@@ -407,9 +407,28 @@ def test_theta_and_gradient_are_homogeneous_in_the_load():
 
 
 def test_dirichlet_node_counts():
-    """Centred 10% of the left edge, inclusive: 3 / 7 / 13 / 25 / 51 nodes for n = 32/64/128/256/512."""
-    for n, cnt in ((32, 3), (64, 7), (128, 13), (256, 25), (512, 51)):
+    """Centred 10% of the left edge, inclusive: 3 / 7 / 9 / 13 / 19 / 25 / 51 nodes for
+    n = 32 / 64 / 96 / 128 / 192 / 256 / 512."""
+    for n, cnt in ((32, 3), (64, 7), (96, 9), (128, 13), (192, 19), (256, 25), (512, 51)):
         assert int(W.dirichlet_left_centre(n, n, 1.0 / n).sum()) == cnt
+
+
+def test_batch48_composition():
+    """The 48-design batching workload: sizes cycled by index mod 5 (10 x 64^2, 10 x 96^2,
+    10 x 128^2, 9 x 192^2, 9 x 256^2), (Nt, Ntau) by index mod 3 over (512, 16), (1024, 32),
+    (2048, 64) (M = 32 throughout), conductivity SIMP, p = 8, rho ~ U(0.2, 0.8) with seed 100 + index."""
+    ds = W.batch48()
+    assert len(ds) == 48 and [d["index"] for d in ds] == list(range(48))
+    sizes = [d["n"] for d in ds]
+    assert {n: sizes.count(n) for n in set(sizes)} == {64: 10, 96: 10, 128: 10, 192: 9, 256: 9}
+    for i, d in enumerate(ds):
+        assert d["n"] == (64, 96, 128, 192, 256)[i % 5]
+        assert (d["Nt"], d["Ntau"]) == ((512, 16), (1024, 32), (2048, 64))[i % 3]
+        assert d["Nt"] // d["Ntau"] == 32 and d["dt"] == 1.0 / d["Nt"] and d["p"] == 8.0
+        assert d["material"] == "simp_k" and d["seed"] == 100 + i
+        rho = d["rho"]
+        assert rho.shape == (d["n"] * d["n"],) and rho.min() >= 0.2 and rho.max() <= 0.8
+        assert np.array_equal(rho, np.random.default_rng(100 + i).uniform(0.2, 0.8, d["n"] * d["n"]))
 
 
 def test_sparse_lu_and_band_cholesky_give_the_same_passes():
